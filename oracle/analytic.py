@@ -1,0 +1,60 @@
+"""Closed-form solutions used to pin the oracle (test infrastructure only).
+
+* ``point_source_2d``: homogeneous 2D medium, rho u_tt = kappa Lap u + delta(x - x0) f(t),
+  zero initial data (Eq. 4).  With c = sqrt(kappa/rho) (Sec. 3.2) the free-space Green's
+  function of the 2D wave equation gives
+      u(r, t) = 1/(2 pi kappa) int_0^{t - r/c} f(tau) / sqrt((t - tau)^2 - r^2/c^2) d tau.
+  This is the Cartesian analogue of the paper's exact solution f(t - r/c)/(2 pi r) of Sec. 3.2
+  (which is 3D, on a free surface); it is derived here, not printed in the paper.  The
+  substitution tau = t - r/c - s^2 removes the inverse-square-root singularity:
+      u = 1/(2 pi kappa) int_0^{sqrt(t - r/c)} 2 f(t - r/c - s^2) / sqrt(2r/c + s^2) ds.
+
+* ``oscillator``: one mode of the semi-discrete problem, rho u'' + q u = f(t), u(0)=u'(0)=0:
+      u(t) = 1/(rho w) int_0^t sin(w (t - tau)) f(tau) d tau,  w = sqrt(q/rho).
+  Its Laguerre coefficients must satisfy the scalar form of the spectral recurrence (Eq. 9):
+      (q + rho h^2/4) R_m = f_m - rho h^2 c_m sum_{k<m} (m-k) c^_k R_k.
+"""
+import math
+
+import numpy as np
+
+
+def _gl(a, b, n):
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (b - a) * x + 0.5 * (b + a), 0.5 * (b - a) * w
+
+
+def point_source_2d(r, t, kappa, rho, fun, nodes=400, panels=64):
+    """u(r, t) for scalar r > 0 and an array of t (composite Gauss-Legendre in s)."""
+    c = math.sqrt(kappa / rho)
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    out = np.zeros_like(t)
+    for j, tj in enumerate(t):
+        smax2 = tj - r / c
+        if smax2 <= 0.0:
+            continue
+        smax = math.sqrt(smax2)
+        edges = np.linspace(0.0, smax, panels + 1)
+        acc = 0.0
+        for a, b in zip(edges[:-1], edges[1:]):
+            s, w = _gl(a, b, max(8, nodes // panels))
+            acc += np.sum(w * 2.0 * fun(tj - r / c - s * s) / np.sqrt(2.0 * r / c + s * s))
+        out[j] = acc / (2.0 * math.pi * kappa)
+    return out
+
+
+def oscillator(t, q, rho, fun, panels=256, order=16):
+    """u(t) of rho u'' + q u = f(t) from zero data, by Duhamel's integral (array t)."""
+    w = math.sqrt(q / rho)
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    out = np.zeros_like(t)
+    for j, tj in enumerate(t):
+        if tj <= 0.0:
+            continue
+        edges = np.linspace(0.0, tj, panels + 1)
+        acc = 0.0
+        for a, b in zip(edges[:-1], edges[1:]):
+            tau, wq = _gl(a, b, order)
+            acc += np.sum(wq * np.sin(w * (tj - tau)) * fun(tau))
+        out[j] = acc / (rho * w)
+    return out

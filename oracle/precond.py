@@ -1,0 +1,76 @@
+"""Laplace-operator preconditioner (oracle).  Test infrastructure only.
+
+Sec. 2.4, Eq. (21): B = Lambda_r + Lambda_z - d with constant coefficients equal to the
+midrange of the medium's (footnote to Eq. 21: f~ = (min f + max f)/2).  Reading of the sign
+garble: Eq. (21) as printed is negative definite; the oracle uses -B, the SPD operator of the
+same form as A (Eqs. 16-18) with kappa == kappa~ and rho == rho~, in Cartesian form:
+
+    -B y = -kappa~ (D_xx + D_zz) y + (rho~ h^2/4) y     (Dirichlet on all sides).
+
+Separation of variables (Sec. 2.4; Sec. 3.1 names FFT + Dichotomy as the two steps):
+  1. y^ = DST_x(r)                                        (orthonormal DST-I, S^2 = I)
+  2. for each x-mode j: T_j y~_j = y^_j along z, with
+        T_j = tridiag(-az~/hz^2,  2 az~/hz^2 + ax~ lambda_j + d~,  -az~/hz^2)
+  3. y = DST_x(y~).
+
+The separable operator is written with separate x / z coefficients (ax~, az~, d~) because
+Eq. (22) needs them: the elastic K = diag(B1, B2) uses
+  B1: ax~ = (lambda+2mu)~, az~ = mu~;   B2: ax~ = mu~, az~ = (lambda+2mu)~;   d~ = rho~ h^2/4
+(the cylindrical 1/r term of B1 has no Cartesian counterpart and is dropped).
+"""
+import numpy as np
+
+from . import dst as _dst
+from .tridiag import thomas
+
+
+def midrange(f):
+    """f~ = (min f + max f) / 2 over all nodes (footnote to Eq. 21)."""
+    f = np.asarray(f, dtype=np.float64)
+    return 0.5 * (f.min() + f.max())
+
+
+def acoustic_params(kappa, rho, h_lag):
+    """(ax~, az~, d~) of the acoustic preconditioner B (Eq. 21)."""
+    kt = midrange(kappa)
+    return kt, kt, midrange(rho) * h_lag ** 2 / 4.0
+
+
+def elastic_params(lam, mu, rho, h_lag):
+    """((ax~, az~, d~) of B1, (ax~, az~, d~) of B2) for K = diag(B1, B2) (Eq. 22)."""
+    pt = midrange(np.asarray(lam) + 2.0 * np.asarray(mu))
+    mt = midrange(mu)
+    dt = midrange(rho) * h_lag ** 2 / 4.0
+    return (pt, mt, dt), (mt, pt, dt)
+
+
+def mode_diagonals(nx, hx, hz, ax_t, az_t, d_t):
+    """Main diagonal of T_j for every mode j: 2 az~/hz^2 + ax~ lambda_j + d~  ([nx])."""
+    return 2.0 * az_t / hz ** 2 + ax_t * _dst.laplace_eigenvalues(nx, hx) + d_t
+
+
+def apply_inverse(r, hx, hz, ax_t, az_t, d_t):
+    """y = (-B)^{-1} r for r [..., nz, nx]: DST along x, Thomas along z per mode, DST back."""
+    r = np.asarray(r, dtype=np.float64)
+    nz, nx = r.shape[-2:]
+    S = _dst.dst_matrix(nx)
+    rh = _dst.dst_x(r, S)                                   # [..., nz, nx]
+    diag = mode_diagonals(nx, hx, hz, ax_t, az_t, d_t)      # [nx]
+    off = -az_t / hz ** 2
+    # move z to axis 0 so each (batch, mode) column is one independent system
+    col = np.moveaxis(rh, -2, 0)                            # [nz, ..., nx]
+    yt = thomas(off, diag, off, col)
+    yh = np.moveaxis(yt, 0, -2)
+    return _dst.dst_x(yh, S)
+
+
+def apply_separable(y, hx, hz, ax_t, az_t, d_t):
+    """The separable operator itself: -ax~ D_xx y - az~ D_zz y + d~ y (Dirichlet), written as
+    a 5-point stencil (used to pin apply_inverse)."""
+    y = np.asarray(y, dtype=np.float64)
+    pad = [(0, 0)] * (y.ndim - 2) + [(1, 1), (1, 1)]
+    yp = np.pad(y, pad)
+    c = yp[..., 1:-1, 1:-1]
+    dxx = (yp[..., 1:-1, 2:] - 2 * c + yp[..., 1:-1, :-2]) / hx ** 2
+    dzz = (yp[..., 2:, 1:-1] - 2 * c + yp[..., :-2, 1:-1]) / hz ** 2
+    return -ax_t * dxx - az_t * dzz + d_t * c

@@ -1,0 +1,123 @@
+"""Pins of the oracle's whole-shot solves and of the elastic operator."""
+import numpy as np
+import pytest
+
+from oracle import analytic, fd, krylov, laguerre, precond, solve
+
+
+def _point_source_error(hx, n_nodes):
+    # homogeneous 2 km x 2 km box, source in the middle, receiver 300 m away; the window ends
+    # before the first boundary reflection reaches the receiver
+    f0, h, alpha, c0, rho0 = 10.0, 400.0, 9, 2000.0, 1000.0
+    t0 = 2.5 / f0
+    t = np.linspace(0.01, 0.9, 120)
+    N = n_nodes
+    off = int(round(300.0 / hx))
+    out = solve.acoustic_shot(np.full((N, N), c0), np.full((N, N), rho0), hx, hx, h, alpha, 160,
+                              (N // 2, N // 2), [(N // 2 + off, N // 2)], t, f0, t0, tol=1e-12)
+    ua = analytic.point_source_2d(off * hx, t, rho0 * c0 ** 2, rho0, laguerre.ricker(f0, t0))
+    eps = np.sqrt(np.sum((out["traces"][0] - ua) ** 2) / np.sum(ua ** 2))   # Sec. 3.2 accuracy
+    return eps, out["iters"]
+
+
+def test_acoustic_shot_matches_2d_point_source_at_second_order():
+    e20, it20 = _point_source_error(20.0, 99)
+    e10, it10 = _point_source_error(10.0, 199)
+    assert np.all(it20 == 1) and np.all(it10 == 1)        # homogeneous: A == B
+    assert e10 < 0.08
+    assert 3.0 < e20 / e10 < 5.5                             # O(h^2) (Sec. 3.2)
+
+
+def test_acoustic_shot_two_layer_small():
+    from paper_1005_0542_gb300 import inputs
+    s = inputs.two_layer(n_harm=8, nx=32, nz=32)
+    out = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, s.sources[0],
+                              s.receivers, s.t_out, s.f0, s.t0, tol=1e-12, keep_fields=True)
+    # every harmonic solves A R_m = b_m: recheck the residual with the dense matrix
+    kappa = fd.kappa_from_velocity(s.c, s.rho)
+    M = fd.assemble_A(kappa, s.rho, s.h, s.hx, s.hz)
+    R = out["fields"]
+    for m in range(s.n_harm):
+        b = np.zeros((32, 32))
+        if m:
+            b -= s.rho * s.h ** 2 * float(laguerre.c_m(m, s.alpha)) * laguerre.history_direct(list(R), m, s.alpha)
+        b[s.sources[0][1], s.sources[0][0]] += out["fm"][m] / (s.hx * s.hz)
+        assert np.linalg.norm(M @ R[m].ravel() - b.ravel()) <= 2e-12 * np.linalg.norm(b)
+    assert np.all(out["iters"] > 1)
+
+
+# ------------------------------------------------------------------------- elastic operator
+def _elastic_medium(nz, nx, seed=3):
+    rng = np.random.default_rng(seed)
+    vp = rng.uniform(2000, 5000, (nz, nx))
+    rho = rng.uniform(1800, 2600, (nz, nx))
+    return solve.elastic_lame(vp, vp / 1.73, rho) + (rho,)
+
+
+def test_elastic_operator_symmetric_positive_definite():
+    lam, mu, rho = _elastic_medium(5, 6)
+    M = fd.assemble_C(lam, mu, rho, 300.0, 2.5, 3.0)
+    assert np.abs(M - M.T).max() / np.abs(M).max() < 1e-14
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def _elastic_manufactured_error(n):
+    sp = pytest.importorskip("sympy")
+    x, z = sp.symbols("x z")
+    lam = 2 + sp.Rational(1, 2) * sp.sin(x) * sp.cos(z)
+    mu = 1 + sp.Rational(3, 10) * sp.cos(x) * sp.sin(z)
+    u = sp.sin(x) * sp.sin(2 * z)
+    w = sp.sin(2 * x) * sp.sin(z)
+    rho, h = 3.0, 2.0
+    p = lam + 2 * mu
+    cu = -(sp.diff(p * sp.diff(u, x), x) + sp.diff(mu * sp.diff(u, z), z)
+           + sp.diff(lam * sp.diff(w, z), x) + sp.diff(mu * sp.diff(w, x), z)) + rho * h * h / 4 * u
+    cw = -(sp.diff(mu * sp.diff(w, x), x) + sp.diff(p * sp.diff(w, z), z)
+           + sp.diff(mu * sp.diff(u, z), x) + sp.diff(lam * sp.diff(u, x), z)) + rho * h * h / 4 * w
+    f = sp.lambdify((x, z), [lam, mu, u, w, cu, cw], "numpy")
+    hh = np.pi / (n + 1)
+    xs = hh * np.arange(1, n + 1)
+    X, Z = np.meshgrid(xs, xs)
+    L_, M_, U, W, CU, CW = [np.broadcast_to(np.asarray(a, dtype=float), X.shape) for a in f(X, Z)]
+    gu, gw = fd.apply_C(U, W, L_, M_, np.full_like(X, rho), h, hh, hh)
+    return max(np.abs(gu - CU)[2:-2, 2:-2].max(), np.abs(gw - CW)[2:-2, 2:-2].max())
+
+
+def test_elastic_operator_second_order_truncation():
+    # plane-strain reading of Eq. (12): every term (incl. both mixed terms) converges at O(h^2)
+    e1, e2 = _elastic_manufactured_error(40), _elastic_manufactured_error(81)
+    assert 3.5 < e1 / e2 < 4.5
+
+
+def test_elastic_gmres_equals_dense_solve():
+    nz, nx, h, hx, hz = 8, 9, 300.0, 2.5, 2.5
+    lam, mu, rho = _elastic_medium(nz, nx, seed=11)
+    M = fd.assemble_C(lam, mu, rho, h, hx, hz)
+    b = np.random.default_rng(5).standard_normal(2 * nz * nx)
+    p1, p2 = precond.elastic_params(lam, mu, rho, h)
+    n = nz * nx
+
+    def Kinv(v):
+        return np.concatenate([precond.apply_inverse(v[:n].reshape(nz, nx), hx, hz, *p1).ravel(),
+                               precond.apply_inverse(v[n:].reshape(nz, nx), hx, hz, *p2).ravel()])
+    x, it, hist = krylov.gmres(lambda v: M @ v, Kinv, b, 20, 1e-13)
+    xd = np.linalg.solve(M, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-11
+    assert it < 200
+
+
+def test_elastic_shot_small_residuals():
+    from paper_1005_0542_gb300 import inputs
+    s = inputs.elastic_layered(nx=24, nz=16, hx=2.5, n_harm=6, nsrc=1)
+    out = solve.elastic_shot(s.c, s.vs, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, s.sources[0],
+                             s.receivers[:4], s.t_out, s.f0, s.t0, tol=1e-12, keep_fields=True)
+    lam, mu = solve.elastic_lame(s.c, s.vs, s.rho)
+    M = fd.assemble_C(lam, mu, s.rho, s.h, s.hx, s.hz)
+    R = out["fields"]
+    for m in range(s.n_harm):
+        b = np.zeros((2, 16, 24))
+        if m:
+            b -= s.rho * s.h ** 2 * float(laguerre.c_m(m, s.alpha)) * laguerre.history_direct(list(R), m, s.alpha)
+        b[1, s.sources[0][1], s.sources[0][0]] += out["fm"][m] / (s.hx * s.hz)
+        assert np.linalg.norm(M @ R[m].ravel() - b.ravel()) <= 5e-12 * np.linalg.norm(b)
+    assert out["traces"].shape == (2, 4, s.t_out.size)
