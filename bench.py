@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the Laguerre-transform acoustic solver (one JSON line on stdout, rank 0).
+
+Workload (default): the 2048 x 1024 random layered acoustic model (5 m spacing, 20 layers with
++-5 % node perturbation, Gardner density, Ricker 25 Hz source at (1024, 16), h = 200, alpha = 9,
+512 harmonics), FP64 path, one shot.  A step is one Laguerre harmonic of the shot: right-hand side
+of Eq. 9, the preconditioned CG solve to 1e-10 (stencil matvec, vector updates, preconditioner =
+DST-I along x, partitioned tridiagonal solves along z, DST-I back), the history update and the
+receiver gather.  The metric is harmonic-solves/s.  Extra keys report the same workload on the
+mixed-precision path and the standalone preconditioner (1024 modes x nz 1024 x 512 RHS).
+
+--impl reference times the CPU oracle (numpy/scipy float64) on the same workload and metric.
+With --gpus N > 1 (torchrun) every rank runs its own replica shot (source shifted along the
+surface line): scaling is weak, there is no data-path collective.
+"""
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Laguerre-harmonic solves/s at 1e-8 rel err vs plain FP64 GPU; p50/p99 latency"
+UNIT = "harmonic-solves/s"
+WORKLOAD = ("random_layered_2048x1024 acoustic FP64 single shot: 5 m, 20 layers c~U(1500,4500)x(1+eps), "
+            "rho=310c^0.25, Ricker 25 Hz at (1024,16), h=200, alpha=9, 512 harmonics, PCG tol 1e-10; "
+            "step = one harmonic")
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures, with the sha1 of the
+# kernel source file at capture time (null when the kernel changed since).  See profiles/.
+NCU_TRAFFIC = {}
+
+
+def sha1_of(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def traffic_for(kernel_file, key):
+    rec = NCU_TRAFFIC.get(key)
+    if not rec:
+        return None
+    if sha1_of(os.path.join(ROOT, "paper_1005_0542_gb300", "csrc", kernel_file)) != rec["sha1"]:
+        return None
+    return rec["bytes"]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 ALU peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
+# (1.25 TFLOP/s nominal; the DFMA probe measured 1.20 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.path is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    from paper_1005_0542_gb300 import inputs
+    from paper_1005_0542_gb300 import lagwave as L
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    ctx = L.create(local_rank, stream=torch.cuda.current_stream().cuda_stream)
+    s = inputs.random_layered()
+    if world > 1:  # replica r: its own source on the line iz = 16
+        s.sources = [((s.nx // 2 + 64 * rank) % s.nx, 16)]
+    peaks, peak_src = load_peaks()
+
+    def make_shot(prec, n_harm=None):
+        g = L.grid(s.nx, s.nz, s.hx, s.hz)
+        lag = L.laguerre(s.h, s.alpha, n_harm or s.n_harm)
+        sv = L.solver(tol=s.tol, prec=prec)
+        w = L.wavelet(s.f0, s.t0)
+        c_, pc = L.f64(s.c)
+        r_, pr = L.f64(s.rho)
+        t_, pt = L.f64(s.t_out)
+        sh = C.c_void_p()
+        L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                                  L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                                  C.byref(sh)), ctx)
+        return sh
+
+    def timed_steps(sh, W, K, sampler=None):
+        for _ in range(W):
+            L.check(L.lag_shot_step(sh, 1), ctx, ok=(L.LAG_OK,))
+        stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = L.lag_kernel_launches(ctx)
+        L.lag_profile_enable(ctx, 1)
+        e0.record(stream)
+        for _ in range(K):
+            L.check(L.lag_shot_step(sh, 1), ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        launches = L.lag_kernel_launches(ctx) - l0
+        nk = L.lag_profile_num_classes()
+        cnt = (C.c_longlong * nk)()
+        ms = (C.c_double * nk)()
+        L.check(L.lag_profile_read(ctx, nk, cnt, ms), ctx)
+        L.lag_profile_enable(ctx, 0)
+        prof = {L.lag_profile_class_name(i).decode(): (cnt[i], ms[i]) for i in range(nk) if cnt[i]}
+        return e0.elapsed_time(e1), launches, prof
+
+    def iters_of(sh, m0, m1):
+        its = np.zeros((1, s.n_harm), dtype=np.int32)
+        st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+        L.lag_shot_stats(sh, C.byref(st))
+        return its[0, m0:m1]
+
+    def traces_of(sh):
+        tr = np.zeros((len(s.receivers), s.t_out.size))
+        L.check(L.lag_shot_traces(sh, tr.ctypes.data_as(L.PD)), ctx)
+        return tr
+
+    W, K = args.warmup, args.steps
+    # ---- headline: FP64 path
+    sh = make_shot(L.LAG_FP64)
+    with ClockSampler(local_rank) as clk:
+        ms, launches, prof = timed_steps(sh, W, K)
+    clocks = clk.summary()
+    its = iters_of(sh, W, W + K)
+    tr64 = traces_of(sh)
+    L.lag_shot_destroy(sh)
+    t_sec = ms / 1e3
+    if dist is not None:
+        t = torch.tensor([t_sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_sec = float(t.item())
+    value = world * K / t_sec
+
+    # roofline of the dominant kernel (FP64 DST GEMM): algorithmic flops of the real launches
+    # (2 per preconditioner apply, one apply per PCG iteration) over the measured DST time
+    ku, kv = (s.nx + 1) // 2, s.nx // 2
+    flops_launch = 2.0 * s.nz * (ku * ku + kv * kv)
+    n_dst, ms_dst = prof.get("dst_f64", (0, 0.0))
+    real = 2 * int(its.sum())
+    achieved = (real * flops_launch) / (ms_dst / 1e3) / 1e12 if ms_dst > 0 else None
+    roofline = {"bound": "alu", "kernel": "dst_simt_kernel<double> (folded FP64 DST GEMM)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": traffic_for("k_dst.cu", "dst_f64"),
+                "flops_per_launch": flops_launch, "launches_timed": n_dst, "launches_real": real,
+                "ms_share": ms_dst / ms if ms > 0 else None,
+                "peak_note": "derived: 152 SM x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded layered medium; no dataset)",
+           "config": {"workload": WORKLOAD, "grid": [s.nx, s.nz], "harmonics_timed": [W, W + K],
+                      "l2": "inputs larger than L2: ~250 MB of vectors/coefficients touched per step",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "gpu_launches": int(launches), "pcg_iters_per_step": float(np.mean(its)),
+           "roofline": roofline,
+           "kernel_ms": {k: {"launches": c, "ms": round(v, 3)} for k, (c, v) in sorted(prof.items())},
+           "clocks": clocks}
+    if rank != 0:
+        return None
+    if args.no_extras:
+        return out
+
+    # ---- mixed-precision path, same workload, same harmonics
+    shm = make_shot(L.LAG_MIXED)
+    msm, launches_m, profm = timed_steps(shm, W, K)
+    itsm = iters_of(shm, W, W + K)
+    trm = traces_of(shm)
+    L.lag_shot_destroy(shm)
+    rel = float(np.linalg.norm(trm - tr64) / np.linalg.norm(tr64))
+    out["mixed"] = {"value": K / (msm / 1e3), "ms_per_step": msm / K, "speedup_vs_fp64_gpu": (K / (msm / 1e3)) / value,
+                    "pcg_iters_per_step": float(np.mean(itsm)), "traces_rel_l2_vs_fp64_gpu": rel,
+                    "gpu_launches": int(launches_m),
+                    "kernel_ms": {k: {"launches": c, "ms": round(v, 3)} for k, (c, v) in sorted(profm.items())}}
+
+    # ---- standalone preconditioner: 1024 modes x nz 1024 x 512 rhs
+    out["precond_bench"] = precond_bench(ctx, s, peaks, peak_src)
+
+    # ---- end to end through the public API from pinned host buffers
+    out["e2e"] = e2e(ctx, s, args.e2e_harmonics)
+
+    # ---- CPU oracle on a bounded sample of the same workload
+    out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
+    L.lag_destroy(ctx)
+    return out
+
+
+def precond_bench(ctx, s, peaks, peak_src):
+    import torch
+    from paper_1005_0542_gb300 import lagwave as L
+    nx, nz, nrhs = 1024, 1024, 512
+    kap = s.rho * s.c ** 2
+    kt = 0.5 * (kap.min() + kap.max())
+    rt = 0.5 * (s.rho.min() + s.rho.max())
+    res = {"config": "1024 modes x nz 1024 x 512 RHS, midrange coefficients of the 2048x1024 model at 5 m"}
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    r = torch.randn((nrhs, nz, nx), dtype=torch.float64, device="cuda", generator=gen)
+    z = torch.empty_like(r)
+    for prec, name in ((L.LAG_FP64, "fp64"), (L.LAG_MIXED, "mixed")):
+        p = C.c_void_p()
+        L.check(L.lag_precond_create(ctx, C.byref(L.grid(nx, nz, 5.0, 5.0)), kt, rt, s.h, prec, C.byref(p)), ctx)
+        for _ in range(2):
+            L.check(L.lag_precond_apply(p, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()), nrhs), ctx)
+        L.lag_synchronize(ctx)
+        L.lag_profile_enable(ctx, 1)
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            L.check(L.lag_precond_apply(p, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()), nrhs), ctx)
+        L.lag_synchronize(ctx)
+        wall = (time.perf_counter() - t0) / reps
+        nk = L.lag_profile_num_classes()
+        cnt = (C.c_longlong * nk)()
+        ms = (C.c_double * nk)()
+        L.check(L.lag_profile_read(ctx, nk, cnt, ms), ctx)
+        L.lag_profile_enable(ctx, 0)
+        prof = {L.lag_profile_class_name(i).decode(): (cnt[i], ms[i] / max(cnt[i], 1)) for i in range(nk) if cnt[i]}
+        pts = nrhs * nx * nz
+        entry = {"apply_ms": wall * 1e3, "ps_per_point": wall * 1e12 / pts,
+                 "kernels": {k: {"avg_ms": v} for k, (c, v) in prof.items()}}
+        tri = prof.get("tri_f64" if prec == L.LAG_FP64 else "tri_f32")
+        if tri:
+            eb = 16 if prec == L.LAG_FP64 else 8
+            gbs = eb * pts / (tri[1] / 1e3) / 1e9
+            entry["tri_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                     "frac": gbs / peaks["hbm_gbs"], "bytes_per_point": eb,
+                                     "peak_source": peak_src}
+        L.lag_precond_destroy(p)
+        res[name] = entry
+    del r, z
+    torch.cuda.empty_cache()
+    return res
+
+
+def e2e(ctx, s, nh):
+    import torch
+    from paper_1005_0542_gb300 import lagwave as L
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    c, rho, tout = pinned(s.c), pinned(s.rho), pinned(s.t_out)
+    tr = torch.empty((1, len(s.receivers), s.t_out.size), dtype=torch.float64, pin_memory=True)
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, nh)
+    sv = L.solver(tol=s.tol)
+    w = L.wavelet(s.f0, s.t0)
+    P = lambda t: C.cast(t.data_ptr(), L.PD)  # noqa: E731
+    t0 = time.perf_counter()
+    L.check(L.lag_solve_acoustic(ctx, C.byref(g), P(c), P(rho), C.byref(lag), C.byref(sv), C.byref(w), 1,
+                                 L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, P(tout),
+                                 P(tr), None), ctx)
+    dt = time.perf_counter() - t0
+    h2d = (c.numel() + rho.numel() + tout.numel()) * 8 + 8 * (1 + len(s.receivers))
+    d2h = tr.numel() * 8
+    return {"value": nh / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / nh, "d2h_bytes_per_step": d2h / nh,
+            "harmonics": nh, "seconds": dt,
+            "api": "lag_solve_acoustic (host medium in, host traces out; includes medium/plan setup)"}
+
+
+def oracle_harmonics(s, budget_s, max_harm, min_harm=1):
+    """Time the oracle on harmonics 0, 1, ... of the shot until the budget is spent."""
+    from oracle import fd, krylov, laguerre, precond
+    kap = fd.kappa_from_velocity(s.c, s.rho)
+    pr = precond.acoustic_params(kap, s.rho, s.h)
+    nz, nx = s.nz, s.nx
+    fm = laguerre.forward_coeffs(laguerre.ricker(s.f0, s.t0), max_harm, s.h, s.alpha, s.t0 + 4.0 / s.f0)
+    R, times, iters = [], [], []
+    src = s.sources[0]
+    for m in range(max_harm):
+        t0 = time.perf_counter()
+        b = np.zeros((nz, nx))
+        if m:
+            b -= s.rho * s.h ** 2 * float(laguerre.c_m(m, s.alpha)) * laguerre.history_direct(R, m, s.alpha)
+        b[src[1], src[0]] += fm[m] / (s.hx * s.hz)
+        x, it, _ = krylov.pcg(lambda v: fd.apply_A(v.reshape(nz, nx), kap, s.rho, s.h, s.hx, s.hz).ravel(),
+                              lambda v: precond.apply_inverse(v.reshape(nz, nx), s.hx, s.hz, *pr).ravel(),
+                              b.ravel(), s.tol)
+        R.append(x.reshape(nz, nx))
+        times.append(time.perf_counter() - t0)
+        iters.append(it)
+        if sum(times) >= budget_s and m + 1 >= min_harm:
+            break
+    return times, iters
+
+
+def cpu_baseline(s, budget):
+    times, iters = oracle_harmonics(s, budget, 64)
+    return {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {len(times)} harmonics of the same shot (oracle PCG, direct DST, Thomas; "
+                      f"{sum(times):.1f} s, {np.mean(iters):.0f} PCG iterations/harmonic)"}
+
+
+# ---------------------------------------------------------------------------------- reference arm
+def reference_arm(args):
+    from paper_1005_0542_gb300 import inputs
+    s = inputs.random_layered()
+    W, K = args.warmup, args.steps
+    # the oracle's harmonics are sequential: W untimed warm-up harmonics, then K timed ones;
+    # each step is bounded by one harmonic of the oracle on the full 2048 x 1024 model
+    times, iters = oracle_harmonics(s, float("inf"), W + K, min_harm=W + K)
+    tk = times[W:W + K]
+    v = len(tk) / sum(tk)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+            "warmup": W, "ms_per_step": 1e3 * sum(tk) / len(tk), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded layered medium; no dataset)",
+            "config": {"workload": WORKLOAD, "grid": [s.nx, s.nz], "harmonics_timed": [W, W + K]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"harmonics {W}..{W + K - 1} of the shot on the host cores"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lagwave", choices=["lagwave", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="headline only (for launch-list captures)")
+    ap.add_argument("--e2e-harmonics", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(reference_arm(args)), flush=True)
+        return
+    out = gpu_arm(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * lagwave.h -- C ABI of the GB300 (sm_103a) Laguerre-transform wave solver.
+ *
+ * Method: Fatyanov & Terekhov, "High-performance modeling acoustic and elastic waves using the
+ * Parallel Dichotomy Algorithm" (arXiv:1005.0542).  The Laguerre transform in time (Sec. 2.1,
+ * Eqs. 7-9) turns the wave equation into one elliptic problem per harmonic m with the SAME
+ * operator and a right-hand side that depends on the earlier harmonics.  Each problem is solved
+ * by preconditioned CG (acoustic, Sec. 2.3) or GMRES(k) (elastic, Sec. 2.3), preconditioned by a
+ * constant-coefficient Laplace operator (Sec. 2.4, Eqs. 21-22) that is inverted by separation of
+ * variables: a sine transform along x, then one tridiagonal system along z per x-mode, solved by
+ * a partitioned ("Dichotomy-style") elimination whose factors are computed once (Sec. 1).
+ *
+ * Problem form used here (2D Cartesian, Dirichlet on all four sides):
+ *   grid      nx x nz interior nodes, x_i = (i+1) dx, z_k = (k+1) dz; u = 0 on the frame.
+ *   layout    every field is row-major [rhs][z][x] (x fastest), float64, interior nodes only.
+ *   acoustic  A R_m = b_m,  A = -div(kappa grad) + rho h^2/4,  kappa = rho c^2,
+ *             b_m = delta_s f_m - rho h^2 c_m sum_{k<m} (m-k) c^_k R_k     (Eq. 9, SPD form),
+ *             c_m = sqrt(m!/(m+alpha)!), c^_k = 1/c_k, delta_s = 1/(dx dz) at the source node.
+ *   elastic   C [Q;U]_m = [0; delta_s f_m] - rho h^2 c_m sum_{k<m}(m-k) c^_k [Q;U]_k  (Eq. 12,
+ *             Cartesian plane strain, vertical point force), fields ordered [rhs][comp][z][x].
+ *
+ * Conventions
+ *   - Every function returns a status (0 = LAG_OK, negative = error) and never throws or aborts.
+ *     lag_strerror() names a status; lag_last_error() gives the context's last message.
+ *   - The caller owns every pointer it passes.  Host arrays ("_host") are read during the call
+ *     (or copied, where stated).  Device arrays ("_dev") must hold the stated number of float64
+ *     values on the context's device and stay valid until the context's stream reaches the work.
+ *   - The library owns contexts, media, plans, shots and their device memory.  All device work is
+ *     issued on the context's CUDA stream.  Functions documented "stream-ordered" return after
+ *     enqueueing; the others return when their results are on the host.
+ *   - One context serves one host thread at a time (the serving loop runs its own thread and
+ *     touches only its own streams).
+ *   - There is no CPU fallback: a missing or unusable GPU returns LAG_ECUDA.
+ */
+#ifndef LAGWAVE_H
+#define LAGWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define LAG_OK          0
+#define LAG_EINVAL     (-1)  /* bad argument: null pointer, size out of range, mismatched objects */
+#define LAG_ENOMEM     (-2)  /* device allocation failed or the context's HBM budget is exceeded */
+#define LAG_ENOTCONV   (-3)  /* Krylov solve hit max_iter; results and stats are still filled in  */
+#define LAG_ENUMERIC   (-4)  /* NaN or Inf in a residual norm                                      */
+#define LAG_ECUDA      (-5)  /* CUDA runtime/driver error (message in lag_last_error)              */
+#define LAG_EAGAIN     (-6)  /* lag_serve_poll: request not finished yet                          */
+#define LAG_ETIMEDOUT  (-7)  /* a bounded device wait gave up (device status word)                 */
+#define LAG_ECANCELED  (-8)  /* request was cancelled                                              */
+
+/* precision of the preconditioner (the Krylov vectors, residuals, dot products, the Laguerre
+ * recurrence and the inverse summation are always float64) */
+#define LAG_FP64   0   /* plain path: preconditioner in float64 (DST as an FP64 GEMM)              */
+#define LAG_MIXED  1   /* preconditioner in float32, DST as a split-bf16 tcgen05 GEMM (FP32 acc.), */
+                       /* flexible (Polak-Ribiere) CG / flexible GMRES                              */
+
+/* wavelet kinds */
+#define LAG_WAVELET_RICKER 0   /* (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2)              */
+#define LAG_WAVELET_PAPER  1   /* exp[-(2 pi f0 (t-t0))^2 / gamma^2] sin(2 pi f0 (t-t0))  (Eq. 23)  */
+
+typedef struct lag_ctx     lag_ctx;
+typedef struct lag_medium  lag_medium;
+typedef struct lag_precond lag_precond;
+typedef struct lag_shot    lag_shot;
+
+typedef struct { int nx, nz; double dx, dz; } lag_grid;           /* interior nodes, spacing (m) */
+typedef struct { double h; int alpha; int n_harm; } lag_laguerre; /* Sec. 2.1: h (1/s), alpha >= 2 */
+typedef struct {
+  double tol;       /* stop when ||r||_2 / ||b||_2 <= tol (recursive residual)                    */
+  int max_iter;     /* Krylov iterations per harmonic (GMRES: inner steps)                         */
+  int restart_k;    /* GMRES(k) restart length (elastic), 1..64                                    */
+  int prec;         /* LAG_FP64 or LAG_MIXED                                                       */
+  int partitions;   /* z-partitions of the tridiagonal solve; 0 = automatic                        */
+} lag_solver;
+typedef struct { int ix, iz; } lag_point;                          /* 0-based interior node        */
+typedef struct { double f0, t0, gamma; int kind; } lag_wavelet;
+
+typedef struct {
+  int    *iters;         /* [nsrc][n_harm] Krylov iterations per harmonic and source, or NULL    */
+  double *relres;        /* [nsrc][n_harm] final recursive ||r||/||b||, or NULL                   */
+  long long total_iters; /* sum over harmonics of the iterations of the batch                      */
+  double   seconds;      /* wall time of the call                                                  */
+} lag_stats;
+
+/* ---------------------------------------------------------------- context */
+const char *lag_strerror(int status);
+const char *lag_last_error(const lag_ctx *ctx);     /* last error text of ctx ("" if none)       */
+int  lag_version(void);                              /* 100 * major + minor                       */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes (0 = no limit) caps the device
+ * memory the context may hold; allocations beyond it fail with LAG_ENOMEM.  cuda_stream is a
+ * cudaStream_t to issue work on (NULL: the context creates its own non-blocking stream). */
+int  lag_create(lag_ctx **ctx, int device, size_t hbm_budget_bytes, void *cuda_stream);
+void lag_destroy(lag_ctx *ctx);                      /* frees everything the context still owns   */
+int  lag_synchronize(lag_ctx *ctx);                  /* waits for the context's stream            */
+size_t lag_bytes_in_use(const lag_ctx *ctx);
+/* Number of the library's kernels launched so far in this process (launch accounting). */
+long long lag_kernel_launches(const lag_ctx *ctx);
+/* Kernel-class timing.  enable(1) clears the records and starts bracketing every launch of the
+ * profiled kernel classes with CUDA events on the launching stream; enable(0) stops.  read()
+ * waits for the recorded events and returns per class the number of launches and the summed
+ * milliseconds (arrays of nclasses entries; class names via lag_profile_class_name). */
+int  lag_profile_enable(lag_ctx *ctx, int on);
+int  lag_profile_read(lag_ctx *ctx, int nclasses, long long *counts, double *ms);
+int  lag_profile_num_classes(void);
+const char *lag_profile_class_name(int cls);
+
+/* ---------------------------------------------------------------- preconditioner (Sec. 2.4)
+ * The plan is the one-time "preparatory" step of the Dichotomy solve (Sec. 1): DST-I matrices
+ * (folded into even/odd halves) and, for every x-mode j, the tridiagonal system
+ *     T_j = tridiag(-az/dz^2, 2 az/dz^2 + ax lambda_j + d, -az/dz^2),
+ *     lambda_j = (4/dx^2) sin^2(pi (j+1) / (2 (nx+1))),
+ * factored once into partition-local eliminations, spike vectors and the reduced (interface)
+ * system.  Acoustic B (Eq. 21): ax = az = kappa~, d = rho~ h^2/4 with f~ = (min f + max f)/2.
+ * Elastic K = diag(B1, B2) (Eq. 22): B1 (ax, az) = ((lambda+2mu)~, mu~), B2 = (mu~, (lambda+2mu)~).
+ * prec = LAG_FP64 or LAG_MIXED.  partitions = 0 picks the partition count automatically. */
+int  lag_precond_create(lag_ctx *ctx, const lag_grid *grid, double kappa_t, double rho_t,
+                        double h_lag, int prec, lag_precond **out);
+int  lag_precond_create_sep(lag_ctx *ctx, const lag_grid *grid, double ax_t, double az_t,
+                            double d_t, int prec, int partitions, lag_precond **out);
+void lag_precond_destroy(lag_precond *p);
+/* z = B^{-1} r for nrhs fields [nrhs][nz][nx] (device, float64).  Stream-ordered.  r and z may
+ * not overlap.  Steps: forward DST-I along x, one tridiagonal solve along z per mode, DST-I. */
+int  lag_precond_apply(lag_precond *p, const double *r_dev, double *z_dev, int nrhs);
+/* The steps alone (parity and roofline of each kernel).  Stream-ordered.
+ * dst:      y[b][k][:] = S x[b][k][:] (orthonormal DST-I, S^2 = I); in the plan's precision.
+ * tridiag:  for every rhs b and mode j solve T_j y[b][:][j] = d[b][:][j] along z (float64 plan).
+ * tridiag_f32: the same on float32 data (LAG_MIXED plan). */
+int  lag_precond_dst(lag_precond *p, const double *x_dev, double *y_dev, int nrhs);
+int  lag_precond_tridiag(lag_precond *p, const double *d_dev, double *y_dev, int nrhs);
+int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, int nrhs);
+/* Mixed plan only: y = S x from a float32 input (the inverse-transform kernel of the mixed path,
+ * float32 in, float64 out).  lag_precond_dst on a mixed plan runs the forward kernel (float64 in,
+ * float32 spectrum) and widens its result to float64. */
+int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int nrhs);
+/* 1 if the plan's DST runs on the tcgen05 tensor cores (mixed path), else 0 */
+int  lag_precond_uses_tensor_cores(const lag_precond *p);
+/* plan facts: partitions P, partition length L, modes per CTA of the tridiagonal kernel */
+int  lag_precond_info(const lag_precond *p, int *partitions, int *part_len, int *modes_per_cta);
+
+/* ---------------------------------------------------------------- medium and operator
+ * Acoustic (Sec. 2.3, Eqs. 16-18, Cartesian SPD form): face coefficient = mean of the two nodal
+ * kappa (boundary faces take the interior node's value), mass w = rho h^2/4.
+ * Elastic (Eq. 12, plane strain): second-derivative terms with face-averaged (lambda+2mu) and mu,
+ * mixed terms as centred differences with nodal lambda and mu; lambda = rho (vp^2 - 2 vs^2),
+ * mu = rho vs^2.  Host arrays [nz][nx] are copied. */
+int  lag_medium_create_acoustic(lag_ctx *ctx, const lag_grid *grid, const double *c_host,
+                                const double *rho_host, double h_lag, lag_medium **out);
+int  lag_medium_create_elastic(lag_ctx *ctx, const lag_grid *grid, const double *vp_host,
+                               const double *vs_host, const double *rho_host, double h_lag,
+                               lag_medium **out);
+void lag_medium_destroy(lag_medium *m);
+/* Midranges computed on the device: acoustic out[0..1] = kappa~, rho~; elastic out[0..2] =
+ * (lambda+2mu)~, mu~, rho~.  Blocking. */
+int  lag_medium_midranges(lag_medium *m, double *out);
+/* q = A p (acoustic: [nrhs][nz][nx]) or q = C p (elastic: [nrhs][2][nz][nx]).  Stream-ordered. */
+int  lag_apply_operator(lag_medium *m, const double *p_dev, double *q_dev, int nrhs);
+
+/* ---------------------------------------------------------------- one harmonic system
+ * Solve A x = b (acoustic: PCG with B; plain CG beta of Fletcher-Reeves for LAG_FP64, flexible
+ * Polak-Ribiere for LAG_MIXED) or C x = b (elastic: right-preconditioned flexible GMRES(k) with
+ * K = diag(B1, B2)) for nrhs independent right-hand sides, zero initial guess.  Blocking.
+ * iters_host[nrhs] / relres_host[nrhs] (may be NULL) receive per-rhs results.
+ * The preconditioner plans must match the medium's grid and the solver's precision. */
+int  lag_solve_system(lag_medium *m, lag_precond *p1, lag_precond *p2, const double *b_dev,
+                      double *x_dev, int nrhs, const lag_solver *s, int *iters_host,
+                      double *relres_host);
+
+/* ---------------------------------------------------------------- Laguerre pieces (Sec. 2.1)
+ * f_m = int f(t) (ht)^{-alpha/2} l_m(ht) dt, m < n_harm, by composite Gauss-Legendre on the
+ * wavelet's support; computed on the device, copied to fm_host[n_harm]. */
+int  lag_source_coeffs(lag_ctx *ctx, const lag_laguerre *lag, const lag_wavelet *w, double *fm_host);
+/* tab[m][j] = (h t_j)^{alpha/2} l_m(h t_j) for the inverse summation u(t) = sum_m R_m tab[m][.]
+ * (Eq. 8); l_m evaluated by a scaled three-term recurrence.  Copied to tab_host[n_harm][nt]. */
+int  lag_laguerre_table(lag_ctx *ctx, const lag_laguerre *lag, int nt, const double *t_host,
+                        double *tab_host);
+
+/* ---------------------------------------------------------------- shots (whole Laguerre loops)
+ * A shot holds the device-resident state of nsrc sources on one medium: the Krylov vectors, the
+ * two running history sums T, S per source (S_m = sum_{k<m}(m-k) c^_k R_k, updated as
+ * T += c^_m R_m, S += T), the receiver values of every harmonic, and its own CUDA stream
+ * (created by the library).  vs_host == NULL selects the acoustic problem. */
+int  lag_shot_create(lag_ctx *ctx, const lag_grid *grid, const double *c_host, const double *vs_host,
+                     const double *rho_host, const lag_laguerre *lag, const lag_solver *s,
+                     const lag_wavelet *w, int nsrc, const lag_point *src, int nrcv,
+                     const lag_point *rcv, int nt, const double *t_out_host, lag_shot **out);
+void lag_shot_destroy(lag_shot *sh);
+/* Advance up to nharm harmonics (blocking).  Returns LAG_OK, LAG_ENOTCONV (a harmonic hit
+ * max_iter; the shot continues from the best iterate) or an error. */
+int  lag_shot_step(lag_shot *sh, int nharm);
+/* Non-blocking progress: issues the next chunk of work if the previous one finished.
+ * *done is set to 1 when all n_harm harmonics are finished. */
+int  lag_shot_pump(lag_shot *sh, int *done);
+int  lag_shot_harmonic(const lag_shot *sh);          /* harmonics completed so far              */
+void *lag_shot_stream(const lag_shot *sh);           /* the shot's cudaStream_t                 */
+/* traces[nsrc][ncomp][nrcv][nt] (ncomp = 1 acoustic, 2 elastic) summed over the harmonics done */
+int  lag_shot_traces(lag_shot *sh, double *traces_host);
+/* receiver values of every finished harmonic: R_rcv[n_harm][nsrc][ncomp][nrcv] */
+int  lag_shot_receiver_harmonics(lag_shot *sh, double *rrcv_host);
+/* device pointer to the latest solved harmonic R_m ([nsrc][ncomp][nz][nx]); valid until the next step */
+const double *lag_shot_field(const lag_shot *sh);
+/* copy the latest solved harmonic into out_dev ([nsrc][ncomp][nz][nx], device); blocking */
+int  lag_shot_copy_field(lag_shot *sh, double *out_dev);
+int  lag_shot_stats(const lag_shot *sh, lag_stats *st);
+
+/* Whole shot in one call: create, step all harmonics, copy traces, destroy.  Blocking.
+ * traces_host[nsrc][nrcv][nt] (acoustic) or [nsrc][2][nrcv][nt] (elastic). */
+int  lag_solve_acoustic(lag_ctx *ctx, const lag_grid *grid, const double *c_host,
+                        const double *rho_host, const lag_laguerre *lag, const lag_solver *s,
+                        const lag_wavelet *w, int nsrc, const lag_point *src, int nrcv,
+                        const lag_point *rcv, int nt, const double *t_out_host,
+                        double *traces_host, lag_stats *stats);
+int  lag_solve_elastic(lag_ctx *ctx, const lag_grid *grid, const double *vp_host,
+                       const double *vs_host, const double *rho_host, const lag_laguerre *lag,
+                       const lag_solver *s, const lag_wavelet *w, int nsrc, const lag_point *src,
+                       int nrcv, const lag_point *rcv, int nt, const double *t_out_host,
+                       double *traces_host, lag_stats *stats);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of shots: a request is admitted when its device memory fits the context's
+ * HBM budget next to the running ones, then advanced chunk by chunk on its own stream alongside
+ * every other admitted request (work of different requests overlaps on the device; results do not
+ * depend on what else runs).  The request's host arrays are copied at submit. */
+typedef struct {
+  int kind;                    /* 0 acoustic, 1 elastic                                   */
+  lag_grid grid;
+  const double *c_host;        /* c (acoustic) or vp (elastic) [nz][nx]                    */
+  const double *vs_host;       /* elastic only                                            */
+  const double *rho_host;
+  lag_laguerre lag;
+  lag_solver solver;
+  lag_wavelet wavelet;
+  int nsrc; const lag_point *src;
+  int nrcv; const lag_point *rcv;
+  int nt;   const double *t_out_host;
+} lag_request;
+
+typedef struct {
+  int status;                  /* LAG_OK, LAG_ENOTCONV, LAG_ECANCELED, ...                 */
+  double *traces_host;         /* caller-provided [nsrc][ncomp][nrcv][nt], filled by poll  */
+  double t_submit, t_admit, t_done;   /* seconds since the context was created             */
+  long long total_iters;
+  size_t device_bytes;         /* device memory the request held                           */
+} lag_result;
+
+int lag_serve_start(lag_ctx *ctx, int max_active);   /* starts the scheduler thread       */
+int lag_serve_stop(lag_ctx *ctx);                    /* drains nothing: cancels the rest  */
+int lag_serve_submit(lag_ctx *ctx, const lag_request *req, uint64_t *ticket);
+int lag_serve_poll(lag_ctx *ctx, uint64_t ticket, lag_result *out);  /* LAG_EAGAIN until done */
+int lag_serve_cancel(lag_ctx *ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAGWAVE_H */

@@ -1,0 +1,420 @@
+// C ABI of the library: contexts, media, preconditioner plans, Krylov drivers and shots.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "solver.h"
+
+using namespace lag;
+
+namespace lag {
+
+double now_seconds() {
+  using namespace std::chrono;
+  return duration_cast<duration<double>>(steady_clock::now().time_since_epoch()).count();
+}
+
+void DevBuf::alloc(lag_ctx *c, size_t nbytes, bool zero) {
+  release();
+  ctx = c;
+  if (nbytes == 0) return;
+  if (ctx != nullptr && ctx->budget != 0 && ctx->in_use.load() + nbytes > ctx->budget)
+    throw Error(LAG_ENOMEM, "HBM budget exceeded: " + std::to_string(ctx->in_use.load() + nbytes) + " > " +
+                                std::to_string(ctx->budget) + " bytes");
+  cudaError_t e = cudaMalloc(&ptr, nbytes);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    cudaGetLastError();
+    throw Error(LAG_ENOMEM, std::string("cudaMalloc(") + std::to_string(nbytes) + "): " + cudaGetErrorString(e));
+  }
+  bytes = nbytes;
+  if (ctx != nullptr) ctx->in_use += nbytes;
+  if (zero) LAG_CUDA_CHECK(cudaMemset(ptr, 0, nbytes));
+}
+
+void DevBuf::release() {
+  if (ptr != nullptr) {
+    cudaFree(ptr);
+    if (ctx != nullptr) ctx->in_use -= bytes;
+  }
+  ptr = nullptr;
+  bytes = 0;
+}
+
+// ------------------------------------------------------------------------------ reduction scratch
+void ReduceBuf::ensure(lag_ctx *ctx, int nrhs_, int cap_, int nv_) {
+  if (nrhs_ <= nrhs && cap_ <= cap && nv_ <= nv) return;
+  nrhs = std::max(nrhs, nrhs_);
+  cap = std::max(cap, cap_);
+  nv = std::max(nv, nv_);
+  part.alloc(ctx, (size_t)nrhs * nv * cap * sizeof(double));
+  count.alloc(ctx, (size_t)nrhs * sizeof(unsigned int), true);
+}
+
+Reduce ReduceBuf::get() const { return Reduce{part.as<double>(), count.as<unsigned int>(), cap, nv * cap}; }
+
+int stencil_blocks(const lag_grid &g) { return ((g.nx + 31) / 32) * ((g.nz + 7) / 8); }
+
+}  // namespace lag
+
+// ------------------------------------------------------------------------------ preconditioner
+void lag_precond::ensure_scratch(int nrhs) {
+  if (nrhs <= scratch_rhs) return;
+  const size_t per = (size_t)grid.nx * grid.nz;
+  scratch.alloc(ctx, per * nrhs * (prec == LAG_FP64 ? sizeof(double) : sizeof(float)));
+  scratch_rhs = nrhs;
+}
+
+void lag_precond::apply(const double *r, double *z, int nrhs, const KrylovScalars *sc, cudaStream_t s) {
+  ensure_scratch(nrhs);
+  const int rows = nrhs * grid.nz;
+  if (prec == LAG_FP64) {
+    double *w = scratch.as<double>();
+    dst_apply_f64(dst, r, w, rows, grid.nz, sc, s);
+    tri_solve_f64(tri64, w, w, nrhs, sc, s);
+    dst_apply_f64(dst, w, z, rows, grid.nz, sc, s);
+  } else {
+    float *w = scratch.as<float>();
+    if (use_tc) dst_apply_tc_d2f(dst, r, w, rows, grid.nz, sc, s);
+    else dst_apply_f32_d2f(dst, r, w, rows, grid.nz, sc, s);
+    tri_solve_f32(tri32, w, w, nrhs, sc, s);
+    if (use_tc) dst_apply_tc_f2d(dst, w, z, rows, grid.nz, sc, s);
+    else dst_apply_f32_f2d(dst, w, z, rows, grid.nz, sc, s);
+  }
+}
+
+lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
+                              int partitions, cudaStream_t s) {
+  if (g.nx < 1 || g.nz < 1 || !(g.dx > 0) || !(g.dz > 0)) throw Error(LAG_EINVAL, "bad grid");
+  if (!(ax > 0) || !(az > 0) || !(d >= 0)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+  if (prec != LAG_FP64 && prec != LAG_MIXED) throw Error(LAG_EINVAL, "prec must be LAG_FP64 or LAG_MIXED");
+  std::unique_ptr<lag_precond> p(new lag_precond());
+  p->ctx = ctx;
+  p->grid = g;
+  p->prec = prec;
+  p->ax = ax;
+  p->az = az;
+  p->d = d;
+  p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = ctx;
+  p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
+  dst_build(p->dst, p->dst_store, g.nx, p->use_tc, s);
+  p->tri64.nx = g.nx;
+  p->tri64.nz = g.nz;
+  tri_choose_layout(p->tri64, 8, partitions);
+  tri_build_factors(p->tri64, p->tri_store, ax, az, d, g.dx, g.dz, s);
+  if (prec == LAG_MIXED) {
+    p->tri32.nx = g.nx;
+    p->tri32.nz = g.nz;
+    tri_choose_layout(p->tri32, 4, partitions);
+    tri_make_f32(p->tri64, p->tri32, p->tri32_store, s);
+  }
+  LAG_CUDA_CHECK(cudaStreamSynchronize(s));
+  return p.release();
+}
+
+// ------------------------------------------------------------------------------ medium
+void lag_medium::apply(const double *p, double *q, int nrhs, const KrylovScalars *sc, const Reduce *red, int mode,
+                       cudaStream_t s) {
+  if (elastic) elastic_apply(*this, p, q, nrhs, sc, red, mode, s);
+  else acoustic_apply(*this, p, q, nrhs, sc, red, mode, s);
+}
+
+lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const double *vs, const double *rho,
+                            double h, cudaStream_t s) {
+  if (g.nx < 1 || g.nz < 1 || !(g.dx > 0) || !(g.dz > 0)) throw Error(LAG_EINVAL, "bad grid");
+  if (c == nullptr || rho == nullptr) throw Error(LAG_EINVAL, "null medium array");
+  if (!(h > 0)) throw Error(LAG_EINVAL, "Laguerre h must be positive");
+  std::unique_ptr<lag_medium> m(new lag_medium());
+  m->ctx = ctx;
+  m->grid = g;
+  m->h = h;
+  m->coef.ctx = m->rho_h2.ctx = ctx;
+  if (vs == nullptr) {
+    m->elastic = false;
+    medium_build_acoustic(*m, c, rho, s);
+  } else {
+    m->elastic = true;
+    medium_build_elastic(*m, c, vs, rho, s);
+  }
+  return m.release();
+}
+
+// ------------------------------------------------------------------------------ C ABI helpers
+static thread_local std::string g_tls_error;
+
+template <typename F>
+static int guarded(lag_ctx *ctx, F &&f) {
+  try {
+    f();
+    return LAG_OK;
+  } catch (const Error &e) {
+    if (ctx) ctx->last_error = e.what();
+    g_tls_error = e.what();
+    return e.status;
+  } catch (const std::bad_alloc &) {
+    if (ctx) ctx->last_error = "host allocation failed";
+    return LAG_ENOMEM;
+  } catch (const std::exception &e) {
+    if (ctx) ctx->last_error = e.what();
+    g_tls_error = e.what();
+    return LAG_ECUDA;
+  }
+}
+
+static void set_device(lag_ctx *ctx) { LAG_CUDA_CHECK(cudaSetDevice(ctx->device)); }
+
+extern "C" {
+
+const char *lag_strerror(int status) {
+  switch (status) {
+    case LAG_OK: return "ok";
+    case LAG_EINVAL: return "invalid argument";
+    case LAG_ENOMEM: return "out of device memory or HBM budget";
+    case LAG_ENOTCONV: return "Krylov solve did not converge within max_iter";
+    case LAG_ENUMERIC: return "NaN or Inf in a residual";
+    case LAG_ECUDA: return "CUDA error";
+    case LAG_EAGAIN: return "not finished yet";
+    case LAG_ETIMEDOUT: return "bounded device wait timed out";
+    case LAG_ECANCELED: return "cancelled";
+    default: return "unknown status";
+  }
+}
+
+const char *lag_last_error(const lag_ctx *ctx) { return ctx ? ctx->last_error.c_str() : g_tls_error.c_str(); }
+int lag_version(void) { return 100; }
+
+int lag_create(lag_ctx **out, int device, size_t budget, void *stream) {
+  if (out == nullptr) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(nullptr, [&] {
+    int ndev = 0;
+    LAG_CUDA_CHECK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) throw Error(LAG_EINVAL, "no such CUDA device");
+    std::unique_ptr<lag_ctx> c(new lag_ctx());
+    c->device = device;
+    c->budget = budget;
+    c->t_created = now_seconds();
+    LAG_CUDA_CHECK(cudaSetDevice(device));
+    if (stream != nullptr) {
+      c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      LAG_CUDA_CHECK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    *out = c.release();
+  });
+}
+
+void lag_destroy(lag_ctx *ctx) {
+  if (ctx == nullptr) return;
+  server_destroy(ctx);
+  cudaSetDevice(ctx->device);
+  if (ctx->own_stream && ctx->stream) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+int lag_synchronize(lag_ctx *ctx) {
+  if (!ctx) return LAG_EINVAL;
+  return guarded(ctx, [&] { LAG_CUDA_CHECK(cudaStreamSynchronize(ctx->stream)); });
+}
+
+size_t lag_bytes_in_use(const lag_ctx *ctx) { return ctx ? ctx->in_use.load() : 0; }
+long long lag_kernel_launches(const lag_ctx *) { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+// ------------------------------------------------------------------------------ preconditioner
+int lag_precond_create(lag_ctx *ctx, const lag_grid *grid, double kappa_t, double rho_t, double h_lag, int prec,
+                       lag_precond **out) {
+  if (!ctx || !grid || !out) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    *out = precond_new(ctx, *grid, kappa_t, kappa_t, rho_t * h_lag * h_lag / 4.0, prec, 0, ctx->stream);
+  });
+}
+
+int lag_precond_create_sep(lag_ctx *ctx, const lag_grid *grid, double ax, double az, double d, int prec,
+                           int partitions, lag_precond **out) {
+  if (!ctx || !grid || !out) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    if (partitions < 0 || partitions > 32) throw Error(LAG_EINVAL, "partitions must be 0..32");
+    *out = precond_new(ctx, *grid, ax, az, d, prec, partitions, ctx->stream);
+  });
+}
+
+void lag_precond_destroy(lag_precond *p) {
+  if (!p) return;
+  cudaSetDevice(p->ctx->device);
+  cudaStreamSynchronize(p->ctx->stream);
+  delete p;
+}
+
+int lag_precond_apply(lag_precond *p, const double *r, double *z, int nrhs) {
+  if (!p || nrhs < 0 || (nrhs > 0 && (!r || !z))) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    if (nrhs == 0) return;
+    p->apply(r, z, nrhs, nullptr, p->ctx->stream);
+  });
+}
+
+int lag_precond_dst(lag_precond *p, const double *x, double *y, int nrhs) {
+  if (!p || nrhs < 0 || (nrhs > 0 && (!x || !y))) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    if (nrhs == 0) return;
+    const int rows = nrhs * p->grid.nz;
+    if (p->prec == LAG_FP64) {
+      dst_apply_f64(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
+    } else {  // float64 -> float32 spectrum -> float64 (both mixed-path kernels, back to back)
+      p->ensure_scratch(nrhs);
+      float *w = p->scratch.as<float>();
+      if (p->use_tc) dst_apply_tc_d2f(p->dst, x, w, rows, p->grid.nz, nullptr, p->ctx->stream);
+      else dst_apply_f32_d2f(p->dst, x, w, rows, p->grid.nz, nullptr, p->ctx->stream);
+      widen_f32(w, y, (size_t)rows * p->grid.nx, p->ctx->stream);
+    }
+  });
+}
+
+int lag_precond_dst_f32(lag_precond *p, const float *x, double *y, int nrhs) {
+  if (!p || nrhs < 0 || (nrhs > 0 && (!x || !y)) || p->prec != LAG_MIXED) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    if (nrhs == 0) return;
+    const int rows = nrhs * p->grid.nz;
+    if (p->use_tc) dst_apply_tc_f2d(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
+    else dst_apply_f32_f2d(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
+  });
+}
+
+int lag_precond_tridiag(lag_precond *p, const double *d, double *y, int nrhs) {
+  if (!p || nrhs < 0 || (nrhs > 0 && (!d || !y))) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    if (nrhs > 0) tri_solve_f64(p->tri64, d, y, nrhs, nullptr, p->ctx->stream);
+  });
+}
+
+int lag_precond_tridiag_f32(lag_precond *p, const float *d, float *y, int nrhs) {
+  if (!p || nrhs < 0 || (nrhs > 0 && (!d || !y)) || p->prec != LAG_MIXED) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    if (nrhs > 0) tri_solve_f32(p->tri32, d, y, nrhs, nullptr, p->ctx->stream);
+  });
+}
+
+int lag_precond_info(const lag_precond *p, int *P, int *L, int *mt) {
+  if (!p) return LAG_EINVAL;
+  const TriFactors &t = (p->prec == LAG_FP64) ? p->tri64 : p->tri32;
+  if (P) *P = t.P;
+  if (L) *L = t.L;
+  if (mt) *mt = t.mt;
+  return LAG_OK;
+}
+
+int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? (p->use_tc ? 1 : 0) : 0; }
+
+// ------------------------------------------------------------------------------ medium
+int lag_medium_create_acoustic(lag_ctx *ctx, const lag_grid *g, const double *c, const double *rho, double h,
+                               lag_medium **out) {
+  if (!ctx || !g || !out) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    *out = medium_new(ctx, *g, c, nullptr, rho, h, ctx->stream);
+  });
+}
+
+int lag_medium_create_elastic(lag_ctx *ctx, const lag_grid *g, const double *vp, const double *vs,
+                              const double *rho, double h, lag_medium **out) {
+  if (!ctx || !g || !out || !vs) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    *out = medium_new(ctx, *g, vp, vs, rho, h, ctx->stream);
+  });
+}
+
+void lag_medium_destroy(lag_medium *m) {
+  if (!m) return;
+  cudaSetDevice(m->ctx->device);
+  cudaStreamSynchronize(m->ctx->stream);
+  delete m;
+}
+
+int lag_medium_midranges(lag_medium *m, double *out) {
+  if (!m || !out) return LAG_EINVAL;
+  out[0] = m->mid[0];
+  out[1] = m->mid[1];
+  if (m->elastic) out[2] = m->mid[2];
+  return LAG_OK;
+}
+
+int lag_apply_operator(lag_medium *m, const double *p, double *q, int nrhs) {
+  if (!m || nrhs < 0 || (nrhs > 0 && (!p || !q))) return LAG_EINVAL;
+  return guarded(m->ctx, [&] {
+    set_device(m->ctx);
+    if (nrhs > 0) m->apply(p, q, nrhs, nullptr, nullptr, 0, m->ctx->stream);
+  });
+}
+
+// ------------------------------------------------------------------------------ one system
+int lag_solve_system(lag_medium *m, lag_precond *p1, lag_precond *p2, const double *b, double *x, int nrhs,
+                     const lag_solver *s, int *iters, double *relres) {
+  if (!m || !p1 || !s || nrhs < 0 || (nrhs > 0 && (!b || !x))) return LAG_EINVAL;
+  int status = LAG_OK;
+  int rc = guarded(m->ctx, [&] {
+    set_device(m->ctx);
+    if (nrhs == 0) return;
+    check_solver(*s, m->elastic);
+    if (p1->grid.nx != m->grid.nx || p1->grid.nz != m->grid.nz) throw Error(LAG_EINVAL, "plan/medium grid mismatch");
+    if (p1->prec != s->prec) throw Error(LAG_EINVAL, "plan precision differs from solver precision");
+    if (m->elastic && (!p2 || p2->prec != s->prec || p2->grid.nx != m->grid.nx || p2->grid.nz != m->grid.nz))
+      throw Error(LAG_EINVAL, "elastic solve needs a second matching plan (B2)");
+    KrylovWork wk;
+    wk.setup(m->ctx, m, p1, p2, *s, nrhs, m->ctx->stream);
+    LAG_CUDA_CHECK(cudaMemcpyAsync(wk.b(), b, wk.n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, m->ctx->stream));
+    status = wk.solve_blocking();
+    wk.copy_result(x);
+    wk.report(iters, relres);
+  });
+  return rc != LAG_OK ? rc : status;
+}
+
+// ------------------------------------------------------------------------------ Laguerre pieces
+int lag_source_coeffs(lag_ctx *ctx, const lag_laguerre *lag, const lag_wavelet *w, double *fm_host) {
+  if (!ctx || !lag || !w || !fm_host || lag->n_harm < 1 || lag->alpha < 0 || !(lag->h > 0) || !(w->f0 > 0))
+    return LAG_EINVAL;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    DevBuf fm, scratch;
+    fm.alloc(ctx, lag->n_harm * sizeof(double));
+    source_coeffs_device(*lag, *w, fm.as<double>(), scratch, ctx, ctx->stream);
+    LAG_CUDA_CHECK(cudaMemcpyAsync(fm_host, fm.ptr, lag->n_harm * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    LAG_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int lag_laguerre_table(lag_ctx *ctx, const lag_laguerre *lag, int nt, const double *t_host, double *tab_host) {
+  if (!ctx || !lag || nt < 0 || (nt > 0 && (!t_host || !tab_host)) || lag->n_harm < 1 || !(lag->h > 0))
+    return LAG_EINVAL;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    if (nt == 0) return;
+    DevBuf t, tab;
+    t.alloc(ctx, nt * sizeof(double));
+    tab.alloc(ctx, (size_t)nt * lag->n_harm * sizeof(double));
+    LAG_CUDA_CHECK(cudaMemcpyAsync(t.ptr, t_host, nt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    laguerre_table_device(*lag, nt, t.as<double>(), tab.as<double>(), ctx->stream);
+    LAG_CUDA_CHECK(cudaMemcpyAsync(tab_host, tab.ptr, (size_t)nt * lag->n_harm * sizeof(double),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    LAG_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+}  // extern "C"

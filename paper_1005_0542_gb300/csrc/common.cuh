@@ -1,0 +1,137 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+
+namespace lag {
+
+// ------------------------------------------------------------------ errors
+// Host code throws lag::Error; the C ABI layer converts it to a status code.
+struct Error : public std::runtime_error {
+  int status;
+  Error(int s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+#define LAG_CUDA_CHECK(call)                                                                  \
+  do {                                                                                        \
+    cudaError_t e__ = (call);                                                                 \
+    if (e__ != cudaSuccess)                                                                   \
+      throw ::lag::Error(-5, std::string(#call) + ": " + cudaGetErrorString(e__) + " (" +     \
+                                 __FILE__ + ":" + std::to_string(__LINE__) + ")");            \
+  } while (0)
+
+#define LAG_LAUNCH_CHECK() LAG_CUDA_CHECK(cudaGetLastError())
+
+// Count of the library's kernel launches (process-wide, for launch accounting).
+extern unsigned long long g_launches;
+inline void count_launch(int n = 1) { __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
+// ------------------------------------------------------------------ Krylov scalars
+// One record per right-hand side, resident on the device.  Kernels read alpha/beta from here
+// and skip a right-hand side whose `state` is not 0, so no host round trip is needed between
+// the steps of an iteration.
+struct KrylovScalars {
+  double bb;      // ||b||^2
+  double rz;      // (r, z) of the current iterate
+  double pq;      // (p, q)
+  double rr;      // (r, r)
+  double zq;      // (z, q)      (Polak-Ribiere beta)
+  double alpha;
+  double beta;
+  double tol2;    // tol^2
+  int state;      // ST_* below
+  int iters;
+  int jdone;      // GMRES: steps taken in the open cycle
+  int pad;
+};
+static_assert(sizeof(KrylovScalars) == 80, "layout");
+
+// ST_MET (GMRES only): the residual estimate met the tolerance inside an open cycle; the true
+// residual at the next cycle start turns it into ST_CONV or back into ST_RUN.
+enum { ST_RUN = 0, ST_CONV = 1, ST_NAN = 2, ST_STOP = 3, ST_MET = 4 };
+
+// Scratch for deterministic two-stage reductions: per rhs a slot of `nblk` partial sums and a
+// completion counter.  The last block to finish sums the partials in index order.
+struct Reduce {
+  double *part;        // [nrhs][rstride]: value i of block b at i * nblk + b
+  unsigned int *count; // [nrhs]  (must start at zero; reset by the last block)
+  int nblk;            // block capacity per value
+  int rstride;         // doubles per rhs (values capacity * nblk)
+};
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of NV values per thread; result valid in thread 0.  blockDim.x multiple of 32, <= 1024.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *sh /* [32*NV] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = lane < nw ? sh[i * 32 + lane] : 0.0;
+      v[i] = warp_sum(t);
+    }
+  }
+}
+
+// After thread 0 of a block has its NV block partials, publish them into red.part for `rhs`
+// and return true in thread 0 of the last block of that rhs, with the totals in `tot`
+// (summed in block-index order: deterministic).  Call from every thread.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(const Reduce &red, int rhs, int blk, int nblk,
+                                                 const double (&v)[NV], double (&tot)[NV]) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    double *p = red.part + (size_t)rhs * red.rstride;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) p[i * red.nblk + blk] = v[i];
+    __threadfence();
+    unsigned int prev = atomicAdd(red.count + rhs, 1u);
+    is_last = (prev == (unsigned int)(nblk - 1));
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  // the last block: every thread helps sum the partials in a fixed order
+  __threadfence();
+  const double *p = red.part + (size_t)rhs * red.rstride;
+  __shared__ double sh[32 * NV];
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    acc[i] = 0.0;
+    // fixed partition: thread t sums blocks t, t + blockDim, ... in order
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc[i] += __ldcg(p + i * red.nblk + b);
+  }
+  block_sum<NV>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) tot[i] = acc[i];
+    red.count[rhs] = 0u;  // ready for the next use
+  }
+  return threadIdx.x == 0;
+}
+
+}  // namespace lag

@@ -1,0 +1,228 @@
+// Host-side structures of the library and the launchers of its kernels.
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lagwave.h"
+#include "common.cuh"
+
+// ----------------------------------------------------------------------------- context
+struct lag_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;                 // 0 = unlimited
+  std::atomic<size_t> in_use{0};
+  std::string last_error;
+  double t_created = 0.0;
+  struct Server *server = nullptr;   // serving loop (lazily created)
+  std::mutex mem_mu;
+};
+
+void server_destroy(lag_ctx *ctx);  // stops the serving thread of ctx, if any
+
+namespace lag {
+
+double now_seconds();
+
+// ------------------------------------------------------------------ kernel-class timing
+enum KClass { KC_DST64 = 0, KC_DST32_FWD, KC_DST32_INV, KC_DSTTC_FWD, KC_DSTTC_INV, KC_TRI64, KC_TRI32,
+              KC_STENCIL_A, KC_STENCIL_E, KC_VEC, KC_LAGUERRE, KC_GMRES, KC_SETUP, NK_CLASSES };
+const char *kclass_name(int c);
+// Records a CUDA event pair around the launches in its scope when profiling is enabled.
+struct ProfScope {
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  bool active = false;
+  ProfScope(int c, cudaStream_t st);
+  ~ProfScope();
+};
+
+// Device buffer owned by a context; counted against its HBM budget.
+struct DevBuf {
+  lag_ctx *ctx = nullptr;
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void alloc(lag_ctx *c, size_t nbytes, bool zero = false);
+  void release();
+  template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// ----------------------------------------------------------------- tridiagonal plan (a2, a8)
+// Factors of the partitioned solve for every x-mode (see k_tridiag.cu for the algorithm).
+struct TriFactors {
+  int nx = 0, nz = 0;   // modes, rows
+  int P = 1, L = 1;     // partitions, partition length (P * L >= nz; rows >= nz are identity)
+  int ncls = 1;         // factor classes (3 for Toeplitz-in-z systems, P in general)
+  int levels = 0;       // PCR levels of the reduced system (P - 1 unknowns)
+  int nf = 3;           // values per separator in the reduced block: 3 + 3 * levels
+  int mt = 1;           // modes per CTA
+  int threads = 32;     // threads per CTA (mt * P rounded up to whole warps)
+  size_t smem = 0;      // dynamic shared memory of the solve kernel
+  // device arrays, element type double or float: [cls][i][j] with j fastest
+  void *fm = nullptr, *fc = nullptr, *fa = nullptr, *sv = nullptr, *sw = nullptr;
+  void *red = nullptr;  // [j][nf][32]
+};
+
+void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P);
+// Build float64 factors of T_j = tridiag(off, 2 az/dz^2 + ax lambda_j + d, off) on the device.
+void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
+                       double dz, cudaStream_t s);
+// Round a float64 factor set to float32 into `store32` (same layout).
+void tri_make_f32(const TriFactors &t64, TriFactors &t32, DevBuf &store32, cudaStream_t s);
+// y = T^{-1} d per (plane, mode); d and y [planes][nz][nx]; in place allowed.  The launch covers
+// `nplanes` planes pstride * i + poff; sc (nullable) skips planes whose right-hand side
+// (plane / ncomp) is no longer iterating.
+void tri_solve_f64(const TriFactors &tf, const double *d, double *y, int nplanes,
+                   const KrylovScalars *sc, cudaStream_t s, int pstride = 1, int poff = 0,
+                   int ncomp = 1);
+void tri_solve_f32(const TriFactors &tf, const float *d, float *y, int nplanes,
+                   const KrylovScalars *sc, cudaStream_t s, int pstride = 1, int poff = 0,
+                   int ncomp = 1);
+
+// ----------------------------------------------------------------- DST (a7, a9)
+struct DstPlan {
+  int n = 0;            // transform length nx
+  int ku = 0, kv = 0;   // ceil(n/2), floor(n/2): inner dimensions of the two folded GEMMs
+  double *su = nullptr; // [ku][ku]  S[j][2k]    (float64)
+  double *sv = nullptr; // [kv][kv]  S[j][2k+1]
+  float *su_f = nullptr, *sv_f = nullptr;  // float32 copies (SIMT float32 kernel)
+  // split-bf16 copies for the tensor-core path: hi and lo parts, K-major [k][j] tiles
+  uint16_t *su_hi = nullptr, *su_lo = nullptr, *sv_hi = nullptr, *sv_lo = nullptr;
+  int kpad_u = 0, kpad_v = 0; // K padded to a multiple of 64 for the tensor-core tiles
+  int npad_u = 0, npad_v = 0; // N padded to the tensor-core N tile
+};
+void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream_t s);
+// Y[row][:] = S X[row][:] for `rows` rows of length n.  Input/output types as named.
+void dst_apply_f64(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
+                   const KrylovScalars *sc, cudaStream_t s);
+// mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
+void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
+                       const KrylovScalars *sc, cudaStream_t s);
+void dst_apply_f32_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
+                       const KrylovScalars *sc, cudaStream_t s);
+// mixed path: float64 in -> float32 out, and float32 in -> float64 out (tensor cores)
+void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
+                      const KrylovScalars *sc, cudaStream_t s);
+void dst_apply_tc_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
+                      const KrylovScalars *sc, cudaStream_t s);
+bool dst_tc_supported(int n);
+
+}  // namespace lag
+
+// ----------------------------------------------------------------------------- preconditioner
+struct lag_precond {
+  lag_ctx *ctx = nullptr;
+  lag_grid grid{};
+  int prec = LAG_FP64;
+  double ax = 0, az = 0, d = 0;
+  lag::DstPlan dst;
+  lag::TriFactors tri64, tri32;
+  lag::DevBuf dst_store, tri_store, tri32_store;
+  lag::DevBuf scratch;      // intermediate spectra (float64 or float32), grows with nrhs
+  int scratch_rhs = 0;
+  bool use_tc = false;      // mixed path: DST on tcgen05 tensor cores (else SIMT float32)
+  void ensure_scratch(int nplanes);
+  // z = B^{-1} r for nrhs planes; sc (nullable) lets converged right-hand sides skip the work
+  void apply(const double *r, double *z, int nrhs, const lag::KrylovScalars *sc, cudaStream_t s);
+};
+
+namespace lag {
+// K^{-1} for ncomp interleaved components ([rhs][comp][nz][nx]): component 0 with p1, 1 with p2.
+void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, double *z, int nrhs,
+                         int ncomp, const KrylovScalars *sc, cudaStream_t s);
+}
+
+// ----------------------------------------------------------------------------- medium
+struct lag_medium {
+  lag_ctx *ctx = nullptr;
+  lag_grid grid{};
+  bool elastic = false;
+  double h = 0;
+  double mid[3] = {0, 0, 0};   // kappa~, rho~ | (l+2m)~, mu~, rho~
+  lag::DevBuf coef;            // operator coefficients (see k_ops.cu)
+  lag::DevBuf rho_h2;          // rho h^2 at nodes (right-hand side history term)
+  size_t ncoef = 0;
+  void apply(const double *p, double *q, int nrhs, const lag::KrylovScalars *sc,
+             const lag::Reduce *red, int mode, cudaStream_t s);
+};
+
+namespace lag {
+// ----------------------------------------------------------------- operator and vector kernels
+void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rho_host,
+                           cudaStream_t s);
+void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs_host,
+                          const double *rho_host, cudaStream_t s);
+// build a medium / a separable preconditioner plan on stream s (blocking)
+lag_medium *medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const double *vs,
+                       const double *rho, double h, cudaStream_t s);
+lag_precond *precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
+                         int partitions, cudaStream_t s);
+// mode 0: q = Ap only; mode 1: also (p,q) -> alpha = rz/pq  (PCG)
+void acoustic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
+                    const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s);
+void elastic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
+                   const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s);
+
+int reduce_blocks(size_t n);  // blocks per rhs of the vector kernels for n values per rhs
+
+// PCG pieces (per rhs, n values each)
+void pcg_start(const double *b, double *x, double *r, size_t n, int nrhs, double tol,
+               KrylovScalars *sc, const Reduce &red, cudaStream_t s);
+void pcg_rz_p(const double *r, const double *z, double *p, size_t n, int nrhs,
+              KrylovScalars *sc, const Reduce &red, cudaStream_t s);
+void pcg_update_xr(double *x, double *r, const double *p, const double *q, size_t n, int nrhs,
+                   int max_iter, KrylovScalars *sc, const Reduce &red, cudaStream_t s);
+void pcg_beta(const double *r, const double *z, const double *q, size_t n, int nrhs, int flexible,
+              KrylovScalars *sc, const Reduce &red, cudaStream_t s);
+void pcg_update_p(double *p, const double *z, size_t n, int nrhs, const KrylovScalars *sc,
+                  cudaStream_t s);
+
+// FGMRES pieces: vectors of n values per rhs; V, Z: [k+1][nrhs][n] bases; H: [nrhs][(k+1)*k]
+struct GmresDev {
+  double *H, *cs, *sn, *g, *y;   // per rhs: H [(k+1) k], cs/sn [k], g [k+1], y [k]
+  double *hcol;                  // per rhs: [k+1] current column (Gram-Schmidt coefficients)
+  int k;
+};
+void gm_start(const double *b, const double *cx, double *v0, size_t n, int nrhs, int first,
+              double tol, int max_iter, KrylovScalars *sc, GmresDev &g, const Reduce &red,
+              cudaStream_t s);
+void gm_orthogonalize(double *w, const double *V, int j, size_t n, int nrhs, size_t vstride,
+                      const KrylovScalars *sc, GmresDev &g, const Reduce &red, int pass,
+                      cudaStream_t s);
+void gm_normalize(double *w, double *vnext, int j, size_t n, int nrhs, KrylovScalars *sc,
+                  GmresDev &g, const Reduce &red, int max_iter, cudaStream_t s);
+void gm_update_x(double *x, const double *Z, int jdone, size_t n, int nrhs, size_t zstride,
+                 const KrylovScalars *sc, GmresDev &g, cudaStream_t s);
+
+// Laguerre pieces
+void source_coeffs_device(const lag_laguerre &lag, const lag_wavelet &w, double *fm_dev,
+                          DevBuf &scratch, lag_ctx *ctx, cudaStream_t s);
+void laguerre_table_device(const lag_laguerre &lag, int nt, const double *t_dev, double *tab_dev,
+                           cudaStream_t s);
+// r = -c_m rho h^2 S (+ f_m/(dx dz) at each source), x = 0, ||r||^2 -> sc.bb; per rhs/comp.
+void laguerre_rhs(const double *rho_h2, const double *S, double cm, const double *fm, int m,
+                  const int *src_idx, int src_comp, double inv_cell, int ncomp, size_t nplane,
+                  int nrhs, double *r, double *x, double tol, KrylovScalars *sc,
+                  const Reduce &red, cudaStream_t s);
+void laguerre_accumulate(const double *x, double *T, double *S, double chat, size_t n, int nrhs,
+                         cudaStream_t s);
+void gather_receivers(const double *x, const int *rcv_idx, int nrcv, int ncomp, size_t nplane,
+                      int nrhs, double *out, cudaStream_t s);
+void inverse_sum(const double *rrcv, const double *tab, int nharm, int nrows, int nt,
+                 double *traces, cudaStream_t s);
+void midrange_device(const double *f, size_t n, double *minmax_dev, cudaStream_t s);
+
+}  // namespace lag

@@ -1,0 +1,158 @@
+// Orthonormal DST-I along x as two folded dense GEMMs (the preconditioner's x-direction step).
+//
+// Sec. 2.4 inverts the Laplace preconditioner by separation of variables; the transform along x
+// (FFTW in the paper, Sec. 3.1) diagonalises the Dirichlet second difference.  With
+//     S[j][k] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1)),   S^2 = I,
+// and S[n-1-j][k] = (-1)^k S[j][k], every row transform y = S x splits into
+//     y[2k']   = sum_{j' < ceil(n/2)}  S[j'][2k']   u[j'],   u[j'] = x[j'] + x[n-1-j']  (middle once)
+//     y[2k'+1] = sum_{j' < floor(n/2)} S[j'][2k'+1] v[j'],   v[j'] = x[j'] - x[n-1-j']
+// i.e. two (n/2 x n/2) GEMMs over all rows at half the flops of the direct product.  The fold is
+// applied while the A tile is staged into shared memory.  n + 1 has large prime factors at the
+// workload sizes (2049 = 3 * 683), so the dense product is used rather than a fast transform.
+#include "internal.h"
+
+namespace lag {
+
+// ------------------------------------------------------------------------------ matrices
+__global__ void dst_matrix_kernel(int n, int ku, int kv, double *su, double *sv, float *suf, float *svf) {
+  const int kp = blockIdx.x * blockDim.x + threadIdx.x;  // output column k' (fastest)
+  const int jp = blockIdx.y;                             // input row j'
+  const double scale = sqrt(2.0 / (double)(n + 1));
+  const long long period = 2LL * (n + 1);
+  if (kp < ku && jp < ku) {
+    const long long m = ((long long)(jp + 1) * (long long)(2 * kp + 1)) % period;
+    const double v = scale * sinpi((double)m / (double)(n + 1));
+    su[(size_t)jp * ku + kp] = v;
+    suf[(size_t)jp * ku + kp] = (float)v;
+  }
+  if (kp < kv && jp < kv) {
+    const long long m = ((long long)(jp + 1) * (long long)(2 * kp + 2)) % period;
+    const double v = scale * sinpi((double)m / (double)(n + 1));
+    sv[(size_t)jp * kv + kp] = v;
+    svf[(size_t)jp * kv + kp] = (float)v;
+  }
+}
+
+void dst_build_tc(DstPlan &dp, DevBuf &store, size_t offset_bytes, cudaStream_t s);
+size_t dst_tc_bytes(int n);
+
+void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream_t s) {
+  dp.n = n;
+  dp.ku = (n + 1) / 2;
+  dp.kv = n / 2;
+  const size_t nu = (size_t)dp.ku * dp.ku, nv = (size_t)dp.kv * dp.kv;
+  size_t bytes = (nu + nv) * (sizeof(double) + sizeof(float)) + 256;
+  const size_t tc_off = (bytes + 1023) & ~(size_t)1023;
+  if (tensor_copies) bytes = tc_off + dst_tc_bytes(n);
+  store.alloc(store.ctx, bytes, true);
+  char *base = store.as<char>();
+  dp.su = reinterpret_cast<double *>(base);
+  dp.sv = dp.su + nu;
+  dp.su_f = reinterpret_cast<float *>(dp.sv + nv);
+  dp.sv_f = dp.su_f + nu;
+  dim3 grid((dp.ku + 127) / 128, dp.ku > 0 ? dp.ku : 1);
+  dst_matrix_kernel<<<grid, 128, 0, s>>>(n, dp.ku, dp.kv, dp.su, dp.sv, dp.su_f, dp.sv_f);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  if (tensor_copies) dst_build_tc(dp, store, tc_off, s);
+}
+
+// ------------------------------------------------------------------------------ SIMT GEMM
+// One launch covers both parities (blockIdx.z).  Tile 64 x 64 x 16, 256 threads, 4 x 4 per thread.
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__device__ __forceinline__ bool tile_all_done(const KrylovScalars *sc, int m0, int rows, int rpr) {
+  if (sc == nullptr) return false;
+  const int r0 = m0 / rpr, r1 = (min(m0 + BM, rows) - 1) / rpr;
+  for (int r = r0; r <= r1; ++r)
+    if (sc[r].state == ST_RUN) return false;
+  return true;
+}
+
+template <typename TI, typename TO, typename TA>
+__global__ void __launch_bounds__(256) dst_simt_kernel(const TI *__restrict__ X, TO *__restrict__ Y, int rows, int n,
+                                                       const TA *__restrict__ Su, const TA *__restrict__ Sv,
+                                                       int ku, int kv, const KrylovScalars *__restrict__ sc, int rpr) {
+  const int parity = blockIdx.z;
+  const int K = parity ? kv : ku;
+  const TA *B = parity ? Sv : Su;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  if (n0 >= K || tile_all_done(sc, m0, rows, rpr)) return;
+  __shared__ __align__(16) TA As[BK][BM + 4];
+  __shared__ __align__(16) TA Bs[BK][BN + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  TA acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = TA(0);
+  const bool odd_n = (n & 1) != 0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + e * 256;
+      const int r = idx / BK, kk = idx % BK;
+      const int row = m0 + r, j = k0 + kk;
+      TA v = TA(0);
+      if (row < rows && j < K) {
+        const TI *xr = X + (size_t)row * n;
+        const TA x1 = (TA)xr[j];
+        if (parity == 0) v = (odd_n && j == K - 1) ? x1 : x1 + (TA)xr[n - 1 - j];
+        else v = x1 - (TA)xr[n - 1 - j];
+      }
+      As[kk][r] = v;
+      const int kb = idx / BN, c = idx % BN;
+      Bs[kb][c] = (k0 + kb < K && n0 + c < K) ? B[(size_t)(k0 + kb) * K + n0 + c] : TA(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TA a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = m0 + ty * 4 + i;
+    if (row >= rows) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = n0 + tx * 4 + j;
+      if (col < K) Y[(size_t)row * n + 2 * col + parity] = (TO)acc[i][j];
+    }
+  }
+}
+
+template <typename TI, typename TO, typename TA>
+static void dst_simt_launch(const DstPlan &dp, const TI *x, TO *y, int rows, int rpr, const TA *su, const TA *sv,
+                            const KrylovScalars *sc, cudaStream_t s, int cls) {
+  if (rows <= 0 || dp.n <= 0) return;
+  ProfScope prof(cls, s);
+  dim3 grid((dp.ku + BN - 1) / BN, (rows + BM - 1) / BM, dp.kv > 0 ? 2 : 1);
+  dst_simt_kernel<TI, TO, TA><<<grid, 256, 0, s>>>(x, y, rows, dp.n, su, sv, dp.ku, dp.kv, sc, rpr);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+void dst_apply_f64(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
+                   cudaStream_t s) {
+  dst_simt_launch<double, double, double>(dp, x, y, rows, rpr, dp.su, dp.sv, sc, s, KC_DST64);
+}
+void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rpr, const KrylovScalars *sc,
+                       cudaStream_t s) {
+  dst_simt_launch<double, float, float>(dp, x, y, rows, rpr, dp.su_f, dp.sv_f, sc, s, KC_DST32_FWD);
+}
+void dst_apply_f32_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rpr, const KrylovScalars *sc,
+                       cudaStream_t s) {
+  dst_simt_launch<float, double, float>(dp, x, y, rows, rpr, dp.su_f, dp.sv_f, sc, s, KC_DST32_INV);
+}
+
+}  // namespace lag

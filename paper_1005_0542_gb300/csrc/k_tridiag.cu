@@ -1,0 +1,383 @@
+// Partitioned tridiagonal solve with precomputed factors (the preconditioner's z-direction step).
+//
+// Sec. 1 and Sec. 2.4 of the paper: after the transform along x, every x-mode j needs the solve of
+// one tridiagonal system T_j along z, and T_j is the same for every right-hand side and every
+// Krylov iteration and harmonic.  The paper uses the Dichotomy Algorithm: an O(N) preparatory
+// step done once, then per right-hand side a partitioned elimination whose only exchange is an
+// associative reduction over the partitions.  On GB300 the partitions are threads of one CTA:
+//
+//   rows are cut into P partitions of length L (rows >= nz are identity rows with zero data).
+//   The first row of partitions 1..P-1 is a separator xi_p; the other rows form blocks I_p.
+//   1. per block: g = T_I^{-1} d_I with the block's precomputed LU factors (fm = 1/pivot,
+//      fc = c * fm, fa = sub-diagonal), forward then backward sweep;
+//   2. the separators satisfy a (P-1)-unknown tridiagonal system whose matrix depends only on
+//      T_j (precomputed) and whose right-hand side is d_sep - a g_{p-1}^last - c g_p^first;
+//      one warp per mode solves it by parallel cyclic reduction in log2(P) shuffle levels
+//      with precomputed per-level multipliers;
+//   3. correction y_I = g - xi_p v - xi_{p+1} w with the precomputed spike vectors
+//      v = T_I^{-1}(a_first e_first), w = T_I^{-1}(c_last e_last).
+//
+// The column tile of MT modes x all rows lives in shared memory: the right-hand side is read
+// once and the solution written once (coalesced rows of MT consecutive modes).
+#include <algorithm>
+
+#include "internal.h"
+
+namespace lag {
+
+// ------------------------------------------------------------------------------ layout
+void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
+  const int nz = tf.nz;
+  int Pt = (want_P > 0) ? std::min(want_P, 32) : 32;
+  while (Pt > 1 && nz / Pt < 4) Pt /= 2;  // at least 4 rows per partition
+  int L = (nz + Pt - 1) / Pt;
+  if (Pt > 1 && L < 2) L = 2;
+  // P = ceil(nz / L): only the last partition holds identity rows beyond nz, so every other
+  // partition of a Toeplitz-in-z system shares the "first" or "middle" factor class
+  int P = (nz + L - 1) / L;
+  if (P <= 1) {
+    P = 1;
+    L = nz;
+  }
+  tf.P = P;
+  tf.L = L;
+  tf.ncls = 3;
+  const int n = P - 1;
+  int lev = 0;
+  while ((1 << lev) < n) ++lev;
+  tf.levels = lev;
+  tf.nf = 3 + 3 * lev;
+  const int nzp = P * L;
+  // modes per CTA: power of two <= 32, threads (rounded up to whole warps) <= 1024,
+  // tile <= ~104 KB (two CTAs per SM)
+  const size_t budget = 104 * 1024;
+  auto threads = [&](int m) { return ((m * P + 31) / 32) * 32; };
+  int mt = 32;
+  while (mt > 1 && ((size_t)mt * nzp * elem_bytes > budget || threads(mt) > 1024)) mt /= 2;
+  while (mt > 1 && mt / 2 >= tf.nx) mt /= 2;  // tiny grids: no idle half tiles
+  tf.mt = mt;
+  tf.threads = threads(mt);
+  tf.smem = (size_t)nzp * mt * elem_bytes + (size_t)(3 * 32 + 33) * mt * elem_bytes;
+  if (tf.smem > 200 * 1024)
+    throw Error(LAG_EINVAL, "nz too large for the shared-memory column tile of the tridiagonal solve");
+}
+
+// ------------------------------------------------------------------------------ factors
+// Matrix of mode j: sub a_k, diag b_k, super c_k (rows >= nz: identity).
+struct TriMatrix {
+  double off, diag0, ax, dx2inv, nxp1;
+  int nz;
+  __device__ double diag(int j) const {
+    const double s = sinpi((double)(j + 1) / (2.0 * nxp1));
+    return diag0 + ax * 4.0 * dx2inv * s * s;
+  }
+  __device__ void row(int k, double dj, double &a, double &b, double &c) const {
+    if (k >= nz) { a = 0.0; b = 1.0; c = 0.0; return; }
+    a = (k >= 1) ? off : 0.0;
+    b = dj;
+    c = (k + 1 < nz) ? off : 0.0;
+  }
+};
+
+__device__ __forceinline__ int rep_partition(int cls, int P) { return cls == 0 ? 0 : (cls == 1 ? 1 : P - 1); }
+
+// one thread per (mode j, class): block LU factors and spikes of the class's representative block
+__global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, double *fm, double *fc,
+                                  double *fa, double *sv, double *sw) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cls = blockIdx.y;
+  if (j >= nx) return;
+  const bool exists = (cls == 0) || (cls == 1 && P >= 3) || (cls == 2 && P >= 2);
+  const size_t base = (size_t)cls * L * nx + j;
+  if (!exists) {
+    for (int i = 0; i < L; ++i) {
+      const size_t f = base + (size_t)i * nx;
+      fm[f] = fc[f] = fa[f] = sv[f] = sw[f] = 0.0;
+    }
+    return;
+  }
+  const int p = rep_partition(cls, P);
+  const double dj = M.diag(j);
+  const int i0 = (p == 0) ? 0 : 1;
+  double a, b, c;
+  // separator row slot (i = 0 of p >= 1) is unused by the sweeps
+  if (i0 == 1) {
+    const size_t f = base;
+    fm[f] = fc[f] = fa[f] = sv[f] = sw[f] = 0.0;
+  }
+  double fc_prev = 0.0;
+  for (int i = i0; i < L; ++i) {
+    M.row(p * L + i, dj, a, b, c);
+    const double den = (i == i0) ? b : b - a * fc_prev;
+    const double m = 1.0 / den;
+    const size_t f = base + (size_t)i * nx;
+    fm[f] = m;
+    fc[f] = c * m;
+    fa[f] = (i == i0) ? 0.0 : a;
+    fc_prev = c * m;
+  }
+  // spikes: v = T^{-1}(a_first e_first) (p >= 1), w = T^{-1}(c_last e_last) (p <= P-2)
+  double a0, b0, c0, aL, bL, cL;
+  M.row(p * L + i0, dj, a0, b0, c0);
+  M.row(p * L + L - 1, dj, aL, bL, cL);
+  const bool has_v = p >= 1, has_w = p <= P - 2;
+  double vp = 0.0, wp = 0.0;
+  for (int i = i0; i < L; ++i) {  // forward elimination of the two unit right-hand sides
+    const size_t f = base + (size_t)i * nx;
+    const double rv = (i == i0 && has_v) ? a0 : 0.0;
+    const double rw = (i == L - 1 && has_w) ? cL : 0.0;
+    vp = (i == i0) ? rv * fm[f] : (rv - fa[f] * vp) * fm[f];
+    wp = (i == i0) ? rw * fm[f] : (rw - fa[f] * wp) * fm[f];
+    sv[f] = vp;
+    sw[f] = wp;
+  }
+  double vn = 0.0, wn = 0.0;
+  for (int i = L - 1; i >= i0; --i) {  // back substitution
+    const size_t f = base + (size_t)i * nx;
+    const double v = (i == L - 1) ? sv[f] : sv[f] - fc[f] * vn;
+    const double w = (i == L - 1) ? sw[f] : sw[f] - fc[f] * wn;
+    sv[f] = v;
+    sw[f] = w;
+    vn = v;
+    wn = w;
+  }
+}
+
+__device__ __forceinline__ int cls_of(int p, int P) { return p == 0 ? 0 : (p == P - 1 ? 2 : 1); }
+
+// one thread per mode: reduced (separator) system and its PCR multipliers
+__global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels, int nf,
+                                   const double *sv, const double *sw, double *red) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nx) return;
+  const int n = P - 1;
+  double A[32], B[32], C[32];
+  double *R = red + (size_t)j * nf * 32;
+  for (int f = 0; f < nf * 32; ++f) R[f] = 0.0;
+  if (n <= 0) return;
+  const double dj = M.diag(j);
+  for (int q = 0; q < n; ++q) {
+    const int p = q + 1;  // separator of partition p at row p L
+    double a, b, c;
+    M.row(p * L, dj, a, b, c);
+    const size_t prevL = (size_t)cls_of(p - 1, P) * L * nx + (size_t)(L - 1) * nx + j;
+    const size_t curF = (size_t)cls_of(p, P) * L * nx + (size_t)1 * nx + j;
+    A[q] = -a * sv[prevL];
+    B[q] = b - a * sw[prevL] - c * sv[curF];
+    C[q] = -c * sw[curF];
+    R[0 * 32 + q] = a;
+    R[1 * 32 + q] = c;
+  }
+  // level-0 normalisation
+  double ka[32], kc[32];
+  for (int q = 0; q < n; ++q) {
+    const double inv = 1.0 / B[q];
+    R[2 * 32 + q] = inv;
+    ka[q] = A[q] * inv;
+    kc[q] = C[q] * inv;
+  }
+  for (int l = 0; l < levels; ++l) {
+    const int s = 1 << l;
+    double na[32], nc[32];
+    for (int q = 0; q < n; ++q) {
+      const double am = (q - s >= 0) ? ka[q - s] : 0.0, cm = (q - s >= 0) ? kc[q - s] : 0.0;
+      const double ap = (q + s < n) ? ka[q + s] : 0.0, cp = (q + s < n) ? kc[q + s] : 0.0;
+      const double den = 1.0 - ka[q] * cm - kc[q] * ap;
+      const double inv = 1.0 / den;
+      R[(3 + 3 * l) * 32 + q] = ka[q];
+      R[(4 + 3 * l) * 32 + q] = kc[q];
+      R[(5 + 3 * l) * 32 + q] = inv;
+      na[q] = -ka[q] * am * inv;
+      nc[q] = -kc[q] * cp * inv;
+    }
+    for (int q = 0; q < n; ++q) { ka[q] = na[q]; kc[q] = nc[q]; }
+  }
+}
+
+void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
+                       double dz, cudaStream_t s) {
+  const size_t per = (size_t)tf.ncls * tf.L * tf.nx;
+  const size_t nred = (size_t)tf.nx * tf.nf * 32;
+  store.alloc(store.ctx, (5 * per + nred) * sizeof(double));
+  double *base = store.as<double>();
+  tf.fm = base;
+  tf.fc = base + per;
+  tf.fa = base + 2 * per;
+  tf.sv = base + 3 * per;
+  tf.sw = base + 4 * per;
+  tf.red = base + 5 * per;
+  TriMatrix M;
+  M.off = -az / (dz * dz);
+  M.diag0 = 2.0 * az / (dz * dz) + d;
+  M.ax = ax;
+  M.dx2inv = 1.0 / (dx * dx);
+  M.nxp1 = (double)(tf.nx + 1);
+  M.nz = tf.nz;
+  dim3 g1((tf.nx + 127) / 128, 3);
+  tri_factor_kernel<<<g1, 128, 0, s>>>(M, tf.nx, tf.P, tf.L, (double *)tf.fm, (double *)tf.fc,
+                                       (double *)tf.fa, (double *)tf.sv, (double *)tf.sw);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  tri_reduced_kernel<<<(tf.nx + 63) / 64, 64, 0, s>>>(M, tf.nx, tf.P, tf.L, tf.levels, tf.nf,
+                                                      (const double *)tf.sv, (const double *)tf.sw,
+                                                      (double *)tf.red);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+__global__ void d2f_kernel(const double *a, float *b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+void tri_make_f32(const TriFactors &t64, TriFactors &t32, DevBuf &store32, cudaStream_t s) {
+  const size_t per = (size_t)t32.ncls * t32.L * t32.nx;
+  const size_t nred = (size_t)t32.nx * t32.nf * 32;
+  store32.alloc(store32.ctx, (5 * per + nred) * sizeof(float));
+  float *base = store32.as<float>();
+  t32.fm = base;
+  t32.fc = base + per;
+  t32.fa = base + 2 * per;
+  t32.sv = base + 3 * per;
+  t32.sw = base + 4 * per;
+  t32.red = base + 5 * per;
+  // the float64 set is contiguous in the same order
+  d2f_kernel<<<1024, 256, 0, s>>>((const double *)t64.fm, base, 5 * per + nred);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------------------ solve
+template <typename T>
+__global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ din, T *__restrict__ yout,
+                                                         int nz, int nx, int P, int L, int levels, int nf,
+                                                         const T *__restrict__ fm, const T *__restrict__ fc,
+                                                         const T *__restrict__ fa, const T *__restrict__ sv,
+                                                         const T *__restrict__ sw, const T *__restrict__ red,
+                                                         const KrylovScalars *__restrict__ sc, int pstride, int poff,
+                                                         int ncomp, int mt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int nzp = P * L;
+  T *gF = tile + (size_t)nzp * mt;  // [mt][32]
+  T *gL = gF + mt * 32;
+  T *ds = gL + mt * 32;
+  T *xi = ds + mt * 32;             // [mt][33]
+  const int b = blockIdx.y * pstride + poff;  // plane index; right-hand side b / ncomp
+  if (sc != nullptr && sc[b / ncomp].state != ST_RUN) return;
+  const int j0 = blockIdx.x * mt;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const T *src = din + (size_t)b * nz * nx;
+  T *dst = yout + (size_t)b * nz * nx;
+
+  // 1. coalesced load of the [nz][mt] tile; identity rows beyond nz hold zero data
+  for (int idx = tid; idx < nzp * mt; idx += nth) {
+    const int r = idx / mt, c = idx - r * mt, j = j0 + c;
+    tile[idx] = (r < nz && j < nx) ? src[(size_t)r * nx + j] : T(0);
+  }
+  __syncthreads();
+
+  // 2. block-local sweeps: thread (c, p); threads beyond mt * P (warp padding) only synchronise
+  const int c = tid % mt, p = tid / mt, j = j0 + c;
+  const bool live = j < nx && p < P;
+  const int cls = (p == 0) ? 0 : (p == P - 1 ? 2 : 1);
+  const int i0 = (p == 0) ? 0 : 1;
+  const size_t fb = (size_t)cls * L * nx + j;
+  T *col = tile + (size_t)p * L * mt + c;  // row i of this partition at col[i * mt]
+  if (live) {
+    T prev = T(0);
+    for (int i = i0; i < L; ++i) {
+      const size_t f = fb + (size_t)i * nx;
+      T dv = col[i * mt];
+      dv = (i == i0) ? dv * fm[f] : (dv - fa[f] * prev) * fm[f];
+      col[i * mt] = dv;
+      prev = dv;
+    }
+    T nxt = T(0);
+    for (int i = L - 1; i >= i0; --i) {
+      const size_t f = fb + (size_t)i * nx;
+      const T g = (i == L - 1) ? col[i * mt] : col[i * mt] - fc[f] * nxt;
+      col[i * mt] = g;
+      nxt = g;
+    }
+    gF[c * 32 + p] = col[i0 * mt];
+    gL[c * 32 + p] = col[(L - 1) * mt];
+    ds[c * 32 + p] = (p >= 1) ? col[0] : T(0);
+  }
+  __syncthreads();
+
+  // 3. separators: one warp per mode, lane q = separator of partition q + 1
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;  // nth is a multiple of 32
+  const int n = P - 1;
+  for (int cc = warp; n > 0 && cc < mt; cc += nwarp) {
+    const int jj = j0 + cc;
+    if (jj >= nx) continue;  // warp-uniform
+    const T *R = red + (size_t)jj * nf * 32;
+    const bool act = lane < n;
+    T rq = T(0);
+    if (act) {
+      const int pp = lane + 1;
+      rq = (ds[cc * 32 + pp] - R[lane] * gL[cc * 32 + pp - 1] - R[32 + lane] * gF[cc * 32 + pp]) * R[64 + lane];
+    }
+    for (int l = 0; l < levels; ++l) {
+      const int s = 1 << l;
+      T rm = __shfl_up_sync(0xffffffffu, rq, s);
+      T rp = __shfl_down_sync(0xffffffffu, rq, s);
+      if (lane < s) rm = T(0);
+      if (lane + s >= n) rp = T(0);
+      if (act) rq = (rq - R[(3 + 3 * l) * 32 + lane] * rm - R[(4 + 3 * l) * 32 + lane] * rp) * R[(5 + 3 * l) * 32 + lane];
+    }
+    xi[cc * 33 + lane + 1] = act ? rq : T(0);
+    if (lane == 0) xi[cc * 33] = T(0);
+  }
+  __syncthreads();
+
+  // 4. correction with the spike vectors
+  if (n == 0 && tid < mt) xi[tid * 33] = T(0);
+  __syncthreads();
+  if (live) {
+    const T xa = xi[c * 33 + p];
+    const T xb = (p + 1 <= P - 1) ? xi[c * 33 + p + 1] : T(0);
+    if (p >= 1) col[0] = xa;
+    for (int i = i0; i < L; ++i) {
+      const size_t f = fb + (size_t)i * nx;
+      col[i * mt] = col[i * mt] - xa * sv[f] - xb * sw[f];
+    }
+  }
+  __syncthreads();
+
+  // 5. coalesced store
+  for (int idx = tid; idx < nz * mt; idx += nth) {
+    const int r = idx / mt, cc = idx - r * mt, jj = j0 + cc;
+    if (jj < nx) dst[(size_t)r * nx + jj] = tile[idx];
+  }
+}
+
+template <typename T>
+static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
+                       cudaStream_t s, int pstride, int poff, int ncomp) {
+  if (nrhs <= 0) return;
+  static bool attr_done = false;
+  if (!attr_done) {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_done = true;
+  }
+  dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
+  ProfScope prof(sizeof(T) == 8 ? KC_TRI64 : KC_TRI32, s);
+  tri_solve_kernel<T><<<grid, tf.threads, tf.smem, s>>>(
+      d, y, tf.nz, tf.nx, tf.P, tf.L, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc,
+      (const T *)tf.fa, (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, tf.mt);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+void tri_solve_f64(const TriFactors &tf, const double *d, double *y, int nrhs, const KrylovScalars *sc,
+                   cudaStream_t s, int pstride, int poff, int ncomp) {
+  tri_launch<double>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+}
+void tri_solve_f32(const TriFactors &tf, const float *d, float *y, int nrhs, const KrylovScalars *sc,
+                   cudaStream_t s, int pstride, int poff, int ncomp) {
+  tri_launch<float>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+}
+
+}  // namespace lag

@@ -1,0 +1,132 @@
+"""Parity of the preconditioner kernels (DST-I GEMM, partitioned tridiagonal solve, whole apply)
+with the oracle, through the C ABI."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import dst as odst
+from oracle import precond as opre
+from oracle.tridiag import thomas
+from paper_1005_0542_gb300 import inputs
+from paper_1005_0542_gb300 import lagwave as L
+
+from gpu_util import make_ctx, dev, empty, host, plan, plan_info, ptr, rel, torch
+
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(77)
+TOL64 = 1e-12          # float64 kernels vs float64 oracle (rounding order only)
+TOL_MIXED = 2e-4       # float32 preconditioner vs float64 oracle
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    L.lag_destroy(c)
+
+
+@pytest.mark.parametrize("nx", [1, 2, 3, 5, 31, 64, 127, 200, 1024])
+def test_dst_f64(ctx, nx):
+    nz, nrhs = 7, 3
+    x = RNG.standard_normal((nrhs, nz, nx))
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    xd, yd = dev(x), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(yd), nrhs), ctx)
+    assert rel(host(yd), odst.dst_x(x)) < 1e-13
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("P", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("nz,nx", [(4, 3), (33, 17), (100, 64), (129, 130), (1024, 40)])
+def test_tridiag_f64_every_partition_count(ctx, P, nz, nx):
+    dx, dz, ax, az, d = 5.0, 3.0, 2.0e9, 1.5e9, 4.0e7
+    p = plan(ctx, nx, nz, dx, dz, ax, az, d, partitions=P)
+    Pgot, Lp, _ = plan_info(p)
+    assert Pgot <= P and Pgot * Lp >= nz
+    nrhs = 2
+    rhs = RNG.standard_normal((nrhs, nz, nx))
+    diag = opre.mode_diagonals(nx, dx, dz, ax, az, d)
+    off = -az / dz ** 2
+    ref = np.moveaxis(thomas(off, diag, off, np.moveaxis(rhs, 1, 0)), 0, 1)
+    dd, yd = dev(rhs), empty(rhs.shape)
+    L.check(L.lag_precond_tridiag(p, ptr(dd), ptr(yd), nrhs), ctx)
+    assert rel(host(yd), ref) < 1e-13
+    # in place gives the same bits
+    L.check(L.lag_precond_tridiag(p, ptr(dd), ptr(dd), nrhs), ctx)
+    assert np.array_equal(host(dd), host(yd))
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nz,nx", [(16, 16), (33, 20), (128, 128), (257, 96)])
+def test_precond_apply_f64(ctx, nz, nx):
+    dx, dz, ax, az, d = 10.0, 7.0, 3.0e9, 3.0e9, 1.0e7
+    p = plan(ctx, nx, nz, dx, dz, ax, az, d)
+    r = RNG.standard_normal((3, nz, nx))
+    rd, zd = dev(r), empty(r.shape)
+    L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 3), ctx)
+    assert rel(host(zd), opre.apply_inverse(r, dx, dz, ax, az, d)) < TOL64
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nz,nx", [(33, 20), (128, 128), (64, 1024)])
+def test_tridiag_f32(ctx, nz, nx):
+    dx, dz, ax, az, d = 5.0, 5.0, 2.0e10, 2.0e10, 1.0e7
+    p = plan(ctx, nx, nz, dx, dz, ax, az, d, prec=L.LAG_MIXED)
+    t = torch()
+    rhs = RNG.standard_normal((2, nz, nx)).astype(np.float32)
+    diag = opre.mode_diagonals(nx, dx, dz, ax, az, d)
+    off = -az / dz ** 2
+    ref = np.moveaxis(thomas(off, diag, off, np.moveaxis(rhs.astype(np.float64), 1, 0)), 0, 1)
+    dd = dev(rhs)
+    yd = t.empty(rhs.shape, dtype=t.float32, device="cuda")
+    L.check(L.lag_precond_tridiag_f32(p, ptr(dd), ptr(yd), 2), ctx)
+    assert rel(host(yd), ref) < 2e-5
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nz,nx", [(33, 20), (128, 128), (64, 1024), (32, 2048)])
+def test_precond_apply_mixed(ctx, nz, nx):
+    dx, dz, ax, az, d = 5.0, 5.0, 2.0e10, 2.0e10, 1.0e7
+    p = plan(ctx, nx, nz, dx, dz, ax, az, d, prec=L.LAG_MIXED)
+    r = RNG.standard_normal((2, nz, nx))
+    rd, zd = dev(r), empty(r.shape)
+    L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
+    assert rel(host(zd), opre.apply_inverse(r, dx, dz, ax, az, d)) < TOL_MIXED
+    L.lag_precond_destroy(p)
+
+
+def test_precond_edge_cases(ctx):
+    p = plan(ctx, 8, 8, 1.0, 1.0, 1.0, 1.0, 0.5)
+    assert L.lag_precond_apply(p, None, None, 0) == L.LAG_OK          # empty batch
+    assert L.lag_precond_apply(p, None, None, -1) == L.LAG_EINVAL
+    assert L.lag_precond_apply(None, None, None, 1) == L.LAG_EINVAL
+    q = C.c_void_p()
+    g = L.grid(8, 8, 1.0, 1.0)
+    assert L.lag_precond_create_sep(ctx, C.byref(g), -1.0, 1.0, 0.0, 0, 0, C.byref(q)) == L.LAG_EINVAL
+    assert L.lag_precond_create_sep(ctx, C.byref(g), 1.0, 1.0, 0.0, 7, 0, C.byref(q)) == L.LAG_EINVAL
+    assert L.lag_precond_tridiag_f32(p, None, None, 1) == L.LAG_EINVAL  # float32 solve needs a mixed plan
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("prec,tol", [(L.LAG_FP64, TOL64), (L.LAG_MIXED, TOL_MIXED)])
+def test_precond_full_size_bench_config(ctx, prec, tol):
+    # the standalone preconditioner workload: 1024 modes x nz = 1024 x 512 right-hand sides,
+    # midrange coefficients of the 2048 x 1024 random layered model at 5 m; two sampled
+    # right-hand sides are checked against the oracle one by one
+    shot = inputs.random_layered(nx=2048, nz=1024, hx=5.0, n_harm=1)
+    kap = shot.rho * shot.c ** 2
+    ax, az, d = opre.acoustic_params(kap, shot.rho, shot.h)
+    nx, nz, nrhs = 1024, 1024, 512
+    p = plan(ctx, nx, nz, 5.0, 5.0, ax, az, d, prec=prec)
+    t = torch()
+    gen = t.Generator(device="cuda").manual_seed(5)
+    rd = t.randn((nrhs, nz, nx), dtype=t.float64, device="cuda", generator=gen)
+    zd = t.empty_like(rd)
+    L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), nrhs), ctx)
+    for b in (0, 311):
+        r = host(rd[b])
+        assert rel(host(zd[b]), opre.apply_inverse(r, 5.0, 5.0, ax, az, d)) < tol
+    L.lag_precond_destroy(p)
+    del rd, zd
+    t.cuda.empty_cache()

@@ -1,0 +1,199 @@
+"""Parity of the Krylov solves, the Laguerre pieces and whole shots with the oracle."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fd, krylov, laguerre, precond, solve
+from paper_1005_0542_gb300 import inputs
+from paper_1005_0542_gb300 import lagwave as L
+
+from gpu_util import make_ctx, dev, empty, host, medium, plan, ptr, rel, rel_l2
+
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(123)
+# Parity runs solve to a tighter tolerance than the workload (1e-10): two solutions that each meet
+# ||r|| <= tol ||b|| differ by up to cond(A) tol; cond(A) ~ 1e2-1e3 here.
+TOL64, GATE64 = 1e-13, 1e-10
+TOLMX, GATEMX = 1e-11, 1e-8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    L.lag_destroy(c)
+
+
+def _oracle_pcg(c, rho, h, dx, dz, b, tol):
+    nz, nx = c.shape
+    kap = fd.kappa_from_velocity(c, rho)
+    pr = precond.acoustic_params(kap, rho, h)
+    out = []
+    for bb in b:
+        x, it, _ = krylov.pcg(lambda v: fd.apply_A(v.reshape(nz, nx), kap, rho, h, dx, dz).ravel(),
+                              lambda v: precond.apply_inverse(v.reshape(nz, nx), dx, dz, *pr).ravel(), bb.ravel(), tol)
+        out.append(x.reshape(nz, nx))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, TOL64, GATE64), (L.LAG_MIXED, TOLMX, GATEMX)])
+@pytest.mark.parametrize("nz,nx", [(24, 40), (65, 33)])
+def test_pcg_system(ctx, prec, tol, gate, nz, nx):
+    c = RNG.uniform(1500, 4500, (nz, nx))
+    rho = 310 * c ** 0.25
+    h, dx, dz = 200.0, 5.0, 5.0
+    m = medium(ctx, nx, nz, dx, dz, c, rho, h)
+    mid = (C.c_double * 3)()
+    L.check(L.lag_medium_midranges(m, mid))
+    p = plan(ctx, nx, nz, dx, dz, mid[0], mid[0], mid[1] * h * h / 4, prec=prec)
+    b = RNG.standard_normal((3, nz, nx))
+    b[1] = 0.0                                          # a zero right-hand side converges at once
+    bd, xd = dev(b), empty(b.shape)
+    its = (C.c_int * 3)()
+    res = (C.c_double * 3)()
+    s = L.solver(tol=tol, prec=prec)
+    L.check(L.lag_solve_system(m, p, None, ptr(bd), ptr(xd), 3, C.byref(s), its, res), ctx)
+    ref = _oracle_pcg(c, rho, h, dx, dz, b, tol)
+    x = host(xd)
+    assert np.all(x[1] == 0.0) and its[1] == 0
+    for i in (0, 2):
+        assert rel_l2(x[i], ref[i]) < gate
+        assert res[i] <= tol and its[i] > 1
+    L.lag_precond_destroy(p)
+    L.lag_medium_destroy(m)
+
+
+def test_source_coeffs_and_table(ctx):
+    lag = L.laguerre(200.0, 9, 256)
+    w = L.wavelet(25.0, 2.5 / 25.0)
+    fm = np.zeros(256)
+    L.check(L.lag_source_coeffs(ctx, C.byref(lag), C.byref(w), fm.ctypes.data_as(L.PD)), ctx)
+    ref = laguerre.forward_coeffs(laguerre.ricker(25.0, 0.1), 256, 200.0, 9, 0.1 + 4.0 / 25.0)
+    assert rel(fm, ref) < 1e-12
+    t = np.concatenate([[0.0], np.linspace(0.001, 12.0, 77)])   # includes h t > 1400 (scaled recurrence)
+    tab = np.zeros((256, t.size))
+    L.check(L.lag_laguerre_table(ctx, C.byref(lag), t.size, t.ctypes.data_as(L.PD), tab.ctypes.data_as(L.PD)), ctx)
+    x = 200.0 * t
+    ext = np.where(x > 0, 4.5 * np.log(np.where(x > 0, x, 1.0)), 0.0)
+    reft = math.sqrt(200.0) * laguerre.ell_table(256, x, 9, extra_log=ext)
+    assert np.all(tab[:, 0] == 0.0)
+    assert rel(tab, reft) < 1e-12
+    # the paper's own wavelet (Eq. 23)
+    w2 = L.wavelet(30.0, 0.2, 4.0, L.LAG_WAVELET_PAPER)
+    L.check(L.lag_source_coeffs(ctx, C.byref(lag), C.byref(w2), fm.ctypes.data_as(L.PD)), ctx)
+    ref2 = laguerre.forward_coeffs(laguerre.paper_wavelet(30.0, 0.2, 4.0), 256, 200.0, 9, 0.2 + 8.0 / 30.0)
+    assert rel(fm, ref2) < 1e-12
+
+
+def _run_shot(ctx, s, prec, tol, nharm=None, nsrc=None, elastic=False):
+    n = nharm or s.n_harm
+    srcs = s.sources[:nsrc] if nsrc else s.sources
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, n)
+    sv = L.solver(tol=tol, prec=prec, restart_k=s.restart)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    ncomp = 2 if elastic else 1
+    traces = np.zeros((len(srcs), ncomp, len(s.receivers), s.t_out.size))
+    its = np.zeros((len(srcs), n), dtype=np.int32)
+    st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+    if elastic:
+        v_, pv = L.f64(s.vs)
+        rc = L.lag_solve_elastic(ctx, C.byref(g), pc, pv, pr, C.byref(lag), C.byref(sv), C.byref(w), len(srcs),
+                                 L.points(srcs), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                                 traces.ctypes.data_as(L.PD), C.byref(st))
+    else:
+        rc = L.lag_solve_acoustic(ctx, C.byref(g), pc, pr, C.byref(lag), C.byref(sv), C.byref(w), len(srcs),
+                                  L.points(srcs), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                                  traces.ctypes.data_as(L.PD), C.byref(st))
+    L.check(rc, ctx)
+    return traces, its
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, TOL64, GATE64), (L.LAG_MIXED, TOLMX, GATEMX)])
+def test_acoustic_shot_two_layer_full(ctx, prec, tol, gate):
+    # the 128 x 128 two-layer workload, all 64 harmonics, every receiver trace
+    s = inputs.two_layer()
+    traces, its = _run_shot(ctx, s, prec, tol)
+    ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, s.sources[0], s.receivers,
+                              s.t_out, s.f0, s.t0, tol=tol)
+    assert rel_l2(traces[0, 0], ref["traces"]) < gate
+    if prec == L.LAG_FP64:
+        assert np.abs(its[0] - ref["iters"]).max() <= 1
+
+
+def test_acoustic_shot_multi_source_ragged(ctx):
+    # several sources batched in one shot on a ragged grid: each equals its own oracle shot
+    s = inputs.random_layered(nx=45, nz=37, hx=20.0, n_harm=12, sources=[(3, 2), (22, 10), (44, 36)], f0=10.0)
+    s.receivers = [(0, 0), (10, 5), (44, 36), (22, 18)]
+    traces, _ = _run_shot(ctx, s, L.LAG_FP64, TOL64)
+    for i, src in enumerate(s.sources):
+        ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, src, s.receivers, s.t_out,
+                                  s.f0, s.t0, tol=TOL64)
+        assert rel_l2(traces[i, 0], ref["traces"]) < GATE64
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, TOL64, GATE64), (L.LAG_MIXED, TOLMX, GATEMX)])
+def test_elastic_shot_small(ctx, prec, tol, gate):
+    s = inputs.elastic_layered(nx=40, nz=24, hx=2.5, n_harm=6, nsrc=2)
+    s.receivers = s.receivers[:6]
+    traces, its = _run_shot(ctx, s, prec, tol, elastic=True)
+    for i, src in enumerate(s.sources):
+        ref = solve.elastic_shot(s.c, s.vs, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, src, s.receivers, s.t_out,
+                                 s.f0, s.t0, tol=tol, restart=s.restart)
+        assert rel_l2(traces[i], ref["traces"]) < gate
+
+
+def test_shot_full_size_first_harmonics(ctx):
+    # the 2048 x 1024 random layered workload in its launch configuration (FP64 path): the first
+    # two harmonics' fields against the oracle, every value
+    s = inputs.random_layered()
+    n = 2
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=TOL64, prec=L.LAG_FP64)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    sh = C.c_void_p()
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                              C.byref(sh)), ctx)
+    ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, n, s.sources[0], s.receivers, s.t_out, s.f0,
+                              s.t0, tol=TOL64, keep_fields=True,
+                              fm=laguerre.forward_coeffs(laguerre.ricker(s.f0, s.t0), s.n_harm, s.h, s.alpha,
+                                                         s.t0 + 4 / s.f0)[:n])
+    field = empty((s.nz, s.nx))
+    for m in range(n):
+        L.check(L.lag_shot_step(sh, 1), ctx)
+        assert L.lag_shot_harmonic(sh) == m + 1
+        L.check(L.lag_shot_copy_field(sh, ptr(field)), ctx)
+        assert rel_l2(host(field), ref["fields"][m]) < GATE64
+    L.lag_shot_destroy(sh)
+
+
+def test_solver_argument_errors(ctx):
+    s = inputs.two_layer(n_harm=2, nx=16, nz=16)
+    g = L.grid(16, 16, 10.0, 10.0)
+    lag = L.laguerre(200.0, 9, 2)
+    w = L.wavelet(30.0, 0.08)
+    c_, pc = L.f64(s.c)
+    r_, pr = L.f64(s.rho)
+    bad = L.solver(tol=0.0)
+    out = np.zeros(1)
+    assert L.lag_solve_acoustic(ctx, C.byref(g), pc, pr, C.byref(lag), C.byref(bad), C.byref(w), 1,
+                                L.points([(1, 1)]), 0, None, 0, None, None, None) == L.LAG_EINVAL
+    ok = L.solver()
+    assert L.lag_solve_acoustic(ctx, C.byref(g), pc, pr, C.byref(lag), C.byref(ok), C.byref(w), 1,
+                                L.points([(16, 1)]), 0, None, 0, None, None, None) == L.LAG_EINVAL
+    # max_iter too small: not converged, but results and status still come back
+    few = L.solver(max_iter=1)
+    rc = L.lag_solve_acoustic(ctx, C.byref(g), pc, pr, C.byref(lag), C.byref(few), C.byref(w), 1,
+                              L.points([(8, 8)]), 1, L.points([(3, 3)]), 1, out.ctypes.data_as(L.PD),
+                              out.ctypes.data_as(L.PD), None)
+    assert rc == L.LAG_ENOTCONV
