@@ -127,6 +127,7 @@ def gpu_arm(args, rank, world, local_rank):
     import torch
     from paper_1005_0542_gb300 import inputs
     from paper_1005_0542_gb300 import lagwave as L
+    from paper_1005_0542_gb300.replicas import replica_source, whole_job_rate
 
     torch.cuda.set_device(local_rank)
     dist = None
@@ -136,8 +137,8 @@ def gpu_arm(args, rank, world, local_rank):
 
     ctx = L.create(local_rank, stream=torch.cuda.current_stream().cuda_stream)
     s = inputs.random_layered()
-    if world > 1:  # replica r: its own source on the line iz = 16
-        s.sources = [((s.nx // 2 + 64 * rank) % s.nx, 16)]
+    if world > 1:  # replica r: its own source on the same row
+        s.sources = [replica_source(s.sources[0], rank, s.nx)]
     peaks, peak_src = load_peaks()
 
     def make_shot(prec, n_harm=None):
@@ -200,12 +201,7 @@ def gpu_arm(args, rank, world, local_rank):
     its = iters_of(sh, W, W + K)
     tr64 = traces_of(sh)
     L.lag_shot_destroy(sh)
-    t_sec = ms / 1e3
-    if dist is not None:
-        t = torch.tensor([t_sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_sec = float(t.item())
-    value = world * K / t_sec
+    value, t_sec = whole_job_rate(ms / 1e3, K, world, dist=dist, device="cuda")
 
     # roofline of the dominant kernel (FP64 DST GEMM): algorithmic flops of the real launches
     # (2 per preconditioner apply, one apply per PCG iteration) over the measured DST time

@@ -63,6 +63,10 @@ void lag_precond::ensure_scratch(int nrhs) {
   if (nrhs <= scratch_rhs) return;
   const size_t per = (size_t)grid.nx * grid.nz;
   scratch.alloc(ctx, per * nrhs * (prec == LAG_FP64 ? sizeof(double) : sizeof(float)));
+  if (use_tc) {
+    tc_scratch.alloc(ctx, dst_tc_scratch_bytes(dst, nrhs * grid.nz));
+    dst.tc_scratch = tc_scratch.as<uint8_t>();
+  }
   scratch_rhs = nrhs;
 }
 
@@ -96,9 +100,10 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   p->ax = ax;
   p->az = az;
   p->d = d;
-  p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = ctx;
+  p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = p->tc_scratch.ctx = ctx;
   p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
   dst_build(p->dst, p->dst_store, g.nx, p->use_tc, s);
+  if (p->use_tc) p->dst.tc_err = reinterpret_cast<int *>(p->dst_store.as<uint8_t>() + p->dst_store.bytes - 256);
   p->tri64.nx = g.nx;
   p->tri64.nz = g.nz;
   tri_choose_layout(p->tri64, 8, partitions);
@@ -107,7 +112,16 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
     p->tri32.nx = g.nx;
     p->tri32.nz = g.nz;
     tri_choose_layout(p->tri32, 4, partitions);
-    tri_make_f32(p->tri64, p->tri32, p->tri32_store, s);
+    if (p->use_tc) {  // the tensor-core DST leaves the spectrum parity-permuted: permuted factors
+      TriFactors tp = p->tri64;
+      DevBuf tmp;
+      tmp.ctx = ctx;
+      tri_build_factors(tp, tmp, ax, az, d, g.dx, g.dz, s, p->dst.ku);
+      tri_make_f32(tp, p->tri32, p->tri32_store, s);
+      LAG_CUDA_CHECK(cudaStreamSynchronize(s));
+    } else {
+      tri_make_f32(p->tri64, p->tri32, p->tri32_store, s);
+    }
   }
   LAG_CUDA_CHECK(cudaStreamSynchronize(s));
   return p.release();
@@ -274,9 +288,13 @@ int lag_precond_dst(lag_precond *p, const double *x, double *y, int nrhs) {
     } else {  // float64 -> float32 spectrum -> float64 (both mixed-path kernels, back to back)
       p->ensure_scratch(nrhs);
       float *w = p->scratch.as<float>();
-      if (p->use_tc) dst_apply_tc_d2f(p->dst, x, w, rows, p->grid.nz, nullptr, p->ctx->stream);
-      else dst_apply_f32_d2f(p->dst, x, w, rows, p->grid.nz, nullptr, p->ctx->stream);
-      widen_f32(w, y, (size_t)rows * p->grid.nx, p->ctx->stream);
+      if (p->use_tc) {
+        dst_apply_tc_d2f(p->dst, x, w, rows, p->grid.nz, nullptr, p->ctx->stream);
+        spectrum_unpermute_widen(w, y, rows, p->grid.nx, p->dst.ku, p->ctx->stream);
+      } else {
+        dst_apply_f32_d2f(p->dst, x, w, rows, p->grid.nz, nullptr, p->ctx->stream);
+        widen_f32(w, y, (size_t)rows * p->grid.nx, p->ctx->stream);
+      }
     }
   });
 }
@@ -287,8 +305,14 @@ int lag_precond_dst_f32(lag_precond *p, const float *x, double *y, int nrhs) {
     set_device(p->ctx);
     if (nrhs == 0) return;
     const int rows = nrhs * p->grid.nz;
-    if (p->use_tc) dst_apply_tc_f2d(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
-    else dst_apply_f32_f2d(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
+    if (p->use_tc) {  // the tensor-core inverse reads a parity-permuted spectrum
+      p->ensure_scratch(nrhs);
+      float *w = p->scratch.as<float>();
+      spectrum_permute(x, w, rows, p->grid.nx, p->dst.ku, true, p->ctx->stream);
+      dst_apply_tc_f2d(p->dst, w, y, rows, p->grid.nz, nullptr, p->ctx->stream);
+    } else {
+      dst_apply_f32_f2d(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
+    }
   });
 }
 
@@ -304,7 +328,17 @@ int lag_precond_tridiag_f32(lag_precond *p, const float *d, float *y, int nrhs) 
   if (!p || nrhs < 0 || (nrhs > 0 && (!d || !y)) || p->prec != LAG_MIXED) return LAG_EINVAL;
   return guarded(p->ctx, [&] {
     set_device(p->ctx);
-    if (nrhs > 0) tri_solve_f32(p->tri32, d, y, nrhs, nullptr, p->ctx->stream);
+    if (nrhs == 0) return;
+    if (p->use_tc) {  // factors are stored for parity-permuted spectra
+      p->ensure_scratch(nrhs);
+      float *w = p->scratch.as<float>();
+      const int rows = nrhs * p->grid.nz;
+      spectrum_permute(d, w, rows, p->grid.nx, p->dst.ku, true, p->ctx->stream);
+      tri_solve_f32(p->tri32, w, w, nrhs, nullptr, p->ctx->stream);
+      spectrum_permute(w, y, rows, p->grid.nx, p->dst.ku, false, p->ctx->stream);
+    } else {
+      tri_solve_f32(p->tri32, d, y, nrhs, nullptr, p->ctx->stream);
+    }
   });
 }
 

@@ -78,8 +78,9 @@ struct TriFactors {
 
 void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P);
 // Build float64 factors of T_j = tridiag(off, 2 az/dz^2 + ax lambda_j + d, off) on the device.
+// perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra)
 void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
-                       double dz, cudaStream_t s);
+                       double dz, cudaStream_t s, int perm_ku = 0);
 // Round a float64 factor set to float32 into `store32` (same layout).
 void tri_make_f32(const TriFactors &t64, TriFactors &t32, DevBuf &store32, cudaStream_t s);
 // y = T^{-1} d per (plane, mode); d and y [planes][nz][nx]; in place allowed.  The launch covers
@@ -99,10 +100,14 @@ struct DstPlan {
   double *su = nullptr; // [ku][ku]  S[j][2k]    (float64)
   double *sv = nullptr; // [kv][kv]  S[j][2k+1]
   float *su_f = nullptr, *sv_f = nullptr;  // float32 copies (SIMT float32 kernel)
-  // split-bf16 copies for the tensor-core path: hi and lo parts, K-major [k][j] tiles
-  uint16_t *su_hi = nullptr, *su_lo = nullptr, *sv_hi = nullptr, *sv_lo = nullptr;
-  int kpad_u = 0, kpad_v = 0; // K padded to a multiple of 64 for the tensor-core tiles
-  int npad_u = 0, npad_v = 0; // N padded to the tensor-core N tile
+  // tensor-core path: four packed split-bf16 B operands (forward even/odd, inverse E/O), each
+  // [n tile][k stage][hi|lo][256 x 64 swizzled]; per-apply A-operand / E-O scratch; error word
+  uint8_t *tc_b = nullptr;
+  size_t tc_bmat_bytes = 0;
+  int kpad_u = 0;             // K stages (64 wide)
+  int npad_u = 0;             // N tiles (256 wide)
+  uint8_t *tc_scratch = nullptr;
+  int *tc_err = nullptr;
 };
 void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream_t s);
 // Y[row][:] = S X[row][:] for `rows` rows of length n.  Input/output types as named.
@@ -119,6 +124,10 @@ void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, in
 void dst_apply_tc_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
                       const KrylovScalars *sc, cudaStream_t s);
 bool dst_tc_supported(int n);
+size_t dst_tc_scratch_bytes(const DstPlan &dp, int rows);
+// parity permutation of a float32 spectrum: natural mode order <-> [even modes | odd modes]
+void spectrum_permute(const float *in, float *out, int rows, int n, int ku, bool to_perm, cudaStream_t s);
+void spectrum_unpermute_widen(const float *in, double *out, int rows, int n, int ku, cudaStream_t s);
 
 }  // namespace lag
 
@@ -132,6 +141,7 @@ struct lag_precond {
   lag::TriFactors tri64, tri32;
   lag::DevBuf dst_store, tri_store, tri32_store;
   lag::DevBuf scratch;      // intermediate spectra (float64 or float32), grows with nrhs
+  lag::DevBuf tc_scratch;   // tensor-core DST: packed A operands and E/O halves
   int scratch_rhs = 0;
   bool use_tc = false;      // mixed path: DST on tcgen05 tensor cores (else SIMT float32)
   void ensure_scratch(int nplanes);

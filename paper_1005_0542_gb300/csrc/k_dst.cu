@@ -43,7 +43,7 @@ void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream
   const size_t nu = (size_t)dp.ku * dp.ku, nv = (size_t)dp.kv * dp.kv;
   size_t bytes = (nu + nv) * (sizeof(double) + sizeof(float)) + 256;
   const size_t tc_off = (bytes + 1023) & ~(size_t)1023;
-  if (tensor_copies) bytes = tc_off + dst_tc_bytes(n);
+  if (tensor_copies) bytes = tc_off + dst_tc_bytes(n) + 256;  // + error word at the end
   store.alloc(store.ctx, bytes, true);
   char *base = store.as<char>();
   dp.su = reinterpret_cast<double *>(base);

@@ -1,17 +1,478 @@
-// Split-bf16 tcgen05 DST (mixed path).  Not enabled yet: dst_tc_supported() is false, so the
-// mixed path runs its DST on the float32 SIMT kernel.
+// DST-I of the mixed path on the tcgen05 tensor cores: split-bf16 folded GEMM, FP32 accumulate.
+//
+// The preconditioner's transform along x (Sec. 2.4) is y = S x per row with S^2 = I.  Folding the
+// input pairs (j, n-1-j) halves the work (see k_dst.cu).  Each operand value v is split into two
+// bf16 numbers hi = bf16(v), lo = bf16(v - hi); the product is formed from hi*hi + hi*lo + lo*hi
+// (lo*lo is below FP32 rounding of the sum), accumulated in FP32 in tensor memory.
+//
+// Forward (x float64 -> spectrum float32): fold on the input,
+//   y[2k']   = sum_j' S[j'][2k']   u[j'],  u = x[j'] + x[n-1-j'] (middle once)   -> "parity 0"
+//   y[2k'+1] = sum_j' S[j'][2k'+1] v[j'],  v = x[j'] - x[n-1-j']                 -> "parity 1"
+// and the spectrum is stored parity-permuted: columns [0, ku) hold the even modes 2k', columns
+// [ku, n) the odd modes 2k'+1 (the tridiagonal factors use the same column order).
+// Inverse (spectrum float32 -> z float64): fold on the output,
+//   E[k] = sum_j' S[2j'][k] y[2j'],  O[k] = sum_j' S[2j'+1][k] y[2j'+1],
+//   z[k] = E[k] + O[k],  z[n-1-k] = E[k] - O[k]           (k < ceil(n/2); O = 0 at the middle).
+//
+// Data movement: a pack kernel writes the A operand (folded / split rows) as 128-row x 64-column
+// bf16 tiles already in the canonical K-major 128-byte-swizzled shared-memory layout; the constant
+// B operands (rows of S) are packed the same way once per plan.  The GEMM kernel then moves every
+// stage with four cp.async.bulk copies (TMA engine) completing on an mbarrier, one thread issues
+// tcgen05.mma from shared-memory descriptors into a 128 x 256 FP32 accumulator in tensor memory,
+// tcgen05.commit releases each stage, and four warps read the accumulator with tcgen05.ld.
+// Every wait is bounded: on expiry the kernel records an error code and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
 #include "internal.h"
 
 namespace lag {
 
-bool dst_tc_supported(int) { return false; }
-size_t dst_tc_bytes(int) { return 0; }
-void dst_build_tc(DstPlan &, DevBuf &, size_t, cudaStream_t) {}
-void dst_apply_tc_d2f(const DstPlan &, const double *, float *, int, int, const KrylovScalars *, cudaStream_t) {
-  throw Error(LAG_EINVAL, "tensor-core DST not available");
+namespace {
+
+constexpr int TM = 128;          // rows per tile (MMA M)
+constexpr int TN = 256;          // output columns per tile (MMA N)
+constexpr int TK = 64;           // K per stage (one 128-byte swizzle atom of bf16)
+constexpr int A_TILE = TM * TK * 2;   // 16 KB
+constexpr int B_TILE = TN * TK * 2;   // 32 KB
+constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;  // hi/lo of A and B: 96 KB
+constexpr int NSTAGE = 2;
+constexpr int SMEM_BYTES = NSTAGE * STAGE + 1024 + 128;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr long long WAIT_LIMIT = 1LL << 26;
+
+// element (r, k) of a rows x 64 tile in the K-major SWIZZLE_128B layout (byte offset)
+__host__ __device__ __forceinline__ uint32_t swz(int r, int k) {
+  return (uint32_t)r * 128u + ((uint32_t)((k >> 3) ^ (r & 7)) << 4) + (uint32_t)(k & 7) * 2u;
 }
-void dst_apply_tc_f2d(const DstPlan &, const float *, double *, int, int, const KrylovScalars *, cudaStream_t) {
-  throw Error(LAG_EINVAL, "tensor-core DST not available");
+
+__device__ __forceinline__ uint16_t bf16_bits(float f) {
+  __nv_bfloat16 b = __float2bfloat16_rn(f);
+  return *reinterpret_cast<uint16_t *>(&b);
+}
+
+// split v into bf16 hi + bf16 lo
+__device__ __forceinline__ void split2(double v, uint16_t &hi, uint16_t &lo) {
+  const float f = (float)v;
+  __nv_bfloat16 h = __float2bfloat16_rn(f);
+  const float r = (float)(v - (double)__bfloat162float(h));
+  hi = *reinterpret_cast<uint16_t *>(&h);
+  lo = bf16_bits(r);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false when the limit expired
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 32) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, M = 128, N = 256
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ packing
+// B operands, once per plan.  which: 0 fwd even (B[n][k] = S[k][2n]), 1 fwd odd (S[k][2n+1]),
+// 2 inv E (S[n][2k]), 3 inv O (S[n][2k+1], zero row at n = kv for odd n).  Layout per matrix:
+// [n tile][k stage][hi | lo][TN x TK swizzled].
+__global__ void pack_b_kernel(const double *su, const double *sv, int ku, int kv, int nks, int nnt, uint8_t *out,
+                              size_t mat_bytes) {
+  const int which = blockIdx.z;
+  const int n = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nnt * TN || k >= nks * TK) return;
+  double v = 0.0;
+  switch (which) {
+    case 0: if (n < ku && k < ku) v = su[(size_t)k * ku + n]; break;
+    case 1: if (n < kv && k < kv) v = sv[(size_t)k * kv + n]; break;
+    case 2: if (n < ku && k < ku) v = su[(size_t)n * ku + k]; break;
+    default: if (n < kv && k < kv) v = sv[(size_t)n * kv + k]; break;
+  }
+  uint16_t hi, lo;
+  split2(v, hi, lo);
+  const size_t tile = (size_t)(n / TN) * nks + (k / TK);
+  uint8_t *base = out + (size_t)which * mat_bytes + tile * 2 * B_TILE;
+  const uint32_t off = swz(n % TN, k % TK);
+  *reinterpret_cast<uint16_t *>(base + off) = hi;
+  *reinterpret_cast<uint16_t *>(base + B_TILE + off) = lo;
+}
+
+// A operand of the forward transform: one thread per (row, 8 consecutive fold indices), both
+// parities; layout [parity][m tile][k stage][hi | lo][TM x TK swizzled]
+template <typename TI>
+__global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ x, int rows, int n, int ku, int kv,
+                                                         int nks, int nmt, uint8_t *__restrict__ out,
+                                                         const KrylovScalars *__restrict__ sc, int rpr) {
+  const int chunks = nks * (TK / 8);
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nmt * TM * chunks) return;
+  const int row = (int)(t / chunks), ch = (int)(t % chunks);
+  const int k0 = ch * 8;
+  const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
+  alignas(16) uint16_t uh[8], ul[8], vh[8], vl[8];
+  const TI *xr = x + (size_t)(live ? row : 0) * n;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int j = k0 + e;
+    double u = 0.0, w = 0.0;
+    if (live) {
+      if (j < kv) {
+        const double a = (double)xr[j], b = (double)xr[n - 1 - j];
+        u = a + b;
+        w = a - b;
+      } else if (j < ku) {
+        u = (double)xr[j];  // middle element of an odd-length row
+      }
+    }
+    split2(u, uh[e], ul[e]);
+    split2(w, vh[e], vl[e]);
+  }
+  const int mt = row / TM, r = row % TM, ks = k0 / TK, kk = k0 % TK;
+  const uint32_t off = swz(r, kk);
+  for (int par = 0; par < 2; ++par) {
+    uint8_t *tile = out + (((size_t)par * nmt + mt) * nks + ks) * 2 * A_TILE;
+    *reinterpret_cast<uint4 *>(tile + off) = *reinterpret_cast<const uint4 *>(par ? vh : uh);
+    *reinterpret_cast<uint4 *>(tile + A_TILE + off) = *reinterpret_cast<const uint4 *>(par ? vl : ul);
+  }
+}
+
+// A operand of the inverse transform from the parity-permuted spectrum (no fold)
+__global__ void __launch_bounds__(256) pack_a_inv_kernel(const float *__restrict__ y, int rows, int n, int ku, int kv,
+                                                         int nks, int nmt, uint8_t *__restrict__ out,
+                                                         const KrylovScalars *__restrict__ sc, int rpr) {
+  const int chunks = nks * (TK / 8);
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nmt * TM * chunks) return;
+  const int row = (int)(t / chunks), ch = (int)(t % chunks);
+  const int k0 = ch * 8;
+  const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
+  const float *yr = y + (size_t)(live ? row : 0) * n;
+  alignas(16) uint16_t eh[8], el[8], oh[8], ol[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int j = k0 + e;
+    const double ev = (live && j < ku) ? (double)yr[j] : 0.0;
+    const double ov = (live && j < kv) ? (double)yr[ku + j] : 0.0;
+    split2(ev, eh[e], el[e]);
+    split2(ov, oh[e], ol[e]);
+  }
+  const int mt = row / TM, r = row % TM, ks = k0 / TK, kk = k0 % TK;
+  const uint32_t off = swz(r, kk);
+  for (int par = 0; par < 2; ++par) {
+    uint8_t *tile = out + (((size_t)par * nmt + mt) * nks + ks) * 2 * A_TILE;
+    *reinterpret_cast<uint4 *>(tile + off) = *reinterpret_cast<const uint4 *>(par ? oh : eh);
+    *reinterpret_cast<uint4 *>(tile + A_TILE + off) = *reinterpret_cast<const uint4 *>(par ? ol : el);
+  }
+}
+
+// ------------------------------------------------------------------------------ GEMM
+// grid (n tiles, m tiles, 2 parities); 128 threads.  out[row * ld + par * ku + col] (float32),
+// col < nvalid[par].
+__global__ void __launch_bounds__(128, 1) dst_tc_gemm_kernel(const uint8_t *__restrict__ apack,
+                                                             const uint8_t *__restrict__ bpack, size_t b_mat_bytes,
+                                                             int nks, int nmt, int nnt, int rows, float *__restrict__ out,
+                                                             int ld, int ku, int nvalid0, int nvalid1,
+                                                             const KrylovScalars *__restrict__ sc, int rpr,
+                                                             int *__restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  const int par = blockIdx.z, mt = blockIdx.y, nt = blockIdx.x;
+  const int nvalid = par ? nvalid1 : nvalid0;
+  const int n0 = nt * TN, m0 = mt * TM;
+  if (n0 >= nvalid) return;
+  if (sc != nullptr) {  // skip tiles whose right-hand sides have all finished
+    const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
+    bool any = false;
+    for (int r = r0; r <= r1; ++r) any |= (sc[r].state == ST_RUN);
+    if (!any) return;
+  }
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + NSTAGE * STAGE;  // full[2], empty[2], done
+  const uint32_t full0 = bars, empty0 = bars + 16, done = bars + 32;
+  volatile uint32_t *holder = reinterpret_cast<volatile uint32_t *>(gbase + NSTAGE * STAGE + 64);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + NSTAGE * STAGE + 72);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)holder)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *holder;
+
+  const uint8_t *atiles = apack + ((size_t)par * nmt + mt) * nks * 2 * A_TILE;
+  const uint8_t *btiles = bpack + (size_t)par * b_mat_bytes + (size_t)nt * nks * 2 * B_TILE;
+
+  if (tid == 0) {  // producer: bulk copies of the pre-packed tiles
+    for (int kk = 0; kk < nks; ++kk) {
+      const int s = kk & 1;
+      if (kk >= 2 && !mbar_wait(empty0 + 8 * s, ((kk >> 1) - 1) & 1)) {
+        atomicExch(err, 1);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const uint32_t st = base + s * STAGE;
+      const uint32_t fb = full0 + 8 * s;
+      mbar_expect_tx(fb, STAGE);
+      const uint8_t *a = atiles + (size_t)kk * 2 * A_TILE;
+      const uint8_t *b = btiles + (size_t)kk * 2 * B_TILE;
+      bulk_g2s(st, a, 2 * A_TILE, fb);                    // A hi | lo
+      bulk_g2s(st + 2 * A_TILE, b, 2 * B_TILE, fb);       // B hi | lo
+    }
+  } else if (tid == 32) {  // MMA issuer
+    bool ok = true;
+    for (int kk = 0; kk < nks; ++kk) {
+      const int s = kk & 1;
+      if (!mbar_wait(full0 + 8 * s, (kk >> 1) & 1)) {
+        atomicExch(err, 2);
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = base + s * STAGE;
+      const uint32_t ahi = st, alo = st + A_TILE, bhi = st + 2 * A_TILE, blo = bhi + B_TILE;
+#pragma unroll
+      for (int sub = 0; sub < TK / 16; ++sub) {
+        const uint32_t o = sub * 32;  // 16 bf16 along K
+        const uint32_t first = (kk == 0 && sub == 0) ? 0u : 1u;
+        mma_bf16(tmem, sdesc(ahi + o), sdesc(bhi + o), first);
+        mma_bf16(tmem, sdesc(ahi + o), sdesc(blo + o), 1u);
+        mma_bf16(tmem, sdesc(alo + o), sdesc(bhi + o), 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                   : "memory");
+    }
+    (void)ok;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done) : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w owns accumulator rows 32 w .. 32 w + 31 (tensor-memory lanes)
+  const bool fin = mbar_wait(done, 0);
+  if (!fin && (tid & 31) == 0) atomicExch(err, 3);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + (tid & 31);
+  const bool vec = ((ld & 3) == 0) && ((ku & 3) == 0);
+  float *orow = out + (size_t)row * ld + (size_t)par * ku + n0;
+  const int ncols = min(TN, nvalid - n0);
+  for (int c0 = 0; c0 < TN; c0 += 32) {
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (!fin || *abort_flag || row >= rows || c0 >= ncols) continue;
+    if (vec && c0 + 32 <= ncols) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4 *>(orow + c0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+      for (int q = 0; q < 32 && c0 + q < ncols; ++q) orow[c0 + q] = v[q];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// z[k] = E[k] + O[k], z[n-1-k] = E[k] - O[k]   (eo rows: [E (ku) | O (ku)])
+__global__ void __launch_bounds__(256) butterfly_kernel(const float *__restrict__ eo, double *__restrict__ z, int rows,
+                                                        int n, int ku, int kv, const KrylovScalars *__restrict__ sc,
+                                                        int rpr) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * ku) return;
+  const int row = (int)(t / ku), k = (int)(t % ku);
+  if (sc != nullptr && sc[row / rpr].state != ST_RUN) return;
+  const float *er = eo + (size_t)row * 2 * ku;
+  const double e = (double)er[k], o = (double)er[ku + k];
+  double *zr = z + (size_t)row * n;
+  zr[k] = e + o;
+  if (k < kv) zr[n - 1 - k] = e - o;
+}
+
+// parity permutation of spectra (natural mode order <-> [even modes | odd modes])
+__global__ void permute_kernel(const float *in, float *out, int rows, int n, int ku, int to_perm) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * n) return;
+  const int row = (int)(t / n), c = (int)(t % n);
+  const int j = (c < ku) ? 2 * c : 2 * (c - ku) + 1;  // mode stored at permuted column c
+  if (to_perm) out[(size_t)row * n + c] = in[(size_t)row * n + j];
+  else out[(size_t)row * n + j] = in[(size_t)row * n + c];
+}
+
+__global__ void unpermute_widen_kernel(const float *in, double *out, int rows, int n, int ku) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * n) return;
+  const int row = (int)(t / n), c = (int)(t % n);
+  const int j = (c < ku) ? 2 * c : 2 * (c - ku) + 1;
+  out[(size_t)row * n + j] = (double)in[(size_t)row * n + c];
+}
+
+// ------------------------------------------------------------------------------ host side
+static int div_up(int a, int b) { return (a + b - 1) / b; }
+
+bool dst_tc_supported(int n) { return n >= 16; }
+
+size_t dst_tc_bytes(int n) {
+  const int ku = (n + 1) / 2;
+  const int nks = div_up(ku, TK), nnt = div_up(ku, TN);
+  return 4 * (size_t)nnt * nks * 2 * B_TILE;
+}
+
+void dst_build_tc(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
+  const int nks = div_up(dp.ku, TK), nnt = div_up(dp.ku, TN);
+  dp.kpad_u = nks;  // stages along K
+  dp.npad_u = nnt;  // tiles along N
+  dp.tc_bmat_bytes = (size_t)nnt * nks * 2 * B_TILE;
+  dp.tc_b = store.as<uint8_t>() + off;
+  dim3 g(div_up(nks * TK, 128), nnt * TN, 4);
+  pack_b_kernel<<<g, 128, 0, s>>>(dp.su, dp.sv, dp.ku, dp.kv, nks, nnt, dp.tc_b, dp.tc_bmat_bytes);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+static void gemm_launch(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
+                        int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(dst_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
+  dim3 g(nnt, nmt, 2);
+  dst_tc_gemm_kernel<<<g, 128, SMEM_BYTES, s>>>(apack, bpack, dp.tc_bmat_bytes, nks, nmt, nnt, rows, out, ld, dp.ku,
+                                                 nvalid0, nvalid1, sc, rpr, err);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+size_t dst_tc_scratch_bytes(const DstPlan &dp, int rows) {
+  const size_t nmt = div_up(rows, TM);
+  return 2 * nmt * dp.kpad_u * 2 * A_TILE + (size_t)rows * 2 * dp.ku * sizeof(float) + 256;
+}
+
+void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rpr, const KrylovScalars *sc,
+                      cudaStream_t s) {
+  if (rows <= 0) return;
+  uint8_t *apack = dp.tc_scratch;
+  const int nks = dp.kpad_u, nmt = div_up(rows, TM);
+  {
+    ProfScope prof(KC_DSTTC_FWD, s);
+    const long long threads = (long long)nmt * TM * nks * (TK / 8);
+    pack_a_fwd_kernel<double><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt,
+                                                                                apack, sc, rpr);
+    count_launch();
+    LAG_LAUNCH_CHECK();
+    gemm_launch(dp, apack, dp.tc_b, rows, y, dp.n, dp.ku, dp.kv, sc, rpr, dp.tc_err, s);
+  }
+}
+
+void dst_apply_tc_f2d(const DstPlan &dp, const float *y, double *z, int rows, int rpr, const KrylovScalars *sc,
+                      cudaStream_t s) {
+  if (rows <= 0) return;
+  uint8_t *apack = dp.tc_scratch;
+  float *eo = reinterpret_cast<float *>(apack + 2 * (size_t)div_up(rows, TM) * dp.kpad_u * 2 * A_TILE);
+  const int nks = dp.kpad_u, nmt = div_up(rows, TM);
+  {
+    ProfScope prof(KC_DSTTC_INV, s);
+    const long long threads = (long long)nmt * TM * nks * (TK / 8);
+    pack_a_inv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(y, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack,
+                                                                         sc, rpr);
+    count_launch();
+    LAG_LAUNCH_CHECK();
+    gemm_launch(dp, apack, dp.tc_b + 2 * dp.tc_bmat_bytes, rows, eo, 2 * dp.ku, dp.ku, dp.ku, sc, rpr, dp.tc_err, s);
+    const long long t = (long long)rows * dp.ku;
+    butterfly_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(eo, z, rows, dp.n, dp.ku, dp.kv, sc, rpr);
+    count_launch();
+    LAG_LAUNCH_CHECK();
+  }
+}
+
+void spectrum_permute(const float *in, float *out, int rows, int n, int ku, bool to_perm, cudaStream_t s) {
+  const long long t = (long long)rows * n;
+  permute_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(in, out, rows, n, ku, to_perm ? 1 : 0);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+void spectrum_unpermute_widen(const float *in, double *out, int rows, int n, int ku, cudaStream_t s) {
+  const long long t = (long long)rows * n;
+  unpermute_widen_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(in, out, rows, n, ku);
+  count_launch();
+  LAG_LAUNCH_CHECK();
 }
 
 }  // namespace lag

@@ -66,8 +66,9 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
 // Matrix of mode j: sub a_k, diag b_k, super c_k (rows >= nz: identity).
 struct TriMatrix {
   double off, diag0, ax, dx2inv, nxp1;
-  int nz;
-  __device__ double diag(int j) const {
+  int nz, perm_ku;
+  __device__ double diag(int c) const {
+    const int j = (perm_ku > 0) ? (c < perm_ku ? 2 * c : 2 * (c - perm_ku) + 1) : c;  // mode at column c
     const double s = sinpi((double)(j + 1) / (2.0 * nxp1));
     return diag0 + ax * 4.0 * dx2inv * s * s;
   }
@@ -195,7 +196,7 @@ __global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels
 }
 
 void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
-                       double dz, cudaStream_t s) {
+                       double dz, cudaStream_t s, int perm_ku) {
   const size_t per = (size_t)tf.ncls * tf.L * tf.nx;
   const size_t nred = (size_t)tf.nx * tf.nf * 32;
   store.alloc(store.ctx, (5 * per + nred) * sizeof(double));
@@ -213,6 +214,7 @@ void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, doub
   M.dx2inv = 1.0 / (dx * dx);
   M.nxp1 = (double)(tf.nx + 1);
   M.nz = tf.nz;
+  M.perm_ku = perm_ku;
   dim3 g1((tf.nx + 127) / 128, 3);
   tri_factor_kernel<<<g1, 128, 0, s>>>(M, tf.nx, tf.P, tf.L, (double *)tf.fm, (double *)tf.fc,
                                        (double *)tf.fa, (double *)tf.sv, (double *)tf.sw);

@@ -185,7 +185,14 @@ def wavelet(f0, t0, gamma=4.0, kind=LAG_WAVELET_RICKER):
     return lag_wavelet(float(f0), float(t0), float(gamma), int(kind))
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream (torch's default stream, handle 0)
+
+
 def create(device=0, budget=0, stream=None):
+    """lag_create; ``stream`` is a cudaStream_t as an int (0 = the legacy default stream),
+    or None for a stream of the library's own."""
     ctx = VP()
-    check(lib.lag_create(C.byref(ctx), int(device), int(budget), VP(stream) if stream else None))
+    if stream is not None and int(stream) == 0:
+        stream = CUDA_STREAM_LEGACY
+    check(lib.lag_create(C.byref(ctx), int(device), int(budget), VP(stream) if stream is not None else None))
     return ctx

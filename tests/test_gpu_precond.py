@@ -130,3 +130,41 @@ def test_precond_full_size_bench_config(ctx, prec, tol):
     L.lag_precond_destroy(p)
     del rd, zd
     t.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("nx", [16, 17, 64, 300, 1024, 2048])
+def test_dst_tensor_cores_forward_and_inverse(ctx, nx):
+    # mixed plans run the DST on tcgen05 (split bf16, FP32 accumulate): forward (float64 in,
+    # float32 spectrum) and inverse (float32 spectrum in, float64 out) against the oracle
+    nz, nrhs = 9, 3
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1, prec=L.LAG_MIXED)
+    assert L.lag_precond_uses_tensor_cores(p) == 1
+    x = RNG.standard_normal((nrhs, nz, nx))
+    xd, yd = dev(x), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(yd), nrhs), ctx)
+    ref = odst.dst_x(x)
+    assert rel(host(yd), ref) < 5e-5
+    t = torch()
+    sf = dev(ref.astype(np.float32))
+    zd = empty(x.shape)
+    L.check(L.lag_precond_dst_f32(p, ptr(sf), ptr(zd), nrhs), ctx)
+    assert rel(host(zd), odst.dst_x(ref.astype(np.float32).astype(np.float64))) < 5e-5
+    L.lag_precond_destroy(p)
+
+
+def test_mixed_apply_simt_and_tensor_cores_agree(ctx, monkeypatch):
+    nx, nz = 256, 64
+    args = (nx, nz, 5.0, 5.0, 2.0e10, 2.0e10, 1.0e7)
+    r = RNG.standard_normal((2, nz, nx))
+    rd = dev(r)
+    p_tc = plan(ctx, *args, prec=L.LAG_MIXED)
+    monkeypatch.setenv("LAGWAVE_DST_KERNEL", "simt")
+    p_simt = plan(ctx, *args, prec=L.LAG_MIXED)
+    assert L.lag_precond_uses_tensor_cores(p_tc) == 1 and L.lag_precond_uses_tensor_cores(p_simt) == 0
+    z1, z2 = empty(r.shape), empty(r.shape)
+    L.check(L.lag_precond_apply(p_tc, ptr(rd), ptr(z1), 2), ctx)
+    L.check(L.lag_precond_apply(p_simt, ptr(rd), ptr(z2), 2), ctx)
+    ref = opre.apply_inverse(r, 5.0, 5.0, 2.0e10, 2.0e10, 1.0e7)
+    assert rel(host(z1), ref) < TOL_MIXED and rel(host(z2), ref) < TOL_MIXED
+    L.lag_precond_destroy(p_tc)
+    L.lag_precond_destroy(p_simt)
