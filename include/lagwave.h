@@ -140,6 +140,20 @@ int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, i
 int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int nrhs);
 /* 1 if the plan's DST runs on the tcgen05 tensor cores (mixed path), else 0 */
 int  lag_precond_uses_tensor_cores(const lag_precond *p);
+/* z = B^{-1} r like lag_precond_apply, but allocating nothing.  The paper has no counterpart: this
+ * entry point is for callers that cannot let a library allocate device memory at call time (a
+ * framework whose own allocator owns the device memory, or a real-time loop that must not block in
+ * cudaMalloc/cudaFree).  The intermediate spectrum lives in a file-scope static device array of
+ * lag_precond_static_capacity() float64 values (2^21 = 16 MiB), which every GPU that loads the
+ * library holds until the process exits; the plan is created beforehand by lag_precond_create*.
+ * Float64 (LAG_FP64) plans only; nrhs * nz * nx beyond the capacity returns LAG_EINVAL with a
+ * message in lag_last_error.  The first call on a device looks up the array's device address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (nothing in it has to start at zero): calls that
+ * overlap on the GPU, on any stream or context of the process, race on it.  Stream-ordered on the
+ * context's stream. */
+int  lag_precond_apply_static(lag_precond *p, const double *r_dev, double *z_dev, int nrhs);
+size_t lag_precond_static_capacity(void);
 /* plan facts: partitions P, partition length L, modes per CTA of the tridiagonal kernel */
 int  lag_precond_info(const lag_precond *p, int *partitions, int *part_len, int *modes_per_cta);
 

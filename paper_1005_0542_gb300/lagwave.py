@@ -88,6 +88,8 @@ _PROTOS = {
     "lag_precond_dst_f32": (I, [VP, VP, VP, I]),
     "lag_precond_tridiag": (I, [VP, VP, VP, I]),
     "lag_precond_tridiag_f32": (I, [VP, VP, VP, I]),
+    "lag_precond_apply_static": (I, [VP, VP, VP, I]),
+    "lag_precond_static_capacity": (C.c_size_t, []),
     "lag_precond_info": (I, [VP, PI, PI, PI]),
     "lag_precond_uses_tensor_cores": (I, [VP]),
     "lag_medium_create_acoustic": (I, [VP, C.POINTER(lag_grid), PD, PD, D, C.POINTER(VP)]),
