@@ -138,7 +138,7 @@ def test_poisoned_request_fails_alone_others_finish():
 
 def test_budget_admission_and_cancel():
     small = inputs.two_layer(n_harm=4, nx=32, nz=32)
-    big = inputs.random_layered(nx=1024, nz=512, hx=5.0, n_harm=4)
+    big = inputs.random_layered(nx=2048, nz=1024, hx=5.0, n_harm=4)   # ~8 float64 fields of 16.8 MB alone
     ctx = L.create(0, budget=96 << 20)
     try:
         keep = []
