@@ -364,6 +364,45 @@ def cpu_baseline(s, budget):
                       f"{sum(times):.1f} s, {np.mean(iters):.0f} PCG iterations/harmonic)"}
 
 
+# ---------------------------------------------------------------------------------- ncu capture
+def capture_kernels(args):
+    """One launch of each hot kernel through the C ABI on inputs larger than L2 (1024 modes x
+    nz 1024 x 16 RHS, float64 arrays of 134 MB), for `ncu -k ... -c N` captures."""
+    import torch
+    from paper_1005_0542_gb300 import lagwave as L
+    ctx = L.create(0, stream=torch.cuda.current_stream().cuda_stream)
+    nx = nz = 1024
+    nrhs = 16
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    r = torch.randn((nrhs, nz, nx), dtype=torch.float64, device="cuda", generator=gen)
+    z = torch.empty_like(r)
+    rf = torch.randn((2 * nrhs, nz, nx), dtype=torch.float32, device="cuda", generator=gen)
+    zf = torch.empty_like(rf)
+    P = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+
+    def plan(prec):
+        p = C.c_void_p()
+        L.check(L.lag_precond_create_sep(ctx, C.byref(L.grid(nx, nz, 5.0, 5.0)), 3e10, 3e10, 2.2e7, prec, 0,
+                                         C.byref(p)), ctx)
+        return p
+    p64, pmx = plan(L.LAG_FP64), plan(L.LAG_MIXED)
+    c = np.full((nz, nx), 3000.0)
+    rho = np.full((nz, nx), 2000.0)
+    m = C.c_void_p()
+    c_, pc = L.f64(c)
+    r_, pr = L.f64(rho)
+    L.check(L.lag_medium_create_acoustic(ctx, C.byref(L.grid(nx, nz, 5.0, 5.0)), pc, pr, 200.0, C.byref(m)), ctx)
+    torch.cuda.synchronize()
+    L.check(L.lag_precond_dst(p64, P(r), P(z), nrhs), ctx)             # folded FP64 DST GEMM
+    L.check(L.lag_precond_tridiag(p64, P(r), P(z), nrhs), ctx)         # FP64 tridiagonal solve
+    L.check(L.lag_precond_dst(pmx, P(r), P(z), nrhs), ctx)             # pack + tcgen05 DST GEMM
+    L.check(L.lag_precond_tridiag_f32(pmx, P(rf), P(zf), 2 * nrhs), ctx)  # FP32 tridiagonal solve
+    L.check(L.lag_apply_operator(m, P(r), P(z), nrhs), ctx)            # acoustic stencil
+    torch.cuda.synchronize()
+    L.lag_destroy(ctx)
+    print(json.dumps({"capture": "ok"}))
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def reference_arm(args):
     from paper_1005_0542_gb300 import inputs
@@ -392,12 +431,17 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="headline only (for launch-list captures)")
     ap.add_argument("--e2e-harmonics", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--capture-kernels", action="store_true",
+                    help="launch each hot kernel once (1024 x 1024 x 16 RHS) for ncu captures, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.capture_kernels:
+        capture_kernels(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

@@ -58,9 +58,12 @@ void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream
 }
 
 // ------------------------------------------------------------------------------ SIMT GEMM
-// One launch covers both parities (blockIdx.z).  Tile 64 x 64 x 16, 256 threads, 4 x 4 per thread.
-constexpr int BM = 64, BN = 64, BK = 16;
+// One launch covers both parities (blockIdx.z).  Tile BM x BN x 16, 256 threads, each thread a
+// (BM/16) x (BN/16) block of outputs.  The tile is picked per launch so that the number of tiles
+// spreads evenly over the 152 SMs (float64 is ALU-bound: the tail wave is what costs).
+constexpr int BK = 16;
 
+template <int BM>
 __device__ __forceinline__ bool tile_all_done(const KrylovScalars *sc, int m0, int rows, int rpr) {
   if (sc == nullptr) return false;
   const int r0 = m0 / rpr, r1 = (min(m0 + BM, rows) - 1) / rpr;
@@ -69,27 +72,29 @@ __device__ __forceinline__ bool tile_all_done(const KrylovScalars *sc, int m0, i
   return true;
 }
 
-template <typename TI, typename TO, typename TA>
+template <typename TI, typename TO, typename TA, int BM, int BN>
 __global__ void __launch_bounds__(256) dst_simt_kernel(const TI *__restrict__ X, TO *__restrict__ Y, int rows, int n,
                                                        const TA *__restrict__ Su, const TA *__restrict__ Sv,
                                                        int ku, int kv, const KrylovScalars *__restrict__ sc, int rpr) {
+  constexpr int UM = BM / 16, UN = BN / 16;       // outputs per thread
+  constexpr int LA = BM * BK / 256, LB = BK * BN / 256;  // tile elements per thread
   const int parity = blockIdx.z;
   const int K = parity ? kv : ku;
   const TA *B = parity ? Sv : Su;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  if (n0 >= K || tile_all_done(sc, m0, rows, rpr)) return;
+  if (n0 >= K || tile_all_done<BM>(sc, m0, rows, rpr)) return;
   __shared__ __align__(16) TA As[BK][BM + 4];
   __shared__ __align__(16) TA Bs[BK][BN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  TA acc[4][4];
+  TA acc[UM][UN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < UM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = TA(0);
+    for (int j = 0; j < UN; ++j) acc[i][j] = TA(0);
   const bool odd_n = (n & 1) != 0;
   for (int k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int e = 0; e < LA; ++e) {
       const int idx = tid + e * 256;
       const int r = idx / BK, kk = idx % BK;
       const int row = m0 + r, j = k0 + kk;
@@ -101,34 +106,45 @@ __global__ void __launch_bounds__(256) dst_simt_kernel(const TI *__restrict__ X,
         else v = x1 - (TA)xr[n - 1 - j];
       }
       As[kk][r] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < LB; ++e) {
+      const int idx = tid + e * 256;
       const int kb = idx / BN, c = idx % BN;
       Bs[kb][c] = (k0 + kb < K && n0 + c < K) ? B[(size_t)(k0 + kb) * K + n0 + c] : TA(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      TA a[4], b[4];
+      TA a[UM], b[UN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < UM; ++i) a[i] = As[kk][ty * UM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < UN; ++j) b[j] = Bs[kk][tx * UN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < UM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < UN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = m0 + ty * 4 + i;
+  for (int i = 0; i < UM; ++i) {
+    const int row = m0 + ty * UM + i;
     if (row >= rows) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int col = n0 + tx * 4 + j;
+    for (int j = 0; j < UN; ++j) {
+      const int col = n0 + tx * UN + j;
       if (col < K) Y[(size_t)row * n + 2 * col + parity] = (TO)acc[i][j];
     }
   }
+}
+
+// fraction of the last wave that is busy when `tiles` equal tiles run over the SMs
+static double wave_efficiency(long long tiles) {
+  const long long sms = 152;
+  const long long waves = (tiles + sms - 1) / sms;
+  return waves ? (double)tiles / (double)(waves * sms) : 1.0;
 }
 
 template <typename TI, typename TO, typename TA>
@@ -136,8 +152,23 @@ static void dst_simt_launch(const DstPlan &dp, const TI *x, TO *y, int rows, int
                             const KrylovScalars *sc, cudaStream_t s, int cls) {
   if (rows <= 0 || dp.n <= 0) return;
   ProfScope prof(cls, s);
-  dim3 grid((dp.ku + BN - 1) / BN, (rows + BM - 1) / BM, dp.kv > 0 ? 2 : 1);
-  dst_simt_kernel<TI, TO, TA><<<grid, 256, 0, s>>>(x, y, rows, dp.n, su, sv, dp.ku, dp.kv, sc, rpr);
+  const int nz = dp.kv > 0 ? 2 : 1;
+  auto tiles = [&](int bm, int bn) {
+    return (long long)((dp.ku + bn - 1) / bn) * ((rows + bm - 1) / bm) * nz;
+  };
+  // largest tile whose tail wave keeps >= 90 % of the SMs busy (smaller tiles cost reuse)
+  int choice = 0;
+  if (wave_efficiency(tiles(64, 64)) < 0.9) choice = (wave_efficiency(tiles(64, 32)) >= 0.9) ? 1 : 2;
+  if (choice == 0) {
+    dim3 grid((dp.ku + 63) / 64, (rows + 63) / 64, nz);
+    dst_simt_kernel<TI, TO, TA, 64, 64><<<grid, 256, 0, s>>>(x, y, rows, dp.n, su, sv, dp.ku, dp.kv, sc, rpr);
+  } else if (choice == 1) {
+    dim3 grid((dp.ku + 31) / 32, (rows + 63) / 64, nz);
+    dst_simt_kernel<TI, TO, TA, 64, 32><<<grid, 256, 0, s>>>(x, y, rows, dp.n, su, sv, dp.ku, dp.kv, sc, rpr);
+  } else {
+    dim3 grid((dp.ku + 31) / 32, (rows + 31) / 32, nz);
+    dst_simt_kernel<TI, TO, TA, 32, 32><<<grid, 256, 0, s>>>(x, y, rows, dp.n, su, sv, dp.ku, dp.kv, sc, rpr);
+  }
   count_launch();
   LAG_LAUNCH_CHECK();
 }

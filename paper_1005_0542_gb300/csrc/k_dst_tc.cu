@@ -53,13 +53,21 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return *reinterpret_cast<uint16_t *>(&b);
 }
 
-// split v into bf16 hi + bf16 lo
+// split v into bf16 hi + bf16 lo (float64 arithmetic: used once per plan for S)
 __device__ __forceinline__ void split2(double v, uint16_t &hi, uint16_t &lo) {
   const float f = (float)v;
   __nv_bfloat16 h = __float2bfloat16_rn(f);
   const float r = (float)(v - (double)__bfloat162float(h));
   hi = *reinterpret_cast<uint16_t *>(&h);
   lo = bf16_bits(r);
+}
+
+// the same split in float32 arithmetic (per apply: FP64 throughput is 1/61 of FP32 on this part;
+// hi + lo keeps 16 significant bits, far inside float32 rounding)
+__device__ __forceinline__ void split2f(float f, uint16_t &hi, uint16_t &lo) {
+  __nv_bfloat16 h = __float2bfloat16_rn(f);
+  hi = *reinterpret_cast<uint16_t *>(&h);
+  lo = bf16_bits(f - __bfloat162float(h));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -175,18 +183,18 @@ __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ 
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int j = k0 + e;
-    double u = 0.0, w = 0.0;
+    float u = 0.f, w = 0.f;
     if (live) {
       if (j < kv) {
-        const double a = (double)xr[j], b = (double)xr[n - 1 - j];
+        const float a = (float)xr[j], b = (float)xr[n - 1 - j];
         u = a + b;
         w = a - b;
       } else if (j < ku) {
-        u = (double)xr[j];  // middle element of an odd-length row
+        u = (float)xr[j];  // middle element of an odd-length row
       }
     }
-    split2(u, uh[e], ul[e]);
-    split2(w, vh[e], vl[e]);
+    split2f(u, uh[e], ul[e]);
+    split2f(w, vh[e], vl[e]);
   }
   const int mt = row / TM, r = row % TM, ks = k0 / TK, kk = k0 % TK;
   const uint32_t off = swz(r, kk);
@@ -212,10 +220,10 @@ __global__ void __launch_bounds__(256) pack_a_inv_kernel(const float *__restrict
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int j = k0 + e;
-    const double ev = (live && j < ku) ? (double)yr[j] : 0.0;
-    const double ov = (live && j < kv) ? (double)yr[ku + j] : 0.0;
-    split2(ev, eh[e], el[e]);
-    split2(ov, oh[e], ol[e]);
+    const float ev = (live && j < ku) ? yr[j] : 0.f;
+    const float ov = (live && j < kv) ? yr[ku + j] : 0.f;
+    split2f(ev, eh[e], el[e]);
+    split2f(ov, oh[e], ol[e]);
   }
   const int mt = row / TM, r = row % TM, ks = k0 / TK, kk = k0 % TK;
   const uint32_t off = swz(r, kk);

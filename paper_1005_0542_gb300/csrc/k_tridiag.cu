@@ -29,15 +29,18 @@ namespace lag {
 void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
   const int nz = tf.nz;
   int Pt = (want_P > 0) ? std::min(want_P, 32) : 32;
-  while (Pt > 1 && nz / Pt < 4) Pt /= 2;  // at least 4 rows per partition
-  int L = (nz + Pt - 1) / Pt;
+  while (Pt > 1 && nz / Pt < 2) Pt /= 2;  // at least 2 rows per partition
+  // partition length: a power of two (the register kernel unrolls its sweeps over it)
+  int L = 1;
+  while (L * Pt < nz) L *= 2;
   if (Pt > 1 && L < 2) L = 2;
   // P = ceil(nz / L): only the last partition holds identity rows beyond nz, so every other
   // partition of a Toeplitz-in-z system shares the "first" or "middle" factor class
   int P = (nz + L - 1) / L;
   if (P <= 1) {
     P = 1;
-    L = nz;
+    L = 1;
+    while (L < nz) L *= 2;
   }
   tf.P = P;
   tf.L = L;
@@ -48,10 +51,21 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
   tf.levels = lev;
   tf.nf = 3 + 3 * lev;
   const int nzp = P * L;
-  // modes per CTA: power of two <= 32, threads (rounded up to whole warps) <= 1024,
+  auto threads = [&](int m) { return ((m * P + 31) / 32) * 32; };
+  tf.reg = (L >= 2 && L <= 64 && (elem_bytes == 4 || L <= 32));
+  if (tf.reg) {
+    // register kernel: a row segment of mt modes is 32 bytes (one sector)
+    int mt = 32 / elem_bytes;
+    while (mt > 1 && threads(mt) > 1024) mt /= 2;
+    while (mt > 1 && mt / 2 >= tf.nx) mt /= 2;
+    tf.mt = mt;
+    tf.threads = threads(mt);
+    tf.smem = (size_t)(5 * 3 * L * mt + (3 * 32 + 33) * mt) * elem_bytes;
+    return;
+  }
+  // shared-memory tile kernel: modes per CTA power of two <= 32, threads <= 1024,
   // tile <= ~104 KB (two CTAs per SM)
   const size_t budget = 104 * 1024;
-  auto threads = [&](int m) { return ((m * P + 31) / 32) * 32; };
   int mt = 32;
   while (mt > 1 && ((size_t)mt * nzp * elem_bytes > budget || threads(mt) > 1024)) mt /= 2;
   while (mt > 1 && mt / 2 >= tf.nx) mt /= 2;  // tiny grids: no idle half tiles
@@ -355,6 +369,131 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
   }
 }
 
+
+// Register-resident variant (partition length L a compile-time power of two): thread (c, p) keeps
+// the L values of its partition in registers, loaded straight from global memory (a warp reads
+// rows of mt consecutive modes: whole 32-byte sectors) and stored back the same way; the factors
+// of the CTA's modes (3 classes x L rows) are staged once in shared memory; only the separator
+// ends and the separator solution pass through shared memory.
+template <typename T, int L>
+__global__ void __launch_bounds__(256) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
+                                                             int nx, int P, int levels, int nf,
+                                                             const T *__restrict__ fm, const T *__restrict__ fc,
+                                                             const T *__restrict__ fa, const T *__restrict__ sv,
+                                                             const T *__restrict__ sw, const T *__restrict__ red,
+                                                             const KrylovScalars *__restrict__ sc, int pstride,
+                                                             int poff, int ncomp, int mt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *F = reinterpret_cast<T *>(smem_raw);    // [5][3][L][mt]: fm, fa, fc, sv, sw
+  T *gF = F + 5 * 3 * L * mt;                // [mt][32]
+  T *gL = gF + mt * 32;
+  T *ds = gL + mt * 32;
+  T *xi = ds + mt * 32;                      // [mt][33]
+  const int b = blockIdx.y * pstride + poff;
+  if (sc != nullptr && sc[b / ncomp].state != ST_RUN) return;
+  const int j0 = blockIdx.x * mt;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  // stage the factors of this CTA's modes
+  const int nclsrow = 3 * L;
+  for (int idx = tid; idx < 5 * nclsrow * mt; idx += nth) {
+    const int c = idx % mt, rest = idx / mt, row = rest % nclsrow, a = rest / nclsrow;
+    const int j = j0 + c;
+    const T *src = a == 0 ? fm : (a == 1 ? fa : (a == 2 ? fc : (a == 3 ? sv : sw)));
+    F[idx] = (j < nx) ? src[(size_t)row * nx + j] : T(0);
+  }
+  const int c = tid % mt, p = tid / mt, j = j0 + c;
+  const bool live = j < nx && p < P;
+  const int cls = (p == 0) ? 0 : (p == P - 1 ? 2 : 1);
+  const int i0 = (p == 0) ? 0 : 1;
+  const size_t plane = (size_t)b * nz * nx;
+  T v[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int r = p * L + i;
+    v[i] = (live && r < nz) ? din[plane + (size_t)r * nx + j] : T(0);
+  }
+  __syncthreads();
+  const T *Fm = F + (0 * nclsrow + cls * L) * mt + c;
+  const T *Fa = F + (1 * nclsrow + cls * L) * mt + c;
+  const T *Fc = F + (2 * nclsrow + cls * L) * mt + c;
+  const T *Sv = F + (3 * nclsrow + cls * L) * mt + c;
+  const T *Sw = F + (4 * nclsrow + cls * L) * mt + c;
+  const T dsep = v[0];  // separator row value (p >= 1)
+  if (live) {
+    // forward elimination over the block rows i0..L-1, then back substitution: v = T_I^{-1} d_I
+    T prev = T(0);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      if (i < i0) continue;
+      const T m = Fm[i * mt];
+      v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * mt] * prev) * m;
+      prev = v[i];
+    }
+#pragma unroll
+    for (int i = L - 2; i >= 0; --i) {
+      if (i < i0) continue;
+      v[i] = v[i] - Fc[i * mt] * v[i + 1];
+    }
+    gF[c * 32 + p] = (i0 == 0) ? v[0] : v[1];
+    gL[c * 32 + p] = v[L - 1];
+    ds[c * 32 + p] = (p >= 1) ? dsep : T(0);
+  }
+  __syncthreads();
+  // separators: one warp per mode, parallel cyclic reduction in shuffles (precomputed multipliers)
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
+  const int n = P - 1;
+  for (int cc = warp; n > 0 && cc < mt; cc += nwarp) {
+    const int jj = j0 + cc;
+    if (jj >= nx) continue;  // warp-uniform
+    const T *R = red + (size_t)jj * nf * 32;
+    const bool act = lane < n;
+    T rq = T(0);
+    if (act) {
+      const int pp = lane + 1;
+      rq = (ds[cc * 32 + pp] - R[lane] * gL[cc * 32 + pp - 1] - R[32 + lane] * gF[cc * 32 + pp]) * R[64 + lane];
+    }
+    for (int l = 0; l < levels; ++l) {
+      const int s = 1 << l;
+      T rm = __shfl_up_sync(0xffffffffu, rq, s);
+      T rp = __shfl_down_sync(0xffffffffu, rq, s);
+      if (lane < s) rm = T(0);
+      if (lane + s >= n) rp = T(0);
+      if (act) rq = (rq - R[(3 + 3 * l) * 32 + lane] * rm - R[(4 + 3 * l) * 32 + lane] * rp) * R[(5 + 3 * l) * 32 + lane];
+    }
+    xi[cc * 33 + lane + 1] = act ? rq : T(0);
+    if (lane == 0) xi[cc * 33] = T(0);
+  }
+  if (n == 0 && tid < mt) xi[tid * 33] = T(0);
+  __syncthreads();
+  if (!live) return;
+  // correction with the spike vectors, store
+  const T xa = xi[c * 33 + p];
+  const T xb = (p + 1 <= P - 1) ? xi[c * 33 + p + 1] : T(0);
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int r = p * L + i;
+    T y;
+    if (i < i0) y = xa;  // separator row
+    else y = v[i] - xa * Sv[i * mt] - xb * Sw[i * mt];
+    if (r < nz) yout[plane + (size_t)r * nx + j] = y;
+  }
+}
+
+template <typename T, int L>
+static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc, cudaStream_t s,
+                           int pstride, int poff, int ncomp) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    attr_done = true;
+  }
+  dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
+  tri_solve_reg_kernel<T, L><<<grid, tf.threads, tf.smem, s>>>(
+      d, y, tf.nz, tf.nx, tf.P, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc, (const T *)tf.fa,
+      (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, tf.mt);
+}
+
 template <typename T>
 static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
                        cudaStream_t s, int pstride, int poff, int ncomp) {
@@ -364,8 +503,21 @@ static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const K
     LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_done = true;
   }
-  dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
   ProfScope prof(sizeof(T) == 8 ? KC_TRI64 : KC_TRI32, s);
+  if (tf.reg) {
+    switch (tf.L) {
+      case 2: tri_reg_launch<T, 2>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+      case 4: tri_reg_launch<T, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+      case 8: tri_reg_launch<T, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+      case 16: tri_reg_launch<T, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+      case 32: tri_reg_launch<T, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+      default: tri_reg_launch<T, 64>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+    }
+    count_launch();
+    LAG_LAUNCH_CHECK();
+    return;
+  }
+  dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
   tri_solve_kernel<T><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.L, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc,
       (const T *)tf.fa, (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, tf.mt);
