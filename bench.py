@@ -244,6 +244,12 @@ def gpu_arm(args, rank, world, local_rank):
                     "gpu_launches": int(launches_m),
                     "kernel_ms": {k: {"launches": c, "ms": round(v, 3)} for k, (c, v) in sorted(profm.items())}}
 
+    # ---- batched mixed path: 64 sources on the surface line share one shot (one launch set per step)
+    out["batched"] = batched_leg(ctx, args)
+
+    # ---- served stream: Poisson arrivals of acoustic / elastic shots, continuous batching
+    out["serving"] = serving_leg(ctx, args)
+
     # ---- standalone preconditioner: 1024 modes x nz 1024 x 512 rhs
     out["precond_bench"] = precond_bench(ctx, s, peaks, peak_src)
 
@@ -254,6 +260,116 @@ def gpu_arm(args, rank, world, local_rank):
     out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
     L.lag_destroy(ctx)
     return out
+
+
+def batched_leg(ctx, args):
+    """64 sources at ix = round((s + 1/2) 2048 / 64), iz = 2 on the 2048 x 1024 model, mixed path."""
+    import torch
+    from paper_1005_0542_gb300 import inputs
+    from paper_1005_0542_gb300 import lagwave as L
+    nsrc = args.batch_sources
+    s = inputs.random_layered(sources=inputs.surface_line_sources(2048, nsrc, iz=2))
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=s.tol, prec=L.LAG_MIXED)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    sh = C.c_void_p()
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), nsrc,
+                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                              C.byref(sh)), ctx)
+    L.check(L.lag_shot_step(sh, 1), ctx)  # warm-up harmonic
+    stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    K = args.batch_steps
+    for _ in range(K):
+        L.check(L.lag_shot_step(sh, 1), ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = np.zeros((nsrc, s.n_harm), dtype=np.int32)
+    st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+    L.lag_shot_stats(sh, C.byref(st))
+    L.lag_shot_destroy(sh)
+    return {"config": f"2048x1024 model, {nsrc} sources on row 2, mixed path, one shot; step = one harmonic of "
+                      f"every source", "value": nsrc * K / (ms / 1e3), "unit": UNIT, "steps": K,
+            "ms_per_step": ms / K, "pcg_iters_per_solve": float(its[:, 1:1 + K].mean())}
+
+
+def serving_leg(ctx, args):
+    """A finite Poisson trace of acoustic / elastic shots (meshes drawn from the served set,
+    harmonics scaled down to bound the run) through lag_serve_submit / lag_serve_poll."""
+    from paper_1005_0542_gb300 import inputs
+    from paper_1005_0542_gb300 import lagwave as L
+    trace = inputs.request_trace(count=args.serve_requests, rate=50.0, n_lo=args.serve_nharm[0],
+                                 n_hi=args.serve_nharm[1])
+    reqs, keep = [], []
+    for q in trace:
+        if q["kind"] == "acoustic":
+            s = inputs.random_layered(nx=q["nx"], nz=q["nz"], hx=5.0, n_harm=q["n_harm"], seed=q["seed"],
+                                      sources=[(q["nx"] // 2, min(16, q["nz"] - 1))])
+        else:
+            s = inputs.elastic_layered(nx=q["nx"], nz=q["nz"], hx=2.5, n_harm=q["n_harm"], seed=q["seed"], nsrc=1)
+        s.receivers = s.receivers[:16]
+        s.t_out = s.t_out[:100]
+        c_, pc = L.f64(s.c)
+        r_, pr = L.f64(s.rho)
+        t_, pt = L.f64(s.t_out)
+        src, rcv = L.points(s.sources), L.points(s.receivers)
+        keep += [c_, r_, t_, src, rcv]
+        rq = L.lag_request()
+        rq.kind = 1 if s.vs is not None else 0
+        rq.grid = L.grid(s.nx, s.nz, s.hx, s.hz)
+        rq.c_host, rq.rho_host = pc, pr
+        if s.vs is not None:
+            v_, pv = L.f64(s.vs)
+            keep.append(v_)
+            rq.vs_host = pv
+        rq.lag = L.laguerre(s.h, s.alpha, s.n_harm)
+        rq.solver = L.solver(tol=s.tol, prec=L.LAG_MIXED, restart_k=s.restart)
+        rq.wavelet = L.wavelet(s.f0, s.t0)
+        rq.nsrc, rq.src = len(s.sources), C.cast(src, C.POINTER(L.lag_point))
+        rq.nrcv, rq.rcv = len(s.receivers), C.cast(rcv, C.POINTER(L.lag_point))
+        rq.nt, rq.t_out_host = s.t_out.size, pt
+        ncomp = 2 if s.vs is not None else 1
+        reqs.append((q, rq, np.zeros(len(s.sources) * ncomp * len(s.receivers) * s.t_out.size)))
+    L.check(L.lag_serve_start(ctx, args.serve_active), ctx)
+    t0 = time.perf_counter()
+    tickets = []
+    for q, rq, buf in reqs:  # submit on the Poisson schedule
+        while time.perf_counter() - t0 < q["arrival"] - trace[0]["arrival"]:
+            time.sleep(0.0005)
+        t = C.c_uint64()
+        L.check(L.lag_serve_submit(ctx, C.byref(rq), C.byref(t)), ctx)
+        tickets.append(t.value)
+    lat, queue, statuses, solves = [], [], [], 0
+    for (q, rq, buf), t in zip(reqs, tickets):
+        res = L.lag_result()
+        res.traces_host = buf.ctypes.data_as(L.PD)
+        while True:
+            rc = L.lag_serve_poll(ctx, t, C.byref(res))
+            if rc == L.LAG_OK:
+                break
+            time.sleep(0.001)
+        statuses.append(res.status)
+        lat.append(res.t_done - res.t_submit)
+        queue.append(res.t_admit - res.t_submit)
+        solves += q["n_harm"] * rq.nsrc
+    makespan = time.perf_counter() - t0
+    L.check(L.lag_serve_stop(ctx), ctx)
+    lat = np.array(lat)
+    return {"config": f"{len(reqs)} Poisson requests (50/s), acoustic/elastic, meshes from "
+                      "{256^2, 512x1024, 1024x2048, 2048x1024, 4096x2048}, "
+                      f"{args.serve_nharm[0]}-{args.serve_nharm[1]} harmonics each, mixed path, "
+                      f"{args.serve_active} concurrent slots",
+            "value": solves / makespan, "unit": UNIT, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s": float(np.mean(queue)),
+            "offered_rps": 50.0, "achieved_rps": len(reqs) / makespan, "makespan_s": makespan,
+            "all_ok": all(st == L.LAG_OK for st in statuses)}
 
 
 def precond_bench(ctx, s, peaks, peak_src):
@@ -431,6 +547,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="headline only (for launch-list captures)")
     ap.add_argument("--e2e-harmonics", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-sources", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-active", type=int, default=8)
+    ap.add_argument("--serve-nharm", type=int, nargs=2, default=[4, 16])
     ap.add_argument("--capture-kernels", action="store_true",
                     help="launch each hot kernel once (1024 x 1024 x 16 RHS) for ncu captures, then exit")
     args = ap.parse_args()

@@ -55,9 +55,7 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
   tf.reg = (L >= 2 && L <= 64 && (elem_bytes == 4 || L <= 32));
   if (tf.reg) {
     // register kernel: a row segment of mt modes is 32 bytes (one sector)
-    int mt = 32 / elem_bytes;
-    while (mt > 1 && threads(mt) > 1024) mt /= 2;
-    while (mt > 1 && mt / 2 >= tf.nx) mt /= 2;
+    const int mt = 32 / elem_bytes;  // fixed: the kernel's mode tile is a compile-time constant
     tf.mt = mt;
     tf.threads = threads(mt);
     tf.smem = (size_t)(5 * 3 * L * mt + (3 * 32 + 33) * mt) * elem_bytes;
@@ -372,126 +370,145 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
 
 // Register-resident variant (partition length L a compile-time power of two): thread (c, p) keeps
 // the L values of its partition in registers, loaded straight from global memory (a warp reads
-// rows of mt consecutive modes: whole 32-byte sectors) and stored back the same way; the factors
-// of the CTA's modes (3 classes x L rows) are staged once in shared memory; only the separator
-// ends and the separator solution pass through shared memory.
-template <typename T, int L>
-__global__ void __launch_bounds__(256) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
-                                                             int nx, int P, int levels, int nf,
-                                                             const T *__restrict__ fm, const T *__restrict__ fc,
-                                                             const T *__restrict__ fa, const T *__restrict__ sv,
-                                                             const T *__restrict__ sw, const T *__restrict__ red,
-                                                             const KrylovScalars *__restrict__ sc, int pstride,
-                                                             int poff, int ncomp, int mt) {
+// rows of MT consecutive modes: whole 32-byte sectors) and stored back the same way; the factors
+// of the CTA's modes (3 classes x L rows) are staged once in shared memory and reused for the
+// `per_cta` right-hand sides the CTA solves in turn; only the separator ends and the separator
+// solution pass through shared memory.
+template <typename T, int L, int MT>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, (L >= 64 ? 2 : 4)) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
+                                                               int nx, int P, int levels, int nf,
+                                                               const T *__restrict__ fm, const T *__restrict__ fc,
+                                                               const T *__restrict__ fa, const T *__restrict__ sv,
+                                                               const T *__restrict__ sw, const T *__restrict__ red,
+                                                               const KrylovScalars *__restrict__ sc, int pstride,
+                                                               int poff, int ncomp, int nplanes, int per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *F = reinterpret_cast<T *>(smem_raw);    // [5][3][L][mt]: fm, fa, fc, sv, sw
-  T *gF = F + 5 * 3 * L * mt;                // [mt][32]
-  T *gL = gF + mt * 32;
-  T *ds = gL + mt * 32;
-  T *xi = ds + mt * 32;                      // [mt][33]
-  const int b = blockIdx.y * pstride + poff;
-  if (sc != nullptr && sc[b / ncomp].state != ST_RUN) return;
-  const int j0 = blockIdx.x * mt;
+  constexpr int NCR = 3 * L;                 // factor rows: 3 classes x L
+  T *F = reinterpret_cast<T *>(smem_raw);    // [5][NCR][MT]: fm, fa, fc, sv, sw
+  T *gF = F + 5 * NCR * MT;                  // [MT][32]
+  T *gL = gF + MT * 32;
+  T *ds = gL + MT * 32;
+  T *xi = ds + MT * 32;                      // [MT][33]
+  const int j0 = blockIdx.x * MT;
   const int tid = threadIdx.x, nth = blockDim.x;
-  // stage the factors of this CTA's modes
-  const int nclsrow = 3 * L;
-  for (int idx = tid; idx < 5 * nclsrow * mt; idx += nth) {
-    const int c = idx % mt, rest = idx / mt, row = rest % nclsrow, a = rest / nclsrow;
-    const int j = j0 + c;
-    const T *src = a == 0 ? fm : (a == 1 ? fa : (a == 2 ? fc : (a == 3 ? sv : sw)));
-    F[idx] = (j < nx) ? src[(size_t)row * nx + j] : T(0);
+  // stage the factors of this CTA's modes: row-major [row][MT], MT a power of two
+  {
+    const int cm = tid % MT, r0 = tid / MT, rstep = nth / MT;
+    const int j = j0 + cm;
+    for (int row = r0; row < NCR; row += rstep) {
+      const size_t g = (size_t)row * nx + j;
+      const bool ok = j < nx;
+      F[(0 * NCR + row) * MT + cm] = ok ? fm[g] : T(0);
+      F[(1 * NCR + row) * MT + cm] = ok ? fa[g] : T(0);
+      F[(2 * NCR + row) * MT + cm] = ok ? fc[g] : T(0);
+      F[(3 * NCR + row) * MT + cm] = ok ? sv[g] : T(0);
+      F[(4 * NCR + row) * MT + cm] = ok ? sw[g] : T(0);
+    }
   }
-  const int c = tid % mt, p = tid / mt, j = j0 + c;
-  const bool live = j < nx && p < P;
+  const int c = tid % MT, p = tid / MT, j = j0 + c;
+  const bool col_ok = j < nx && p < P;
   const int cls = (p == 0) ? 0 : (p == P - 1 ? 2 : 1);
   const int i0 = (p == 0) ? 0 : 1;
-  const size_t plane = (size_t)b * nz * nx;
-  T v[L];
-#pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const int r = p * L + i;
-    v[i] = (live && r < nz) ? din[plane + (size_t)r * nx + j] : T(0);
-  }
-  __syncthreads();
-  const T *Fm = F + (0 * nclsrow + cls * L) * mt + c;
-  const T *Fa = F + (1 * nclsrow + cls * L) * mt + c;
-  const T *Fc = F + (2 * nclsrow + cls * L) * mt + c;
-  const T *Sv = F + (3 * nclsrow + cls * L) * mt + c;
-  const T *Sw = F + (4 * nclsrow + cls * L) * mt + c;
-  const T dsep = v[0];  // separator row value (p >= 1)
-  if (live) {
-    // forward elimination over the block rows i0..L-1, then back substitution: v = T_I^{-1} d_I
-    T prev = T(0);
-#pragma unroll
-    for (int i = 0; i < L; ++i) {
-      if (i < i0) continue;
-      const T m = Fm[i * mt];
-      v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * mt] * prev) * m;
-      prev = v[i];
-    }
-#pragma unroll
-    for (int i = L - 2; i >= 0; --i) {
-      if (i < i0) continue;
-      v[i] = v[i] - Fc[i * mt] * v[i + 1];
-    }
-    gF[c * 32 + p] = (i0 == 0) ? v[0] : v[1];
-    gL[c * 32 + p] = v[L - 1];
-    ds[c * 32 + p] = (p >= 1) ? dsep : T(0);
-  }
-  __syncthreads();
-  // separators: one warp per mode, parallel cyclic reduction in shuffles (precomputed multipliers)
+  const T *Fm = F + (0 * NCR + cls * L) * MT + c;
+  const T *Fa = F + (1 * NCR + cls * L) * MT + c;
+  const T *Fc = F + (2 * NCR + cls * L) * MT + c;
+  const T *Sv = F + (3 * NCR + cls * L) * MT + c;
+  const T *Sw = F + (4 * NCR + cls * L) * MT + c;
   const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
   const int n = P - 1;
-  for (int cc = warp; n > 0 && cc < mt; cc += nwarp) {
-    const int jj = j0 + cc;
-    if (jj >= nx) continue;  // warp-uniform
-    const T *R = red + (size_t)jj * nf * 32;
-    const bool act = lane < n;
-    T rq = T(0);
-    if (act) {
-      const int pp = lane + 1;
-      rq = (ds[cc * 32 + pp] - R[lane] * gL[cc * 32 + pp - 1] - R[32 + lane] * gF[cc * 32 + pp]) * R[64 + lane];
-    }
-    for (int l = 0; l < levels; ++l) {
-      const int s = 1 << l;
-      T rm = __shfl_up_sync(0xffffffffu, rq, s);
-      T rp = __shfl_down_sync(0xffffffffu, rq, s);
-      if (lane < s) rm = T(0);
-      if (lane + s >= n) rp = T(0);
-      if (act) rq = (rq - R[(3 + 3 * l) * 32 + lane] * rm - R[(4 + 3 * l) * 32 + lane] * rp) * R[(5 + 3 * l) * 32 + lane];
-    }
-    xi[cc * 33 + lane + 1] = act ? rq : T(0);
-    if (lane == 0) xi[cc * 33] = T(0);
-  }
-  if (n == 0 && tid < mt) xi[tid * 33] = T(0);
   __syncthreads();
-  if (!live) return;
-  // correction with the spike vectors, store
-  const T xa = xi[c * 33 + p];
-  const T xb = (p + 1 <= P - 1) ? xi[c * 33 + p + 1] : T(0);
+  for (int k = 0; k < per_cta; ++k) {
+    const int bi = blockIdx.y * per_cta + k;
+    if (bi >= nplanes) break;                                  // uniform over the CTA
+    const int b = bi * pstride + poff;
+    if (sc != nullptr && sc[b / ncomp].state != ST_RUN) continue;  // uniform over the CTA
+    const bool live = col_ok;
+    const T *src = din + (size_t)b * nz * nx + j;
+    T *dst = yout + (size_t)b * nz * nx + j;
+    T v[L];
 #pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const int r = p * L + i;
-    T y;
-    if (i < i0) y = xa;  // separator row
-    else y = v[i] - xa * Sv[i * mt] - xb * Sw[i * mt];
-    if (r < nz) yout[plane + (size_t)r * nx + j] = y;
+    for (int i = 0; i < L; ++i) {
+      const int r = p * L + i;
+      v[i] = (live && r < nz) ? src[(size_t)r * nx] : T(0);
+    }
+    const T dsep = v[0];  // separator row value (p >= 1)
+    if (live) {
+      // forward elimination over the block rows i0..L-1, then back substitution: v = T_I^{-1} d_I
+      T prev = T(0);
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        if (i < i0) continue;
+        const T m = Fm[i * MT];
+        v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * MT] * prev) * m;
+        prev = v[i];
+      }
+#pragma unroll
+      for (int i = L - 2; i >= 0; --i) {
+        if (i < i0) continue;
+        v[i] = v[i] - Fc[i * MT] * v[i + 1];
+      }
+      gF[c * 32 + p] = (i0 == 0) ? v[0] : v[1];
+      gL[c * 32 + p] = v[L - 1];
+      ds[c * 32 + p] = (p >= 1) ? dsep : T(0);
+    }
+    __syncthreads();
+    // separators: one warp per mode, parallel cyclic reduction in shuffles (precomputed multipliers)
+    for (int cc = warp; n > 0 && cc < MT; cc += nwarp) {
+      const int jj = j0 + cc;
+      if (jj >= nx) continue;  // warp-uniform
+      const T *R = red + (size_t)jj * nf * 32;
+      const bool act = lane < n;
+      T rq = T(0);
+      if (act) {
+        const int pp = lane + 1;
+        rq = (ds[cc * 32 + pp] - R[lane] * gL[cc * 32 + pp - 1] - R[32 + lane] * gF[cc * 32 + pp]) * R[64 + lane];
+      }
+      for (int l = 0; l < levels; ++l) {
+        const int s = 1 << l;
+        T rm = __shfl_up_sync(0xffffffffu, rq, s);
+        T rp = __shfl_down_sync(0xffffffffu, rq, s);
+        if (lane < s) rm = T(0);
+        if (lane + s >= n) rp = T(0);
+        if (act) rq = (rq - R[(3 + 3 * l) * 32 + lane] * rm - R[(4 + 3 * l) * 32 + lane] * rp) * R[(5 + 3 * l) * 32 + lane];
+      }
+      xi[cc * 33 + lane + 1] = act ? rq : T(0);
+      if (lane == 0) xi[cc * 33] = T(0);
+    }
+    if (n == 0 && tid < MT) xi[tid * 33] = T(0);
+    __syncthreads();
+    if (live) {
+      // correction with the spike vectors, store
+      const T xa = xi[c * 33 + p];
+      const T xb = (p + 1 <= P - 1) ? xi[c * 33 + p + 1] : T(0);
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const int r = p * L + i;
+        const T y = (i < i0) ? xa : v[i] - xa * Sv[i * MT] - xb * Sw[i * MT];
+        if (r < nz) dst[(size_t)r * nx] = y;
+      }
+    }
+    __syncthreads();  // gF/gL/ds/xi are reused by the next right-hand side
   }
 }
 
 template <typename T, int L>
 static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc, cudaStream_t s,
                            int pstride, int poff, int ncomp) {
+  constexpr int MT = 32 / (int)sizeof(T);
   static bool attr_done = false;
   if (!attr_done) {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
     attr_done = true;
   }
-  dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
-  tri_solve_reg_kernel<T, L><<<grid, tf.threads, tf.smem, s>>>(
+  // several right-hand sides per CTA when there are plenty of CTAs anyway (factor reuse)
+  const int ctas_x = (tf.nx + MT - 1) / MT;
+  int per_cta = 1;
+  while (per_cta < 8 && (long long)ctas_x * ((nrhs + 2 * per_cta - 1) / (2 * per_cta)) >= 152 * 8) per_cta *= 2;
+  dim3 grid(ctas_x, (nrhs + per_cta - 1) / per_cta);
+  tri_solve_reg_kernel<T, L, MT><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc, (const T *)tf.fa,
-      (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, tf.mt);
+      (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, nrhs, per_cta);
 }
 
 template <typename T>
