@@ -140,6 +140,13 @@ int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, i
 int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int nrhs);
 /* 1 if the plan's DST runs on the tcgen05 tensor cores (mixed path), else 0 */
 int  lag_precond_uses_tensor_cores(const lag_precond *p);
+/* Tensor-core DST of a mixed plan: number of bf16 products per K step (3: split hi*hi + hi*lo +
+ * lo*hi, relative error ~1e-5; 2: hi*hi + lo*hi with S rounded to bf16, ~2e-3; 1: hi*hi, ~4e-3).
+ * Default 3 (or the environment variable LAGWAVE_DST_PRODUCTS at plan creation).  The flexible
+ * Krylov solvers converge to the same float64 tolerance with any of them; fewer products move
+ * fewer operand bytes and issue fewer MMAs.  LAG_EINVAL for other values or plans without the
+ * tensor-core DST (3 is accepted there as a no-op). */
+int  lag_precond_set_dst_products(lag_precond *p, int products);
 /* z = B^{-1} r like lag_precond_apply, but allocating nothing.  The paper has no counterpart: this
  * entry point is for callers that cannot let a library allocate device memory at call time (a
  * framework whose own allocator owns the device memory, or a real-time loop that must not block in

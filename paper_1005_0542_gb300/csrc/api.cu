@@ -1,6 +1,7 @@
 // C ABI of the library: contexts, media, preconditioner plans, Krylov drivers and shots.
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -103,7 +104,11 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = p->tc_scratch.ctx = ctx;
   p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
   dst_build(p->dst, p->dst_store, g.nx, p->use_tc, s);
-  if (p->use_tc) p->dst.tc_err = reinterpret_cast<int *>(p->dst_store.as<uint8_t>() + p->dst_store.bytes - 256);
+  if (p->use_tc) {
+    p->dst.tc_err = reinterpret_cast<int *>(p->dst_store.as<uint8_t>() + p->dst_store.bytes - 256);
+    const char *ev = std::getenv("LAGWAVE_DST_PRODUCTS");  // default split-product count
+    if (ev != nullptr && (ev[0] == '1' || ev[0] == '2' || ev[0] == '3') && ev[1] == 0) p->dst.tc_products = ev[0] - '0';
+  }
   p->tri64.nx = g.nx;
   p->tri64.nz = g.nz;
   tri_choose_layout(p->tri64, 8, partitions);
@@ -352,6 +357,13 @@ int lag_precond_info(const lag_precond *p, int *P, int *L, int *mt) {
 }
 
 int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? (p->use_tc ? 1 : 0) : 0; }
+
+int lag_precond_set_dst_products(lag_precond *p, int products) {
+  if (!p || products < 1 || products > 3) return LAG_EINVAL;
+  if (!p->use_tc) return products == 3 ? LAG_OK : LAG_EINVAL;
+  p->dst.tc_products = products;
+  return LAG_OK;
+}
 
 // ------------------------------------------------------------------------------ medium
 int lag_medium_create_acoustic(lag_ctx *ctx, const lag_grid *g, const double *c, const double *rho, double h,

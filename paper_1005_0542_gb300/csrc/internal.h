@@ -109,6 +109,7 @@ struct DstPlan {
   int npad_u = 0;             // N tiles (256 wide)
   uint8_t *tc_scratch = nullptr;
   int *tc_err = nullptr;
+  int tc_products = 3;        // split products per K step: 3 (hi*hi+hi*lo+lo*hi), 2 or 1
 };
 void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream_t s);
 // Y[row][:] = S X[row][:] for `rows` rows of length n.  Input/output types as named.

@@ -37,9 +37,6 @@ constexpr int TN = 256;          // output columns per tile (MMA N)
 constexpr int TK = 64;           // K per stage (one 128-byte swizzle atom of bf16)
 constexpr int A_TILE = TM * TK * 2;   // 16 KB
 constexpr int B_TILE = TN * TK * 2;   // 32 KB
-constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;  // hi/lo of A and B: 96 KB
-constexpr int NSTAGE = 2;
-constexpr int SMEM_BYTES = NSTAGE * STAGE + 1024 + 128;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr long long WAIT_LIMIT = 1LL << 26;
 
@@ -235,46 +232,60 @@ __global__ void __launch_bounds__(256) pack_a_inv_kernel(const float *__restrict
 }
 
 // ------------------------------------------------------------------------------ GEMM
-// grid (n tiles, m tiles, 2 parities); 128 threads.  out[row * ld + par * ku + col] (float32),
-// col < nvalid[par].
-__global__ void __launch_bounds__(128, 1) dst_tc_gemm_kernel(const uint8_t *__restrict__ apack,
+// Persistent, warp-specialised: grid = min(tiles, SMs), 192 threads.
+//   warp 0 (one lane): producer, cp.async.bulk of the packed A / B tiles into a ring of stages;
+//   warp 1 (one lane): MMA issuer, NPROD split products per 16-wide K step into one of two
+//                      tensor-memory accumulators (256 columns each);
+//   warps 2-5:         epilogue, tcgen05.ld of the finished accumulator (warp w reads lanes
+//                      32 (w % 4) ..), stores, then hands the accumulator back.
+// The stage ring runs across tile boundaries and the two accumulators let the epilogue of one
+// tile overlap the main loop of the next.  Tiles are ordered (parity, m tile, n tile), n fastest,
+// so consecutive tiles reuse the same A rows from L2.  NPROD = 3: hi*hi + hi*lo + lo*hi;
+// NPROD = 2: hi*hi + lo*hi (B = bf16(S)); NPROD = 1: hi*hi.
+template <int NPROD>
+struct TcCfg {
+  static constexpr int A_BYTES = (NPROD >= 2 ? 2 : 1) * A_TILE;
+  static constexpr int B_BYTES = (NPROD >= 3 ? 2 : 1) * B_TILE;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int NST = (NPROD == 3) ? 2 : (NPROD == 2 ? 3 : 4);
+  static constexpr int SMEM = NST * STAGE_BYTES + 1024 + 256;
+};
+
+template <int NPROD>
+__global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__restrict__ apack,
                                                              const uint8_t *__restrict__ bpack, size_t b_mat_bytes,
                                                              int nks, int nmt, int nnt, int rows, float *__restrict__ out,
                                                              int ld, int ku, int nvalid0, int nvalid1,
                                                              const KrylovScalars *__restrict__ sc, int rpr,
                                                              int *__restrict__ err) {
+  using Cfg = TcCfg<NPROD>;
+  constexpr int NST = Cfg::NST;
   extern __shared__ uint8_t smem_raw[];
-  const int par = blockIdx.z, mt = blockIdx.y, nt = blockIdx.x;
-  const int nvalid = par ? nvalid1 : nvalid0;
-  const int n0 = nt * TN, m0 = mt * TM;
-  if (n0 >= nvalid) return;
-  if (sc != nullptr) {  // skip tiles whose right-hand sides have all finished
-    const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
-    bool any = false;
-    for (int r = r0; r <= r1; ++r) any |= (sc[r].state == ST_RUN);
-    if (!any) return;
-  }
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t *gbase = smem_raw + (base - raw);
-  const uint32_t bars = base + NSTAGE * STAGE;  // full[2], empty[2], done
-  const uint32_t full0 = bars, empty0 = bars + 16, done = bars + 32;
-  volatile uint32_t *holder = reinterpret_cast<volatile uint32_t *>(gbase + NSTAGE * STAGE + 64);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + NSTAGE * STAGE + 72);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t bars = base + NST * Cfg::STAGE_BYTES;
+  const uint32_t full0 = bars, empty0 = bars + 8 * NST, tfull0 = bars + 16 * NST, tempty0 = tfull0 + 16;
+  volatile uint32_t *holder = reinterpret_cast<volatile uint32_t *>(gbase + NST * Cfg::STAGE_BYTES + 16 * NST + 32);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + NST * Cfg::STAGE_BYTES + 16 * NST + 40);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = 2 * nmt * nnt;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)holder)),
-                 "r"(TMEM_COLS)
+                 "r"(2 * TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int s = 0; s < NSTAGE; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 4);  // one arrive per epilogue warp
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -283,77 +294,131 @@ __global__ void __launch_bounds__(128, 1) dst_tc_gemm_kernel(const uint8_t *__re
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *holder;
 
-  const uint8_t *atiles = apack + ((size_t)par * nmt + mt) * nks * 2 * A_TILE;
-  const uint8_t *btiles = bpack + (size_t)par * b_mat_bytes + (size_t)nt * nks * 2 * B_TILE;
+  // tile t -> (parity, m tile, n tile); tiles that only hold finished right-hand sides, or lie
+  // beyond a parity's valid columns, are skipped by every role alike
+  auto decode = [&](int t, int &par, int &mt, int &nt) {
+    nt = t % nnt;
+    mt = (t / nnt) % nmt;
+    par = t / (nnt * nmt);
+  };
+  auto wanted = [&](int par, int mt, int nt) -> bool {
+    if (nt * TN >= (par ? nvalid1 : nvalid0)) return false;
+    if (sc == nullptr) return true;
+    const int m0 = mt * TM;
+    const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
+    for (int r = r0; r <= r1; ++r)
+      if (sc[r].state == ST_RUN) return true;
+    return false;
+  };
 
-  if (tid == 0) {  // producer: bulk copies of the pre-packed tiles
-    for (int kk = 0; kk < nks; ++kk) {
-      const int s = kk & 1;
-      if (kk >= 2 && !mbar_wait(empty0 + 8 * s, ((kk >> 1) - 1) & 1)) {
-        atomicExch(err, 1);
-        *abort_flag = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int par, mt, nt;
+        decode(t, par, mt, nt);
+        if (!wanted(par, mt, nt)) continue;
+        const uint8_t *atiles = apack + ((size_t)par * nmt + mt) * nks * 2 * A_TILE;
+        const uint8_t *btiles = bpack + (size_t)par * b_mat_bytes + (size_t)nt * nks * 2 * B_TILE;
+        for (int kk = 0; kk < nks; ++kk, ++it) {
+          const int s = it % NST, use = it / NST;
+          if (it >= NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
+            atomicExch(err, 1);
+            *abort_flag = 1;
+            break;
+          }
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+          const uint32_t fb = full0 + 8 * s;
+          mbar_expect_tx(fb, Cfg::STAGE_BYTES);
+          bulk_g2s(st, atiles + (size_t)kk * 2 * A_TILE, Cfg::A_BYTES, fb);
+          bulk_g2s(st + Cfg::A_BYTES, btiles + (size_t)kk * 2 * B_TILE, Cfg::B_BYTES, fb);
+        }
       }
-      if (*abort_flag) break;
-      const uint32_t st = base + s * STAGE;
-      const uint32_t fb = full0 + 8 * s;
-      mbar_expect_tx(fb, STAGE);
-      const uint8_t *a = atiles + (size_t)kk * 2 * A_TILE;
-      const uint8_t *b = btiles + (size_t)kk * 2 * B_TILE;
-      bulk_g2s(st, a, 2 * A_TILE, fb);                    // A hi | lo
-      bulk_g2s(st + 2 * A_TILE, b, 2 * B_TILE, fb);       // B hi | lo
     }
-  } else if (tid == 32) {  // MMA issuer
-    bool ok = true;
-    for (int kk = 0; kk < nks; ++kk) {
-      const int s = kk & 1;
-      if (!mbar_wait(full0 + 8 * s, (kk >> 1) & 1)) {
-        atomicExch(err, 2);
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int it = 0, tc = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int par, mt, nt;
+        decode(t, par, mt, nt);
+        if (!wanted(par, mt, nt)) continue;
+        const int acc = tc & 1, ause = tc >> 1;
+        if (tc >= 2 && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) {
+          atomicExch(err, 4);
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(acc * TMEM_COLS);
+        for (int kk = 0; kk < nks; ++kk, ++it) {
+          const int s = it % NST, use = it / NST;
+          if (!mbar_wait(full0 + 8 * s, use & 1)) {
+            atomicExch(err, 2);
+            *abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * Cfg::STAGE_BYTES;
+          const uint32_t ahi = st, alo = st + A_TILE, bhi = st + Cfg::A_BYTES, blo = bhi + B_TILE;
+#pragma unroll
+          for (int sub = 0; sub < TK / 16; ++sub) {
+            const uint32_t o = sub * 32;  // 16 bf16 along K
+            mma_bf16(d, sdesc(ahi + o), sdesc(bhi + o), (kk == 0 && sub == 0) ? 0u : 1u);
+            if (NPROD >= 3) mma_bf16(d, sdesc(ahi + o), sdesc(blo + o), 1u);
+            if (NPROD >= 2) mma_bf16(d, sdesc(alo + o), sdesc(bhi + o), 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tfull0 + 8 * acc)
+                     : "memory");
+        ++tc;
+      }
+    }
+  } else {  // epilogue warps 2..5: tensor-memory lanes 32 (warp % 4) ..
+    const int lg = warp & 3;
+    const bool vec = ((ld & 3) == 0) && ((ku & 3) == 0);
+    int tc = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int par, mt, nt;
+      decode(t, par, mt, nt);
+      if (!wanted(par, mt, nt)) continue;
+      const int acc = tc & 1, ause = tc >> 1;
+      const bool ok = mbar_wait(tfull0 + 8 * acc, ause & 1);
+      __syncwarp();
+      if (!ok) {
+        if (lane == 0) atomicExch(err, 3);
         *abort_flag = 1;
-        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = base + s * STAGE;
-      const uint32_t ahi = st, alo = st + A_TILE, bhi = st + 2 * A_TILE, blo = bhi + B_TILE;
+      const int row = mt * TM + lg * 32 + lane;
+      const int n0 = nt * TN;
+      const int ncols = min(TN, (par ? nvalid1 : nvalid0) - n0);
+      float *orow = out + (size_t)row * ld + (size_t)par * ku + n0;
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * TMEM_COLS + c0), v);
+        if (row >= rows || c0 >= ncols) continue;
+        if (vec && c0 + 32 <= ncols) {
 #pragma unroll
-      for (int sub = 0; sub < TK / 16; ++sub) {
-        const uint32_t o = sub * 32;  // 16 bf16 along K
-        const uint32_t first = (kk == 0 && sub == 0) ? 0u : 1u;
-        mma_bf16(tmem, sdesc(ahi + o), sdesc(bhi + o), first);
-        mma_bf16(tmem, sdesc(ahi + o), sdesc(blo + o), 1u);
-        mma_bf16(tmem, sdesc(alo + o), sdesc(bhi + o), 1u);
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4 *>(orow + c0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (c0 + q < ncols) orow[c0 + q] = v[q];
+        }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
-                   : "memory");
-    }
-    (void)ok;
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done) : "memory");
-  }
-  __syncwarp();
-  // epilogue: warp w owns accumulator rows 32 w .. 32 w + 31 (tensor-memory lanes)
-  const bool fin = mbar_wait(done, 0);
-  if (!fin && (tid & 31) == 0) atomicExch(err, 3);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + warp * 32 + (tid & 31);
-  const bool vec = ((ld & 3) == 0) && ((ku & 3) == 0);
-  float *orow = out + (size_t)row * ld + (size_t)par * ku + n0;
-  const int ncols = min(TN, nvalid - n0);
-  for (int c0 = 0; c0 < TN; c0 += 32) {
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (!fin || *abort_flag || row >= rows || c0 >= ncols) continue;
-    if (vec && c0 + 32 <= ncols) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        *reinterpret_cast<float4 *>(orow + c0 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else {
-      for (int q = 0; q < 32 && c0 + q < ncols; ++q) orow[c0 + q] = v[q];
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * acc) : "memory");
+      ++tc;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS) : "memory");
 }
 
 // z[k] = E[k] + O[k], z[n-1-k] = E[k] - O[k]   (eo rows: [E (ku) | O (ku)])
@@ -412,17 +477,29 @@ void dst_build_tc(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
   LAG_LAUNCH_CHECK();
 }
 
-static void gemm_launch(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
-                        int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
+template <int NPROD>
+static void gemm_launch_n(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
+                          int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(dst_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(dst_tc_gemm_kernel<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        TcCfg<NPROD>::SMEM));
     attr = true;
   }
   const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
-  dim3 g(nnt, nmt, 2);
-  dst_tc_gemm_kernel<<<g, 128, SMEM_BYTES, s>>>(apack, bpack, dp.tc_bmat_bytes, nks, nmt, nnt, rows, out, ld, dp.ku,
-                                                 nvalid0, nvalid1, sc, rpr, err);
+  const int ntiles = 2 * nmt * nnt;
+  const int grid = std::min(ntiles, 152);
+  dst_tc_gemm_kernel<NPROD><<<grid, 192, TcCfg<NPROD>::SMEM, s>>>(apack, bpack, dp.tc_bmat_bytes, nks, nmt, nnt, rows,
+                                                                   out, ld, dp.ku, nvalid0, nvalid1, sc, rpr, err);
+}
+
+static void gemm_launch(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
+                        int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
+  switch (dp.tc_products) {
+    case 1: gemm_launch_n<1>(dp, apack, bpack, rows, out, ld, nvalid0, nvalid1, sc, rpr, err, s); break;
+    case 2: gemm_launch_n<2>(dp, apack, bpack, rows, out, ld, nvalid0, nvalid1, sc, rpr, err, s); break;
+    default: gemm_launch_n<3>(dp, apack, bpack, rows, out, ld, nvalid0, nvalid1, sc, rpr, err, s); break;
+  }
   count_launch();
   LAG_LAUNCH_CHECK();
 }

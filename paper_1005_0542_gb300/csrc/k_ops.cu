@@ -107,41 +107,45 @@ void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rh
 }
 
 // ------------------------------------------------------------------------------ acoustic apply
-// block 32 x 8 points; grid (x tiles, z tiles, rhs).  mode 1: also (p, q) -> alpha = rz / pq.
+// 32 x 8 point tiles walked grid-stride by a bounded number of blocks per rhs (the partial sums of
+// (p, q) stay few, so the last block's deterministic sum is short).  mode 1: also alpha = rz / pq.
 __global__ void __launch_bounds__(256) acoustic_apply_kernel(const double *__restrict__ p, double *__restrict__ q,
                                                              int nx, int nz, const double *__restrict__ ax,
                                                              const double *__restrict__ az,
                                                              const double *__restrict__ dg, KrylovScalars *sc,
                                                              Reduce red, int mode) {
-  const int b = blockIdx.z;
+  const int b = blockIdx.y;
   if (sc != nullptr && sc[b].state != ST_RUN) return;
-  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int k = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int tx = (nx + 31) / 32, tz = (nz + 7) / 8;
   const size_t plane = (size_t)nx * nz;
   const double *pb = p + (size_t)b * plane;
+  double *qb = q + (size_t)b * plane;
   double dot = 0.0;
-  if (i < nx && k < nz) {
-    const size_t o = (size_t)k * nx + i;
-    const double pc = pb[o];
-    const double pw = (i > 0) ? pb[o - 1] : 0.0;
-    const double pe = (i + 1 < nx) ? pb[o + 1] : 0.0;
-    const double pn = (k > 0) ? pb[o - nx] : 0.0;
-    const double ps = (k + 1 < nz) ? pb[o + nx] : 0.0;
-    const size_t fx = (size_t)k * (nx + 1) + i;
-    double v = dg[o] * pc;
-    v = fma(-ax[fx], pw, v);
-    v = fma(-ax[fx + 1], pe, v);
-    v = fma(-az[o], pn, v);
-    v = fma(-az[o + nx], ps, v);
-    q[(size_t)b * plane + o] = v;
-    dot = pc * v;
+  for (int t = blockIdx.x; t < tx * tz; t += gridDim.x) {
+    const int i = (t % tx) * 32 + (threadIdx.x & 31);
+    const int k = (t / tx) * 8 + (threadIdx.x >> 5);
+    if (i < nx && k < nz) {
+      const size_t o = (size_t)k * nx + i;
+      const double pc = pb[o];
+      const double pw = (i > 0) ? pb[o - 1] : 0.0;
+      const double pe = (i + 1 < nx) ? pb[o + 1] : 0.0;
+      const double pn = (k > 0) ? pb[o - nx] : 0.0;
+      const double ps = (k + 1 < nz) ? pb[o + nx] : 0.0;
+      const size_t fx = (size_t)k * (nx + 1) + i;
+      double v = dg[o] * pc;
+      v = fma(-ax[fx], pw, v);
+      v = fma(-ax[fx + 1], pe, v);
+      v = fma(-az[o], pn, v);
+      v = fma(-az[o + nx], ps, v);
+      qb[o] = v;
+      dot = fma(pc, v, dot);
+    }
   }
   if (mode == 1) {
     double v1[1] = {dot}, tot[1];
     __shared__ double sh[32];
     block_sum<1>(v1, sh);
-    const int nblk = gridDim.x * gridDim.y, blk = blockIdx.y * gridDim.x + blockIdx.x;
-    if (publish_partials<1>(red, b, blk, nblk, v1, tot)) {
+    if (publish_partials<1>(red, b, blockIdx.x, gridDim.x, v1, tot)) {
       const double pq = tot[0];
       sc[b].pq = pq;
       if (!(pq > 0.0) || !isfinite(pq)) sc[b].state = ST_NAN;
@@ -150,12 +154,17 @@ __global__ void __launch_bounds__(256) acoustic_apply_kernel(const double *__res
   }
 }
 
+int stencil_blocks_per_rhs(int nx, int nz) {
+  const int tiles = ((nx + 31) / 32) * ((nz + 7) / 8);
+  return tiles < 1216 ? tiles : 1216;
+}
+
 void acoustic_apply(const lag_medium &m, const double *p, double *q, int nrhs, const KrylovScalars *sc,
                     const Reduce *red, int mode, cudaStream_t s) {
   const int nx = m.grid.nx, nz = m.grid.nz;
   const size_t nax = (size_t)nz * (nx + 1), naz = (size_t)(nz + 1) * nx;
   const double *ax = m.coef.as<double>(), *az = ax + nax, *dg = az + naz;
-  dim3 g((nx + 31) / 32, (nz + 7) / 8, nrhs);
+  dim3 g(stencil_blocks_per_rhs(nx, nz), nrhs);
   Reduce r = red ? *red : Reduce{nullptr, nullptr, 0, 0};
   ProfScope prof(KC_STENCIL_A, s);
   acoustic_apply_kernel<<<g, 256, 0, s>>>(p, q, nx, nz, ax, az, dg, const_cast<KrylovScalars *>(sc), r, mode);

@@ -92,6 +92,7 @@ _PROTOS = {
     "lag_precond_static_capacity": (C.c_size_t, []),
     "lag_precond_info": (I, [VP, PI, PI, PI]),
     "lag_precond_uses_tensor_cores": (I, [VP]),
+    "lag_precond_set_dst_products": (I, [VP, I]),
     "lag_medium_create_acoustic": (I, [VP, C.POINTER(lag_grid), PD, PD, D, C.POINTER(VP)]),
     "lag_medium_create_elastic": (I, [VP, C.POINTER(lag_grid), PD, PD, PD, D, C.POINTER(VP)]),
     "lag_medium_destroy": (None, [VP]),
