@@ -76,6 +76,7 @@ typedef struct {
   int restart_k;    /* GMRES(k) restart length (elastic), 1..64                                    */
   int prec;         /* LAG_FP64 or LAG_MIXED                                                       */
   int partitions;   /* z-partitions of the tridiagonal solve; 0 = automatic                        */
+  int tune;         /* 1: shots run lag_precond_autotune on their plans at creation                */
 } lag_solver;
 typedef struct { int ix, iz; } lag_point;                          /* 0-based interior node        */
 typedef struct { double f0, t0, gamma; int kind; } lag_wavelet;
@@ -161,6 +162,14 @@ int  lag_precond_set_dst_products(lag_precond *p, int products);
  * context's stream. */
 int  lag_precond_apply_static(lag_precond *p, const double *r_dev, double *z_dev, int nrhs);
 size_t lag_precond_static_capacity(void);
+/* Autotuner (no counterpart in the paper; the tuning choices of this implementation): times the
+ * tridiagonal partition counts 8, 16 and 32 and, on mixed plans with the tensor-core DST, the bf16
+ * product counts 3, 2 and 1 on nrhs seeded right-hand sides (a few applies each, CUDA events on the
+ * context's stream), keeps the fastest (a product count only if its result is within 2e-2 relative
+ * L2 of the 3-product split) and leaves the plan configured with it.  Blocking; allocates
+ * 3 nrhs nz nx float64 scratch values for the duration of the call. */
+int  lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_out, int *products_out,
+                          double *ms_per_apply_out);
 /* plan facts: partitions P, partition length L, modes per CTA of the tridiagonal kernel */
 int  lag_precond_info(const lag_precond *p, int *partitions, int *part_len, int *modes_per_cta);
 

@@ -126,6 +126,9 @@ void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, in
 void dst_apply_tc_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
                       const KrylovScalars *sc, cudaStream_t s);
 bool dst_tc_supported(int n);
+// inverse tensor-core DST fused with the CG beta of the next step (per rhs: rpr rows)
+void dst_apply_tc_f2d_beta(const DstPlan &dp, const float *y, double *z, int nrhs, int rpr, const double *r,
+                           const double *q, int flexible, KrylovScalars *sc, const Reduce &red, cudaStream_t s);
 size_t dst_tc_scratch_bytes(const DstPlan &dp, int rows);
 // parity permutation of a float32 spectrum: natural mode order <-> [even modes | odd modes]
 void spectrum_permute(const float *in, float *out, int rows, int n, int ku, bool to_perm, cudaStream_t s);

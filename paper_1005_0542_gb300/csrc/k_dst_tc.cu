@@ -436,6 +436,49 @@ __global__ void __launch_bounds__(256) butterfly_kernel(const float *__restrict_
   if (k < kv) zr[n - 1 - k] = e - o;
 }
 
+// The butterfly fused with the CG update of the next step: per right-hand side (rpr rows each),
+// z = butterfly(E, O), then rz_new = (r, z), zq = (z, q) and beta (Fletcher-Reeves or
+// Polak-Ribiere), finished by the last block in a fixed order.  grid (blocks, nrhs).
+__global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__restrict__ eo, double *__restrict__ z,
+                                                             const double *__restrict__ r, const double *__restrict__ q,
+                                                             int n, int ku, int kv, int rpr, int flexible,
+                                                             KrylovScalars *sc, Reduce red) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].state != ST_RUN) return;
+  const long long per = (long long)rpr * ku;
+  const size_t row0 = (size_t)rhs * rpr;
+  double a0 = 0.0, a1 = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per; t += (long long)gridDim.x * blockDim.x) {
+    const size_t row = row0 + (size_t)(t / ku);
+    const int k = (int)(t % ku);
+    const float *er = eo + row * 2 * ku;
+    const double e = (double)er[k], o = (double)er[ku + k];
+    const size_t i1 = row * n + k;
+    const double z1 = e + o;
+    z[i1] = z1;
+    a0 = fma(r[i1], z1, a0);
+    if (flexible) a1 = fma(z1, q[i1], a1);
+    if (k < kv) {
+      const size_t i2 = row * n + (n - 1 - k);
+      const double z2 = e - o;
+      z[i2] = z2;
+      a0 = fma(r[i2], z2, a0);
+      if (flexible) a1 = fma(z2, q[i2], a1);
+    }
+  }
+  double v2[2] = {a0, a1}, tot[2];
+  __shared__ double sh[64];
+  block_sum<2>(v2, sh);
+  if (publish_partials<2>(red, rhs, blockIdx.x, gridDim.x, v2, tot)) {
+    KrylovScalars &S = sc[rhs];
+    const double rz_new = tot[0];
+    S.zq = tot[1];
+    S.beta = flexible ? (-S.alpha * tot[1] / S.rz) : (rz_new / S.rz);
+    S.rz = rz_new;
+    if (!isfinite(S.beta)) S.state = ST_NAN;
+  }
+}
+
 // parity permutation of spectra (natural mode order <-> [even modes | odd modes])
 __global__ void permute_kernel(const float *in, float *out, int rows, int n, int ku, int to_perm) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -544,6 +587,29 @@ void dst_apply_tc_f2d(const DstPlan &dp, const float *y, double *z, int rows, in
     count_launch();
     LAG_LAUNCH_CHECK();
   }
+}
+
+void dst_apply_tc_f2d_beta(const DstPlan &dp, const float *y, double *z, int nrhs, int rpr, const double *r,
+                           const double *q, int flexible, KrylovScalars *sc, const Reduce &red, cudaStream_t s) {
+  const int rows = nrhs * rpr;
+  if (rows <= 0) return;
+  uint8_t *apack = dp.tc_scratch;
+  float *eo = reinterpret_cast<float *>(apack + 2 * (size_t)div_up(rows, TM) * dp.kpad_u * 2 * A_TILE);
+  const int nks = dp.kpad_u, nmt = div_up(rows, TM);
+  ProfScope prof(KC_DSTTC_INV, s);
+  const long long threads = (long long)nmt * TM * nks * (TK / 8);
+  pack_a_inv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(y, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack, sc,
+                                                                       rpr);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  gemm_launch(dp, apack, dp.tc_b + 2 * dp.tc_bmat_bytes, rows, eo, 2 * dp.ku, dp.ku, dp.ku, sc, rpr, dp.tc_err, s);
+  const long long per = (long long)rpr * dp.ku;
+  int blocks = (int)std::min<long long>((per + 1023) / 1024, 1216);
+  if (blocks < 1) blocks = 1;
+  dim3 g(blocks, nrhs);
+  butterfly_beta_kernel<<<g, 256, 0, s>>>(eo, z, r, q, dp.n, dp.ku, dp.kv, rpr, flexible, sc, red);
+  count_launch();
+  LAG_LAUNCH_CHECK();
 }
 
 void spectrum_permute(const float *in, float *out, int rows, int n, int ku, bool to_perm, cudaStream_t s) {

@@ -32,6 +32,7 @@ void check_solver(const lag_solver &s, bool elastic) {
   if (s.prec != LAG_FP64 && s.prec != LAG_MIXED) throw Error(LAG_EINVAL, "prec must be LAG_FP64 or LAG_MIXED");
   if (elastic && (s.restart_k < 1 || s.restart_k > 64)) throw Error(LAG_EINVAL, "restart_k must be 1..64");
   if (s.partitions < 0 || s.partitions > 32) throw Error(LAG_EINVAL, "partitions must be 0..32");
+  if (s.tune != 0 && s.tune != 1) throw Error(LAG_EINVAL, "tune must be 0 or 1");
 }
 
 void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, double *z, int nrhs, int ncomp,
@@ -134,10 +135,22 @@ void KrylovWork::start_from_r() {
 void KrylovWork::pcg_iteration() {
   double *p = vec(3), *q = vec(4), *z = vec(5);
   Reduce rd = red.get();
+  const int flexible = s.prec == LAG_MIXED ? 1 : 0;
   m->apply(p, q, nrhs, sc(), &rd, 1, stream);                        // q = A p, alpha
   pcg_update_xr(x(), r(), p, q, n, nrhs, s.max_iter, sc(), rd, stream);  // x, r, ||r||, state
-  precond(r(), z);                                                   // z = B^{-1} r
-  pcg_beta(r(), z, q, n, nrhs, s.prec == LAG_MIXED ? 1 : 0, sc(), rd, stream);
+  if (p1->use_tc) {
+    // mixed path: forward DST, tridiagonal solve, then the inverse DST whose butterfly also forms
+    // (r, z), (z, q) and beta
+    const int rows = nrhs * p1->grid.nz;
+    p1->ensure_scratch(nrhs);
+    float *w = p1->scratch.as<float>();
+    dst_apply_tc_d2f(p1->dst, r(), w, rows, p1->grid.nz, sc(), stream);
+    tri_solve_f32(p1->tri32, w, w, nrhs, sc(), stream);
+    dst_apply_tc_f2d_beta(p1->dst, w, z, nrhs, p1->grid.nz, r(), q, flexible, sc(), rd, stream);
+  } else {
+    precond(r(), z);                                                 // z = B^{-1} r
+    pcg_beta(r(), z, q, n, nrhs, flexible, sc(), rd, stream);
+  }
   pcg_update_p(p, z, n, nrhs, sc(), stream);                         // p = z + beta p
 }
 

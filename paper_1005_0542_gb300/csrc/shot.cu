@@ -71,6 +71,13 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
     sh->p1 = precond_new(ctx, g, mid[0], mid[1], d, s.prec, s.partitions, st);
     sh->p2 = precond_new(ctx, g, mid[1], mid[0], d, s.prec, s.partitions, st);
   }
+  if (s.tune) {  // the autotuner issues on the context stream: the plans are complete already
+    for (lag_precond *q : {sh->p1, sh->p2}) {
+      if (q == nullptr) continue;
+      const int rc = lag_precond_autotune(q, nsrc * sh->ncomp, nullptr, nullptr, nullptr);
+      if (rc != LAG_OK) throw Error(rc, std::string("autotune: ") + ctx->last_error);
+    }
+  }
   sh->wk.setup(ctx, sh->medium, sh->p1, sh->p2, s, nsrc, st);
   const size_t n = sh->wk.n;
   sh->hist.alloc(ctx, 2 * n * nsrc * sizeof(double), true);

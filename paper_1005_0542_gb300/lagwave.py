@@ -30,7 +30,7 @@ class lag_laguerre(C.Structure):
 
 class lag_solver(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("restart_k", C.c_int), ("prec", C.c_int),
-                ("partitions", C.c_int)]
+                ("partitions", C.c_int), ("tune", C.c_int)]
 
 
 class lag_point(C.Structure):
@@ -91,6 +91,7 @@ _PROTOS = {
     "lag_precond_apply_static": (I, [VP, VP, VP, I]),
     "lag_precond_static_capacity": (C.c_size_t, []),
     "lag_precond_info": (I, [VP, PI, PI, PI]),
+    "lag_precond_autotune": (I, [VP, I, PI, PI, PD]),
     "lag_precond_uses_tensor_cores": (I, [VP]),
     "lag_precond_set_dst_products": (I, [VP, I]),
     "lag_medium_create_acoustic": (I, [VP, C.POINTER(lag_grid), PD, PD, D, C.POINTER(VP)]),
@@ -176,8 +177,8 @@ def grid(nx, nz, dx, dz):
     return lag_grid(int(nx), int(nz), float(dx), float(dz))
 
 
-def solver(tol=1e-10, max_iter=2000, restart_k=20, prec=LAG_FP64, partitions=0):
-    return lag_solver(float(tol), int(max_iter), int(restart_k), int(prec), int(partitions))
+def solver(tol=1e-10, max_iter=2000, restart_k=20, prec=LAG_FP64, partitions=0, tune=0):
+    return lag_solver(float(tol), int(max_iter), int(restart_k), int(prec), int(partitions), int(tune))
 
 
 def laguerre(h, alpha, n_harm):

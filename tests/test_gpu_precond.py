@@ -209,3 +209,25 @@ def test_mixed_pcg_converges_with_every_product_count(ctx, products):
         assert np.linalg.norm(r) / np.linalg.norm(b[i]) < 1e-10
     L.lag_precond_destroy(p)
     L.lag_medium_destroy(m)
+
+
+def test_autotune_keeps_a_valid_preconditioner(ctx):
+    nx, nz, nrhs = 512, 256, 4
+    args = (nx, nz, 5.0, 5.0, 2.0e10, 2.0e10, 1.0e7)
+    p = plan(ctx, *args, prec=L.LAG_MIXED)
+    P, K, ms = C.c_int(), C.c_int(), C.c_double()
+    L.check(L.lag_precond_autotune(p, nrhs, C.byref(P), C.byref(K), C.byref(ms)), ctx)
+    assert 1 <= P.value <= 32 and K.value in (1, 2, 3) and ms.value > 0
+    assert plan_info(p)[0] == P.value
+    r = RNG.standard_normal((2, nz, nx))
+    rd, zd = dev(r), empty(r.shape)
+    L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
+    tol = TOL_MIXED if K.value == 3 else 2e-2
+    assert rel(host(zd), opre.apply_inverse(r, *args[2:])) < tol
+    L.lag_precond_destroy(p)
+    q = plan(ctx, *args, prec=L.LAG_FP64)
+    L.check(L.lag_precond_autotune(q, nrhs, C.byref(P), C.byref(K), C.byref(ms)), ctx)
+    assert K.value == 3
+    L.check(L.lag_precond_apply(q, ptr(rd), ptr(zd), 2), ctx)
+    assert rel(host(zd), opre.apply_inverse(r, *args[2:])) < TOL64
+    L.lag_precond_destroy(q)

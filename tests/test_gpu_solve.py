@@ -87,12 +87,12 @@ def test_source_coeffs_and_table(ctx):
     assert rel(fm, ref2) < 1e-12
 
 
-def _run_shot(ctx, s, prec, tol, nharm=None, nsrc=None, elastic=False):
+def _run_shot(ctx, s, prec, tol, nharm=None, nsrc=None, elastic=False, tune=0):
     n = nharm or s.n_harm
     srcs = s.sources[:nsrc] if nsrc else s.sources
     g = L.grid(s.nx, s.nz, s.hx, s.hz)
     lag = L.laguerre(s.h, s.alpha, n)
-    sv = L.solver(tol=tol, prec=prec, restart_k=s.restart)
+    sv = L.solver(tol=tol, prec=prec, restart_k=s.restart, tune=tune)
     w = L.wavelet(s.f0, s.t0)
     c_, pc = L.f64(s.c)
     r_, pr = L.f64(s.rho)
@@ -124,6 +124,18 @@ def test_acoustic_shot_two_layer_full(ctx, prec, tol, gate):
     assert rel_l2(traces[0, 0], ref["traces"]) < gate
     if prec == L.LAG_FP64:
         assert np.abs(its[0] - ref["iters"]).max() <= 1
+
+
+def test_acoustic_shot_mixed_autotuned(ctx):
+    # the autotuned mixed path (partition count and bf16 product count picked by timing) still
+    # meets the mixed-path gate against the oracle
+    s = inputs.random_layered(nx=160, nz=96, hx=10.0, n_harm=10, sources=[(40, 3), (120, 50)], f0=12.0)
+    s.receivers = s.receivers[:10]
+    traces, _ = _run_shot(ctx, s, L.LAG_MIXED, TOLMX, tune=1)
+    for i, src in enumerate(s.sources):
+        ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, src, s.receivers, s.t_out,
+                                  s.f0, s.t0, tol=TOLMX)
+        assert rel_l2(traces[i, 0], ref["traces"]) < GATEMX
 
 
 def test_acoustic_shot_multi_source_ragged(ctx):
