@@ -172,6 +172,11 @@ int  lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_out, int *pr
                           double *ms_per_apply_out);
 /* plan facts: partitions P, partition length L, modes per CTA of the tridiagonal kernel */
 int  lag_precond_info(const lag_precond *p, int *partitions, int *part_len, int *modes_per_cta);
+/* Waits for the context's stream, then reports the plan's device error word: LAG_OK, or
+ * LAG_ETIMEDOUT when a bounded pipeline wait inside the tensor-core DST gave up since the plan was
+ * created (sticky; that apply's output is invalid and the plan should be rebuilt).  Krylov solves
+ * and shots read the same word after every chunk of iterations and fail with LAG_ETIMEDOUT. */
+int  lag_precond_status(lag_precond *p);
 
 /* ---------------------------------------------------------------- medium and operator
  * Acoustic (Sec. 2.3, Eqs. 16-18, Cartesian SPD form): face coefficient = mean of the two nodal
@@ -237,6 +242,14 @@ const double *lag_shot_field(const lag_shot *sh);
 /* copy the latest solved harmonic into out_dev ([nsrc][ncomp][nz][nx], device); blocking */
 int  lag_shot_copy_field(lag_shot *sh, double *out_dev);
 int  lag_shot_stats(const lag_shot *sh, lag_stats *st);
+/* Checkpoint between harmonics (no counterpart in the paper): the state after harmonic m is m, the
+ * two history sums of every source, the receiver values of harmonics < m and the statistics.
+ * checkpoint copies it into host_buf (lag_shot_checkpoint_size bytes, blocking); restore loads it
+ * into a shot created from the same inputs, which then continues with identical arithmetic
+ * (a resumed run equals an uninterrupted one bit for bit).  LAG_EINVAL on a size/shape mismatch. */
+size_t lag_shot_checkpoint_size(const lag_shot *sh);
+int  lag_shot_checkpoint(lag_shot *sh, void *host_buf, size_t bytes);
+int  lag_shot_restore(lag_shot *sh, const void *host_buf, size_t bytes);
 
 /* Whole shot in one call: create, step all harmonics, copy traces, destroy.  Blocking.
  * traces_host[nsrc][nrcv][nt] (acoustic) or [nsrc][2][nrcv][nt] (elastic). */
@@ -277,6 +290,12 @@ typedef struct {
   long long total_iters;
   size_t device_bytes;         /* device memory the request held                           */
 } lag_result;
+
+/* Failure-detection self-test (no counterpart in the paper): launches one kernel that waits on an
+ * mbarrier nothing arrives on, for at most `polls` polls (about 1 us each), and returns
+ * LAG_ETIMEDOUT when the bounded wait gives up; the context stays usable.  Every wait in the
+ * library's kernels is bounded the same way and reports through an error word. */
+int lag_selftest_wait_timeout(lag_ctx *ctx, long long polls);
 
 int lag_serve_start(lag_ctx *ctx, int max_active);   /* starts the scheduler thread       */
 int lag_serve_stop(lag_ctx *ctx);                    /* drains nothing: cancels the rest  */

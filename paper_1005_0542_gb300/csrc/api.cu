@@ -273,6 +273,19 @@ void lag_precond_destroy(lag_precond *p) {
   delete p;
 }
 
+int lag_precond_status(lag_precond *p) {
+  if (!p) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    LAG_CUDA_CHECK(cudaStreamSynchronize(p->ctx->stream));
+    if (!p->use_tc || p->dst.tc_err == nullptr) return;
+    int h = 0;
+    LAG_CUDA_CHECK(cudaMemcpy(&h, p->dst.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0)
+      throw Error(LAG_ETIMEDOUT, "tensor-core DST: a bounded pipeline wait gave up (code " + std::to_string(h) + ")");
+  });
+}
+
 int lag_precond_apply(lag_precond *p, const double *r, double *z, int nrhs) {
   if (!p || nrhs < 0 || (nrhs > 0 && (!r || !z))) return LAG_EINVAL;
   return guarded(p->ctx, [&] {

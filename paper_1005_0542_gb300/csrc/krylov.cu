@@ -101,8 +101,9 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
     gdev.y = gdev.g + (size_t)nrhs * (k + 1);
     gdev.hcol = gdev.y + (size_t)nrhs * k;
   }
-  LAG_CUDA_CHECK(cudaMallocHost(&hsc, (size_t)nrhs * sizeof(KrylovScalars)));
-  std::memset(hsc, 0, (size_t)nrhs * sizeof(KrylovScalars));
+  // pinned mirror: the scalars, then the error words of the two plans' tensor-core kernels
+  LAG_CUDA_CHECK(cudaMallocHost(&hsc, (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int)));
+  std::memset(hsc, 0, (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int));
   LAG_CUDA_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
 }
 
@@ -166,10 +167,19 @@ void KrylovWork::enqueue_chunk() {
     }
     iters_this_solve += chunk;
   }
+  mirror_state();
+  if (chunk < 16) chunk *= 2;
+}
+
+void KrylovWork::mirror_state() {
   LAG_CUDA_CHECK(cudaMemcpyAsync(hsc, sc(), (size_t)nrhs * sizeof(KrylovScalars), cudaMemcpyDeviceToHost, stream));
+  int *herr = reinterpret_cast<int *>(hsc + nrhs);
+  const lag_precond *pl[2] = {p1, p2};
+  for (int i = 0; i < 2; ++i)
+    if (pl[i] != nullptr && pl[i]->use_tc && pl[i]->dst.tc_err != nullptr)
+      LAG_CUDA_CHECK(cudaMemcpyAsync(herr + i, pl[i]->dst.tc_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
   LAG_CUDA_CHECK(cudaEventRecord(ev, stream));
   pending = true;
-  if (chunk < 16) chunk *= 2;
 }
 
 int KrylovWork::poll(bool block) {
@@ -182,6 +192,10 @@ int KrylovWork::poll(bool block) {
       LAG_CUDA_CHECK(e);
     }
     pending = false;
+    const int *herr = reinterpret_cast<const int *>(hsc + nrhs);
+    if (herr[0] != 0 || herr[1] != 0)
+      throw Error(LAG_ETIMEDOUT, "tensor-core DST: a bounded pipeline wait gave up (code " +
+                                     std::to_string(herr[0] ? herr[0] : herr[1]) + "); the preconditioner output is invalid");
   }
   bool any_run = false, any_met = false;
   for (int i = 0; i < nrhs; ++i) {
@@ -195,9 +209,7 @@ int KrylovWork::poll(bool block) {
     // recheck the true residual; after the recheck no system is left in ST_MET
     if (cycle_open) gmres_end_cycle();
     gmres_begin_cycle(false);
-    LAG_CUDA_CHECK(cudaMemcpyAsync(hsc, sc(), (size_t)nrhs * sizeof(KrylovScalars), cudaMemcpyDeviceToHost, stream));
-    LAG_CUDA_CHECK(cudaEventRecord(ev, stream));
-    pending = true;
+    mirror_state();
     return poll(block);
   }
   cycle_open = false;  // systems stop only at a cycle start: no update is pending

@@ -66,6 +66,7 @@ struct KrylovWork {
 
  private:
   void pcg_iteration();
+  void mirror_state();        // async copy of the scalars and the plans' error words + event
   void gmres_begin_cycle(bool first);
   void gmres_step();
   void gmres_end_cycle();

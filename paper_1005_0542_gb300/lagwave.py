@@ -115,6 +115,11 @@ _PROTOS = {
     "lag_shot_field": (VP, [VP]),
     "lag_shot_copy_field": (I, [VP, VP]),
     "lag_shot_stats": (I, [VP, C.POINTER(lag_stats)]),
+    "lag_precond_status": (I, [VP]),
+    "lag_shot_checkpoint_size": (C.c_size_t, [VP]),
+    "lag_shot_checkpoint": (I, [VP, VP, C.c_size_t]),
+    "lag_shot_restore": (I, [VP, VP, C.c_size_t]),
+    "lag_selftest_wait_timeout": (I, [VP, C.c_longlong]),
     "lag_solve_acoustic": (I, [VP, C.POINTER(lag_grid), PD, PD, C.POINTER(lag_laguerre), C.POINTER(lag_solver),
                                C.POINTER(lag_wavelet), I, C.POINTER(lag_point), I, C.POINTER(lag_point), I, PD, PD,
                                C.POINTER(lag_stats)]),

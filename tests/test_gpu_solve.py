@@ -128,8 +128,12 @@ def test_acoustic_shot_two_layer_full(ctx, prec, tol, gate):
 
 def test_acoustic_shot_mixed_autotuned(ctx):
     # the autotuned mixed path (partition count and bf16 product count picked by timing) still
-    # meets the mixed-path gate against the oracle
-    s = inputs.random_layered(nx=160, nz=96, hx=10.0, n_harm=10, sources=[(40, 3), (120, 50)], f0=12.0)
+    # meets the mixed-path gate against the oracle.  Both sources lie within a few cells of the
+    # receiver row: the Laguerre harmonics decay exponentially away from a source (the mass term
+    # rho h^2 / 4 of Eq. 9), and at receivers where they have fallen below the solver tolerance
+    # times their peak (1e-10 for a source 48 cells deeper) two solutions that both meet the
+    # tolerance differ in every digit there.
+    s = inputs.random_layered(nx=160, nz=96, hx=10.0, n_harm=10, sources=[(40, 3), (12, 8)], f0=12.0)
     s.receivers = s.receivers[:10]
     traces, _ = _run_shot(ctx, s, L.LAG_MIXED, TOLMX, tune=1)
     for i, src in enumerate(s.sources):
