@@ -28,8 +28,13 @@ struct Error : public std::runtime_error {
 #define LAG_LAUNCH_CHECK() LAG_CUDA_CHECK(cudaGetLastError())
 
 // Count of the library's kernel launches (process-wide, for launch accounting).
+// While a thread captures a CUDA graph its launches are not counted (the graph's kernel nodes
+// are counted at every replay instead).
 extern unsigned long long g_launches;
-inline void count_launch(int n = 1) { __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+extern thread_local bool g_capturing;
+inline void count_launch(int n = 1) {
+  if (!g_capturing) __atomic_add_fetch(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED);
+}
 
 // ------------------------------------------------------------------ Krylov scalars
 // One record per right-hand side, resident on the device.  Kernels read alpha/beta from here

@@ -36,6 +36,7 @@ double now_seconds();
 enum KClass { KC_DST64 = 0, KC_DST32_FWD, KC_DST32_INV, KC_DSTTC_FWD, KC_DSTTC_INV, KC_TRI64, KC_TRI32,
               KC_STENCIL_A, KC_STENCIL_E, KC_VEC, KC_LAGUERRE, KC_GMRES, KC_SETUP, NK_CLASSES };
 const char *kclass_name(int c);
+bool profiling_on();  // kernel-class timing enabled (no graph capture then: events are per launch)
 // Records a CUDA event pair around the launches in its scope when profiling is enabled.
 struct ProfScope {
   int cls;

@@ -12,6 +12,7 @@
 namespace lag {
 
 unsigned long long g_launches = 0;
+thread_local bool g_capturing = false;
 
 // ------------------------------------------------------------------------------ medium
 __global__ void acoustic_coef_kernel(const double *__restrict__ c, const double *__restrict__ rho, int nx, int nz,

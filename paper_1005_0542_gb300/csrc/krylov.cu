@@ -65,11 +65,19 @@ void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, doub
 
 KrylovWork::~KrylovWork() {
   if (hsc) cudaFreeHost(hsc);
+  for (auto &g : gexec)
+    if (g) cudaGraphExecDestroy(g);
   if (ev) cudaEventDestroy(ev);
 }
 
 void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond *q2, const lag_solver &sol,
                        int nr, cudaStream_t st) {
+  for (auto &g : gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  eager_done = false;
   ctx = c;
   m = med;
   p1 = q1;
@@ -155,9 +163,60 @@ void KrylovWork::pcg_iteration() {
   pcg_update_p(p, z, n, nrhs, sc(), stream);                         // p = z + beta p
 }
 
+static bool graphs_disabled() {
+  const char *e = std::getenv("LAGWAVE_GRAPHS");
+  return e != nullptr && e[0] == '0';
+}
+
+void KrylovWork::pcg_chunk(int iters) {
+  int idx = 0;
+  while ((1 << idx) < iters && idx < 4) ++idx;
+  // the first chunk runs eagerly: it also performs the one-time kernel attribute setup, which
+  // must not happen inside a capture
+  // (the legacy default stream cannot be captured)
+  const bool capturable = stream != nullptr && stream != cudaStreamLegacy && stream != cudaStreamPerThread;
+  if (!eager_done || (1 << idx) != iters || !capturable || profiling_on() || graphs_disabled()) {
+    for (int i = 0; i < iters; ++i) pcg_iteration();
+    eager_done = true;
+    return;
+  }
+  if (p1->use_tc) p1->ensure_scratch(nrhs);
+  const void *key[3] = {p1->scratch.ptr, p1->tc_scratch.ptr, vecs.ptr};
+  const int prod = p1->dst.tc_products;
+  if (gexec[idx] != nullptr && (std::memcmp(key, gkey[idx], sizeof(key)) != 0 || prod != gprod[idx])) {
+    cudaGraphExecDestroy(gexec[idx]);
+    gexec[idx] = nullptr;
+  }
+  if (gexec[idx] == nullptr) {
+    cudaGraph_t g = nullptr;
+    LAG_CUDA_CHECK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    try {
+      for (int i = 0; i < iters; ++i) pcg_iteration();
+    } catch (...) {
+      g_capturing = false;
+      cudaStreamEndCapture(stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    g_capturing = false;
+    LAG_CUDA_CHECK(cudaStreamEndCapture(stream, &g));
+    size_t nodes = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nodes);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec[idx], g, 0);
+    cudaGraphDestroy(g);
+    LAG_CUDA_CHECK(e);
+    gnodes[idx] = nodes;
+    std::memcpy(gkey[idx], key, sizeof(key));
+    gprod[idx] = prod;
+  }
+  LAG_CUDA_CHECK(cudaGraphLaunch(gexec[idx], stream));
+  count_launch((int)gnodes[idx]);
+}
+
 void KrylovWork::enqueue_chunk() {
   if (!elastic) {
-    for (int i = 0; i < chunk; ++i) pcg_iteration();
+    pcg_chunk(chunk);
     iters_this_solve += chunk;
   } else {
     for (int i = 0; i < chunk; ++i) {

@@ -29,6 +29,8 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+bool profiling_on() { return g_on; }
+
 const char *kclass_name(int c) {
   static const char *names[NK_CLASSES] = {"dst_f64", "dst_f32_fwd", "dst_f32_inv", "dst_tc_fwd", "dst_tc_inv",
                                           "tri_f64", "tri_f32", "stencil_acoustic", "stencil_elastic",

@@ -42,6 +42,13 @@ struct KrylovWork {
   int gj = 0, gk = 0;
   bool cycle_open = false;
   GmresDev gdev{};
+  // CUDA graphs of PCG chunks (1, 2, 4, 8, 16 iterations), replayed instead of launching each
+  // kernel; captured again when a pointer or the DST product count they baked in changes
+  cudaGraphExec_t gexec[5] = {};
+  unsigned long long gnodes[5] = {};
+  const void *gkey[5][3] = {};
+  int gprod[5] = {};
+  bool eager_done = false;
 
   ~KrylovWork();
   void setup(lag_ctx *ctx, lag_medium *m, lag_precond *p1, lag_precond *p2, const lag_solver &s, int nrhs,
@@ -66,6 +73,7 @@ struct KrylovWork {
 
  private:
   void pcg_iteration();
+  void pcg_chunk(int iters);  // iters PCG iterations, through a replayed graph where possible
   void mirror_state();        // async copy of the scalars and the plans' error words + event
   void gmres_begin_cycle(bool first);
   void gmres_step();
