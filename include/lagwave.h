@@ -162,14 +162,22 @@ int  lag_precond_set_dst_products(lag_precond *p, int products);
  * context's stream. */
 int  lag_precond_apply_static(lag_precond *p, const double *r_dev, double *z_dev, int nrhs);
 size_t lag_precond_static_capacity(void);
-/* Autotuner (no counterpart in the paper; the tuning choices of this implementation): times the
- * tridiagonal partition counts 8, 16 and 32 and, on mixed plans with the tensor-core DST, the bf16
- * product counts 3, 2 and 1 on nrhs seeded right-hand sides (a few applies each, CUDA events on the
- * context's stream), keeps the fastest (a product count only if its result is within 2e-2 relative
- * L2 of the 3-product split) and leaves the plan configured with it.  Blocking; allocates
- * 3 nrhs nz nx float64 scratch values for the duration of the call. */
-int  lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_out, int *products_out,
-                          double *ms_per_apply_out);
+/* Layout of the partitioned tridiagonal solve (Sec. 1; partitions are the paper's subdomains, here
+ * threads of one CTA): partitions 1..32 (0 = automatic, the largest count with >= 2 rows each) and
+ * the register kernel's mode tile, the x-modes one CTA solves together (float32 plans 8, 16, 32
+ * (the last only with partition length <= 32), float64 plans 4, 8; 0 = default 16 / 4).  Rebuilds
+ * the factors (blocking).  LAG_EINVAL for values outside those sets or a tile the layout cannot
+ * use (partition length > 64, which takes the shared-memory kernel). */
+int  lag_precond_set_layout(lag_precond *p, int partitions, int modes_per_cta);
+/* Autotuner (no counterpart in the paper; the tuning choices of this implementation): times every
+ * (partition count 8, 16, 32) x (mode tile, see lag_precond_set_layout) layout of the tridiagonal
+ * solve and, on mixed plans with the tensor-core DST, the bf16 product counts 3, 2 and 1 on nrhs
+ * seeded right-hand sides (a few applies each, CUDA events on the context's stream), keeps the
+ * fastest (a product count only if its result is within 2e-2 relative L2 of the 3-product split)
+ * and leaves the plan configured with it.  Blocking; allocates 3 nrhs nz nx float64 scratch values
+ * for the duration of the call.  Outputs may be NULL. */
+int  lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_out, int *modes_per_cta_out,
+                          int *products_out, double *ms_per_apply_out);
 /* plan facts: partitions P, partition length L, modes per CTA of the tridiagonal kernel */
 int  lag_precond_info(const lag_precond *p, int *partitions, int *part_len, int *modes_per_cta);
 /* Waits for the context's stream, then reports the plan's device error word: LAG_OK, or

@@ -371,6 +371,23 @@ int lag_precond_info(const lag_precond *p, int *P, int *L, int *mt) {
 
 int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? (p->use_tc ? 1 : 0) : 0; }
 
+int lag_precond_set_layout(lag_precond *p, int partitions, int modes_per_cta) {
+  if (!p || partitions < 0 || partitions > 32 || modes_per_cta < 0) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    const int eb = (p->prec == LAG_FP64) ? 8 : 4;
+    TriFactors probe;
+    probe.nx = p->grid.nx;
+    probe.nz = p->grid.nz;
+    tri_choose_layout(probe, eb, partitions, 0);
+    if (modes_per_cta != 0 && (!probe.reg || !tri_mode_tile_ok(eb, probe.L, modes_per_cta)))
+      throw Error(LAG_EINVAL, "mode tile not available for this layout (float32: 8, 16, 32 (L <= 32); "
+                              "float64: 4, 8; register kernel only)");
+    LAG_CUDA_CHECK(cudaStreamSynchronize(p->ctx->stream));
+    precond_rebuild_tri(p, partitions, modes_per_cta, p->ctx->stream);
+  });
+}
+
 int lag_precond_set_dst_products(lag_precond *p, int products) {
   if (!p || products < 1 || products > 3) return LAG_EINVAL;
   if (!p->use_tc) return products == 3 ? LAG_OK : LAG_EINVAL;

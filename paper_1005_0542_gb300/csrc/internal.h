@@ -78,7 +78,8 @@ struct TriFactors {
   void *red = nullptr;  // [j][nf][32]
 };
 
-void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P);
+void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt = 0);
+bool tri_mode_tile_ok(int elem_bytes, int L, int mt);
 // Build float64 factors of T_j = tridiag(off, 2 az/dz^2 + ax lambda_j + d, off) on the device.
 // perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra)
 void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
@@ -184,6 +185,9 @@ void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs
 // build a medium / a separable preconditioner plan on stream s (blocking)
 lag_medium *medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const double *vs,
                        const double *rho, double h, cudaStream_t s);
+// rebuild the tridiagonal factors with another partition count / register-kernel mode tile
+// (0 = automatic); used by lag_precond_set_layout and the autotuner
+void precond_rebuild_tri(lag_precond *p, int want_P, int want_mt, cudaStream_t s);
 lag_precond *precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
                          int partitions, cudaStream_t s);
 // mode 0: q = Ap only; mode 1: also (p,q) -> alpha = rz/pq  (PCG)

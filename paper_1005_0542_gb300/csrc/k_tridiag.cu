@@ -26,7 +26,12 @@
 namespace lag {
 
 // ------------------------------------------------------------------------------ layout
-void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
+bool tri_mode_tile_ok(int elem_bytes, int L, int mt) {
+  if (elem_bytes == 4) return (mt == 8 || mt == 16 || (mt == 32 && L <= 32));
+  return (mt == 4 || mt == 8);
+}
+
+void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt) {
   const int nz = tf.nz;
   int Pt = (want_P > 0) ? std::min(want_P, 32) : 32;
   while (Pt > 1 && nz / Pt < 2) Pt /= 2;  // at least 2 rows per partition
@@ -54,8 +59,12 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P) {
   auto threads = [&](int m) { return ((m * P + 31) / 32) * 32; };
   tf.reg = (L >= 2 && L <= 64 && (elem_bytes == 4 || L <= 32));
   if (tf.reg) {
-    // register kernel: a row segment of mt modes is 32 bytes (one sector)
-    const int mt = 32 / elem_bytes;  // fixed: the kernel's mode tile is a compile-time constant
+    // register kernel: the mode tile (a compile-time constant of the kernel) sets the bytes a warp
+    // reads per row and instruction: float32 8 / 16 / 32 modes (32 / 64 / 128 bytes, a warp covering
+    // 4 / 2 / 1 partitions), float64 4 / 8 modes.  Default 16 (float32) and 4 (float64, bound by the
+    // FP64 pipe rather than the loads); the autotuner times the others.
+    int mt = (elem_bytes == 4) ? 16 : 4;
+    if (want_mt > 0 && tri_mode_tile_ok(elem_bytes, L, want_mt)) mt = want_mt;
     tf.mt = mt;
     tf.threads = threads(mt);
     tf.smem = (size_t)(5 * 3 * L * mt + (3 * 32 + 33) * mt) * elem_bytes;
@@ -370,12 +379,22 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
 
 // Register-resident variant (partition length L a compile-time power of two): thread (c, p) keeps
 // the L values of its partition in registers, loaded straight from global memory (a warp reads
-// rows of MT consecutive modes: whole 32-byte sectors) and stored back the same way; the factors
+// rows of MT consecutive modes: whole 32-byte sectors, 64 bytes per row for float32) and stored
+// back the same way; the factors
 // of the CTA's modes (3 classes x L rows) are staged once in shared memory and reused for the
 // `per_cta` right-hand sides the CTA solves in turn; only the separator ends and the separator
 // solution pass through shared memory.
+// occupancy target of the register kernel: 64 (float32) / 128 (float64) registers a thread at
+// L <= 32, twice that at L = 64
 template <typename T, int L, int MT>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, (L >= 64 ? 2 : 4)) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
+struct RegBounds {
+  static constexpr int threads = MT * 32;
+  static constexpr int per_sm = (sizeof(T) == 8 ? 512 : 1024) / (L >= 64 ? 2 : 1);
+  static constexpr int blocks = per_sm / threads > 0 ? per_sm / threads : 1;
+};
+
+template <typename T, int L, int MT>
+__global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, MT>::blocks) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
                                                                int nx, int P, int levels, int nf,
                                                                const T *__restrict__ fm, const T *__restrict__ fc,
                                                                const T *__restrict__ fa, const T *__restrict__ sv,
@@ -491,10 +510,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 128 : 256, (L >= 64 ? 2 : 4))
   }
 }
 
-template <typename T, int L>
-static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc, cudaStream_t s,
-                           int pstride, int poff, int ncomp) {
-  constexpr int MT = 32 / (int)sizeof(T);
+template <typename T, int L, int MT>
+static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
+                              cudaStream_t s, int pstride, int poff, int ncomp) {
   static bool attr_done = false;
   if (!attr_done) {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -509,6 +527,23 @@ static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, con
   tri_solve_reg_kernel<T, L, MT><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc, (const T *)tf.fa,
       (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, nrhs, per_cta);
+}
+
+template <typename T, int L>
+static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc, cudaStream_t s,
+                           int pstride, int poff, int ncomp) {
+  if constexpr (sizeof(T) == 4) {
+    if (tf.mt == 8) tri_reg_launch_mt<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    else if constexpr (L <= 32) {
+      if (tf.mt == 32) tri_reg_launch_mt<T, L, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+      else tri_reg_launch_mt<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    } else {
+      tri_reg_launch_mt<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    }
+  } else {
+    if (tf.mt == 8) tri_reg_launch_mt<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    else tri_reg_launch_mt<T, L, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+  }
 }
 
 template <typename T>

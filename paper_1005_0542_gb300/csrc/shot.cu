@@ -74,7 +74,7 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
   if (s.tune) {  // the autotuner issues on the context stream: the plans are complete already
     for (lag_precond *q : {sh->p1, sh->p2}) {
       if (q == nullptr) continue;
-      const int rc = lag_precond_autotune(q, nsrc * sh->ncomp, nullptr, nullptr, nullptr);
+      const int rc = lag_precond_autotune(q, nsrc * sh->ncomp, nullptr, nullptr, nullptr, nullptr);
       if (rc != LAG_OK) throw Error(rc, std::string("autotune: ") + ctx->last_error);
     }
   }

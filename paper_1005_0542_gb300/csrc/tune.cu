@@ -1,5 +1,5 @@
-// Autotuner of a preconditioner plan: partition count of the tridiagonal solve and, on mixed plans,
-// the number of bf16 products of the tensor-core DST.  Each candidate is timed with CUDA events on
+// Autotuner of a preconditioner plan: partition count and mode tile of the tridiagonal solve and,
+// on mixed plans, the number of bf16 products of the tensor-core DST.  Each candidate is timed with CUDA events on
 // the context's stream over a few applies to nrhs seeded right-hand sides; a product count is kept
 // only if its result stays within 2e-2 (relative L2) of the 3-product split, i.e. the
 // preconditioner remains the same operator up to bf16 rounding.
@@ -54,18 +54,18 @@ static float time_applies(lag_precond *p, const double *r, double *z, int nrhs, 
   return ms / reps;
 }
 
-static void rebuild_tri(lag_precond *p, int want_P, cudaStream_t s) {
+void precond_rebuild_tri(lag_precond *p, int want_P, int want_mt, cudaStream_t s) {
   TriFactors t64;
   t64.nx = p->grid.nx;
   t64.nz = p->grid.nz;
-  tri_choose_layout(t64, 8, want_P);
+  tri_choose_layout(t64, 8, want_P, p->prec == LAG_FP64 ? want_mt : 0);
   tri_build_factors(t64, p->tri_store, p->ax, p->az, p->d, p->grid.dx, p->grid.dz, s);
   p->tri64 = t64;
   if (p->prec == LAG_MIXED) {
     TriFactors t32;
     t32.nx = p->grid.nx;
     t32.nz = p->grid.nz;
-    tri_choose_layout(t32, 4, want_P);
+    tri_choose_layout(t32, 4, want_P, want_mt);
     if (p->use_tc) {
       TriFactors tp = t64;
       DevBuf tmp;
@@ -85,7 +85,8 @@ static void rebuild_tri(lag_precond *p, int want_P, cudaStream_t s) {
 
 using namespace lag;
 
-extern "C" int lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_out, int *products_out, double *ms_out) {
+extern "C" int lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_out, int *mt_out, int *products_out,
+                                    double *ms_out) {
   if (!p || nrhs < 1) return LAG_EINVAL;
   try {
     LAG_CUDA_CHECK(cudaSetDevice(p->ctx->device));
@@ -98,20 +99,29 @@ extern "C" int lag_precond_autotune(lag_precond *p, int nrhs, int *partitions_ou
     count_launch();
     LAG_LAUNCH_CHECK();
     const int reps = 3;
-    // 1. partition count
-    int bestP = p->prec == LAG_FP64 ? p->tri64.P : p->tri32.P;
+    // 1. partition count x mode tile of the register kernel (float32 8 / 16 / 32 modes per CTA,
+    //    float64 4 / 8; a layout that falls back to the shared-memory kernel ignores the tile)
+    const bool f64 = p->prec == LAG_FP64;
+    const std::vector<int> tiles = f64 ? std::vector<int>{4, 8} : std::vector<int>{8, 16, 32};
     float best = 1e30f;
-    int bestWant = 32;
+    int bestWant = 32, bestMt = 0;
     for (int want : {8, 16, 32}) {
-      rebuild_tri(p, want, s);
-      const float ms = time_applies(p, r, z, nrhs, reps);
-      if (ms < best) {
-        best = ms;
-        bestWant = want;
+      for (int mt : tiles) {
+        precond_rebuild_tri(p, want, mt, s);
+        const TriFactors &t = f64 ? p->tri64 : p->tri32;
+        if (t.reg && t.mt != mt) continue;  // tile not available at this partition length
+        if (!t.reg && mt != tiles[0]) continue;  // the shared-memory kernel: time once per count
+        const float ms = time_applies(p, r, z, nrhs, reps);
+        if (ms < best) {
+          best = ms;
+          bestWant = want;
+          bestMt = mt;
+        }
       }
     }
-    rebuild_tri(p, bestWant, s);
-    bestP = p->prec == LAG_FP64 ? p->tri64.P : p->tri32.P;
+    precond_rebuild_tri(p, bestWant, bestMt, s);
+    const int bestP = f64 ? p->tri64.P : p->tri32.P;
+    if (mt_out) *mt_out = f64 ? p->tri64.mt : p->tri32.mt;
     // 2. bf16 products of the tensor-core DST (quality-checked against the split)
     int bestK = p->use_tc ? p->dst.tc_products : 3;
     if (p->use_tc) {

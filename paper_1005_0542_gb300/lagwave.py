@@ -91,7 +91,8 @@ _PROTOS = {
     "lag_precond_apply_static": (I, [VP, VP, VP, I]),
     "lag_precond_static_capacity": (C.c_size_t, []),
     "lag_precond_info": (I, [VP, PI, PI, PI]),
-    "lag_precond_autotune": (I, [VP, I, PI, PI, PD]),
+    "lag_precond_autotune": (I, [VP, I, PI, PI, PI, PD]),
+    "lag_precond_set_layout": (I, [VP, I, I]),
     "lag_precond_uses_tensor_cores": (I, [VP]),
     "lag_precond_set_dst_products": (I, [VP, I]),
     "lag_medium_create_acoustic": (I, [VP, C.POINTER(lag_grid), PD, PD, D, C.POINTER(VP)]),

@@ -215,10 +215,10 @@ def test_autotune_keeps_a_valid_preconditioner(ctx):
     nx, nz, nrhs = 512, 256, 4
     args = (nx, nz, 5.0, 5.0, 2.0e10, 2.0e10, 1.0e7)
     p = plan(ctx, *args, prec=L.LAG_MIXED)
-    P, K, ms = C.c_int(), C.c_int(), C.c_double()
-    L.check(L.lag_precond_autotune(p, nrhs, C.byref(P), C.byref(K), C.byref(ms)), ctx)
+    P, MT, K, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+    L.check(L.lag_precond_autotune(p, nrhs, C.byref(P), C.byref(MT), C.byref(K), C.byref(ms)), ctx)
     assert 1 <= P.value <= 32 and K.value in (1, 2, 3) and ms.value > 0
-    assert plan_info(p)[0] == P.value
+    assert plan_info(p)[0] == P.value and plan_info(p)[2] == MT.value
     r = RNG.standard_normal((2, nz, nx))
     rd, zd = dev(r), empty(r.shape)
     L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
@@ -226,8 +226,45 @@ def test_autotune_keeps_a_valid_preconditioner(ctx):
     assert rel(host(zd), opre.apply_inverse(r, *args[2:])) < tol
     L.lag_precond_destroy(p)
     q = plan(ctx, *args, prec=L.LAG_FP64)
-    L.check(L.lag_precond_autotune(q, nrhs, C.byref(P), C.byref(K), C.byref(ms)), ctx)
-    assert K.value == 3
+    L.check(L.lag_precond_autotune(q, nrhs, C.byref(P), C.byref(MT), C.byref(K), C.byref(ms)), ctx)
+    assert K.value == 3 and plan_info(q)[2] == MT.value
     L.check(L.lag_precond_apply(q, ptr(rd), ptr(zd), 2), ctx)
     assert rel(host(zd), opre.apply_inverse(r, *args[2:])) < TOL64
     L.lag_precond_destroy(q)
+
+
+@pytest.mark.parametrize("prec", [L.LAG_FP64, L.LAG_MIXED])
+def test_every_layout_of_the_tridiagonal_solve(ctx, prec):
+    # every (partition count, mode tile) the register kernel offers solves the same systems
+    # (ragged nx so the last mode tile is partial, ragged nz so the last partition is padded)
+    nx, nz, nrhs = 75, 100, 3
+    dx, dz, ax, az, d = 5.0, 4.0, 2.0e10, 1.5e10, 1.0e7
+    p = plan(ctx, nx, nz, dx, dz, ax, az, d, prec=prec)
+    f64 = prec == L.LAG_FP64
+    tiles = (4, 8) if f64 else (8, 16, 32)
+    rhs = RNG.standard_normal((nrhs, nz, nx))
+    diag = opre.mode_diagonals(nx, dx, dz, ax, az, d)
+    off = -az / dz ** 2
+    ref = np.moveaxis(thomas(off, diag, off, np.moveaxis(rhs, 1, 0)), 0, 1)
+    t = torch()
+    seen = set()
+    for parts in (4, 8, 16, 32):          # nz = 100: (P, L) = (4, 32), (7, 16), (13, 8), (25, 4)
+        for mt in tiles:
+            L.check(L.lag_precond_set_layout(p, parts, mt), ctx)
+            P, Lp, got_mt = plan_info(p)
+            assert got_mt == mt and P * Lp >= nz
+            seen.add((P, mt))
+            if f64:
+                dd, yd = dev(rhs), empty(rhs.shape)
+                L.check(L.lag_precond_tridiag(p, ptr(dd), ptr(yd), nrhs), ctx)
+                assert rel(host(yd), ref) < 1e-13
+            else:
+                dd = dev(rhs.astype(np.float32))
+                yd = t.empty(rhs.shape, dtype=t.float32, device="cuda")
+                L.check(L.lag_precond_tridiag_f32(p, ptr(dd), ptr(yd), nrhs), ctx)
+                assert rel(host(yd), ref) < 2e-5
+    assert len(seen) == 4 * len(tiles)
+    assert L.lag_precond_set_layout(p, 8, 12) == L.LAG_EINVAL     # not a tile of the kernel
+    assert L.lag_precond_set_layout(p, 1, 8) == L.LAG_EINVAL      # L = 128: shared-memory kernel
+    assert L.lag_precond_set_layout(p, 33, 0) == L.LAG_EINVAL     # more partitions than lanes
+    L.lag_precond_destroy(p)
