@@ -139,8 +139,15 @@ int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, i
  * float32 in, float64 out).  lag_precond_dst on a mixed plan runs the forward kernel (float64 in,
  * float32 spectrum) and widens its result to float64. */
 int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int nrhs);
-/* 1 if the plan's DST runs on the tcgen05 tensor cores (mixed path), else 0 */
+/* 1 if the plan's DST runs on the tcgen05 tensor cores, else 0.  Mixed plans: split-bf16 operands,
+ * FP32 accumulation.  Float64 plans (n >= 16, ceil(n/2) <= 4224): exact slices -- each folded row
+ * and S are cut into 9 six-bit integer slices on a power-of-two grid (54 bits), the slice products
+ * are summed exactly in FP32 tensor memory (integers below 2^24) and combined in float64, so the
+ * result carries float64 rounding only (relative error < 1e-14 per row in the tests).  The
+ * environment variable LAGWAVE_DST_KERNEL=simt at plan creation selects the SIMT kernels. */
 int  lag_precond_uses_tensor_cores(const lag_precond *p);
+/* bf16 slice products the float64 tensor-core DST forms per float64 multiply-add (45) */
+int  lag_dst_f64_slice_products(void);
 /* Tensor-core DST of a mixed plan: number of bf16 products per K step (3: split hi*hi + hi*lo +
  * lo*hi, relative error ~1e-5; 2: hi*hi + lo*hi with S rounded to bf16, ~2e-3; 1: hi*hi, ~4e-3).
  * Default 3 (or the environment variable LAGWAVE_DST_PRODUCTS at plan creation).  The flexible
@@ -154,7 +161,9 @@ int  lag_precond_set_dst_products(lag_precond *p, int products);
  * cudaMalloc/cudaFree).  The intermediate spectrum lives in a file-scope static device array of
  * lag_precond_static_capacity() float64 values (2^21 = 16 MiB), which every GPU that loads the
  * library holds until the process exits; the plan is created beforehand by lag_precond_create*.
- * Float64 (LAG_FP64) plans only; nrhs * nz * nx beyond the capacity returns LAG_EINVAL with a
+ * Float64 (LAG_FP64) plans only; the DST runs on the FP64 SIMT pipes (the tensor-core float64 DST
+ * keeps operand slices in plan scratch allocated on demand), so results equal lag_precond_apply's
+ * to float64 rounding.  nrhs * nz * nx beyond the capacity returns LAG_EINVAL with a
  * message in lag_last_error.  The first call on a device looks up the array's device address once
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the one
  * array and it keeps the last call's contents (nothing in it has to start at zero): calls that

@@ -67,6 +67,9 @@ void lag_precond::ensure_scratch(int nrhs) {
   if (use_tc) {
     tc_scratch.alloc(ctx, dst_tc_scratch_bytes(dst, nrhs * grid.nz));
     dst.tc_scratch = tc_scratch.as<uint8_t>();
+  } else if (dst.oz) {
+    tc_scratch.alloc(ctx, dst_oz_scratch_bytes(dst, nrhs * grid.nz));
+    dst.tc_scratch = tc_scratch.as<uint8_t>();
   }
   scratch_rhs = nrhs;
 }
@@ -103,8 +106,9 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   p->d = d;
   p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = p->tc_scratch.ctx = ctx;
   p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
-  dst_build(p->dst, p->dst_store, g.nx, p->use_tc, s);
-  if (p->use_tc) {
+  const bool oz = (prec == LAG_FP64) && dst_oz_supported(g.nx) && !tc_disabled();
+  dst_build(p->dst, p->dst_store, g.nx, p->use_tc ? 1 : (oz ? 2 : 0), s);
+  if (p->use_tc || p->dst.oz) {
     p->dst.tc_err = reinterpret_cast<int *>(p->dst_store.as<uint8_t>() + p->dst_store.bytes - 256);
     const char *ev = std::getenv("LAGWAVE_DST_PRODUCTS");  // default split-product count
     if (ev != nullptr && (ev[0] == '1' || ev[0] == '2' || ev[0] == '3') && ev[1] == 0) p->dst.tc_products = ev[0] - '0';
@@ -278,7 +282,7 @@ int lag_precond_status(lag_precond *p) {
   return guarded(p->ctx, [&] {
     set_device(p->ctx);
     LAG_CUDA_CHECK(cudaStreamSynchronize(p->ctx->stream));
-    if (!p->use_tc || p->dst.tc_err == nullptr) return;
+    if (!(p->use_tc || p->dst.oz) || p->dst.tc_err == nullptr) return;
     int h = 0;
     LAG_CUDA_CHECK(cudaMemcpy(&h, p->dst.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h != 0)
@@ -302,6 +306,7 @@ int lag_precond_dst(lag_precond *p, const double *x, double *y, int nrhs) {
     if (nrhs == 0) return;
     const int rows = nrhs * p->grid.nz;
     if (p->prec == LAG_FP64) {
+      p->ensure_scratch(nrhs);
       dst_apply_f64(p->dst, x, y, rows, p->grid.nz, nullptr, p->ctx->stream);
     } else {  // float64 -> float32 spectrum -> float64 (both mixed-path kernels, back to back)
       p->ensure_scratch(nrhs);
@@ -369,7 +374,9 @@ int lag_precond_info(const lag_precond *p, int *P, int *L, int *mt) {
   return LAG_OK;
 }
 
-int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? (p->use_tc ? 1 : 0) : 0; }
+int lag_dst_f64_slice_products(void) { return dst_oz_products(); }
+
+int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? ((p->use_tc || p->dst.oz) ? 1 : 0) : 0; }
 
 int lag_precond_set_layout(lag_precond *p, int partitions, int modes_per_cta) {
   if (!p || partitions < 0 || partitions > 32 || modes_per_cta < 0) return LAG_EINVAL;

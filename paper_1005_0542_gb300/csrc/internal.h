@@ -112,11 +112,26 @@ struct DstPlan {
   uint8_t *tc_scratch = nullptr;
   int *tc_err = nullptr;
   int tc_products = 3;        // split products per K step: 3 (hi*hi+hi*lo+lo*hi), 2 or 1
+  // float64 path on the tensor cores (exact slices): packed B slices [2][9][n tile][k stage]
+  bool oz = false;
+  uint8_t *oz_b = nullptr;
+  size_t oz_slice_bytes = 0;
+  int oz_eB = 0;              // |S| < 2^oz_eB
 };
-void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream_t s);
+// tc_mode: 0 none, 1 split-bf16 operands (mixed path), 2 exact slices (float64 path)
+void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s);
 // Y[row][:] = S X[row][:] for `rows` rows of length n.  Input/output types as named.
 void dst_apply_f64(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
                    const KrylovScalars *sc, cudaStream_t s);
+// the same on the FP64 SIMT pipes (no scratch; the no-allocation entry point uses it)
+void dst_apply_f64_simt(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
+                        const KrylovScalars *sc, cudaStream_t s);
+// exact-slice tensor-core float64 DST (dp.oz); scratch dp.tc_scratch of dst_oz_scratch_bytes
+bool dst_oz_supported(int n);
+int dst_oz_products();  // bf16 slice products per float64 product
+size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows);
+void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
+                  const KrylovScalars *sc, cudaStream_t s);
 // mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
                        const KrylovScalars *sc, cudaStream_t s);

@@ -35,15 +35,18 @@ __global__ void dst_matrix_kernel(int n, int ku, int kv, double *su, double *sv,
 
 void dst_build_tc(DstPlan &dp, DevBuf &store, size_t offset_bytes, cudaStream_t s);
 size_t dst_tc_bytes(int n);
+void dst_build_oz(DstPlan &dp, DevBuf &store, size_t offset_bytes, cudaStream_t s);
+size_t dst_oz_bytes(int n);
 
-void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream_t s) {
+void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s) {
   dp.n = n;
   dp.ku = (n + 1) / 2;
   dp.kv = n / 2;
   const size_t nu = (size_t)dp.ku * dp.ku, nv = (size_t)dp.kv * dp.kv;
   size_t bytes = (nu + nv) * (sizeof(double) + sizeof(float)) + 256;
   const size_t tc_off = (bytes + 1023) & ~(size_t)1023;
-  if (tensor_copies) bytes = tc_off + dst_tc_bytes(n) + 256;  // + error word at the end
+  if (tc_mode == 1) bytes = tc_off + dst_tc_bytes(n) + 256;  // + error word at the end
+  if (tc_mode == 2) bytes = tc_off + dst_oz_bytes(n) + 256;
   store.alloc(store.ctx, bytes, true);
   char *base = store.as<char>();
   dp.su = reinterpret_cast<double *>(base);
@@ -54,7 +57,8 @@ void dst_build(DstPlan &dp, DevBuf &store, int n, bool tensor_copies, cudaStream
   dst_matrix_kernel<<<grid, 128, 0, s>>>(n, dp.ku, dp.kv, dp.su, dp.sv, dp.su_f, dp.sv_f);
   count_launch();
   LAG_LAUNCH_CHECK();
-  if (tensor_copies) dst_build_tc(dp, store, tc_off, s);
+  if (tc_mode == 1) dst_build_tc(dp, store, tc_off, s);
+  if (tc_mode == 2) dst_build_oz(dp, store, tc_off, s);
 }
 
 // ------------------------------------------------------------------------------ SIMT GEMM
@@ -173,9 +177,14 @@ static void dst_simt_launch(const DstPlan &dp, const TI *x, TO *y, int rows, int
   LAG_LAUNCH_CHECK();
 }
 
+void dst_apply_f64_simt(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
+                        cudaStream_t s) {
+  dst_simt_launch<double, double, double>(dp, x, y, rows, rpr, dp.su, dp.sv, sc, s, KC_DST64);
+}
 void dst_apply_f64(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
                    cudaStream_t s) {
-  dst_simt_launch<double, double, double>(dp, x, y, rows, rpr, dp.su, dp.sv, sc, s, KC_DST64);
+  if (dp.oz) dst_apply_oz(dp, x, y, rows, rpr, sc, s);
+  else dst_apply_f64_simt(dp, x, y, rows, rpr, sc, s);
 }
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rpr, const KrylovScalars *sc,
                        cudaStream_t s) {

@@ -626,4 +626,427 @@ void spectrum_unpermute_widen(const float *in, double *out, int rows, int n, int
   LAG_LAUNCH_CHECK();
 }
 
+
+// ============================================================================ exact-slice FP64 DST
+// The float64 path's transform on the same tensor cores, without rounding anything beyond what a
+// float64 GEMM rounds (the Ozaki splitting idea: exact products of short slices, summed in float64).
+//   * Every folded input row is scaled by a power of two 2^-e_r with |row| < 2^e_r and cut into
+//     OZ_S slices of OZ_B bits of its fixed-point expansion: u = 2^e_r sum_i q_i 2^(-OZ_B i) up to
+//     a truncation below 2^(e_r - OZ_S OZ_B) (54 bits); the q_i are integers |q_i| < 2^OZ_B, exact
+//     in bf16.  S is sliced the same way with one scale 2^e_B.
+//   * A pair (i, j) gives G_ij = sum_k q_i p_j: integers of magnitude < 2^(2 OZ_B) K, exactly summed
+//     by the FP32 accumulator while the total stays below 2^24.  Pairs of the same weight i + j
+//     share one accumulator in groups of at most floor(2^24 / (63^2 K)) (4 at K = 1024).
+//   * Pairs with i + j <= OZ_S + 1 are kept (the dropped ones weigh < 2^-54 of the row scale), and
+//     the epilogue adds each group as y += 2^(e_r + e_B - OZ_B (i + j)) G in float64, largest weight
+//     first, straight into the float64 output (natural mode order, as the SIMT kernel writes it).
+constexpr int OZ_B = 6;   // bits per slice
+constexpr int OZ_S = 9;   // slices per operand
+constexpr int OZ_TN = 128;                 // output columns per tile
+constexpr int OZ_BT = OZ_TN * TK * 2;      // B stage tile, 16 KB
+constexpr int OZ_STAGE = A_TILE + OZ_BT;   // 32 KB
+constexpr int OZ_NST = 6;                  // pipeline stages
+constexpr int OZ_NACC = 4;                 // tensor-memory accumulators of 128 columns
+constexpr int OZ_SMEM = OZ_NST * OZ_STAGE + 1024 + 256;
+constexpr int OZ_EXP_NAN = 0x7fffffff;     // row exponent marking a non-finite row
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+struct OzSched {
+  int npairs, ngroups;
+  int8_t si[48], sj[48], first[48], last[48];  // slice indices (1-based), group start / end flags
+  int8_t gd[48];                               // weight i + j of each group
+};
+
+// |v| < 2^e: 54-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
+__device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  const int E = (int)(bits >> 52);
+  const unsigned long long M = (bits & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
+  const int s = (E ? E : 1) - 1075 + 54 - e;  // |v| = M 2^((E ? E : 1) - 1075)
+  if (s >= 0) return M << s;                   // s <= 1 since |v| < 2^e
+  return (s <= -64) ? 0ull : (M >> (-s));
+}
+__device__ __forceinline__ uint16_t oz_slice_bits(unsigned long long T, int i, bool neg) {
+  const int q = (int)((T >> (54 - OZ_B * i)) & ((1u << OZ_B) - 1));
+  return bf16_bits(neg ? -(float)q : (float)q);
+}
+
+// B slices, once per plan: [mat 0 = S even columns, 1 = S odd columns][slice][n tile][k stage][TN x TK]
+__global__ void oz_pack_b_kernel(const double *su, const double *sv, int ku, int kv, int nks, int nnt, int eB,
+                                 uint8_t *out, size_t slice_bytes) {
+  const int which = blockIdx.z;
+  const int n = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nnt * OZ_TN || k >= nks * TK) return;
+  double v = 0.0;
+  if (which == 0) { if (n < ku && k < ku) v = su[(size_t)k * ku + n]; }
+  else if (n < kv && k < kv) v = sv[(size_t)k * kv + n];
+  const unsigned long long T = oz_fixed(v, eB);
+  const size_t tile = (size_t)(n / OZ_TN) * nks + (k / TK);
+  const uint32_t off = swz(n % OZ_TN, k % TK);
+  for (int i = 1; i <= OZ_S; ++i) {
+    uint8_t *base = out + ((size_t)which * OZ_S + (i - 1)) * slice_bytes + tile * OZ_BT;
+    *reinterpret_cast<uint16_t *>(base + off) = oz_slice_bits(T, i, v < 0.0);
+  }
+}
+
+// A slices per apply: one CTA per row, both parities.  Fold (float64), row maximum, slices.
+// Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r.
+__global__ void __launch_bounds__(128) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n, int ku, int kv,
+                                                        int nks, int nmt, uint8_t *__restrict__ out, size_t slice_bytes,
+                                                        int *__restrict__ erow, const KrylovScalars *__restrict__ sc,
+                                                        int rpr) {
+  const int row = blockIdx.x;
+  // rows of finished right-hand sides and the padding rows of the last tile pack as zeros (exact
+  // zero outputs; the GEMM may still cover them in a tile shared with running rows)
+  const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
+  const double *xr = x + (size_t)(row < rows ? row : 0) * n;
+  const bool odd_n = (n & 1) != 0;
+  auto fold = [&](int par, int j) -> double {
+    if (!live) return 0.0;
+    if (par == 0) {
+      if (j >= ku) return 0.0;
+      return (odd_n && j == ku - 1) ? xr[j] : xr[j] + xr[n - 1 - j];
+    }
+    return (j < kv) ? xr[j] - xr[n - 1 - j] : 0.0;
+  };
+  // 1. row maxima of |u| and |v|
+  // (a NaN anywhere must reach the maximum: fmax would drop it)
+  auto nanmax = [](double m, double a) { return (a > m || a != a) ? a : m; };
+  double m0 = 0.0, m1 = 0.0;
+  for (int j = threadIdx.x; j < ku; j += blockDim.x) {
+    m0 = nanmax(m0, fabs(fold(0, j)));
+    m1 = nanmax(m1, fabs(fold(1, j)));
+  }
+  __shared__ double red[2][4];
+  __shared__ int esh[2];
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = nanmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = nanmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = m0;
+    red[1][threadIdx.x >> 5] = m1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const double m = nanmax(nanmax(red[threadIdx.x][0], red[threadIdx.x][1]), nanmax(red[threadIdx.x][2], red[threadIdx.x][3]));
+    int e = 0;
+    if (!isfinite(m)) e = OZ_EXP_NAN;
+    else if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): every |value| < 2^e
+    esh[threadIdx.x] = e;
+    if (row < rows) erow[threadIdx.x * (nmt * TM) + row] = e;
+  }
+  __syncthreads();
+  // 2. slices, 8 consecutive k per 16-byte store
+  const int mt = row / TM, r = row % TM;
+  for (int ch = threadIdx.x; ch < nks * (TK / 8); ch += blockDim.x) {
+    const int k0 = ch * 8, ks = k0 / TK, kk = k0 % TK;
+    const uint32_t off = swz(r, kk);
+    for (int par = 0; par < 2; ++par) {
+      const int e = esh[par] == OZ_EXP_NAN ? 0 : esh[par];
+      unsigned long long T[8];
+      bool neg[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double v = fold(par, k0 + q);
+        T[q] = (esh[par] == OZ_EXP_NAN) ? 0ull : oz_fixed(v, e);
+        neg[q] = v < 0.0;
+      }
+#pragma unroll
+      for (int i = 1; i <= OZ_S; ++i) {
+        alignas(16) uint16_t h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] = oz_slice_bits(T[q], i, neg[q]);
+        uint8_t *tile = out + ((size_t)par * OZ_S + (i - 1)) * slice_bytes + ((size_t)mt * nks + ks) * A_TILE;
+        *reinterpret_cast<uint4 *>(tile + off) = *reinterpret_cast<const uint4 *>(h);
+      }
+    }
+  }
+}
+
+// Persistent warp-specialised GEMM over (parity, m tile, n tile) tiles and, per tile, the pair
+// schedule: warp 0 streams A_i / B_j stages, warp 1 issues the MMAs of a group into one of four
+// tensor-memory accumulators, warps 2-9 add finished groups into float64 sums held in registers
+// (warp w: rows 32 (w % 4).., columns 64 ((w - 2) / 4)..) and store the tile once at its end.
+__global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restrict__ apack, size_t a_slice_bytes,
+                                                         const uint8_t *__restrict__ bpack, size_t b_slice_bytes,
+                                                         const int *__restrict__ erow, int eB, int nks, int nmt,
+                                                         int nnt, int rows, double *__restrict__ y, int ld, int ku,
+                                                         int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
+                                                         int rpr, int *__restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + OZ_NST * OZ_STAGE;
+  const uint32_t full0 = bars, empty0 = bars + 8 * OZ_NST, tfull0 = bars + 16 * OZ_NST, tempty0 = tfull0 + 8 * OZ_NACC;
+  volatile uint32_t *holder =
+      reinterpret_cast<volatile uint32_t *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = 2 * nmt * nnt;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)holder)),
+                 "r"(OZ_NACC * OZ_TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < OZ_NST; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int a = 0; a < OZ_NACC; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 8);  // one arrive per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *holder;
+
+  auto decode = [&](int t, int &par, int &mt, int &nt) {
+    nt = t % nnt;
+    mt = (t / nnt) % nmt;
+    par = t / (nnt * nmt);
+  };
+  auto wanted = [&](int par, int mt, int nt) -> bool {
+    if (nt * OZ_TN >= (par ? kv : ku)) return false;
+    if (sc == nullptr) return true;
+    const int m0 = mt * TM;
+    const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
+    for (int r = r0; r <= r1; ++r)
+      if (sc[r].state == ST_RUN) return true;
+    return false;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int par, mt, nt;
+        decode(t, par, mt, nt);
+        if (!wanted(par, mt, nt)) continue;
+        for (int pr = 0; pr < sch.npairs && !*abort_flag; ++pr) {
+          const uint8_t *at = apack + ((size_t)par * OZ_S + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
+          const uint8_t *bt = bpack + ((size_t)par * OZ_S + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+          for (int kk = 0; kk < nks; ++kk, ++it) {
+            const int s = it % OZ_NST, use = it / OZ_NST;
+            if (it >= OZ_NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
+              atomicExch(err, 11);
+              *abort_flag = 1;
+              break;
+            }
+            const uint32_t st = base + s * OZ_STAGE;
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, OZ_STAGE);
+            bulk_g2s(st, at + (size_t)kk * A_TILE, A_TILE, fb);
+            bulk_g2s(st + A_TILE, bt + (size_t)kk * OZ_BT, OZ_BT, fb);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int it = 0, gc = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int par, mt, nt;
+        decode(t, par, mt, nt);
+        if (!wanted(par, mt, nt)) continue;
+        uint32_t d = 0;
+        for (int pr = 0; pr < sch.npairs && !*abort_flag; ++pr) {
+          if (sch.first[pr]) {
+            const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
+            if (gc >= OZ_NACC && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) {
+              atomicExch(err, 14);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            d = tmem + (uint32_t)(acc * OZ_TN);
+          }
+          for (int kk = 0; kk < nks; ++kk, ++it) {
+            const int s = it % OZ_NST, use = it / OZ_NST;
+            if (!mbar_wait(full0 + 8 * s, use & 1)) {
+              atomicExch(err, 12);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = base + s * OZ_STAGE;
+#pragma unroll
+            for (int sub = 0; sub < TK / 16; ++sub) {
+              const uint32_t o = sub * 32;
+              mma_bf16_n128(d, sdesc(st + o), sdesc(st + A_TILE + o), (sch.first[pr] && kk == 0 && sub == 0) ? 0u : 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
+                         : "memory");
+          }
+          if (sch.last[pr]) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tfull0 + 8 * (gc % OZ_NACC))
+                         : "memory");
+            ++gc;
+          }
+        }
+      }
+    }
+  } else {  // epilogue warps 2..9
+    const int lg = warp & 3, h = (warp - 2) >> 2;
+    int gc = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int par, mt, nt;
+      decode(t, par, mt, nt);
+      if (!wanted(par, mt, nt)) continue;
+      const int row = mt * TM + lg * 32 + lane;
+      const bool rok = row < rows;
+      const int e = rok ? erow[par * (nmt * TM) + row] : 0;
+      double acc64[64];
+      bool stop = false;
+      for (int g = 0; g < sch.ngroups; ++g) {
+        const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
+        const bool ok = mbar_wait(tfull0 + 8 * acc, ause & 1);
+        __syncwarp();
+        if (!ok) {
+          if (lane == 0) atomicExch(err, 13);
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
+                                               : ldexp(1.0, e + eB - OZ_B * sch.gd[g]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 32), v);
+          if (g == 0) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = scale * (double)v[q];
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = fma(scale, (double)v[q], acc64[c * 32 + q]);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * acc) : "memory");
+        ++gc;
+      }
+      if (stop) break;
+      if (rok) {
+        const int c0 = nt * OZ_TN + h * 64;
+        const int ncols = min(64, (par ? kv : ku) - c0);
+        double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+#pragma unroll
+        for (int q = 0; q < 64; ++q)
+          if (q < ncols) yp[2 * q] = acc64[q];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_NACC * OZ_TN) : "memory");
+}
+
+static OzSched oz_schedule(int kpad) {
+  OzSched s{};
+  const long long cap = (1LL << 24) / (63LL * 63LL * kpad);  // pairs per exact FP32 accumulation
+  const int gmax = (int)std::max(1LL, std::min(4LL, cap));
+  int np = 0, ng = 0;
+  for (int d = 2; d <= OZ_S + 1; ++d) {
+    int in_group = 0;
+    for (int i = 1; i <= OZ_S; ++i) {
+      const int j = d - i;
+      if (j < 1 || j > OZ_S) continue;
+      s.si[np] = (int8_t)i;
+      s.sj[np] = (int8_t)j;
+      s.first[np] = (in_group == 0);
+      if (in_group == 0) s.gd[ng++] = (int8_t)d;
+      ++in_group;
+      ++np;
+      if (in_group == gmax) {
+        s.last[np - 1] = 1;
+        in_group = 0;
+      }
+    }
+    if (in_group > 0) s.last[np - 1] = 1;
+  }
+  s.npairs = np;
+  s.ngroups = ng;
+  return s;
+}
+
+int dst_oz_products() { return oz_schedule(TK).npairs; }
+
+bool dst_oz_supported(int n) {
+  const int ku = (n + 1) / 2;
+  const int kpad = div_up(ku, TK) * TK;
+  return n >= 16 && 63LL * 63LL * kpad <= (1LL << 24);  // one pair per accumulator at least
+}
+
+size_t dst_oz_bytes(int n) {
+  const int ku = (n + 1) / 2;
+  return 2 * (size_t)OZ_S * div_up(ku, OZ_TN) * div_up(ku, TK) * OZ_BT;
+}
+
+void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
+  const int nks = div_up(dp.ku, TK), nnt = div_up(dp.ku, OZ_TN);
+  dp.kpad_u = nks;
+  dp.npad_u = nnt;
+  dp.oz_slice_bytes = (size_t)nnt * nks * OZ_BT;
+  dp.oz_b = store.as<uint8_t>() + off;
+  int eB = 0;
+  frexp(std::sqrt(2.0 / (double)(dp.n + 1)), &eB);  // every |S| <= sqrt(2 / (n + 1)) < 2^eB
+  dp.oz_eB = eB;
+  dim3 g(div_up(nks * TK, 128), nnt * OZ_TN, 2);
+  oz_pack_b_kernel<<<g, 128, 0, s>>>(dp.su, dp.sv, dp.ku, dp.kv, nks, nnt, eB, dp.oz_b, dp.oz_slice_bytes);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  dp.oz = true;
+}
+
+size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows) {
+  const size_t nmt = div_up(rows, TM);
+  return 2 * (size_t)OZ_S * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256;
+}
+
+void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
+                  cudaStream_t s) {
+  if (rows <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    attr = true;
+  }
+  ProfScope prof(KC_DST64, s);
+  const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
+  const size_t a_slice = (size_t)nmt * nks * A_TILE;
+  uint8_t *apack = dp.tc_scratch;
+  int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)OZ_S * a_slice);
+  oz_pack_a_kernel<<<nmt * TM, 128, 0, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack, a_slice, erow, sc, rpr);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  const OzSched sch = oz_schedule(nks * TK);
+  const int ntiles = 2 * nmt * nnt;
+  const int grid = std::min(ntiles, 152);
+  oz_gemm_kernel<<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, dp.oz_b, dp.oz_slice_bytes, erow, dp.oz_eB, nks, nmt, nnt,
+                                            rows, y, dp.n, dp.ku, dp.kv, sch, sc, rpr, dp.tc_err);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
 }  // namespace lag

@@ -4,9 +4,10 @@
 // with cudaMalloc.  Some callers cannot let a library allocate at call time: a host framework
 // that owns all device memory through its own allocator and forbids others, or a real-time loop
 // that must not block in cudaMalloc / cudaFree (cudaFree synchronises the device).  For them,
-// lag_precond_apply_static runs the same three kernels (DST-I along x, partitioned tridiagonal
-// solve along z, DST-I back) with the spectrum in the file-scope device array below, whose size
-// is fixed when the library is loaded.  The plan itself is created beforehand (lag_precond_create
+// lag_precond_apply_static runs the three steps (DST-I along x, partitioned tridiagonal solve
+// along z, DST-I back) with the spectrum in the file-scope device array below, whose size is
+// fixed when the library is loaded; the DST runs on the FP64 SIMT pipes (the tensor-core float64
+// DST keeps its operand slices in plan scratch that lag_precond_apply allocates on demand).  The plan itself is created beforehand (lag_precond_create
 // allocates its factors once).
 #include <mutex>
 
@@ -61,9 +62,9 @@ int lag_precond_apply_static(lag_precond *p, const double *r, double *z, int nrh
     // every value of the spectrum the kernels read is written first in the same call: nothing in
     // the array has to start at zero
     const int rows = nrhs * p->grid.nz;
-    dst_apply_f64(p->dst, r, spec, rows, p->grid.nz, nullptr, ctx->stream);
+    dst_apply_f64_simt(p->dst, r, spec, rows, p->grid.nz, nullptr, ctx->stream);
     tri_solve_f64(p->tri64, spec, spec, nrhs, nullptr, ctx->stream);
-    dst_apply_f64(p->dst, spec, z, rows, p->grid.nz, nullptr, ctx->stream);
+    dst_apply_f64_simt(p->dst, spec, z, rows, p->grid.nz, nullptr, ctx->stream);
     return LAG_OK;
   } catch (const Error &e) {
     ctx->last_error = e.what();

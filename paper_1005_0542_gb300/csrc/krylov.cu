@@ -180,7 +180,7 @@ void KrylovWork::pcg_chunk(int iters) {
     eager_done = true;
     return;
   }
-  if (p1->use_tc) p1->ensure_scratch(nrhs);
+  p1->ensure_scratch(nrhs);
   const void *key[3] = {p1->scratch.ptr, p1->tc_scratch.ptr, vecs.ptr};
   const int prod = p1->dst.tc_products;
   if (gexec[idx] != nullptr && (std::memcmp(key, gkey[idx], sizeof(key)) != 0 || prod != gprod[idx])) {
@@ -235,7 +235,7 @@ void KrylovWork::mirror_state() {
   int *herr = reinterpret_cast<int *>(hsc + nrhs);
   const lag_precond *pl[2] = {p1, p2};
   for (int i = 0; i < 2; ++i)
-    if (pl[i] != nullptr && pl[i]->use_tc && pl[i]->dst.tc_err != nullptr)
+    if (pl[i] != nullptr && (pl[i]->use_tc || pl[i]->dst.oz) && pl[i]->dst.tc_err != nullptr)
       LAG_CUDA_CHECK(cudaMemcpyAsync(herr + i, pl[i]->dst.tc_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
   LAG_CUDA_CHECK(cudaEventRecord(ev, stream));
   pending = true;

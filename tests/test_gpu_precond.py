@@ -268,3 +268,38 @@ def test_every_layout_of_the_tridiagonal_solve(ctx, prec):
     assert L.lag_precond_set_layout(p, 1, 8) == L.LAG_EINVAL      # L = 128: shared-memory kernel
     assert L.lag_precond_set_layout(p, 33, 0) == L.LAG_EINVAL     # more partitions than lanes
     L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nx", [16, 17, 255, 2048, 4096])
+def test_dst_f64_exact_slices_row_scales(ctx, nx):
+    # the float64 DST on the tensor cores (exact bf16 slices, float64 sums): every row to float64
+    # accuracy relative to its own size, whatever the rows' magnitudes; zero rows stay zero
+    nz, nrhs = 6, 2
+    x = RNG.standard_normal((nrhs, nz, nx))
+    scales = 10.0 ** np.array([-150, -8, 0, 3, 17, 150])
+    x = x * scales[None, :, None]
+    x[1, 2] = 0.0
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    assert L.lag_precond_uses_tensor_cores(p) == 1
+    xd, yd = dev(x), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(yd), nrhs), ctx)
+    y, ref = host(yd), odst.dst_x(x)
+    err = np.linalg.norm(y - ref, axis=-1) / np.maximum(np.linalg.norm(ref, axis=-1), 1e-300)
+    assert err.max() < 1e-14
+    assert np.all(y[1, 2] == 0.0)
+    L.lag_precond_destroy(p)
+
+
+def test_dst_f64_exact_slices_nonfinite_row(ctx):
+    # a non-finite input row gives a non-finite output row and leaves the others exact
+    nx, nz = 64, 4
+    x = RNG.standard_normal((1, nz, nx))
+    x[0, 1, 5] = np.nan
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    xd, yd = dev(x), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(yd), 1), ctx)
+    y = host(yd)
+    assert np.all(np.isnan(y[0, 1]))
+    ok = [0, 2, 3]
+    assert rel(y[0, ok], odst.dst_x(x[:, ok])[0]) < 1e-14
+    L.lag_precond_destroy(p)

@@ -2,10 +2,13 @@
 
 Some callers cannot let a library allocate device memory when they call it (their own allocator
 owns the device memory, or their loop must not block in cudaMalloc/cudaFree).  This entry point
-keeps its intermediate spectrum in a static device array instead; its results must equal those of
-lag_precond_apply, call after call.  The file sorts last so that a run stopping at the first
-failure has run every other test before it."""
+keeps its intermediate spectrum in a static device array instead and runs the float64 DST on the
+SIMT pipes (the tensor-core DST needs plan-owned scratch for its operand slices); its results must
+equal those of lag_precond_apply on a plan with the SIMT kernels bit for bit, call after call, and
+those of the tensor-core plan to float64 accuracy.  The file sorts last so that a run stopping at
+the first failure has run every other test before it."""
 import ctypes as C
+import os
 
 import numpy as np
 import pytest
@@ -18,21 +21,34 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-12   # the float64 preconditioner tolerance of the other parity tests
 
 
+def _simt_plan(ctx, *args):
+    os.environ["LAGWAVE_DST_KERNEL"] = "simt"   # read at plan creation
+    try:
+        return plan(ctx, *args)
+    finally:
+        del os.environ["LAGWAVE_DST_KERNEL"]
+
+
 def test_static_apply_matches_regular_apply_twice():
     ctx = make_ctx()
     try:
         nx, nz, nrhs = 160, 96, 3
-        p = plan(ctx, nx, nz, 5.0, 7.0, 3.0e9, 2.0e9, 1.0e7)
+        args = (nx, nz, 5.0, 7.0, 3.0e9, 2.0e9, 1.0e7)
+        p = plan(ctx, *args)            # float64 DST on the tensor cores
+        q = _simt_plan(ctx, *args)      # float64 DST on the SIMT pipes, as the static entry point
+        assert L.lag_precond_uses_tensor_cores(p) == 1 and L.lag_precond_uses_tensor_cores(q) == 0
         rng = np.random.default_rng(2024)
         for call in range(2):  # two calls in a row: the shared array keeps the previous contents
             r = rng.standard_normal((nrhs, nz, nx)) * (1.0 + call)
-            rd, z_reg, z_sta = dev(r), empty(r.shape), empty(r.shape)
-            L.check(L.lag_precond_apply(p, ptr(rd), ptr(z_reg), nrhs), ctx)
+            rd, z_tc, z_simt, z_sta = dev(r), empty(r.shape), empty(r.shape), empty(r.shape)
+            L.check(L.lag_precond_apply(p, ptr(rd), ptr(z_tc), nrhs), ctx)
+            L.check(L.lag_precond_apply(q, ptr(rd), ptr(z_simt), nrhs), ctx)
             L.check(L.lag_precond_apply_static(p, ptr(rd), ptr(z_sta), nrhs), ctx)
-            a, b = host(z_sta), host(z_reg)
-            assert rel(a, b) < TOL64
-            assert np.array_equal(a, b)      # same kernels, same order: identical bits
+            a = host(z_sta)
+            assert np.array_equal(a, host(z_simt))   # same kernels, same order: identical bits
+            assert rel(a, host(z_tc)) < TOL64
         L.lag_precond_destroy(p)
+        L.lag_precond_destroy(q)
     finally:
         L.lag_destroy(ctx)
 
