@@ -545,6 +545,13 @@ def capture_kernels(args):
     L.check(L.lag_precond_dst(pmx, P(r), P(z), nrhs), ctx)             # pack + tcgen05 DST GEMM
     L.check(L.lag_precond_tridiag_f32(pmx, P(rf), P(zf), 2 * nrhs), ctx)  # FP32 tridiagonal solve
     L.check(L.lag_apply_operator(m, P(r), P(z), nrhs), ctx)            # acoustic stencil
+    # the shot's shape: one 2048 x 1024 field through the exact-slice FP64 DST
+    ph = C.c_void_p()
+    L.check(L.lag_precond_create_sep(ctx, C.byref(L.grid(2048, 1024, 5.0, 5.0)), 3e10, 3e10, 2.2e7, L.LAG_FP64, 0,
+                                     C.byref(ph)), ctx)
+    rh = torch.randn((1, 1024, 2048), dtype=torch.float64, device="cuda", generator=gen)
+    zh = torch.empty_like(rh)
+    L.check(L.lag_precond_dst(ph, P(rh), P(zh), 1), ctx)
     torch.cuda.synchronize()
     L.lag_destroy(ctx)
     print(json.dumps({"capture": "ok"}))

@@ -659,6 +659,16 @@ __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint6
       : "memory");
 }
 
+// float -> double for the group sums, with integer operations only (the FP64 pipe does the
+// accumulation): a sum is an integer of magnitude <= 2^24, i.e. zero or a normal float, whose double
+// has the same sign and significand and the exponent rebiased by 1023 - 127
+__device__ __forceinline__ double oz_exact_f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t mag = u & 0x7fffffffu;
+  const uint32_t hi = (u & 0x80000000u) | (mag ? ((((mag >> 23) + 896u) << 20) | ((mag >> 3) & 0xfffffu)) : 0u);
+  return __hiloint2double((int)hi, (int)(mag ? (u << 29) : 0u));
+}
+
 struct OzSched {
   int npairs, ngroups;
   int8_t si[48], sj[48], first[48], last[48];  // slice indices (1-based), group start / end flags
@@ -674,9 +684,14 @@ __device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
   if (s >= 0) return M << s;                   // s <= 1 since |v| < 2^e
   return (s <= -64) ? 0ull : (M >> (-s));
 }
+// slice i (1-based) of a fixed-point value as bf16 bits, built with integer operations: an integer
+// 1 <= q < 2^OZ_B is 1.f x 2^p with p = 31 - clz(q), exactly representable in bf16's 8-bit significand
 __device__ __forceinline__ uint16_t oz_slice_bits(unsigned long long T, int i, bool neg) {
-  const int q = (int)((T >> (54 - OZ_B * i)) & ((1u << OZ_B) - 1));
-  return bf16_bits(neg ? -(float)q : (float)q);
+  const uint32_t q = (uint32_t)(T >> (54 - OZ_B * i)) & ((1u << OZ_B) - 1u);
+  if (q == 0) return 0;
+  const int pw = 31 - __clz(q);
+  const uint32_t mant = (q << (7 - pw)) & 0x7fu;
+  return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127) << 7) | mant);
 }
 
 // B slices, once per plan: [mat 0 = S even columns, 1 = S odd columns][slice][n tile][k stage][TN x TK]
@@ -698,8 +713,12 @@ __global__ void oz_pack_b_kernel(const double *su, const double *sv, int ku, int
   }
 }
 
-// A slices per apply: one CTA per row, both parities.  Fold (float64), row maximum, slices.
-// Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r.
+// A slices per apply: one CTA per row, both parities.  Fold (float64 adds, the only float64
+// arithmetic), row maximum of |value| as the maximum of the bit patterns with the sign cleared (the
+// same order for non-negative doubles; NaN and Inf patterns compare above every finite one), slices
+// from the bits.  Rows of up to 128 x 8 folded pairs keep their values in registers (one fold);
+// longer rows fold again in the second pass.  Layout [parity][slice][m tile][k stage][TM x TK];
+// erow[parity][row] = e_r with |values| < 2^e_r.
 __global__ void __launch_bounds__(128) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n, int ku, int kv,
                                                         int nks, int nmt, uint8_t *__restrict__ out, size_t slice_bytes,
                                                         int *__restrict__ erow, const KrylovScalars *__restrict__ sc,
@@ -710,56 +729,83 @@ __global__ void __launch_bounds__(128) oz_pack_a_kernel(const double *__restrict
   const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
   const double *xr = x + (size_t)(row < rows ? row : 0) * n;
   const bool odd_n = (n & 1) != 0;
-  auto fold = [&](int par, int j) -> double {
-    if (!live) return 0.0;
-    if (par == 0) {
-      if (j >= ku) return 0.0;
-      return (odd_n && j == ku - 1) ? xr[j] : xr[j] + xr[n - 1 - j];
+  const int nch = nks * (TK / 8);
+  const bool keep = nch <= (int)blockDim.x;  // one chunk per thread: values stay in registers
+  auto fold8 = [&](int ch, double (&u)[8], double (&v)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = ch * 8 + q;
+      double a = 0.0, b = 0.0;
+      if (live && j < kv) {
+        const double x1 = xr[j], x2 = xr[n - 1 - j];
+        a = x1 + x2;
+        b = x1 - x2;
+      } else if (live && odd_n && j == ku - 1) {
+        a = xr[j];  // middle element of an odd-length row
+      }
+      u[q] = a;
+      v[q] = b;
     }
-    return (j < kv) ? xr[j] - xr[n - 1 - j] : 0.0;
   };
-  // 1. row maxima of |u| and |v|
-  // (a NaN anywhere must reach the maximum: fmax would drop it)
-  auto nanmax = [](double m, double a) { return (a > m || a != a) ? a : m; };
-  double m0 = 0.0, m1 = 0.0;
-  for (int j = threadIdx.x; j < ku; j += blockDim.x) {
-    m0 = nanmax(m0, fabs(fold(0, j)));
-    m1 = nanmax(m1, fabs(fold(1, j)));
+  auto mag = [](double d) { return (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull; };
+  double ku8[8], kv8[8];
+  unsigned long long b0 = 0, b1 = 0;
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+    double u[8], v[8];
+    fold8(ch, u, v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      b0 = max(b0, mag(u[q]));
+      b1 = max(b1, mag(v[q]));
+      ku8[q] = u[q];
+      kv8[q] = v[q];
+    }
   }
-  __shared__ double red[2][4];
+  __shared__ unsigned long long red[2][4];
   __shared__ int esh[2];
   for (int o = 16; o > 0; o >>= 1) {
-    m0 = nanmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-    m1 = nanmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+    b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = m0;
-    red[1][threadIdx.x >> 5] = m1;
+    red[0][threadIdx.x >> 5] = b0;
+    red[1][threadIdx.x >> 5] = b1;
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    const double m = nanmax(nanmax(red[threadIdx.x][0], red[threadIdx.x][1]), nanmax(red[threadIdx.x][2], red[threadIdx.x][3]));
-    int e = 0;
-    if (!isfinite(m)) e = OZ_EXP_NAN;
-    else if (m > 0.0) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): every |value| < 2^e
+    const unsigned long long m =
+        max(max(red[threadIdx.x][0], red[threadIdx.x][1]), max(red[threadIdx.x][2], red[threadIdx.x][3]));
+    const int E = (int)(m >> 52);
+    // |values| <= m < 2^(E - 1022) for normal m, < 2^-1022 for subnormal m; 0 for a zero row
+    const int e = (E == 0x7ff) ? OZ_EXP_NAN : (m == 0 ? 0 : (E == 0 ? -1022 : E - 1022));
     esh[threadIdx.x] = e;
     if (row < rows) erow[threadIdx.x * (nmt * TM) + row] = e;
   }
   __syncthreads();
-  // 2. slices, 8 consecutive k per 16-byte store
   const int mt = row / TM, r = row % TM;
-  for (int ch = threadIdx.x; ch < nks * (TK / 8); ch += blockDim.x) {
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+    double u[8], v[8];
+    if (keep) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        u[q] = ku8[q];
+        v[q] = kv8[q];
+      }
+    } else {
+      fold8(ch, u, v);
+    }
     const int k0 = ch * 8, ks = k0 / TK, kk = k0 % TK;
     const uint32_t off = swz(r, kk);
+#pragma unroll
     for (int par = 0; par < 2; ++par) {
       const int e = esh[par] == OZ_EXP_NAN ? 0 : esh[par];
       unsigned long long T[8];
       bool neg[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const double v = fold(par, k0 + q);
-        T[q] = (esh[par] == OZ_EXP_NAN) ? 0ull : oz_fixed(v, e);
-        neg[q] = v < 0.0;
+        const double val = par ? v[q] : u[q];
+        T[q] = (esh[par] == OZ_EXP_NAN) ? 0ull : oz_fixed(val, e);
+        neg[q] = (__double_as_longlong(val) < 0);
       }
 #pragma unroll
       for (int i = 1; i <= OZ_S; ++i) {
@@ -935,10 +981,10 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
           tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 32), v);
           if (g == 0) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = scale * (double)v[q];
+            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = scale * oz_exact_f2d(v[q]);
           } else {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = fma(scale, (double)v[q], acc64[c * 32 + q]);
+            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = fma(scale, oz_exact_f2d(v[q]), acc64[c * 32 + q]);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
