@@ -277,6 +277,9 @@ def gpu_arm(args, rank, world, local_rank):
 
     # ---- batched mixed path: 64 sources on the surface line share one shot (one launch set per step)
     out["batched"] = batched_leg(ctx, args)
+    # ---- elastic 4096 x 2048, 16 sources, FGMRES(20), float32 vector preconditioner
+    if args.elastic_sources > 0:
+        out["elastic"] = elastic_leg(ctx, args)
 
     # ---- served stream: Poisson arrivals of acoustic / elastic shots, continuous batching
     out["serving"] = serving_leg(ctx, args)
@@ -329,6 +332,50 @@ def batched_leg(ctx, args):
     return {"config": f"2048x1024 model, {nsrc} sources on row 2, mixed path, autotuned plan, one shot; "
                       f"step = one harmonic of every source", "value": nsrc * K / (ms / 1e3), "unit": UNIT, "steps": K,
             "ms_per_step": ms / K, "pcg_iters_per_solve": float(its[:, 1:1 + K].mean())}
+
+
+def elastic_leg(ctx, args):
+    """The elastic workload: 4096 x 2048 at 2.5 m, layered Vp / Vs / rho with a dipping interface,
+    vertical-force Ricker 20 Hz, sources on the surface line batched in one shot, FGMRES(20) to
+    1e-10 with the float32 vector preconditioner (tensor-core DST) and float64 Krylov vectors;
+    step = one harmonic of every source."""
+    import torch
+    from paper_1005_0542_gb300 import inputs
+    from paper_1005_0542_gb300 import lagwave as L
+    nsrc = args.elastic_sources
+    s = inputs.elastic_layered(nsrc=nsrc)
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=1e-10, prec=L.LAG_MIXED, restart_k=s.restart)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    v_, pv = L.f64(s.vs)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    sh = C.c_void_p()
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, pv, pr, C.byref(lag), C.byref(sv), C.byref(w), nsrc,
+                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                              C.byref(sh)), ctx)
+    held = L.lag_bytes_in_use(ctx)
+    L.check(L.lag_shot_step(sh, 1), ctx)  # warm-up harmonic
+    stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    K = args.elastic_steps
+    for _ in range(K):
+        L.check(L.lag_shot_step(sh, 1), ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = np.zeros((nsrc, s.n_harm), dtype=np.int32)
+    st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+    L.lag_shot_stats(sh, C.byref(st))
+    L.lag_shot_destroy(sh)
+    return {"config": f"{s.nx}x{s.nz} elastic, 2.5 m, {nsrc} sources on row 2, FGMRES({s.restart}) to 1e-10, "
+                      f"float32 preconditioner; step = one harmonic of every source",
+            "value": nsrc * K / (ms / 1e3), "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+            "gmres_iters_per_solve": float(its[:, 1:1 + K].mean()), "device_gb": held / 1e9}
 
 
 def serving_leg(ctx, args):
@@ -588,6 +635,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-sources", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--elastic-sources", type=int, default=16, help="0 skips the elastic leg")
+    ap.add_argument("--elastic-steps", type=int, default=2)
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-active", type=int, default=8)
     ap.add_argument("--serve-nharm", type=int, nargs=2, default=[4, 16])

@@ -193,6 +193,43 @@ def test_shot_full_size_first_harmonics(ctx):
     L.lag_shot_destroy(sh)
 
 
+def test_elastic_full_size_first_harmonic_true_residual(ctx):
+    # the 4096 x 2048 elastic workload (2 of its surface sources, mixed path, FGMRES(20)): the first
+    # harmonic meets the tolerance in the true residual b - C R_0, formed with the operator kernel
+    # (itself pinned to the oracle's operator in test_gpu_operator.py) and b = f_0 / (hx hz) at each
+    # source's vertical component
+    s = inputs.elastic_layered(nsrc=2)
+    tol = 1e-10
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=tol, prec=L.LAG_MIXED, restart_k=s.restart)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    v_, pv = L.f64(s.vs)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    sh = C.c_void_p()
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, pv, pr, C.byref(lag), C.byref(sv), C.byref(w), 2,
+                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                              C.byref(sh)), ctx)
+    L.check(L.lag_shot_step(sh, 1), ctx)
+    x = empty((2, 2, s.nz, s.nx))
+    L.check(L.lag_shot_copy_field(sh, ptr(x)), ctx)
+    L.lag_shot_destroy(sh)
+    fm = np.zeros(s.n_harm)
+    L.check(L.lag_source_coeffs(ctx, C.byref(lag), C.byref(w), fm.ctypes.data_as(L.PD)), ctx)
+    b = np.zeros((2, 2, s.nz, s.nx))
+    for i, (ix, iz) in enumerate(s.sources):
+        b[i, 1, iz, ix] = fm[0] / (s.hx * s.hz)
+    m = medium(ctx, s.nx, s.nz, s.hx, s.hz, s.c, s.rho, s.h, vs=s.vs)
+    y = empty(x.shape)
+    L.check(L.lag_apply_operator(m, ptr(x), ptr(y), 2), ctx)
+    res = (b - host(y)).reshape(2, -1)
+    rel_res = np.linalg.norm(res, axis=1) / np.linalg.norm(b.reshape(2, -1), axis=1)
+    assert rel_res.max() < 2 * tol
+    L.lag_medium_destroy(m)
+
+
 def test_solver_argument_errors(ctx):
     s = inputs.two_layer(n_harm=2, nx=16, nz=16)
     g = L.grid(16, 16, 10.0, 10.0)
