@@ -649,6 +649,11 @@ constexpr int OZ_NST = 6;                  // pipeline stages
 constexpr int OZ_NACC = 4;                 // tensor-memory accumulators of 128 columns
 constexpr int OZ_SMEM = OZ_NST * OZ_STAGE + 1024 + 256;
 constexpr int OZ_EXP_NAN = 0x7fffffff;     // row exponent marking a non-finite row
+// pairs of weight i + j >= tail share one accumulator with FP32 rounding: together they weigh
+// < 2^-(OZ_B (tail - 2)) of the leading products (2^-36 at tail = 8), so that rounding stays below
+// 2^-50 of the row scale, under the float64 rounding of the product itself; lighter weights are
+// exact.  tail = 8 up to K = 1024 and one weight later per doubling of K (the rounding grows with K).
+constexpr int OZ_TAIL = 8;
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -684,14 +689,17 @@ __device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
   if (s >= 0) return M << s;                   // s <= 1 since |v| < 2^e
   return (s <= -64) ? 0ull : (M >> (-s));
 }
-// slice i (1-based) of a fixed-point value as bf16 bits, built with integer operations: an integer
-// 1 <= q < 2^OZ_B is 1.f x 2^p with p = 31 - clz(q), exactly representable in bf16's 8-bit significand
+// slice i (1-based) of a fixed-point value as bf16 bits, built with integer operations and stored
+// pre-scaled by 2^-(OZ_B (i - 1)): the integer 1 <= q < 2^OZ_B is 1.f x 2^p with p = 31 - clz(q),
+// exactly representable in bf16's 8-bit significand, and the scale only moves the exponent.  A
+// product of slices i and j then carries 2^-(OZ_B (i + j - 2)) already, so products of different
+// weights can share an accumulator.
 __device__ __forceinline__ uint16_t oz_slice_bits(unsigned long long T, int i, bool neg) {
   const uint32_t q = (uint32_t)(T >> (54 - OZ_B * i)) & ((1u << OZ_B) - 1u);
   if (q == 0) return 0;
   const int pw = 31 - __clz(q);
   const uint32_t mant = (q << (7 - pw)) & 0x7fu;
-  return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127) << 7) | mant);
+  return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127 - OZ_B * (i - 1)) << 7) | mant);
 }
 
 // B slices, once per plan: [mat 0 = S even columns, 1 = S odd columns][slice][n tile][k stage][TN x TK]
@@ -974,7 +982,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
-                                               : ldexp(1.0, e + eB - OZ_B * sch.gd[g]);
+                                               : ldexp(1.0, e + eB - 2 * OZ_B);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           float v[32];
@@ -1012,25 +1020,30 @@ static OzSched oz_schedule(int kpad) {
   OzSched s{};
   const long long cap = (1LL << 24) / (63LL * 63LL * kpad);  // pairs per exact FP32 accumulation
   const int gmax = (int)std::max(1LL, std::min(4LL, cap));
+  int tail_d = OZ_TAIL;
+  for (long long k = 1024; k < kpad; k *= 2) ++tail_d;
   int np = 0, ng = 0;
   for (int d = 2; d <= OZ_S + 1; ++d) {
     int in_group = 0;
+    const bool tail = d >= tail_d;
     for (int i = 1; i <= OZ_S; ++i) {
       const int j = d - i;
       if (j < 1 || j > OZ_S) continue;
       s.si[np] = (int8_t)i;
       s.sj[np] = (int8_t)j;
-      s.first[np] = (in_group == 0);
-      if (in_group == 0) s.gd[ng++] = (int8_t)d;
+      const bool starts = tail ? (d == tail_d && in_group == 0) : (in_group == 0);
+      s.first[np] = starts;
+      if (starts) s.gd[ng++] = (int8_t)d;
       ++in_group;
       ++np;
-      if (in_group == gmax) {
+      if (!tail && in_group == gmax) {
         s.last[np - 1] = 1;
         in_group = 0;
       }
     }
-    if (in_group > 0) s.last[np - 1] = 1;
+    if (!tail && in_group > 0) s.last[np - 1] = 1;
   }
+  s.last[np - 1] = 1;  // the tail group ends with the last pair
   s.npairs = np;
   s.ngroups = ng;
   return s;
