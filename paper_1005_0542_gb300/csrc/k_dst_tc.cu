@@ -644,8 +644,9 @@ constexpr int OZ_B = 6;   // bits per slice
 constexpr int OZ_S = 9;   // slices per operand
 constexpr int OZ_TN = 128;                 // output columns per tile
 constexpr int OZ_BT = OZ_TN * TK * 2;      // B stage tile, 16 KB
-constexpr int OZ_STAGE = A_TILE + OZ_BT;   // 32 KB
-constexpr int OZ_NST = 6;                  // pipeline stages
+constexpr int OZ_KT = 2;                   // 64-wide K tiles per pipeline stage
+constexpr int OZ_STAGE = OZ_KT * (A_TILE + OZ_BT);  // 64 KB: [A k tiles][B k tiles]
+constexpr int OZ_NST = 3;                  // pipeline stages
 constexpr int OZ_NACC = 4;                 // tensor-memory accumulators of 128 columns
 constexpr int OZ_SMEM = OZ_NST * OZ_STAGE + 1024 + 256;
 constexpr int OZ_EXP_NAN = 0x7fffffff;     // row exponent marking a non-finite row
@@ -897,7 +898,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         for (int pr = 0; pr < sch.npairs && !*abort_flag; ++pr) {
           const uint8_t *at = apack + ((size_t)par * OZ_S + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
           const uint8_t *bt = bpack + ((size_t)par * OZ_S + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
-          for (int kk = 0; kk < nks; ++kk, ++it) {
+          for (int kk = 0; kk < nks; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, nks - kk);  // K tiles in this stage
             const int s = it % OZ_NST, use = it / OZ_NST;
             if (it >= OZ_NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
               atomicExch(err, 11);
@@ -906,9 +908,9 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
             }
             const uint32_t st = base + s * OZ_STAGE;
             const uint32_t fb = full0 + 8 * s;
-            mbar_expect_tx(fb, OZ_STAGE);
-            bulk_g2s(st, at + (size_t)kk * A_TILE, A_TILE, fb);
-            bulk_g2s(st + A_TILE, bt + (size_t)kk * OZ_BT, OZ_BT, fb);
+            mbar_expect_tx(fb, (uint32_t)(kt * (A_TILE + OZ_BT)));
+            bulk_g2s(st, at + (size_t)kk * A_TILE, (uint32_t)(kt * A_TILE), fb);
+            bulk_g2s(st + OZ_KT * A_TILE, bt + (size_t)kk * OZ_BT, (uint32_t)(kt * OZ_BT), fb);
           }
         }
       }
@@ -932,7 +934,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             d = tmem + (uint32_t)(acc * OZ_TN);
           }
-          for (int kk = 0; kk < nks; ++kk, ++it) {
+          for (int kk = 0; kk < nks; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, nks - kk);
             const int s = it % OZ_NST, use = it / OZ_NST;
             if (!mbar_wait(full0 + 8 * s, use & 1)) {
               atomicExch(err, 12);
@@ -941,10 +944,13 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t st = base + s * OZ_STAGE;
+            for (int t = 0; t < kt; ++t) {
 #pragma unroll
-            for (int sub = 0; sub < TK / 16; ++sub) {
-              const uint32_t o = sub * 32;
-              mma_bf16_n128(d, sdesc(st + o), sdesc(st + A_TILE + o), (sch.first[pr] && kk == 0 && sub == 0) ? 0u : 1u);
+              for (int sub = 0; sub < TK / 16; ++sub) {
+                const uint32_t o = sub * 32;
+                mma_bf16_n128(d, sdesc(st + t * A_TILE + o), sdesc(st + OZ_KT * A_TILE + t * OZ_BT + o),
+                              (sch.first[pr] && kk == 0 && t == 0 && sub == 0) ? 0u : 1u);
+              }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
                          : "memory");
