@@ -14,6 +14,10 @@ A = -(Lambda_x + Lambda_z) + w, cf. "A = A* > 0" below Eq. (15)):
 
 Reading of "kappa at the half point" (Eq. 18): the arithmetic mean of the two adjacent nodal
 values; a boundary face takes the value of its interior node.
+
+Free surface (Sec. 2.1, Eq. (3): du/dz = 0 at z = 0): ``free_surface=True`` makes the top face of
+node row k = 0 carry no flux, i.e. its coefficient az_{-1/2} is zero (the zero-flux finite-volume
+form of the Neumann condition on this grid); the other three sides stay Dirichlet.
 """
 import numpy as np
 
@@ -37,9 +41,13 @@ def face_x(coef):
     return out
 
 
-def face_z(coef):
-    """Coefficient on the nz+1 z-faces of each column ([nz+1, nx]), same rule as face_x."""
-    return face_x(np.asarray(coef, dtype=np.float64).T).T
+def face_z(coef, free_surface=False):
+    """Coefficient on the nz+1 z-faces of each column ([nz+1, nx]), same rule as face_x; with a
+    free surface the top face (above row 0) carries zero."""
+    out = face_x(np.asarray(coef, dtype=np.float64).T).T
+    if free_surface:
+        out[0, :] = 0.0
+    return out
 
 
 def _pad(y):
@@ -49,11 +57,11 @@ def _pad(y):
     return np.pad(y, pad)
 
 
-def apply_A(y, kappa, rho, h_lag, hx, hz):
+def apply_A(y, kappa, rho, h_lag, hx, hz, free_surface=False):
     """Acoustic operator A y (Eqs. 16-18, Cartesian SPD form).  y: [..., nz, nx]."""
     kappa = np.asarray(kappa, dtype=np.float64)
     ax = face_x(kappa)   # [nz, nx+1]
-    az = face_z(kappa)   # [nz+1, nx]
+    az = face_z(kappa, free_surface)   # [nz+1, nx]
     w = np.asarray(rho, dtype=np.float64) * h_lag ** 2 / 4.0
     yp = _pad(y)
     c = yp[..., 1:-1, 1:-1]
@@ -64,7 +72,7 @@ def apply_A(y, kappa, rho, h_lag, hx, hz):
     return -(lap_x + lap_z) + w * c
 
 
-def assemble_A(kappa, rho, h_lag, hx, hz):
+def assemble_A(kappa, rho, h_lag, hx, hz, free_surface=False):
     """Dense matrix of A (tiny grids only), unknown index k*nx + i.  Built entry by entry
     from the stencil written out, independently of ``apply_A``."""
     kappa = np.asarray(kappa, dtype=np.float64)
@@ -82,7 +90,7 @@ def assemble_A(kappa, rho, h_lag, hx, hz):
 
     def kz(f, i):  # z-face f of column i
         if f == 0:
-            return kappa[0, i]
+            return 0.0 if free_surface else kappa[0, i]
         if f == nz:
             return kappa[nz - 1, i]
         return 0.5 * (kappa[f - 1, i] + kappa[f, i])

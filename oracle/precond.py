@@ -49,13 +49,19 @@ def mode_diagonals(nx, hx, hz, ax_t, az_t, d_t):
     return 2.0 * az_t / hz ** 2 + ax_t * _dst.laplace_eigenvalues(nx, hx) + d_t
 
 
-def apply_inverse(r, hx, hz, ax_t, az_t, d_t):
-    """y = (-B)^{-1} r for r [..., nz, nx]: DST along x, Thomas along z per mode, DST back."""
+def apply_inverse(r, hx, hz, ax_t, az_t, d_t, free_surface=False):
+    """y = (-B)^{-1} r for r [..., nz, nx]: DST along x, Thomas along z per mode, DST back.
+    With a free surface the first row of every T_j loses the flux through the top face:
+    diagonal az~/hz^2 + ax~ lambda_j + d~ (the same zero-flux reading as the operator)."""
     r = np.asarray(r, dtype=np.float64)
     nz, nx = r.shape[-2:]
     S = _dst.dst_matrix(nx)
     rh = _dst.dst_x(r, S)                                   # [..., nz, nx]
     diag = mode_diagonals(nx, hx, hz, ax_t, az_t, d_t)      # [nx]
+    if free_surface:
+        diag = np.broadcast_to(diag, (nz, nx)).copy()
+        diag[0] -= az_t / hz ** 2
+        diag = diag.reshape((nz,) + (1,) * (r.ndim - 2) + (nx,))
     off = -az_t / hz ** 2
     # move z to axis 0 so each (batch, mode) column is one independent system
     col = np.moveaxis(rh, -2, 0)                            # [nz, ..., nx]
@@ -64,12 +70,15 @@ def apply_inverse(r, hx, hz, ax_t, az_t, d_t):
     return _dst.dst_x(yh, S)
 
 
-def apply_separable(y, hx, hz, ax_t, az_t, d_t):
-    """The separable operator itself: -ax~ D_xx y - az~ D_zz y + d~ y (Dirichlet), written as
+def apply_separable(y, hx, hz, ax_t, az_t, d_t, free_surface=False):
+    """The separable operator itself: -ax~ D_xx y - az~ D_zz y + d~ y (Dirichlet; with a free
+    surface the ghost above row 0 mirrors row 0, i.e. no flux through the top face), written as
     a 5-point stencil (used to pin apply_inverse)."""
     y = np.asarray(y, dtype=np.float64)
     pad = [(0, 0)] * (y.ndim - 2) + [(1, 1), (1, 1)]
     yp = np.pad(y, pad)
+    if free_surface:
+        yp[..., 0, 1:-1] = yp[..., 1, 1:-1]
     c = yp[..., 1:-1, 1:-1]
     dxx = (yp[..., 1:-1, 2:] - 2 * c + yp[..., 1:-1, :-2]) / hx ** 2
     dzz = (yp[..., 2:, 1:-1] - 2 * c + yp[..., :-2, 1:-1]) / hz ** 2

@@ -29,7 +29,7 @@ def source_coeffs(n, h, alpha, f0, t0, kind="ricker", gamma=4.0):
 
 
 def acoustic_shot(c, rho, hx, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
-                  tol=1e-10, max_iter=2000, keep_fields=False, fm=None, wavelet="ricker"):
+                  tol=1e-10, max_iter=2000, keep_fields=False, fm=None, wavelet="ricker", free_surface=False):
     """One acoustic shot.  c, rho: [nz, nx]; src = (ix, iz); rcv = [(ix, iz), ...].
 
     Returns dict(R_rcv [n, nrcv], traces [nrcv, nt], iters [n], fm [n], fields (optional))."""
@@ -42,10 +42,10 @@ def acoustic_shot(c, rho, hx, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
         fm = source_coeffs(n_harm, h, alpha, f0, t0, kind=wavelet)
 
     def A(v):
-        return fd.apply_A(v.reshape(nz, nx), kappa, rho, h, hx, hz).ravel()
+        return fd.apply_A(v.reshape(nz, nx), kappa, rho, h, hx, hz, free_surface).ravel()
 
     def Minv(v):
-        return precond.apply_inverse(v.reshape(nz, nx), hx, hz, ax_t, az_t, d_t).ravel()
+        return precond.apply_inverse(v.reshape(nz, nx), hx, hz, ax_t, az_t, d_t, free_surface).ravel()
 
     R = []
     iters = []

@@ -199,3 +199,71 @@ def test_gmres_dense_limits():
     Ainv = np.linalg.inv(A)
     x2, it2, _ = krylov.gmres(lambda v: A @ v, lambda v: Ainv @ v, b, k=5, tol=1e-12)
     assert it2 == 1 and np.linalg.norm(x2 - xd) / np.linalg.norm(xd) < 1e-11
+
+
+# ------------------------------------------------------------------- free surface (Eq. 3)
+def _neumann_dirichlet_mode(nz, q, hz):
+    """Closed form of the z-operator with no flux through the top face and u = 0 below row
+    nz - 1: v_k = cos(theta (k + 1/2)), theta = pi (q + 1/2) / (nz + 1/2), eigenvalue
+    (4 / hz^2) sin^2(theta / 2) (the mirror ghost v_{-1} = v_0 holds since cos is even about
+    k = -1/2, and v_nz = cos(pi (q + 1/2)) = 0)."""
+    th = np.pi * (q + 0.5) / (nz + 0.5)
+    return np.cos(th * (np.arange(nz) + 0.5)), 4.0 / hz ** 2 * np.sin(th / 2) ** 2
+
+
+def test_free_surface_operator_closed_form_eigenfunction():
+    nz, nx, hx, hz, h = 9, 12, 3.0, 4.0, 50.0
+    kappa, rho = 7.0, 2.0
+    p, q = 4, 6
+    vz, mu = _neumann_dirichlet_mode(nz, q, hz)
+    v = np.outer(vz, dst.dst_matrix(nx)[:, p])
+    Av = fd.apply_A(v, np.full((nz, nx), kappa), np.full((nz, nx), rho), h, hx, hz, free_surface=True)
+    ev = kappa * (dst.laplace_eigenvalues(nx, hx)[p] + mu) + rho * h * h / 4
+    assert np.abs(Av - ev * v).max() < 1e-12 * ev
+    # the Dirichlet operator does not have this eigenvector: its row 0 differs by the top-face
+    # flux kappa v_0 / hz^2 (and by nothing else)
+    Ad = fd.apply_A(v, np.full((nz, nx), kappa), np.full((nz, nx), rho), h, hx, hz)
+    assert np.allclose((Ad - Av)[0], kappa / hz ** 2 * v[0], rtol=1e-12, atol=0)
+    assert np.abs((Ad - Av)[1:]).max() < 1e-12 * ev
+
+
+def test_free_surface_assembly_spd_and_only_top_row_changes():
+    nz, nx, hx, hz, h = 5, 7, 10.0, 7.0, 200.0
+    kappa, rho = _medium(nz, nx)
+    M = fd.assemble_A(kappa, rho, h, hx, hz, free_surface=True)
+    cols = np.stack([fd.apply_A(e.reshape(nz, nx), kappa, rho, h, hx, hz, free_surface=True).ravel()
+                     for e in np.eye(nz * nx)], axis=1)
+    assert np.abs(cols - M).max() / np.abs(M).max() < 1e-14
+    assert np.abs(M - M.T).max() / np.abs(M).max() < 1e-15
+    assert np.linalg.eigvalsh(M).min() > 0
+    D = fd.assemble_A(kappa, rho, h, hx, hz) - M
+    # the difference is the top-face flux of row 0 only: kappa_{0,i} / hz^2 on those diagonals
+    assert np.allclose(np.diag(D)[:nx], kappa[0] / hz ** 2, rtol=1e-14)
+    D[np.arange(nx), np.arange(nx)] = 0.0
+    assert np.abs(D).max() == 0.0
+
+
+def test_free_surface_preconditioner_closed_form_and_inverse():
+    nz, nx, hx, hz = 11, 14, 2.0, 3.0
+    ax, az, d = 3.0, 1.0, 0.2
+    p, q = 3, 7
+    vz, mu = _neumann_dirichlet_mode(nz, q, hz)
+    v = np.outer(vz, dst.dst_matrix(nx)[:, p])
+    ev = ax * dst.laplace_eigenvalues(nx, hx)[p] + az * mu + d
+    assert np.abs(precond.apply_inverse(v, hx, hz, ax, az, d, free_surface=True) - v / ev).max() < 1e-13 / ev
+    y = RNG.standard_normal((2, nz, nx))
+    By = precond.apply_separable(y, hx, hz, ax, az, d, free_surface=True)
+    assert np.abs(precond.apply_inverse(By, hx, hz, ax, az, d, free_surface=True) - y).max() < 1e-12
+
+
+def test_free_surface_pcg_homogeneous_one_iteration():
+    nz, nx, hx, hz, h = 12, 10, 5.0, 5.0, 200.0
+    kh, rh = np.full((nz, nx), 9e9), np.full((nz, nx), 2000.0)
+    pr = precond.acoustic_params(kh, rh, h)
+    b = RNG.standard_normal(nz * nx)
+    x, it, _ = krylov.pcg(lambda v: fd.apply_A(v.reshape(nz, nx), kh, rh, h, hx, hz, free_surface=True).ravel(),
+                          lambda v: precond.apply_inverse(v.reshape(nz, nx), hx, hz, *pr, free_surface=True).ravel(),
+                          b, 1e-12)
+    assert it == 1
+    M = fd.assemble_A(kh, rh, h, hx, hz, free_surface=True)
+    assert np.linalg.norm(M @ x - b) / np.linalg.norm(b) < 1e-11
