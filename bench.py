@@ -141,8 +141,8 @@ def gpu_arm(args, rank, world, local_rank):
         s.sources = [replica_source(s.sources[0], rank, s.nx)]
     peaks, peak_src = load_peaks()
 
-    def make_shot(prec, n_harm=None, tune=0):
-        g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    def make_shot(prec, n_harm=None, tune=0, free_surface=False):
+        g = L.grid(s.nx, s.nz, s.hx, s.hz, free_surface)
         lag = L.laguerre(s.h, s.alpha, n_harm or s.n_harm)
         sv = L.solver(tol=s.tol, prec=prec, tune=tune)
         w = L.wavelet(s.f0, s.t0)
@@ -274,6 +274,16 @@ def gpu_arm(args, rank, world, local_rank):
     out["mixed_tuned"] = {"value": K / (mst / 1e3), "ms_per_step": mst / K,
                           "traces_rel_l2_vs_fp64_gpu": float(np.linalg.norm(trt - tr64) / np.linalg.norm(tr64)),
                           "kernel_ms": {k: {"launches": c, "ms": round(v, 3)} for k, (c, v) in sorted(proft.items())}}
+
+    # ---- the same shot with a free surface on top (Sec. 2.1, Eq. 3), float64 path
+    shf = make_shot(L.LAG_FP64, free_surface=True)
+    Kf = min(K, 16)
+    msf, _, proff = timed_steps(shf, W, Kf)
+    itsf = iters_of(shf, W, W + Kf)
+    L.lag_shot_destroy(shf)
+    out["free_surface"] = {"config": "the 2048x1024 shot with a free surface at z = 0 (zero-flux top face), FP64",
+                           "value": Kf / (msf / 1e3), "unit": UNIT, "steps": Kf, "ms_per_step": msf / Kf,
+                           "pcg_iters_per_step": float(np.mean(itsf))}
 
     # ---- batched mixed path: 64 sources on the surface line share one shot (one launch set per step)
     out["batched"] = batched_leg(ctx, args)

@@ -68,7 +68,11 @@ typedef struct lag_medium  lag_medium;
 typedef struct lag_precond lag_precond;
 typedef struct lag_shot    lag_shot;
 
-typedef struct { int nx, nz; double dx, dz; } lag_grid;           /* interior nodes, spacing (m) */
+/* Interior nodes nx x nz with spacing dx, dz (m); u = 0 on the ghost nodes around them, except
+ * that free_surface = 1 puts a free surface on top (Sec. 2.1, Eq. 3: du/dz = 0 at z = 0), read
+ * as a top face of node row 0 that carries no flux (acoustic problems only; elastic media return
+ * LAG_EINVAL).  The surface lies half a cell above row 0. */
+typedef struct { int nx, nz; double dx, dz; int free_surface; } lag_grid;
 typedef struct { double h; int alpha; int n_harm; } lag_laguerre; /* Sec. 2.1: h (1/s), alpha >= 2 */
 typedef struct {
   double tol;       /* stop when ||r||_2 / ||b||_2 <= tol (recursive residual)                    */

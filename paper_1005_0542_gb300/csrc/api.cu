@@ -116,7 +116,7 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   p->tri64.nx = g.nx;
   p->tri64.nz = g.nz;
   tri_choose_layout(p->tri64, 8, partitions);
-  tri_build_factors(p->tri64, p->tri_store, ax, az, d, g.dx, g.dz, s);
+  tri_build_factors(p->tri64, p->tri_store, ax, az, d, g.dx, g.dz, s, 0, g.free_surface != 0);
   if (prec == LAG_MIXED) {
     p->tri32.nx = g.nx;
     p->tri32.nz = g.nz;
@@ -125,7 +125,7 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
       TriFactors tp = p->tri64;
       DevBuf tmp;
       tmp.ctx = ctx;
-      tri_build_factors(tp, tmp, ax, az, d, g.dx, g.dz, s, p->dst.ku);
+      tri_build_factors(tp, tmp, ax, az, d, g.dx, g.dz, s, p->dst.ku, g.free_surface != 0);
       tri_make_f32(tp, p->tri32, p->tri32_store, s);
       LAG_CUDA_CHECK(cudaStreamSynchronize(s));
     } else {
@@ -157,6 +157,8 @@ lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, co
     m->elastic = false;
     medium_build_acoustic(*m, c, rho, s);
   } else {
+    if (g.free_surface)
+      throw Error(LAG_EINVAL, "free_surface applies to acoustic media only (the elastic traction-free surface is not built)");
     m->elastic = true;
     medium_build_elastic(*m, c, vs, rho, s);
   }

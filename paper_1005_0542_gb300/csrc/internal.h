@@ -81,9 +81,10 @@ struct TriFactors {
 void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt = 0);
 bool tri_mode_tile_ok(int elem_bytes, int L, int mt);
 // Build float64 factors of T_j = tridiag(off, 2 az/dz^2 + ax lambda_j + d, off) on the device.
-// perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra)
+// perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra);
+// free_surface: row 0 has no flux through its top face (diagonal az/dz^2 + ax lambda_j + d)
 void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
-                       double dz, cudaStream_t s, int perm_ku = 0);
+                       double dz, cudaStream_t s, int perm_ku = 0, bool free_surface = false);
 // Round a float64 factor set to float32 into `store32` (same layout).
 void tri_make_f32(const TriFactors &t64, TriFactors &t32, DevBuf &store32, cudaStream_t s);
 // y = T^{-1} d per (plane, mode); d and y [planes][nz][nx]; in place allowed.  The launch covers

@@ -17,7 +17,7 @@ thread_local bool g_capturing = false;
 // ------------------------------------------------------------------------------ medium
 __global__ void acoustic_coef_kernel(const double *__restrict__ c, const double *__restrict__ rho, int nx, int nz,
                                      double idx2, double idz2, double h2, double *ax, double *az, double *dg,
-                                     double *rh2, double *kap) {
+                                     double *rh2, double *kap, int free_surface) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (i > nx || k > nz) return;
@@ -26,8 +26,8 @@ __global__ void acoustic_coef_kernel(const double *__restrict__ c, const double 
     const double v = (i == 0) ? K(k, 0) : (i == nx ? K(k, nx - 1) : 0.5 * (K(k, i - 1) + K(k, i)));
     ax[(size_t)k * (nx + 1) + i] = v * idx2;
   }
-  if (i < nx) {  // z-face k of column i
-    const double v = (k == 0) ? K(0, i) : (k == nz ? K(nz - 1, i) : 0.5 * (K(k - 1, i) + K(k, i)));
+  if (i < nx) {  // z-face k of column i (the top face carries no flux under a free surface)
+    const double v = (k == 0) ? (free_surface ? 0.0 : K(0, i)) : (k == nz ? K(nz - 1, i) : 0.5 * (K(k - 1, i) + K(k, i)));
     az[(size_t)k * nx + i] = v * idz2;
   }
   if (i < nx && k < nz) {
@@ -90,7 +90,7 @@ void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rh
   dim3 g((nx + 1 + 127) / 128, nz + 1);
   acoustic_coef_kernel<<<g, 128, 0, s>>>(dc, drho, nx, nz, 1.0 / (m.grid.dx * m.grid.dx),
                                          1.0 / (m.grid.dz * m.grid.dz), m.h * m.h, ax, az, dg,
-                                         m.rho_h2.as<double>(), kap);
+                                         m.rho_h2.as<double>(), kap, m.grid.free_surface ? 1 : 0);
   count_launch();
   LAG_LAUNCH_CHECK();
   dim3 g2((nx + 127) / 128, nz);

@@ -87,6 +87,7 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt) 
 // Matrix of mode j: sub a_k, diag b_k, super c_k (rows >= nz: identity).
 struct TriMatrix {
   double off, diag0, ax, dx2inv, nxp1;
+  double top0;  // added to row 0's diagonal: off (= -az/dz^2) under a free surface, else 0
   int nz, perm_ku;
   __device__ double diag(int c) const {
     const int j = (perm_ku > 0) ? (c < perm_ku ? 2 * c : 2 * (c - perm_ku) + 1) : c;  // mode at column c
@@ -96,7 +97,7 @@ struct TriMatrix {
   __device__ void row(int k, double dj, double &a, double &b, double &c) const {
     if (k >= nz) { a = 0.0; b = 1.0; c = 0.0; return; }
     a = (k >= 1) ? off : 0.0;
-    b = dj;
+    b = (k == 0) ? dj + top0 : dj;
     c = (k + 1 < nz) ? off : 0.0;
   }
 };
@@ -217,7 +218,7 @@ __global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels
 }
 
 void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
-                       double dz, cudaStream_t s, int perm_ku) {
+                       double dz, cudaStream_t s, int perm_ku, bool free_surface) {
   const size_t per = (size_t)tf.ncls * tf.L * tf.nx;
   const size_t nred = (size_t)tf.nx * tf.nf * 32;
   store.alloc(store.ctx, (5 * per + nred) * sizeof(double));
@@ -231,6 +232,7 @@ void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, doub
   TriMatrix M;
   M.off = -az / (dz * dz);
   M.diag0 = 2.0 * az / (dz * dz) + d;
+  M.top0 = free_surface ? M.off : 0.0;
   M.ax = ax;
   M.dx2inv = 1.0 / (dx * dx);
   M.nxp1 = (double)(tf.nx + 1);

@@ -21,7 +21,8 @@ LAG_WAVELET_RICKER, LAG_WAVELET_PAPER = 0, 1
 
 
 class lag_grid(C.Structure):
-    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dz", C.c_double)]
+    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dz", C.c_double),
+                ("free_surface", C.c_int)]
 
 
 class lag_laguerre(C.Structure):
@@ -180,8 +181,8 @@ def points(pts):
     return arr
 
 
-def grid(nx, nz, dx, dz):
-    return lag_grid(int(nx), int(nz), float(dx), float(dz))
+def grid(nx, nz, dx, dz, free_surface=False):
+    return lag_grid(int(nx), int(nz), float(dx), float(dz), 1 if free_surface else 0)
 
 
 def solver(tol=1e-10, max_iter=2000, restart_k=20, prec=LAG_FP64, partitions=0, tune=0):

@@ -54,9 +54,10 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (s if s > 0 else 1.0))
 
 
-def plan(ctx, nx, nz, dx, dz, ax, az, d, prec=L.LAG_FP64, partitions=0):
+def plan(ctx, nx, nz, dx, dz, ax, az, d, prec=L.LAG_FP64, partitions=0, free_surface=False):
     p = C.c_void_p()
-    L.check(L.lag_precond_create_sep(ctx, C.byref(L.grid(nx, nz, dx, dz)), ax, az, d, prec, partitions, C.byref(p)), ctx)
+    g = L.grid(nx, nz, dx, dz, free_surface)
+    L.check(L.lag_precond_create_sep(ctx, C.byref(g), ax, az, d, prec, partitions, C.byref(p)), ctx)
     return p
 
 
@@ -66,9 +67,9 @@ def plan_info(p):
     return P.value, Lp.value, mt.value
 
 
-def medium(ctx, nx, nz, dx, dz, c, rho, h, vs=None):
+def medium(ctx, nx, nz, dx, dz, c, rho, h, vs=None, free_surface=False):
     m = C.c_void_p()
-    g = L.grid(nx, nz, dx, dz)
+    g = L.grid(nx, nz, dx, dz, free_surface)
     c_, pc = L.f64(c)
     r_, pr = L.f64(rho)
     if vs is None:
