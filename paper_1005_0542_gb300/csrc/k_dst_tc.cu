@@ -722,55 +722,44 @@ __global__ void oz_pack_b_kernel(const double *su, const double *sv, int ku, int
   }
 }
 
-// A slices per apply: one CTA per row, both parities.  Fold (float64 adds, the only float64
-// arithmetic), row maximum of |value| as the maximum of the bit patterns with the sign cleared (the
-// same order for non-negative doubles; NaN and Inf patterns compare above every finite one), slices
-// from the bits.  Rows of up to 128 x 8 folded pairs keep their values in registers (one fold);
-// longer rows fold again in the second pass.  Layout [parity][slice][m tile][k stage][TM x TK];
-// erow[parity][row] = e_r with |values| < 2^e_r.
-__global__ void __launch_bounds__(128) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n, int ku, int kv,
-                                                        int nks, int nmt, uint8_t *__restrict__ out, size_t slice_bytes,
-                                                        int *__restrict__ erow, const KrylovScalars *__restrict__ sc,
-                                                        int rpr) {
+// A slices per apply: one CTA of OZ_PACK_THREADS per row, both parities.  Pass 1 folds the row
+// (float64 adds, the only float64 arithmetic) into shared memory and takes the row maximum of
+// |value| as the maximum of the bit patterns with the sign cleared (the same order for
+// non-negative doubles; NaN and Inf patterns compare above every finite one).  Pass 2 cuts each
+// group of 8 consecutive values into slices from the bits and stores them 16 bytes at a time.
+// Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r with |values| < 2^e_r.
+constexpr int OZ_PACK_THREADS = 256;
+constexpr int OZ_PACK_MAXK = 4224;  // ceil(n / 2) bound of the exact-slice path (K pad <= 4224)
+__global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n,
+                                                                    int ku, int kv, int nks, int nmt,
+                                                                    uint8_t *__restrict__ out, size_t slice_bytes,
+                                                                    int *__restrict__ erow,
+                                                                    const KrylovScalars *__restrict__ sc, int rpr) {
+  extern __shared__ double fold_sm[];  // [2][nks * TK]: u then v
   const int row = blockIdx.x;
   // rows of finished right-hand sides and the padding rows of the last tile pack as zeros (exact
   // zero outputs; the GEMM may still cover them in a tile shared with running rows)
   const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
   const double *xr = x + (size_t)(row < rows ? row : 0) * n;
   const bool odd_n = (n & 1) != 0;
-  const int nch = nks * (TK / 8);
-  const bool keep = nch <= (int)blockDim.x;  // one chunk per thread: values stay in registers
-  auto fold8 = [&](int ch, double (&u)[8], double (&v)[8]) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int j = ch * 8 + q;
-      double a = 0.0, b = 0.0;
-      if (live && j < kv) {
-        const double x1 = xr[j], x2 = xr[n - 1 - j];
-        a = x1 + x2;
-        b = x1 - x2;
-      } else if (live && odd_n && j == ku - 1) {
-        a = xr[j];  // middle element of an odd-length row
-      }
-      u[q] = a;
-      v[q] = b;
-    }
-  };
-  auto mag = [](double d) { return (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull; };
-  double ku8[8], kv8[8];
+  const int kp = nks * TK;
+  double *su = fold_sm, *sv = fold_sm + kp;
   unsigned long long b0 = 0, b1 = 0;
-  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
-    double u[8], v[8];
-    fold8(ch, u, v);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      b0 = max(b0, mag(u[q]));
-      b1 = max(b1, mag(v[q]));
-      ku8[q] = u[q];
-      kv8[q] = v[q];
+  for (int j = threadIdx.x; j < kp; j += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    if (live && j < kv) {
+      const double x1 = __ldg(xr + j), x2 = __ldg(xr + n - 1 - j);
+      a = x1 + x2;
+      b = x1 - x2;
+    } else if (live && odd_n && j == ku - 1) {
+      a = __ldg(xr + j);  // middle element of an odd-length row
     }
+    su[j] = a;
+    sv[j] = b;
+    b0 = max(b0, (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull);
+    b1 = max(b1, (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffull);
   }
-  __shared__ unsigned long long red[2][4];
+  __shared__ unsigned long long red[2][OZ_PACK_THREADS / 32];
   __shared__ int esh[2];
   for (int o = 16; o > 0; o >>= 1) {
     b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
@@ -782,8 +771,8 @@ __global__ void __launch_bounds__(128) oz_pack_a_kernel(const double *__restrict
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    const unsigned long long m =
-        max(max(red[threadIdx.x][0], red[threadIdx.x][1]), max(red[threadIdx.x][2], red[threadIdx.x][3]));
+    unsigned long long m = 0;
+    for (int w = 0; w < OZ_PACK_THREADS / 32; ++w) m = max(m, red[threadIdx.x][w]);
     const int E = (int)(m >> 52);
     // |values| <= m < 2^(E - 1022) for normal m, < 2^-1022 for subnormal m; 0 for a zero row
     const int e = (E == 0x7ff) ? OZ_EXP_NAN : (m == 0 ? 0 : (E == 0 ? -1022 : E - 1022));
@@ -792,38 +781,29 @@ __global__ void __launch_bounds__(128) oz_pack_a_kernel(const double *__restrict
   }
   __syncthreads();
   const int mt = row / TM, r = row % TM;
-  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
-    double u[8], v[8];
-    if (keep) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        u[q] = ku8[q];
-        v[q] = kv8[q];
-      }
-    } else {
-      fold8(ch, u, v);
-    }
+  // one (parity, 8-value chunk) per thread and step
+  for (int w = threadIdx.x; w < 2 * (kp / 8); w += blockDim.x) {
+    const int par = w & 1, ch = w >> 1;
     const int k0 = ch * 8, ks = k0 / TK, kk = k0 % TK;
+    const double *src = (par ? sv : su) + k0;
+    const bool bad = esh[par] == OZ_EXP_NAN;
+    const int e = bad ? 0 : esh[par];
+    unsigned long long T[8];
+    uint32_t negm = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double val = src[q];
+      T[q] = bad ? 0ull : oz_fixed(val, e);
+      negm |= (__double_as_longlong(val) < 0 ? 1u : 0u) << q;
+    }
     const uint32_t off = swz(r, kk);
+    uint8_t *tile0 = out + (size_t)par * OZ_S * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
 #pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      const int e = esh[par] == OZ_EXP_NAN ? 0 : esh[par];
-      unsigned long long T[8];
-      bool neg[8];
+    for (int i = 1; i <= OZ_S; ++i) {
+      alignas(16) uint16_t hv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const double val = par ? v[q] : u[q];
-        T[q] = (esh[par] == OZ_EXP_NAN) ? 0ull : oz_fixed(val, e);
-        neg[q] = (__double_as_longlong(val) < 0);
-      }
-#pragma unroll
-      for (int i = 1; i <= OZ_S; ++i) {
-        alignas(16) uint16_t h[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) h[q] = oz_slice_bits(T[q], i, neg[q]);
-        uint8_t *tile = out + ((size_t)par * OZ_S + (i - 1)) * slice_bytes + ((size_t)mt * nks + ks) * A_TILE;
-        *reinterpret_cast<uint4 *>(tile + off) = *reinterpret_cast<const uint4 *>(h);
-      }
+      for (int q = 0; q < 8; ++q) hv[q] = oz_slice_bits(T[q], i, (negm >> q) & 1u);
+      *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = *reinterpret_cast<const uint4 *>(hv);
     }
   }
 }
@@ -1102,7 +1082,15 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
   const size_t a_slice = (size_t)nmt * nks * A_TILE;
   uint8_t *apack = dp.tc_scratch;
   int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)OZ_S * a_slice);
-  oz_pack_a_kernel<<<nmt * TM, 128, 0, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack, a_slice, erow, sc, rpr);
+  const size_t pack_smem = 2 * (size_t)nks * TK * sizeof(double);
+  static bool pack_attr = false;
+  if (!pack_attr) {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        2 * OZ_PACK_MAXK * (int)sizeof(double)));
+    pack_attr = true;
+  }
+  oz_pack_a_kernel<<<nmt * TM, OZ_PACK_THREADS, pack_smem, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack, a_slice,
+                                                                 erow, sc, rpr);
   count_launch();
   LAG_LAUNCH_CHECK();
   const OzSched sch = oz_schedule(nks * TK);
