@@ -37,7 +37,11 @@ WORKLOAD = ("random_layered_2048x1024 acoustic FP64 single shot: 5 m, 20 layers 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures, with the sha1 of the
 # kernel source file at capture time (null when the kernel changed since).  See profiles/.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # oz_pack_a_kernel (16.9 MB) + oz_gemm_kernel (79.9 MB), one 2048-mode x 1024-row launch each
+    # (bench.py --capture-kernels; profiles/kernels_dst_precond.md)
+    "dst_f64_oz": {"bytes": 96.8e6, "sha1": "4094580d3127"},
+}
 
 
 def sha1_of(path):
