@@ -258,17 +258,25 @@ __global__ void __launch_bounds__(256) gm_dots_kernel(const double *__restrict__
   const int rhs = blockIdx.y;
   if (sc[rhs].state != ST_RUN) return;
   const size_t off = (size_t)rhs * n;
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 8];
   __shared__ bool is_last;
   double *part = red.part + (size_t)rhs * red.rstride;
-  for (int i = 0; i <= j; ++i) {
-    const double *vi = V + (size_t)i * vstride + off;
-    double acc = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-      acc = fma(w[off + e], vi[e], acc);
-    double v1[1] = {acc};
-    block_sum<1>(v1, sh);
-    if (threadIdx.x == 0) part[(size_t)i * red.nblk + blockIdx.x] = v1[0];
+  // eight basis vectors per sweep: w is read once per eight dots instead of once per dot (w does
+  // not stay in L2 across a batch of right-hand sides); each dot keeps its own summation order
+  for (int i0 = 0; i0 <= j; i0 += 8) {
+    const int cnt = min(8, j + 1 - i0);
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+      const double we = w[off + e];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < cnt) acc[q] = fma(we, V[(size_t)(i0 + q) * vstride + off + e], acc[q]);
+    }
+    block_sum<8>(acc, sh);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < cnt; ++q) part[(size_t)(i0 + q) * red.nblk + blockIdx.x] = acc[q];
   }
   if (threadIdx.x == 0) {
     __threadfence();
