@@ -83,3 +83,71 @@ def apply_separable(y, hx, hz, ax_t, az_t, d_t, free_surface=False):
     dxx = (yp[..., 1:-1, 2:] - 2 * c + yp[..., 1:-1, :-2]) / hx ** 2
     dzz = (yp[..., 2:, 1:-1] - 2 * c + yp[..., :-2, 1:-1]) / hz ** 2
     return -ax_t * dxx - az_t * dzz + d_t * c
+
+
+# ----------------------------------------------------------------------------------------
+# Layered variant (a design extension beyond the paper): coefficients that vary with z only,
+# ax~(z), az~(z), d~(z), each the midrange over its node row.  The x-operator still commutes
+# with the DST along x (it only scales each row), so the separation of variables holds; the
+# z-systems become general tridiagonal matrices (no longer Toeplitz):
+#     T_j(k, k-1) = -az_f(k)/hz^2,   T_j(k, k+1) = -az_f(k+1)/hz^2,
+#     T_j(k, k)   = (az_f(k) + az_f(k+1))/hz^2 + ax~(k) lambda_j + d~(k),
+# with z-face coefficients az_f by the rule of the operator (mean of the two rows, a boundary face
+# takes its row's value, the top face carries zero under a free surface).  For a medium whose
+# kappa and rho depend on z only this operator equals A exactly.
+# ----------------------------------------------------------------------------------------
+
+def row_midranges(f):
+    """Per-row midrange f~(z) = (min_x f + max_x f) / 2, shape [nz]."""
+    f = np.asarray(f, dtype=np.float64)
+    return 0.5 * (f.min(axis=1) + f.max(axis=1))
+
+
+def acoustic_params_layered(kappa, rho, h_lag):
+    """(ax~(z), az~(z), d~(z)) of the layered acoustic preconditioner."""
+    kz = row_midranges(kappa)
+    return kz, kz.copy(), row_midranges(rho) * h_lag ** 2 / 4.0
+
+
+def _z_faces(az_z, free_surface):
+    nz = az_z.shape[0]
+    f = np.empty(nz + 1)
+    f[1:nz] = 0.5 * (az_z[:-1] + az_z[1:])
+    f[0] = 0.0 if free_surface else az_z[0]
+    f[nz] = az_z[nz - 1]
+    return f
+
+
+def apply_inverse_layered(r, hx, hz, ax_z, az_z, d_z, free_surface=False):
+    """y = (-B)^{-1} r for the layered preconditioner; r [..., nz, nx]."""
+    r = np.asarray(r, dtype=np.float64)
+    nz, nx = r.shape[-2:]
+    ax_z, az_z, d_z = (np.asarray(v, dtype=np.float64) for v in (ax_z, az_z, d_z))
+    S = _dst.dst_matrix(nx)
+    rh = _dst.dst_x(r, S)
+    lam = _dst.laplace_eigenvalues(nx, hx)
+    f = _z_faces(az_z, free_surface)
+    extra = (1,) * (r.ndim - 2)
+    sub = (-f[:nz] / hz ** 2).reshape((nz,) + extra + (1,))
+    sup = (-f[1:] / hz ** 2).reshape((nz,) + extra + (1,))
+    diag = ((f[:nz] + f[1:]) / hz ** 2)[:, None] + ax_z[:, None] * lam[None, :] + d_z[:, None]
+    diag = diag.reshape((nz,) + extra + (nx,))
+    col = np.moveaxis(rh, -2, 0)
+    yt = thomas(sub, diag, sup, col)
+    return _dst.dst_x(np.moveaxis(yt, 0, -2), S)
+
+
+def apply_separable_layered(y, hx, hz, ax_z, az_z, d_z, free_surface=False):
+    """The layered operator itself as a 5-point stencil (used to pin apply_inverse_layered):
+    -ax~(z) D_xx y - D_z(az_f D_z y) + d~(z) y, Dirichlet (free surface: no flux on top)."""
+    y = np.asarray(y, dtype=np.float64)
+    nz = y.shape[-2]
+    ax_z, az_z, d_z = (np.asarray(v, dtype=np.float64) for v in (ax_z, az_z, d_z))
+    pad = [(0, 0)] * (y.ndim - 2) + [(1, 1), (1, 1)]
+    yp = np.pad(y, pad)
+    c = yp[..., 1:-1, 1:-1]
+    dxx = (yp[..., 1:-1, 2:] - 2 * c + yp[..., 1:-1, :-2]) / hx ** 2
+    f = _z_faces(az_z, free_surface)
+    south, north = yp[..., 2:, 1:-1], yp[..., :-2, 1:-1]
+    flux = (f[1:, None] * (south - c) - f[:nz, None] * (c - north)) / hz ** 2
+    return -ax_z[:, None] * dxx - flux + d_z[:, None] * c

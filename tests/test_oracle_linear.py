@@ -267,3 +267,59 @@ def test_free_surface_pcg_homogeneous_one_iteration():
     assert it == 1
     M = fd.assemble_A(kh, rh, h, hx, hz, free_surface=True)
     assert np.linalg.norm(M @ x - b) / np.linalg.norm(b) < 1e-11
+
+
+# ------------------------------------------------ layered preconditioner (design extension)
+@pytest.mark.parametrize("free_surface", [False, True])
+def test_layered_precond_inverts_its_operator_and_reduces_to_constant(free_surface):
+    nz, nx, hx, hz = 17, 23, 4.0, 3.0
+    ax = RNG.uniform(1.0, 3.0, nz)
+    az = RNG.uniform(1.0, 3.0, nz)
+    d = RNG.uniform(0.1, 0.5, nz)
+    y = RNG.standard_normal((2, nz, nx))
+    By = precond.apply_separable_layered(y, hx, hz, ax, az, d, free_surface)
+    assert np.abs(precond.apply_inverse_layered(By, hx, hz, ax, az, d, free_surface) - y).max() < 1e-12
+    # constant rows: the layered preconditioner is the constant one
+    c = np.ones(nz)
+    r = RNG.standard_normal((nz, nx))
+    a = precond.apply_inverse_layered(r, hx, hz, 2.0 * c, 1.5 * c, 0.3 * c, free_surface)
+    b = precond.apply_inverse(r, hx, hz, 2.0, 1.5, 0.3, free_surface)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("free_surface", [False, True])
+def test_layered_precond_equals_A_for_a_z_only_medium(free_surface):
+    # kappa and rho depending on z only: the layered operator IS A, and PCG takes one iteration
+    nz, nx, hx, hz, h = 14, 11, 5.0, 4.0, 200.0
+    kz = RNG.uniform(1e9, 9e9, nz)
+    rz = RNG.uniform(1000.0, 2500.0, nz)
+    kappa = np.repeat(kz[:, None], nx, axis=1)
+    rho = np.repeat(rz[:, None], nx, axis=1)
+    ax, az, d = precond.acoustic_params_layered(kappa, rho, h)
+    y = RNG.standard_normal((nz, nx))
+    Ay = fd.apply_A(y, kappa, rho, h, hx, hz, free_surface)
+    By = precond.apply_separable_layered(y, hx, hz, ax, az, d, free_surface)
+    assert np.abs(Ay - By).max() < 1e-12 * np.abs(Ay).max()
+    b = RNG.standard_normal(nz * nx)
+    x, it, _ = krylov.pcg(lambda v: fd.apply_A(v.reshape(nz, nx), kappa, rho, h, hx, hz, free_surface).ravel(),
+                          lambda v: precond.apply_inverse_layered(v.reshape(nz, nx), hx, hz, ax, az, d,
+                                                                  free_surface).ravel(), b, 1e-12)
+    assert it == 1
+
+
+def test_layered_precond_needs_fewer_iterations_on_layers():
+    # the property the extension is for: on a layered model with noise it beats the constant one
+    nz, nx, hx, h = 48, 40, 10.0, 200.0
+    layers = (np.arange(nz) * 6) // nz
+    c = RNG.uniform(1500, 4500, 6)[layers][:, None] * (1 + 0.02 * RNG.standard_normal((nz, nx)))
+    rho = 310 * c ** 0.25
+    kappa = fd.kappa_from_velocity(c, rho)
+    A = lambda v: fd.apply_A(v.reshape(nz, nx), kappa, rho, h, hx, hx).ravel()
+    b = RNG.standard_normal(nz * nx)
+    pc = precond.acoustic_params(kappa, rho, h)
+    pl = precond.acoustic_params_layered(kappa, rho, h)
+    _, it_c, _ = krylov.pcg(A, lambda v: precond.apply_inverse(v.reshape(nz, nx), hx, hx, *pc).ravel(), b, 1e-10)
+    xl, it_l, _ = krylov.pcg(A, lambda v: precond.apply_inverse_layered(v.reshape(nz, nx), hx, hx, *pl).ravel(), b, 1e-10)
+    assert it_l < it_c / 2
+    M = fd.assemble_A(kappa, rho, h, hx, hx)
+    assert np.linalg.norm(M @ xl - b) / np.linalg.norm(b) < 1e-9
