@@ -145,10 +145,10 @@ def gpu_arm(args, rank, world, local_rank):
         s.sources = [replica_source(s.sources[0], rank, s.nx)]
     peaks, peak_src = load_peaks()
 
-    def make_shot(prec, n_harm=None, tune=0, free_surface=False):
+    def make_shot(prec, n_harm=None, tune=0, free_surface=False, layered=0):
         g = L.grid(s.nx, s.nz, s.hx, s.hz, free_surface)
         lag = L.laguerre(s.h, s.alpha, n_harm or s.n_harm)
-        sv = L.solver(tol=s.tol, prec=prec, tune=tune)
+        sv = L.solver(tol=s.tol, prec=prec, tune=tune, layered=layered)
         w = L.wavelet(s.f0, s.t0)
         c_, pc = L.f64(s.c)
         r_, pr = L.f64(s.rho)
@@ -288,6 +288,22 @@ def gpu_arm(args, rank, world, local_rank):
     out["free_surface"] = {"config": "the 2048x1024 shot with a free surface at z = 0 (zero-flux top face), FP64",
                            "value": Kf / (msf / 1e3), "unit": UNIT, "steps": Kf, "ms_per_step": msf / Kf,
                            "pcg_iters_per_step": float(np.mean(itsf))}
+
+    # ---- the same shot with the layered preconditioner (per-row midranges), both paths
+    for key, prec in (("layered", L.LAG_FP64), ("layered_mixed", L.LAG_MIXED)):
+        shl = make_shot(prec, layered=1)
+        msl, launches_l, profl = timed_steps(shl, W, K)
+        itsl = iters_of(shl, W, W + K)
+        trl = traces_of(shl)
+        L.lag_shot_destroy(shl)
+        out[key] = {"config": "the 2048x1024 shot preconditioned with per-row midranges kappa~(z), rho~(z) "
+                              f"({'FP64' if prec == L.LAG_FP64 else 'mixed'} path)",
+                    "value": K / (msl / 1e3), "unit": UNIT, "ms_per_step": msl / K,
+                    "speedup_vs_fp64_gpu": (K / (msl / 1e3)) / value,
+                    "pcg_iters_per_step": float(np.mean(itsl)),
+                    "traces_rel_l2_vs_fp64_gpu": float(np.linalg.norm(trl - tr64) / np.linalg.norm(tr64)),
+                    "gpu_launches": int(launches_l),
+                    "kernel_ms": {k: {"launches": c, "ms": round(v, 3)} for k, (c, v) in sorted(profl.items())}}
 
     # ---- batched mixed path: 64 sources on the surface line share one shot (one launch set per step)
     out["batched"] = batched_leg(ctx, args)

@@ -81,6 +81,8 @@ typedef struct {
   int prec;         /* LAG_FP64 or LAG_MIXED                                                       */
   int partitions;   /* z-partitions of the tridiagonal solve; 0 = automatic                        */
   int tune;         /* 1: shots run lag_precond_autotune on their plans at creation                */
+  int layered;      /* 1: acoustic shots precondition with per-row midranges (lag_precond_create_
+                       layered) instead of the whole-medium midranges of Eq. 21; elastic: 0 only  */
 } lag_solver;
 typedef struct { int ix, iz; } lag_point;                          /* 0-based interior node        */
 typedef struct { double f0, t0, gamma; int kind; } lag_wavelet;
@@ -128,6 +130,21 @@ int  lag_precond_create(lag_ctx *ctx, const lag_grid *grid, double kappa_t, doub
                         double h_lag, int prec, lag_precond **out);
 int  lag_precond_create_sep(lag_ctx *ctx, const lag_grid *grid, double ax_t, double az_t,
                             double d_t, int prec, int partitions, lag_precond **out);
+/* Layered preconditioner (an extension of Eq. 21; the paper has no counterpart): coefficients that
+ * vary with z only, ax~(z), az~(z), d~(z) (host arrays of nz values, positive / d >= 0; a shot
+ * with lag_solver.layered takes the midranges of kappa and rho over each node row).  The x part
+ * still commutes with the DST along x, so Sec. 2.4's separation of variables holds; each T_j
+ * becomes a general tridiagonal matrix with rows
+ *     (-zf_k,  zf_k + zf_{k+1} + ax~(k) lambda_j + d~(k),  -zf_{k+1}),   zf_k = az_f(k) / dz^2,
+ * az_f the z-face coefficient (mean of the two rows; a boundary face takes its row's value; the
+ * top face carries no flux under a free surface).  For a medium whose kappa and rho depend on z
+ * only, this operator equals A.  The factors are stored per partition (nz x nx values of each of
+ * five factor arrays instead of 3 L x nx).  Everything else (apply, steps, layout, autotune) is
+ * as for the other plans. */
+int  lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double *ax_z,
+                                const double *az_z, const double *d_z, int prec, int partitions,
+                                lag_precond **out);
+int  lag_precond_is_layered(const lag_precond *p);   /* 1 for plans of lag_precond_create_layered */
 void lag_precond_destroy(lag_precond *p);
 /* z = B^{-1} r for nrhs fields [nrhs][nz][nx] (device, float64).  Stream-ordered.  r and z may
  * not overlap.  Steps: forward DST-I along x, one tridiagonal solve along z per mode, DST-I. */

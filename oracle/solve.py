@@ -29,8 +29,11 @@ def source_coeffs(n, h, alpha, f0, t0, kind="ricker", gamma=4.0):
 
 
 def acoustic_shot(c, rho, hx, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
-                  tol=1e-10, max_iter=2000, keep_fields=False, fm=None, wavelet="ricker", free_surface=False):
+                  tol=1e-10, max_iter=2000, keep_fields=False, fm=None, wavelet="ricker", free_surface=False,
+                  layered=False):
     """One acoustic shot.  c, rho: [nz, nx]; src = (ix, iz); rcv = [(ix, iz), ...].
+    layered: precondition with the per-row midranges (precond.apply_inverse_layered) instead of
+    the whole-medium midranges of Eq. (21).
 
     Returns dict(R_rcv [n, nrcv], traces [nrcv, nt], iters [n], fm [n], fields (optional))."""
     c = np.asarray(c, dtype=np.float64)
@@ -44,8 +47,14 @@ def acoustic_shot(c, rho, hx, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
     def A(v):
         return fd.apply_A(v.reshape(nz, nx), kappa, rho, h, hx, hz, free_surface).ravel()
 
-    def Minv(v):
-        return precond.apply_inverse(v.reshape(nz, nx), hx, hz, ax_t, az_t, d_t, free_surface).ravel()
+    if layered:
+        lz = precond.acoustic_params_layered(kappa, rho, h)
+
+        def Minv(v):
+            return precond.apply_inverse_layered(v.reshape(nz, nx), hx, hz, *lz, free_surface).ravel()
+    else:
+        def Minv(v):
+            return precond.apply_inverse(v.reshape(nz, nx), hx, hz, ax_t, az_t, d_t, free_surface).ravel()
 
     R = []
     iters = []

@@ -1,4 +1,5 @@
 // C ABI of the library: contexts, media, preconditioner plans, Krylov drivers and shots.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -92,10 +93,41 @@ void lag_precond::apply(const double *r, double *z, int nrhs, const KrylovScalar
   }
 }
 
+lag::TriCoef lag_precond::coef() const {
+  lag::TriCoef k;
+  k.ax = ax;
+  k.az = az;
+  k.d = d;
+  k.zrows = zrows.ptr ? zrows.as<double>() : nullptr;
+  k.free_surface = grid.free_surface != 0;
+  return k;
+}
+
 lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
-                              int partitions, cudaStream_t s) {
+                              int partitions, cudaStream_t s, const double *layered) {
   if (g.nx < 1 || g.nz < 1 || !(g.dx > 0) || !(g.dz > 0)) throw Error(LAG_EINVAL, "bad grid");
-  if (!(ax > 0) || !(az > 0) || !(d >= 0)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+  std::vector<double> zr;
+  if (layered != nullptr) {
+    // per-row coefficients -> z faces (mean of the two rows; a boundary face takes its row's value,
+    // the top face carries no flux under a free surface), each over dz^2
+    const int nz = g.nz;
+    const double *lax = layered, *laz = layered + nz, *ld = layered + 2 * nz;
+    for (int k = 0; k < nz; ++k)
+      if (!(lax[k] > 0) || !(laz[k] > 0) || !(ld[k] >= 0) || !std::isfinite(lax[k] + laz[k] + ld[k]))
+        throw Error(LAG_EINVAL, "layered preconditioner coefficients must be positive and finite");
+    const double dz2 = g.dz * g.dz;
+    zr.resize(3 * (size_t)nz + 1);
+    zr[0] = g.free_surface ? 0.0 : laz[0] / dz2;
+    for (int k = 1; k < nz; ++k) zr[k] = 0.5 * (laz[k - 1] + laz[k]) / dz2;
+    zr[nz] = laz[nz - 1] / dz2;
+    for (int k = 0; k < nz; ++k) {
+      zr[nz + 1 + k] = lax[k];
+      zr[2 * nz + 1 + k] = ld[k];
+    }
+    ax = az = d = 0.0;
+  } else if (!(ax > 0) || !(az > 0) || !(d >= 0)) {
+    throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+  }
   if (prec != LAG_FP64 && prec != LAG_MIXED) throw Error(LAG_EINVAL, "prec must be LAG_FP64 or LAG_MIXED");
   std::unique_ptr<lag_precond> p(new lag_precond());
   p->ctx = ctx;
@@ -105,6 +137,12 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   p->az = az;
   p->d = d;
   p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = p->tc_scratch.ctx = ctx;
+  p->zrows.ctx = ctx;
+  const bool gen = layered != nullptr;
+  if (gen) {
+    p->zrows.alloc(ctx, zr.size() * sizeof(double));
+    LAG_CUDA_CHECK(cudaMemcpyAsync(p->zrows.ptr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
   p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
   const bool oz = (prec == LAG_FP64) && dst_oz_supported(g.nx) && !tc_disabled();
   dst_build(p->dst, p->dst_store, g.nx, p->use_tc ? 1 : (oz ? 2 : 0), s);
@@ -115,17 +153,17 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   }
   p->tri64.nx = g.nx;
   p->tri64.nz = g.nz;
-  tri_choose_layout(p->tri64, 8, partitions);
-  tri_build_factors(p->tri64, p->tri_store, ax, az, d, g.dx, g.dz, s, 0, g.free_surface != 0);
+  tri_choose_layout(p->tri64, 8, partitions, 0, gen);
+  tri_build_factors(p->tri64, p->tri_store, p->coef(), g.dx, g.dz, s, 0);
   if (prec == LAG_MIXED) {
     p->tri32.nx = g.nx;
     p->tri32.nz = g.nz;
-    tri_choose_layout(p->tri32, 4, partitions);
+    tri_choose_layout(p->tri32, 4, partitions, 0, gen);
     if (p->use_tc) {  // the tensor-core DST leaves the spectrum parity-permuted: permuted factors
       TriFactors tp = p->tri64;
       DevBuf tmp;
       tmp.ctx = ctx;
-      tri_build_factors(tp, tmp, ax, az, d, g.dx, g.dz, s, p->dst.ku, g.free_surface != 0);
+      tri_build_factors(tp, tmp, p->coef(), g.dx, g.dz, s, p->dst.ku);
       tri_make_f32(tp, p->tri32, p->tri32_store, s);
       LAG_CUDA_CHECK(cudaStreamSynchronize(s));
     } else {
@@ -152,7 +190,7 @@ lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, co
   m->ctx = ctx;
   m->grid = g;
   m->h = h;
-  m->coef.ctx = m->rho_h2.ctx = ctx;
+  m->coef.ctx = m->rho_h2.ctx = m->rowmm.ctx = ctx;
   if (vs == nullptr) {
     m->elastic = false;
     medium_build_acoustic(*m, c, rho, s);
@@ -271,6 +309,24 @@ int lag_precond_create_sep(lag_ctx *ctx, const lag_grid *grid, double ax, double
     *out = precond_new(ctx, *grid, ax, az, d, prec, partitions, ctx->stream);
   });
 }
+
+int lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double *ax_z, const double *az_z,
+                               const double *d_z, int prec, int partitions, lag_precond **out) {
+  if (!ctx || !grid || !out || !ax_z || !az_z || !d_z) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    if (partitions < 0 || partitions > 32) throw Error(LAG_EINVAL, "partitions must be 0..32");
+    if (grid->nz < 1) throw Error(LAG_EINVAL, "bad grid");
+    std::vector<double> rows(3 * (size_t)grid->nz);
+    std::copy(ax_z, ax_z + grid->nz, rows.begin());
+    std::copy(az_z, az_z + grid->nz, rows.begin() + grid->nz);
+    std::copy(d_z, d_z + grid->nz, rows.begin() + 2 * (size_t)grid->nz);
+    *out = precond_new(ctx, *grid, 0.0, 0.0, 0.0, prec, partitions, ctx->stream, rows.data());
+  });
+}
+
+int lag_precond_is_layered(const lag_precond *p) { return (p && p->zrows.ptr) ? 1 : 0; }
 
 void lag_precond_destroy(lag_precond *p) {
   if (!p) return;

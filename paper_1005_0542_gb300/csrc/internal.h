@@ -66,7 +66,8 @@ struct DevBuf {
 struct TriFactors {
   int nx = 0, nz = 0;   // modes, rows
   int P = 1, L = 1;     // partitions, partition length (P * L >= nz; rows >= nz are identity)
-  int ncls = 1;         // factor classes (3 for Toeplitz-in-z systems, P in general)
+  int ncls = 1;         // factor sets (3 classes for Toeplitz-in-z systems, one per partition in general)
+  bool gen = false;     // general (layered) systems: one factor set per partition
   int levels = 0;       // PCR levels of the reduced system (P - 1 unknowns)
   int nf = 3;           // values per separator in the reduced block: 3 + 3 * levels
   int mt = 1;           // modes per CTA
@@ -78,13 +79,22 @@ struct TriFactors {
   void *red = nullptr;  // [j][nf][32]
 };
 
-void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt = 0);
+void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt = 0, bool general = false);
 bool tri_mode_tile_ok(int elem_bytes, int L, int mt);
-// Build float64 factors of T_j = tridiag(off, 2 az/dz^2 + ax lambda_j + d, off) on the device.
-// perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra);
-// free_surface: row 0 has no flux through its top face (diagonal az/dz^2 + ax lambda_j + d)
-void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
-                       double dz, cudaStream_t s, int perm_ku = 0, bool free_surface = false);
+// Coefficients of the z-systems T_j.  Constant (Eq. 21 midranges): T_j = tridiag(-az/dz^2,
+// 2 az/dz^2 + ax lambda_j + d, -az/dz^2); free_surface: row 0 has no flux through its top face
+// (diagonal az/dz^2 + ax lambda_j + d).  Layered (zrows != null, device, nz*3 + 1 values):
+// [zf: nz + 1 z-face coefficients over dz^2 | ax(z): nz | d(z): nz], row k of T_j being
+// (-zf[k], zf[k] + zf[k+1] + ax(k) lambda_j + d(k), -zf[k+1]); the free surface is zf[0] = 0.
+struct TriCoef {
+  double ax = 0, az = 0, d = 0;
+  const double *zrows = nullptr;
+  bool free_surface = false;
+};
+// Build float64 factors of every T_j on the device (tf.gen must equal k.zrows != null).
+// perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra)
+void tri_build_factors(TriFactors &tf, DevBuf &store, const TriCoef &k, double dx, double dz, cudaStream_t s,
+                       int perm_ku = 0);
 // Round a float64 factor set to float32 into `store32` (same layout).
 void tri_make_f32(const TriFactors &t64, TriFactors &t32, DevBuf &store32, cudaStream_t s);
 // y = T^{-1} d per (plane, mode); d and y [planes][nz][nx]; in place allowed.  The launch covers
@@ -160,6 +170,8 @@ struct lag_precond {
   lag_grid grid{};
   int prec = LAG_FP64;
   double ax = 0, az = 0, d = 0;
+  lag::DevBuf zrows;        // layered plans: z-face / per-row coefficients (see lag::TriCoef)
+  lag::TriCoef coef() const;
   lag::DstPlan dst;
   lag::TriFactors tri64, tri32;
   lag::DevBuf dst_store, tri_store, tri32_store;
@@ -187,6 +199,7 @@ struct lag_medium {
   double mid[3] = {0, 0, 0};   // kappa~, rho~ | (l+2m)~, mu~, rho~
   lag::DevBuf coef;            // operator coefficients (see k_ops.cu)
   lag::DevBuf rho_h2;          // rho h^2 at nodes (right-hand side history term)
+  lag::DevBuf rowmm;           // acoustic: per-row [kappa | rho][nz][min, max] (layered preconditioner)
   size_t ncoef = 0;
   void apply(const double *p, double *q, int nrhs, const lag::KrylovScalars *sc,
              const lag::Reduce *red, int mode, cudaStream_t s);
@@ -204,8 +217,10 @@ lag_medium *medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const d
 // rebuild the tridiagonal factors with another partition count / register-kernel mode tile
 // (0 = automatic); used by lag_precond_set_layout and the autotuner
 void precond_rebuild_tri(lag_precond *p, int want_P, int want_mt, cudaStream_t s);
+// layered (nullable, host): [ax(z): nz | az(z): nz | d(z): nz] per-row coefficients; then ax, az, d
+// are unused
 lag_precond *precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
-                         int partitions, cudaStream_t s);
+                         int partitions, cudaStream_t s, const double *layered = nullptr);
 // mode 0: q = Ap only; mode 1: also (p,q) -> alpha = rz/pq  (PCG)
 void acoustic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
                     const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s);
@@ -260,5 +275,7 @@ void gather_receivers(const double *x, const int *rcv_idx, int nrcv, int ncomp, 
 void inverse_sum(const double *rrcv, const double *tab, int nharm, int nrows, int nt,
                  double *traces, cudaStream_t s);
 void midrange_device(const double *f, size_t n, double *minmax_dev, cudaStream_t s);
+// per-row min/max of f [nz][nx] -> minmax_dev [nz][2]
+void row_minmax_device(const double *f, int nx, int nz, double *minmax_dev, cudaStream_t s);
 
 }  // namespace lag

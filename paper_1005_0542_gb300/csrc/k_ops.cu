@@ -46,8 +46,11 @@ __global__ void acoustic_diag_kernel(const double *ax, const double *az, const d
           az[(size_t)(k + 1) * nx + i] + 0.25 * rh2[o];
 }
 
-// single-block min/max (setup only)
+// min/max of f[blockIdx.x * n ...][n] -> out[2 blockIdx.x], out[2 blockIdx.x + 1] (setup only; one
+// block per row, or one block for the whole array)
 __global__ void minmax_kernel(const double *f, size_t n, double *out) {
+  f += (size_t)blockIdx.x * n;
+  out += 2 * (size_t)blockIdx.x;
   double lo = INFINITY, hi = -INFINITY;
   for (size_t i = threadIdx.x; i < n; i += blockDim.x) { lo = fmin(lo, f[i]); hi = fmax(hi, f[i]); }
   __shared__ double sl[32], sh[32];
@@ -69,6 +72,12 @@ __global__ void minmax_kernel(const double *f, size_t n, double *out) {
 
 void midrange_device(const double *f, size_t n, double *minmax_dev, cudaStream_t s) {
   minmax_kernel<<<1, 1024, 0, s>>>(f, n, minmax_dev);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+void row_minmax_device(const double *f, int nx, int nz, double *minmax_dev, cudaStream_t s) {
+  minmax_kernel<<<nz, 256, 0, s>>>(f, (size_t)nx, minmax_dev);
   count_launch();
   LAG_LAUNCH_CHECK();
 }
@@ -105,6 +114,11 @@ void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rh
   LAG_CUDA_CHECK(cudaStreamSynchronize(s));
   m.mid[0] = 0.5 * (h_mm[0] + h_mm[1]);
   m.mid[1] = 0.5 * (h_mm[2] + h_mm[3]);
+  // per-row extremes of kappa and rho (layered preconditioner): [kappa | rho][nz][min, max]
+  m.rowmm.alloc(m.ctx, 4 * (size_t)nz * sizeof(double));
+  row_minmax_device(kap, nx, nz, m.rowmm.as<double>(), s);
+  row_minmax_device(drho, nx, nz, m.rowmm.as<double>() + 2 * (size_t)nz, s);
+  LAG_CUDA_CHECK(cudaStreamSynchronize(s));
 }
 
 // ------------------------------------------------------------------------------ acoustic apply

@@ -31,7 +31,7 @@ bool tri_mode_tile_ok(int elem_bytes, int L, int mt) {
   return (mt == 4 || mt == 8);
 }
 
-void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt) {
+void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt, bool general) {
   const int nz = tf.nz;
   int Pt = (want_P > 0) ? std::min(want_P, 32) : 32;
   while (Pt > 1 && nz / Pt < 2) Pt /= 2;  // at least 2 rows per partition
@@ -49,7 +49,8 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt) 
   }
   tf.P = P;
   tf.L = L;
-  tf.ncls = 3;
+  tf.gen = general;
+  tf.ncls = general ? P : 3;
   const int n = P - 1;
   int lev = 0;
   while ((1 << lev) < n) ++lev;
@@ -67,7 +68,9 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt) 
     if (want_mt > 0 && tri_mode_tile_ok(elem_bytes, L, want_mt)) mt = want_mt;
     tf.mt = mt;
     tf.threads = threads(mt);
-    tf.smem = (size_t)(5 * 3 * L * mt + (3 * 32 + 33) * mt) * elem_bytes;
+    // constant coefficients: the 3 factor classes are staged in shared memory; general systems
+    // (one factor set per partition) read theirs from global memory (L2)
+    tf.smem = (size_t)((general ? 0 : 5 * 3 * L * mt) + (3 * 32 + 33) * mt) * elem_bytes;
     return;
   }
   // shared-memory tile kernel: modes per CTA power of two <= 32, threads <= 1024,
@@ -84,33 +87,52 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt) 
 }
 
 // ------------------------------------------------------------------------------ factors
-// Matrix of mode j: sub a_k, diag b_k, super c_k (rows >= nz: identity).
+// Matrix of mode j: sub a_k, diag b_k, super c_k (rows >= nz: identity).  Constant coefficients
+// (Toeplitz in z): a = c = off, b = diag0 + ax lambda_j (+ top0 on row 0).  Layered coefficients
+// (zf != null): a_k = -zf[k], c_k = -zf[k+1], b_k = zf[k] + zf[k+1] + zax[k] lambda_j + zd[k], with
+// zf the z-face coefficients over dz^2 (zf[0] = 0 under a free surface).
 struct TriMatrix {
   double off, diag0, ax, dx2inv, nxp1;
   double top0;  // added to row 0's diagonal: off (= -az/dz^2) under a free surface, else 0
+  const double *zf, *zax, *zd;
   int nz, perm_ku;
-  __device__ double diag(int c) const {
+  __device__ double sin2(int c) const {
     const int j = (perm_ku > 0) ? (c < perm_ku ? 2 * c : 2 * (c - perm_ku) + 1) : c;  // mode at column c
+    const double s = sinpi((double)(j + 1) / (2.0 * nxp1));
+    return s * s;
+  }
+  // per-mode value handed to row(): the diagonal (constant) or lambda_j (layered)
+  __device__ double mode_value(int c) const {
+    if (zf != nullptr) return 4.0 * dx2inv * sin2(c);
+    const int j = (perm_ku > 0) ? (c < perm_ku ? 2 * c : 2 * (c - perm_ku) + 1) : c;
     const double s = sinpi((double)(j + 1) / (2.0 * nxp1));
     return diag0 + ax * 4.0 * dx2inv * s * s;
   }
-  __device__ void row(int k, double dj, double &a, double &b, double &c) const {
+  __device__ void row(int k, double mv, double &a, double &b, double &c) const {
     if (k >= nz) { a = 0.0; b = 1.0; c = 0.0; return; }
+    if (zf != nullptr) {
+      a = (k >= 1) ? -zf[k] : 0.0;
+      c = (k + 1 < nz) ? -zf[k + 1] : 0.0;
+      b = zf[k] + zf[k + 1] + zax[k] * mv + zd[k];
+      return;
+    }
     a = (k >= 1) ? off : 0.0;
-    b = (k == 0) ? dj + top0 : dj;
+    b = (k == 0) ? mv + top0 : mv;
     c = (k + 1 < nz) ? off : 0.0;
   }
 };
 
 __device__ __forceinline__ int rep_partition(int cls, int P) { return cls == 0 ? 0 : (cls == 1 ? 1 : P - 1); }
 
-// one thread per (mode j, class): block LU factors and spikes of the class's representative block
-__global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, double *fm, double *fc,
+// one thread per (mode j, factor set): block LU factors and spikes of one partition.  Constant
+// coefficients: sets 0/1/2 are the representative first / middle / last partitions; general: set
+// p is partition p.
+__global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, int gen, double *fm, double *fc,
                                   double *fa, double *sv, double *sw) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int cls = blockIdx.y;
   if (j >= nx) return;
-  const bool exists = (cls == 0) || (cls == 1 && P >= 3) || (cls == 2 && P >= 2);
+  const bool exists = gen || (cls == 0) || (cls == 1 && P >= 3) || (cls == 2 && P >= 2);
   const size_t base = (size_t)cls * L * nx + j;
   if (!exists) {
     for (int i = 0; i < L; ++i) {
@@ -119,8 +141,8 @@ __global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, double *fm,
     }
     return;
   }
-  const int p = rep_partition(cls, P);
-  const double dj = M.diag(j);
+  const int p = gen ? cls : rep_partition(cls, P);
+  const double mv = M.mode_value(j);
   const int i0 = (p == 0) ? 0 : 1;
   double a, b, c;
   // separator row slot (i = 0 of p >= 1) is unused by the sweeps
@@ -130,7 +152,7 @@ __global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, double *fm,
   }
   double fc_prev = 0.0;
   for (int i = i0; i < L; ++i) {
-    M.row(p * L + i, dj, a, b, c);
+    M.row(p * L + i, mv, a, b, c);
     const double den = (i == i0) ? b : b - a * fc_prev;
     const double m = 1.0 / den;
     const size_t f = base + (size_t)i * nx;
@@ -141,8 +163,8 @@ __global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, double *fm,
   }
   // spikes: v = T^{-1}(a_first e_first) (p >= 1), w = T^{-1}(c_last e_last) (p <= P-2)
   double a0, b0, c0, aL, bL, cL;
-  M.row(p * L + i0, dj, a0, b0, c0);
-  M.row(p * L + L - 1, dj, aL, bL, cL);
+  M.row(p * L + i0, mv, a0, b0, c0);
+  M.row(p * L + L - 1, mv, aL, bL, cL);
   const bool has_v = p >= 1, has_w = p <= P - 2;
   double vp = 0.0, wp = 0.0;
   for (int i = i0; i < L; ++i) {  // forward elimination of the two unit right-hand sides
@@ -166,10 +188,11 @@ __global__ void tri_factor_kernel(TriMatrix M, int nx, int P, int L, double *fm,
   }
 }
 
-__device__ __forceinline__ int cls_of(int p, int P) { return p == 0 ? 0 : (p == P - 1 ? 2 : 1); }
+// factor set of partition p: itself (general) or its class
+__device__ __forceinline__ int set_of(int p, int P, int gen) { return gen ? p : (p == 0 ? 0 : (p == P - 1 ? 2 : 1)); }
 
 // one thread per mode: reduced (separator) system and its PCR multipliers
-__global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels, int nf,
+__global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels, int nf, int gen,
                                    const double *sv, const double *sw, double *red) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nx) return;
@@ -178,13 +201,13 @@ __global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels
   double *R = red + (size_t)j * nf * 32;
   for (int f = 0; f < nf * 32; ++f) R[f] = 0.0;
   if (n <= 0) return;
-  const double dj = M.diag(j);
+  const double mv = M.mode_value(j);
   for (int q = 0; q < n; ++q) {
     const int p = q + 1;  // separator of partition p at row p L
     double a, b, c;
-    M.row(p * L, dj, a, b, c);
-    const size_t prevL = (size_t)cls_of(p - 1, P) * L * nx + (size_t)(L - 1) * nx + j;
-    const size_t curF = (size_t)cls_of(p, P) * L * nx + (size_t)1 * nx + j;
+    M.row(p * L, mv, a, b, c);
+    const size_t prevL = (size_t)set_of(p - 1, P, gen) * L * nx + (size_t)(L - 1) * nx + j;
+    const size_t curF = (size_t)set_of(p, P, gen) * L * nx + (size_t)1 * nx + j;
     A[q] = -a * sv[prevL];
     B[q] = b - a * sw[prevL] - c * sv[curF];
     C[q] = -c * sw[curF];
@@ -217,8 +240,9 @@ __global__ void tri_reduced_kernel(TriMatrix M, int nx, int P, int L, int levels
   }
 }
 
-void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, double d, double dx,
-                       double dz, cudaStream_t s, int perm_ku, bool free_surface) {
+void tri_build_factors(TriFactors &tf, DevBuf &store, const TriCoef &k, double dx, double dz, cudaStream_t s,
+                       int perm_ku) {
+  if (tf.gen != (k.zrows != nullptr)) throw Error(LAG_EINVAL, "factor layout does not match the coefficients");
   const size_t per = (size_t)tf.ncls * tf.L * tf.nx;
   const size_t nred = (size_t)tf.nx * tf.nf * 32;
   store.alloc(store.ctx, (5 * per + nred) * sizeof(double));
@@ -230,20 +254,24 @@ void tri_build_factors(TriFactors &tf, DevBuf &store, double ax, double az, doub
   tf.sw = base + 4 * per;
   tf.red = base + 5 * per;
   TriMatrix M;
-  M.off = -az / (dz * dz);
-  M.diag0 = 2.0 * az / (dz * dz) + d;
-  M.top0 = free_surface ? M.off : 0.0;
-  M.ax = ax;
+  M.off = -k.az / (dz * dz);
+  M.diag0 = 2.0 * k.az / (dz * dz) + k.d;
+  M.top0 = k.free_surface ? M.off : 0.0;
+  M.ax = k.ax;
   M.dx2inv = 1.0 / (dx * dx);
   M.nxp1 = (double)(tf.nx + 1);
+  M.zf = k.zrows;
+  M.zax = k.zrows ? k.zrows + tf.nz + 1 : nullptr;
+  M.zd = k.zrows ? k.zrows + 2 * tf.nz + 1 : nullptr;
   M.nz = tf.nz;
   M.perm_ku = perm_ku;
-  dim3 g1((tf.nx + 127) / 128, 3);
-  tri_factor_kernel<<<g1, 128, 0, s>>>(M, tf.nx, tf.P, tf.L, (double *)tf.fm, (double *)tf.fc,
+  const int gen = tf.gen ? 1 : 0;
+  dim3 g1((tf.nx + 127) / 128, tf.ncls);
+  tri_factor_kernel<<<g1, 128, 0, s>>>(M, tf.nx, tf.P, tf.L, gen, (double *)tf.fm, (double *)tf.fc,
                                        (double *)tf.fa, (double *)tf.sv, (double *)tf.sw);
   count_launch();
   LAG_LAUNCH_CHECK();
-  tri_reduced_kernel<<<(tf.nx + 63) / 64, 64, 0, s>>>(M, tf.nx, tf.P, tf.L, tf.levels, tf.nf,
+  tri_reduced_kernel<<<(tf.nx + 63) / 64, 64, 0, s>>>(M, tf.nx, tf.P, tf.L, tf.levels, tf.nf, gen,
                                                       (const double *)tf.sv, (const double *)tf.sw,
                                                       (double *)tf.red);
   count_launch();
@@ -280,7 +308,7 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
                                                          const T *__restrict__ fa, const T *__restrict__ sv,
                                                          const T *__restrict__ sw, const T *__restrict__ red,
                                                          const KrylovScalars *__restrict__ sc, int pstride, int poff,
-                                                         int ncomp, int mt) {
+                                                         int ncomp, int mt, int gen) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
   const int nzp = P * L;
@@ -305,9 +333,8 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
   // 2. block-local sweeps: thread (c, p); threads beyond mt * P (warp padding) only synchronise
   const int c = tid % mt, p = tid / mt, j = j0 + c;
   const bool live = j < nx && p < P;
-  const int cls = (p == 0) ? 0 : (p == P - 1 ? 2 : 1);
   const int i0 = (p == 0) ? 0 : 1;
-  const size_t fb = (size_t)cls * L * nx + j;
+  const size_t fb = (size_t)set_of(p, P, gen) * L * nx + j;
   T *col = tile + (size_t)p * L * mt + c;  // row i of this partition at col[i * mt]
   if (live) {
     T prev = T(0);
@@ -382,21 +409,24 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
 // Register-resident variant (partition length L a compile-time power of two): thread (c, p) keeps
 // the L values of its partition in registers, loaded straight from global memory (a warp reads
 // rows of MT consecutive modes: whole 32-byte sectors, 64 bytes per row for float32) and stored
-// back the same way; the factors
-// of the CTA's modes (3 classes x L rows) are staged once in shared memory and reused for the
-// `per_cta` right-hand sides the CTA solves in turn; only the separator ends and the separator
-// solution pass through shared memory.
+// back the same way; only the separator ends and the separator solution pass through shared
+// memory.  Constant coefficients (GEN false): the factors of the CTA's modes (3 classes x L rows)
+// are staged once in shared memory and reused for the `per_cta` right-hand sides the CTA solves in
+// turn.  General systems (GEN true, one factor set per partition): each thread reads its
+// partition's factors from global memory with the same access pattern as the data (L2-resident
+// across the right-hand sides of the CTA).
 // occupancy target of the register kernel: 64 (float32) / 128 (float64) registers a thread at
-// L <= 32, twice that at L = 64
-template <typename T, int L, int MT>
+// L <= 32, twice that at L = 64; general systems (factor addresses per row) twice that again at
+// L >= 32
+template <typename T, int L, int MT, bool GEN>
 struct RegBounds {
   static constexpr int threads = MT * 32;
-  static constexpr int per_sm = (sizeof(T) == 8 ? 512 : 1024) / (L >= 64 ? 2 : 1);
+  static constexpr int per_sm = (sizeof(T) == 8 ? 512 : 1024) / (L >= 64 ? 2 : 1) / ((GEN && L >= 32) ? 2 : 1);
   static constexpr int blocks = per_sm / threads > 0 ? per_sm / threads : 1;
 };
 
-template <typename T, int L, int MT>
-__global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, MT>::blocks) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
+template <typename T, int L, int MT, bool GEN>
+__global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T, L, MT, GEN>::blocks) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
                                                                int nx, int P, int levels, int nf,
                                                                const T *__restrict__ fm, const T *__restrict__ fc,
                                                                const T *__restrict__ fa, const T *__restrict__ sv,
@@ -404,7 +434,7 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, 
                                                                const KrylovScalars *__restrict__ sc, int pstride,
                                                                int poff, int ncomp, int nplanes, int per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int NCR = 3 * L;                 // factor rows: 3 classes x L
+  constexpr int NCR = GEN ? 0 : 3 * L;       // staged factor rows: 3 classes x L
   T *F = reinterpret_cast<T *>(smem_raw);    // [5][NCR][MT]: fm, fa, fc, sv, sw
   T *gF = F + 5 * NCR * MT;                  // [MT][32]
   T *gL = gF + MT * 32;
@@ -413,7 +443,7 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, 
   const int j0 = blockIdx.x * MT;
   const int tid = threadIdx.x, nth = blockDim.x;
   // stage the factors of this CTA's modes: row-major [row][MT], MT a power of two
-  {
+  if constexpr (!GEN) {
     const int cm = tid % MT, r0 = tid / MT, rstep = nth / MT;
     const int j = j0 + cm;
     for (int row = r0; row < NCR; row += rstep) {
@@ -428,13 +458,16 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, 
   }
   const int c = tid % MT, p = tid / MT, j = j0 + c;
   const bool col_ok = j < nx && p < P;
-  const int cls = (p == 0) ? 0 : (p == P - 1 ? 2 : 1);
   const int i0 = (p == 0) ? 0 : 1;
-  const T *Fm = F + (0 * NCR + cls * L) * MT + c;
-  const T *Fa = F + (1 * NCR + cls * L) * MT + c;
-  const T *Fc = F + (2 * NCR + cls * L) * MT + c;
-  const T *Sv = F + (3 * NCR + cls * L) * MT + c;
-  const T *Sw = F + (4 * NCR + cls * L) * MT + c;
+  // factor rows of this thread's partition: stride FS between rows
+  constexpr int FS_SMEM = MT;
+  const int FS = GEN ? nx : FS_SMEM;
+  const size_t fo = GEN ? (size_t)p * L * nx + j : (size_t)(set_of(p, P, 0) * L) * MT + c;
+  const T *Fm = (GEN ? fm : F + 0 * NCR * MT) + fo;
+  const T *Fa = (GEN ? fa : F + 1 * NCR * MT) + fo;
+  const T *Fc = (GEN ? fc : F + 2 * NCR * MT) + fo;
+  const T *Sv = (GEN ? sv : F + 3 * NCR * MT) + fo;
+  const T *Sw = (GEN ? sw : F + 4 * NCR * MT) + fo;
   const int warp = tid >> 5, lane = tid & 31, nwarp = nth >> 5;
   const int n = P - 1;
   __syncthreads();
@@ -459,14 +492,14 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, 
 #pragma unroll
       for (int i = 0; i < L; ++i) {
         if (i < i0) continue;
-        const T m = Fm[i * MT];
-        v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * MT] * prev) * m;
+        const T m = Fm[i * FS];
+        v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * FS] * prev) * m;
         prev = v[i];
       }
 #pragma unroll
       for (int i = L - 2; i >= 0; --i) {
         if (i < i0) continue;
-        v[i] = v[i] - Fc[i * MT] * v[i + 1];
+        v[i] = v[i] - Fc[i * FS] * v[i + 1];
       }
       gF[c * 32 + p] = (i0 == 0) ? v[0] : v[1];
       gL[c * 32 + p] = v[L - 1];
@@ -504,7 +537,7 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, 
 #pragma unroll
       for (int i = 0; i < L; ++i) {
         const int r = p * L + i;
-        const T y = (i < i0) ? xa : v[i] - xa * Sv[i * MT] - xb * Sw[i * MT];
+        const T y = (i < i0) ? xa : v[i] - xa * Sv[i * FS] - xb * Sw[i * FS];
         if (r < nz) dst[(size_t)r * nx] = y;
       }
     }
@@ -512,13 +545,13 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT>::threads, RegBounds<T, L, 
   }
 }
 
-template <typename T, int L, int MT>
+template <typename T, int L, int MT, bool GEN>
 static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
                               cudaStream_t s, int pstride, int poff, int ncomp) {
   static bool attr_done = false;
   if (!attr_done) {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT, GEN>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_done = true;
   }
   // several right-hand sides per CTA when there are plenty of CTAs anyway (factor reuse)
@@ -526,25 +559,32 @@ static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, 
   int per_cta = 1;
   while (per_cta < 8 && (long long)ctas_x * ((nrhs + 2 * per_cta - 1) / (2 * per_cta)) >= 152 * 8) per_cta *= 2;
   dim3 grid(ctas_x, (nrhs + per_cta - 1) / per_cta);
-  tri_solve_reg_kernel<T, L, MT><<<grid, tf.threads, tf.smem, s>>>(
+  tri_solve_reg_kernel<T, L, MT, GEN><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc, (const T *)tf.fa,
       (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, nrhs, per_cta);
+}
+
+template <typename T, int L, int MT>
+static void tri_reg_launch_gen(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
+                               cudaStream_t s, int pstride, int poff, int ncomp) {
+  if (tf.gen) tri_reg_launch_mt<T, L, MT, true>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+  else tri_reg_launch_mt<T, L, MT, false>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
 }
 
 template <typename T, int L>
 static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc, cudaStream_t s,
                            int pstride, int poff, int ncomp) {
   if constexpr (sizeof(T) == 4) {
-    if (tf.mt == 8) tri_reg_launch_mt<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    if (tf.mt == 8) tri_reg_launch_gen<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
     else if constexpr (L <= 32) {
-      if (tf.mt == 32) tri_reg_launch_mt<T, L, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
-      else tri_reg_launch_mt<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+      if (tf.mt == 32) tri_reg_launch_gen<T, L, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+      else tri_reg_launch_gen<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
     } else {
-      tri_reg_launch_mt<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+      tri_reg_launch_gen<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
     }
   } else {
-    if (tf.mt == 8) tri_reg_launch_mt<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
-    else tri_reg_launch_mt<T, L, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    if (tf.mt == 8) tri_reg_launch_gen<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    else tri_reg_launch_gen<T, L, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
   }
 }
 
@@ -574,7 +614,8 @@ static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const K
   dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
   tri_solve_kernel<T><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.L, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc,
-      (const T *)tf.fa, (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, tf.mt);
+      (const T *)tf.fa, (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, tf.mt,
+      tf.gen ? 1 : 0);
   count_launch();
   LAG_LAUNCH_CHECK();
 }

@@ -9,6 +9,7 @@
 // the series is carried in two running sums per source instead of all earlier harmonics.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "solver.h"
 
@@ -64,7 +65,21 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
   cudaStream_t st = sh->stream;
   sh->medium = medium_new(ctx, g, c, vs, rho, lag.h, st);
   const double *mid = sh->medium->mid;
-  if (!elastic) {
+  if (!elastic && s.layered) {
+    // per-row midranges kappa~(z), rho~(z): ax = az = kappa~(z), d = rho~(z) h^2 / 4
+    const int nz = g.nz;
+    std::vector<double> mm(4 * (size_t)nz), rows(3 * (size_t)nz);
+    LAG_CUDA_CHECK(cudaMemcpyAsync(mm.data(), sh->medium->rowmm.ptr, mm.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+    LAG_CUDA_CHECK(cudaStreamSynchronize(st));
+    for (int k = 0; k < nz; ++k) {
+      const double kz = 0.5 * (mm[2 * k] + mm[2 * k + 1]);
+      const double rz = 0.5 * (mm[2 * (nz + k)] + mm[2 * (nz + k) + 1]);
+      rows[k] = rows[nz + k] = kz;
+      rows[2 * nz + k] = rz * lag.h * lag.h / 4.0;
+    }
+    sh->p1 = precond_new(ctx, g, 0.0, 0.0, 0.0, s.prec, s.partitions, st, rows.data());
+  } else if (!elastic) {
     sh->p1 = precond_new(ctx, g, mid[0], mid[0], mid[1] * lag.h * lag.h / 4.0, s.prec, s.partitions, st);
   } else {  // K = diag(B1, B2), Eq. (22): B1 (ax, az) = ((l+2m)~, mu~), B2 = (mu~, (l+2m)~)
     const double d = mid[2] * lag.h * lag.h / 4.0;

@@ -58,20 +58,20 @@ void precond_rebuild_tri(lag_precond *p, int want_P, int want_mt, cudaStream_t s
   TriFactors t64;
   t64.nx = p->grid.nx;
   t64.nz = p->grid.nz;
-  tri_choose_layout(t64, 8, want_P, p->prec == LAG_FP64 ? want_mt : 0);
-  tri_build_factors(t64, p->tri_store, p->ax, p->az, p->d, p->grid.dx, p->grid.dz, s, 0, p->grid.free_surface != 0);
+  const bool gen = p->zrows.ptr != nullptr;
+  tri_choose_layout(t64, 8, want_P, p->prec == LAG_FP64 ? want_mt : 0, gen);
+  tri_build_factors(t64, p->tri_store, p->coef(), p->grid.dx, p->grid.dz, s, 0);
   p->tri64 = t64;
   if (p->prec == LAG_MIXED) {
     TriFactors t32;
     t32.nx = p->grid.nx;
     t32.nz = p->grid.nz;
-    tri_choose_layout(t32, 4, want_P, want_mt);
+    tri_choose_layout(t32, 4, want_P, want_mt, gen);
     if (p->use_tc) {
       TriFactors tp = t64;
       DevBuf tmp;
       tmp.ctx = p->ctx;
-      tri_build_factors(tp, tmp, p->ax, p->az, p->d, p->grid.dx, p->grid.dz, s, p->dst.ku,
-                        p->grid.free_surface != 0);
+      tri_build_factors(tp, tmp, p->coef(), p->grid.dx, p->grid.dz, s, p->dst.ku);
       tri_make_f32(tp, t32, p->tri32_store, s);
       LAG_CUDA_CHECK(cudaStreamSynchronize(s));
     } else {

@@ -31,7 +31,7 @@ class lag_laguerre(C.Structure):
 
 class lag_solver(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("restart_k", C.c_int), ("prec", C.c_int),
-                ("partitions", C.c_int), ("tune", C.c_int)]
+                ("partitions", C.c_int), ("tune", C.c_int), ("layered", C.c_int)]
 
 
 class lag_point(C.Structure):
@@ -83,6 +83,8 @@ _PROTOS = {
     "lag_profile_class_name": (C.c_char_p, [I]),
     "lag_precond_create": (I, [VP, C.POINTER(lag_grid), D, D, D, I, C.POINTER(VP)]),
     "lag_precond_create_sep": (I, [VP, C.POINTER(lag_grid), D, D, D, I, I, C.POINTER(VP)]),
+    "lag_precond_create_layered": (I, [VP, C.POINTER(lag_grid), PD, PD, PD, I, I, C.POINTER(VP)]),
+    "lag_precond_is_layered": (I, [VP]),
     "lag_precond_destroy": (None, [VP]),
     "lag_precond_apply": (I, [VP, VP, VP, I]),
     "lag_precond_dst": (I, [VP, VP, VP, I]),
@@ -185,8 +187,9 @@ def grid(nx, nz, dx, dz, free_surface=False):
     return lag_grid(int(nx), int(nz), float(dx), float(dz), 1 if free_surface else 0)
 
 
-def solver(tol=1e-10, max_iter=2000, restart_k=20, prec=LAG_FP64, partitions=0, tune=0):
-    return lag_solver(float(tol), int(max_iter), int(restart_k), int(prec), int(partitions), int(tune))
+def solver(tol=1e-10, max_iter=2000, restart_k=20, prec=LAG_FP64, partitions=0, tune=0, layered=0):
+    return lag_solver(float(tol), int(max_iter), int(restart_k), int(prec), int(partitions), int(tune),
+                      int(layered))
 
 
 def laguerre(h, alpha, n_harm):

@@ -78,6 +78,18 @@ def test_acoustic_shot_two_layer_small():
     assert np.all(out["iters"] > 1)
 
 
+def test_layered_shot_same_traces_fewer_iterations():
+    # the preconditioner changes the iteration, not the solution: traces equal to the tolerance,
+    # and the per-row midranges take far fewer PCG iterations on a layered medium
+    from paper_1005_0542_gb300 import inputs
+    s = inputs.random_layered(nx=40, nz=32, hx=10.0, n_harm=6)
+    args = (s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, s.sources[0], s.receivers, s.t_out, s.f0, s.t0)
+    a = solve.acoustic_shot(*args, tol=1e-12)
+    b = solve.acoustic_shot(*args, tol=1e-12, layered=True)
+    assert np.linalg.norm(a["traces"] - b["traces"]) <= 1e-9 * np.linalg.norm(a["traces"])
+    assert b["iters"].sum() * 2 < a["iters"].sum()
+
+
 # ------------------------------------------------------------------------- elastic operator
 def _elastic_medium(nz, nx, seed=3):
     rng = np.random.default_rng(seed)
