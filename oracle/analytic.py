@@ -9,6 +9,12 @@
   substitution tau = t - r/c - s^2 removes the inverse-square-root singularity:
       u = 1/(2 pi kappa) int_0^{sqrt(t - r/c)} 2 f(t - r/c - s^2) / sqrt(2r/c + s^2) ds.
 
+* ``point_source_3d``: homogeneous 3D medium, rho u_tt = kappa Lap u + delta_3(x - x0) f(t):
+      u(R, t) = f(t - R/c) / (4 pi kappa R),   R = |x - x0|.
+  In cylindrical coordinates delta_3 = delta(r) delta(z - z0) / (2 pi r) on the axis, the source of
+  Eq. 1; a free surface at z = 0 adds the mirror source at -z0 (the paper's exact solution of
+  Sec. 3.2, f(t - r/c) / (2 pi r) with kappa = 1, is the case z0 = 0 seen on the surface).
+
 * ``oscillator``: one mode of the semi-discrete problem, rho u'' + q u = f(t), u(0)=u'(0)=0:
       u(t) = 1/(rho w) int_0^t sin(w (t - tau)) f(tau) d tau,  w = sqrt(q/rho).
   Its Laguerre coefficients must satisfy the scalar form of the spectral recurrence (Eq. 9):
@@ -41,6 +47,13 @@ def point_source_2d(r, t, kappa, rho, fun, nodes=400, panels=64):
             acc += np.sum(w * 2.0 * fun(tj - r / c - s * s) / np.sqrt(2.0 * r / c + s * s))
         out[j] = acc / (2.0 * math.pi * kappa)
     return out
+
+
+def point_source_3d(R, t, kappa, rho, fun):
+    """u(R, t) for scalar R > 0 and an array of t."""
+    c = math.sqrt(kappa / rho)
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    return np.where(t > R / c, fun(t - R / c), 0.0) / (4.0 * math.pi * kappa * R)
 
 
 def oscillator(t, q, rho, fun, panels=256, order=16):
