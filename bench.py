@@ -311,6 +311,10 @@ def gpu_arm(args, rank, world, local_rank):
     if args.elastic_sources > 0:
         out["elastic"] = elastic_leg(ctx, args)
 
+    # ---- the paper's own 2.5D axisymmetric (r, z) acoustic problem
+    if args.cyl_steps > 0:
+        out["cylindrical"] = cylindrical_leg(ctx, args)
+
     # ---- served stream: Poisson arrivals of acoustic / elastic shots, continuous batching
     out["serving"] = serving_leg(ctx, args)
 
@@ -362,6 +366,56 @@ def batched_leg(ctx, args):
     return {"config": f"2048x1024 model, {nsrc} sources on row 2, mixed path, autotuned plan, one shot; "
                       f"step = one harmonic of every source", "value": nsrc * K / (ms / 1e3), "unit": UNIT, "steps": K,
             "ms_per_step": ms / K, "pcg_iters_per_solve": float(its[:, 1:1 + K].mean())}
+
+
+def cylindrical_leg(ctx, args):
+    """The paper's own 2.5D axisymmetric acoustic problem (Sec. 2.1, the r-weighted scheme of
+    Sec. 2.3, the cylindrical preconditioner: DCT-II along z + general tridiagonal systems along r).
+    Sec. 3.2's experiment: homogeneous half space, a point source on the axis at the surface, the
+    wavelet of Eq. 23 (30 Hz, t0 = 0.2 s, gamma = 4), alpha = 9, h = 400, mesh step lambda/40, on
+    2^k x 2^k nodes; here 2048 x 2048 (the paper's smallest mesh is 4096^2), FP64 path, where A == B
+    and PCG takes one iteration; plus a random layered half space (layers along z) at 2048 x 1024
+    for the iterative case.  step = one harmonic."""
+    import torch
+    from paper_1005_0542_gb300 import inputs
+    from paper_1005_0542_gb300 import lagwave as L
+    out = {}
+    for key, nr, nz, layered, prec in (("homogeneous_fp64", 2048, 2048, False, L.LAG_FP64),
+                                       ("layered_fp64", 2048, 1024, True, L.LAG_FP64),
+                                       ("layered_mixed", 2048, 1024, True, L.LAG_MIXED)):
+        s = inputs.cylindrical(nr=nr, nz=nz, n_harm=64, layered=layered)
+        g = L.grid(s.nx, s.nz, s.hx, s.hz, cylindrical=True)
+        lag = L.laguerre(s.h, s.alpha, s.n_harm)
+        sv = L.solver(tol=1e-10, prec=prec)
+        w = L.wavelet(s.f0, s.t0, 4.0, L.LAG_WAVELET_PAPER)
+        c_, pc = L.f64(s.c)
+        r_, pr = L.f64(s.rho)
+        t_, pt = L.f64(s.t_out)
+        sh = C.c_void_p()
+        L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                                  L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                                  C.byref(sh)), ctx)
+        W, K = 3, args.cyl_steps
+        for _ in range(W):
+            L.check(L.lag_shot_step(sh, 1), ctx)
+        stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            L.check(L.lag_shot_step(sh, 1), ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        its = np.zeros((1, s.n_harm), dtype=np.int32)
+        st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+        L.lag_shot_stats(sh, C.byref(st))
+        L.lag_shot_destroy(sh)
+        out[key] = {"grid_r_z": [nr, nz], "h_m": s.hx, "value": K / (ms / 1e3), "unit": UNIT, "steps": K,
+                    "ms_per_step": ms / K, "pcg_iters_per_step": float(its[0, W:W + K].mean())}
+    out["config"] = ("2.5D axisymmetric acoustic half space (r, z), source on the axis, Eq. 23 wavelet 30 Hz, "
+                     "mesh lambda/40; homogeneous (Sec. 3.2) and random layered media")
+    return out
 
 
 def elastic_leg(ctx, args):
@@ -667,6 +721,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--elastic-sources", type=int, default=16, help="0 skips the elastic leg")
     ap.add_argument("--elastic-steps", type=int, default=2)
+    ap.add_argument("--cyl-steps", type=int, default=8, help="harmonics timed per cylindrical case; 0 skips the leg")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-active", type=int, default=8)
     ap.add_argument("--serve-nharm", type=int, nargs=2, default=[4, 16])

@@ -71,8 +71,18 @@ typedef struct lag_shot    lag_shot;
 /* Interior nodes nx x nz with spacing dx, dz (m); u = 0 on the ghost nodes around them, except
  * that free_surface = 1 puts a free surface on top (Sec. 2.1, Eq. 3: du/dz = 0 at z = 0), read
  * as a top face of node row 0 that carries no flux (acoustic problems only; elastic media return
- * LAG_EINVAL).  The surface lies half a cell above row 0. */
-typedef struct { int nx, nz; double dx, dz; int free_surface; } lag_grid;
+ * LAG_EINVAL).  The surface lies half a cell above row 0.  Fields are [nz][nx], x fastest.
+ *
+ * cylindrical = 1: the paper's own 2.5D axisymmetric problem (Sec. 2.1 Eqs. 1-5, the scheme of
+ * Sec. 2.3 Eqs. 17-19), acoustic only.  x is then the radius r: nodes r_i = (i + 1/2) dx from the
+ * axis (the axis face carries no flux, Eq. 5), u = 0 on the ghost node r = (nx + 1/2) dx; z_k =
+ * (k + 1/2) dz with zero-flux faces at z = 0 (the free surface, Eq. 3) and at z = nz dz (the
+ * auxiliary boundary).  free_surface must be 1.  Every term carries the factor r (a1 = rbar
+ * kappa, a2 = r kappa, w = r rho h^2/4; the source f_m / (2 pi dx dz) at its node, the history
+ * term r rho h^2).  Fields of cylindrical grids are [nx][nz]: radius index slow, depth index
+ * fastest (the DCT-II along z runs over contiguous rows, the general tridiagonal systems along r
+ * over columns); lag_point (ix, iz) is still (radius index, depth index). */
+typedef struct { int nx, nz; double dx, dz; int free_surface; int cylindrical; } lag_grid;
 typedef struct { double h; int alpha; int n_harm; } lag_laguerre; /* Sec. 2.1: h (1/s), alpha >= 2 */
 typedef struct {
   double tol;       /* stop when ||r||_2 / ||b||_2 <= tol (recursive residual)                    */
@@ -154,6 +164,10 @@ int  lag_precond_apply(lag_precond *p, const double *r_dev, double *z_dev, int n
  * tridiag:  for every rhs b and mode j solve T_j y[b][:][j] = d[b][:][j] along z (float64 plan).
  * tridiag_f32: the same on float32 data (LAG_MIXED plan). */
 int  lag_precond_dst(lag_precond *p, const double *x_dev, double *y_dev, int nrhs);
+/* The inverse transform of a float64 plan: the forward one again for the DST-I (S^2 = I); for
+ * cylindrical plans x = V y with the orthonormal DCT-II V[k][q] = c_q cos(pi q (k + 1/2) / n)
+ * (lag_precond_dst applies V^T there).  LAG_EINVAL for mixed plans. */
+int  lag_precond_dst_inverse(lag_precond *p, const double *x_dev, double *y_dev, int nrhs);
 int  lag_precond_tridiag(lag_precond *p, const double *d_dev, double *y_dev, int nrhs);
 int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, int nrhs);
 /* Mixed plan only: y = S x from a float32 input (the inverse-transform kernel of the mixed path,

@@ -75,21 +75,22 @@ void lag_precond::ensure_scratch(int nrhs) {
   scratch_rhs = nrhs;
 }
 
-void lag_precond::apply(const double *r, double *z, int nrhs, const KrylovScalars *sc, cudaStream_t s) {
+void lag_precond::apply(const double *r, double *z, int nrhs, const KrylovScalars *sc, cudaStream_t s,
+                        bool rscale) {
   ensure_scratch(nrhs);
   const int rows = nrhs * grid.nz;
   if (prec == LAG_FP64) {
     double *w = scratch.as<double>();
     dst_apply_f64(dst, r, w, rows, grid.nz, sc, s);
     tri_solve_f64(tri64, w, w, nrhs, sc, s);
-    dst_apply_f64(dst, w, z, rows, grid.nz, sc, s);
+    dst_inverse_f64(dst, w, z, rows, grid.nz, sc, s);
   } else {
     float *w = scratch.as<float>();
     if (use_tc) dst_apply_tc_d2f(dst, r, w, rows, grid.nz, sc, s);
-    else dst_apply_f32_d2f(dst, r, w, rows, grid.nz, sc, s);
+    else dst_apply_f32_d2f(dst, r, w, rows, grid.nz, sc, s, rscale);
     tri_solve_f32(tri32, w, w, nrhs, sc, s);
     if (use_tc) dst_apply_tc_f2d(dst, w, z, rows, grid.nz, sc, s);
-    else dst_apply_f32_f2d(dst, w, z, rows, grid.nz, sc, s);
+    else dst_inverse_f32_f2d(dst, w, z, rows, grid.nz, sc, s, rscale);
   }
 }
 
@@ -100,14 +101,46 @@ lag::TriCoef lag_precond::coef() const {
   k.d = d;
   k.zrows = zrows.ptr ? zrows.as<double>() : nullptr;
   k.free_surface = grid.free_surface != 0;
+  k.dct = grid.cylindrical != 0;
   return k;
 }
 
-lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
-                              int partitions, cudaStream_t s, const double *layered) {
+lag_grid lag::kernel_grid(const lag_grid &g) {
   if (g.nx < 1 || g.nz < 1 || !(g.dx > 0) || !(g.dz > 0)) throw Error(LAG_EINVAL, "bad grid");
+  if ((g.free_surface != 0 && g.free_surface != 1) || (g.cylindrical != 0 && g.cylindrical != 1))
+    throw Error(LAG_EINVAL, "free_surface and cylindrical must be 0 or 1");
+  if (!g.cylindrical) return g;
+  if (!g.free_surface) throw Error(LAG_EINVAL, "cylindrical grids have a free surface on top: set free_surface = 1");
+  lag_grid k{};
+  k.nx = g.nz;
+  k.nz = g.nx;
+  k.dx = g.dz;
+  k.dz = g.dx;
+  k.free_surface = 0;  // the zero-flux faces are part of the cylindrical coefficients
+  k.cylindrical = 1;
+  return k;
+}
+
+lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, double az, double d, int prec,
+                              int partitions, cudaStream_t s, const double *layered) {
+  const lag_grid g = kernel_grid(gu);
   std::vector<double> zr;
-  if (layered != nullptr) {
+  if (g.cylindrical) {
+    // Eq. 21 with the cylindrical coefficients a1 = rbar ax, a2 = r az, d(r) = r d: after the
+    // DCT-II along z, per z-mode q the system along r has the rows
+    //   (-ax i/dr, ax (2i+1)/dr + r_i az mu_q + r_i d, -ax (i+1)/dr)   (r_i = (i + 1/2) dr)
+    if (layered != nullptr) throw Error(LAG_EINVAL, "the layered preconditioner is Cartesian only");
+    if (!(ax > 0) || !(az > 0) || !(d >= 0)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+    const int nr = g.nz;
+    const double dr = g.dz;
+    zr.resize(3 * (size_t)nr + 1);
+    for (int i = 0; i <= nr; ++i) zr[i] = ax * (double)i / dr;   // rbar ax / dr^2 with rbar = i dr
+    for (int i = 0; i < nr; ++i) {
+      const double ri = (i + 0.5) * dr;
+      zr[nr + 1 + i] = ri * az;
+      zr[2 * nr + 1 + i] = ri * d;
+    }
+  } else if (layered != nullptr) {
     // per-row coefficients -> z faces (mean of the two rows; a boundary face takes its row's value,
     // the top face carries no flux under a free surface), each over dz^2
     const int nz = g.nz;
@@ -125,7 +158,8 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
       zr[2 * nz + 1 + k] = ld[k];
     }
     ax = az = d = 0.0;
-  } else if (!(ax > 0) || !(az > 0) || !(d >= 0)) {
+  }
+  if (!g.cylindrical && layered == nullptr && (!(ax > 0) || !(az > 0) || !(d >= 0))) {
     throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
   }
   if (prec != LAG_FP64 && prec != LAG_MIXED) throw Error(LAG_EINVAL, "prec must be LAG_FP64 or LAG_MIXED");
@@ -138,14 +172,15 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double
   p->d = d;
   p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = p->tc_scratch.ctx = ctx;
   p->zrows.ctx = ctx;
-  const bool gen = layered != nullptr;
+  const bool gen = !zr.empty();
   if (gen) {
     p->zrows.alloc(ctx, zr.size() * sizeof(double));
     LAG_CUDA_CHECK(cudaMemcpyAsync(p->zrows.ptr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
-  const bool oz = (prec == LAG_FP64) && dst_oz_supported(g.nx) && !tc_disabled();
-  dst_build(p->dst, p->dst_store, g.nx, p->use_tc ? 1 : (oz ? 2 : 0), s);
+  // the DCT-II of cylindrical plans runs on the SIMT pipes (no tensor-core variant)
+  p->use_tc = (prec == LAG_MIXED) && !g.cylindrical && dst_tc_supported(g.nx) && !tc_disabled();
+  const bool oz = (prec == LAG_FP64) && !g.cylindrical && dst_oz_supported(g.nx) && !tc_disabled();
+  dst_build(p->dst, p->dst_store, g.nx, p->use_tc ? 1 : (oz ? 2 : 0), s, g.cylindrical ? 1 : 0);
   if (p->use_tc || p->dst.oz) {
     p->dst.tc_err = reinterpret_cast<int *>(p->dst_store.as<uint8_t>() + p->dst_store.bytes - 256);
     const char *ev = std::getenv("LAGWAVE_DST_PRODUCTS");  // default split-product count
@@ -181,9 +216,9 @@ void lag_medium::apply(const double *p, double *q, int nrhs, const KrylovScalars
   else acoustic_apply(*this, p, q, nrhs, sc, red, mode, s);
 }
 
-lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const double *vs, const double *rho,
+lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &gu, const double *c, const double *vs, const double *rho,
                             double h, cudaStream_t s) {
-  if (g.nx < 1 || g.nz < 1 || !(g.dx > 0) || !(g.dz > 0)) throw Error(LAG_EINVAL, "bad grid");
+  const lag_grid g = kernel_grid(gu);
   if (c == nullptr || rho == nullptr) throw Error(LAG_EINVAL, "null medium array");
   if (!(h > 0)) throw Error(LAG_EINVAL, "Laguerre h must be positive");
   std::unique_ptr<lag_medium> m(new lag_medium());
@@ -193,8 +228,10 @@ lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, co
   m->coef.ctx = m->rho_h2.ctx = m->rowmm.ctx = ctx;
   if (vs == nullptr) {
     m->elastic = false;
-    medium_build_acoustic(*m, c, rho, s);
+    if (g.cylindrical) medium_build_cylindrical(*m, c, rho, s);
+    else medium_build_acoustic(*m, c, rho, s);
   } else {
+    if (g.cylindrical) throw Error(LAG_EINVAL, "cylindrical grids are acoustic only (the elastic 2.5D problem is not built)");
     if (g.free_surface)
       throw Error(LAG_EINVAL, "free_surface applies to acoustic media only (the elastic traction-free surface is not built)");
     m->elastic = true;
@@ -377,6 +414,16 @@ int lag_precond_dst(lag_precond *p, const double *x, double *y, int nrhs) {
         widen_f32(w, y, (size_t)rows * p->grid.nx, p->ctx->stream);
       }
     }
+  });
+}
+
+int lag_precond_dst_inverse(lag_precond *p, const double *x, double *y, int nrhs) {
+  if (!p || nrhs < 0 || (nrhs > 0 && (!x || !y)) || p->prec != LAG_FP64) return LAG_EINVAL;
+  return guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    if (nrhs == 0) return;
+    p->ensure_scratch(nrhs);
+    dst_inverse_f64(p->dst, x, y, nrhs * p->grid.nz, p->grid.nz, nullptr, p->ctx->stream);
   });
 }
 

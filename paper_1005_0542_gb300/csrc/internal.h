@@ -90,6 +90,7 @@ struct TriCoef {
   double ax = 0, az = 0, d = 0;
   const double *zrows = nullptr;
   bool free_surface = false;
+  bool dct = false;  // modes of a DCT-II plan (cylindrical z): lambda_j = 4/dx^2 sin^2(pi j / (2 nx))
 };
 // Build float64 factors of every T_j on the device (tf.gen must equal k.zrows != null).
 // perm_ku > 0: column c holds mode 2c (c < perm_ku) or 2(c - perm_ku) + 1 (parity-permuted spectra)
@@ -109,11 +110,15 @@ void tri_solve_f32(const TriFactors &tf, const float *d, float *y, int nplanes,
 
 // ----------------------------------------------------------------- DST (a7, a9)
 struct DstPlan {
+  int kind = 0;         // 0: DST-I (Dirichlet, self-inverse); 1: DCT-II (zero-flux faces, cylindrical z)
   int n = 0;            // transform length nx
   int ku = 0, kv = 0;   // ceil(n/2), floor(n/2): inner dimensions of the two folded GEMMs
   double *su = nullptr; // [ku][ku]  S[j][2k]    (float64)
   double *sv = nullptr; // [kv][kv]  S[j][2k+1]
   float *su_f = nullptr, *sv_f = nullptr;  // float32 copies (SIMT float32 kernel)
+  // DCT-II inverse (kind 1): ie [ku][ku] = V[k][2q'] as [q'][k], io [kv][ku] = V[k][2q'+1] as [q'][k]
+  double *ie = nullptr, *io = nullptr;
+  float *ie_f = nullptr, *io_f = nullptr;
   // tensor-core path: four packed split-bf16 B operands (forward even/odd, inverse E/O), each
   // [n tile][k stage][hi|lo][256 x 64 swizzled]; per-apply A-operand / E-O scratch; error word
   uint8_t *tc_b = nullptr;
@@ -129,8 +134,18 @@ struct DstPlan {
   size_t oz_slice_bytes = 0;
   int oz_eB = 0;              // |S| < 2^oz_eB
 };
-// tc_mode: 0 none, 1 split-bf16 operands (mixed path), 2 exact slices (float64 path)
-void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s);
+// tc_mode: 0 none, 1 split-bf16 operands (mixed path), 2 exact slices (float64 path); kind 1
+// (DCT-II) takes tc_mode 0 only
+void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s, int kind = 0);
+// the inverse transform: the forward one again for DST-I (S^2 = I), the transpose for DCT-II
+void dst_inverse_f64(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
+                     const KrylovScalars *sc, cudaStream_t s);
+void dst_inverse_f64_simt(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
+                          const KrylovScalars *sc, cudaStream_t s);
+// rscale (PCG only, sc non-null): the float32 pipeline sees each right-hand side scaled by 2^-e,
+// e = the binary exponent of its residual norm sc[b].rr, undone exactly on the float64 output
+void dst_inverse_f32_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
+                         const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
 // Y[row][:] = S X[row][:] for `rows` rows of length n.  Input/output types as named.
 void dst_apply_f64(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
                    const KrylovScalars *sc, cudaStream_t s);
@@ -145,9 +160,9 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
                   const KrylovScalars *sc, cudaStream_t s);
 // mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
-                       const KrylovScalars *sc, cudaStream_t s);
+                       const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
 void dst_apply_f32_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
-                       const KrylovScalars *sc, cudaStream_t s);
+                       const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
 // mixed path: float64 in -> float32 out, and float32 in -> float64 out (tensor cores)
 void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
                       const KrylovScalars *sc, cudaStream_t s);
@@ -180,8 +195,10 @@ struct lag_precond {
   int scratch_rhs = 0;
   bool use_tc = false;      // mixed path: DST on tcgen05 tensor cores (else SIMT float32)
   void ensure_scratch(int nplanes);
-  // z = B^{-1} r for nrhs planes; sc (nullable) lets converged right-hand sides skip the work
-  void apply(const double *r, double *z, int nrhs, const lag::KrylovScalars *sc, cudaStream_t s);
+  // z = B^{-1} r for nrhs planes; sc (nullable) lets converged right-hand sides skip the work;
+  // rscale: r is a PCG residual whose norm is sc[b].rr (scales the float32 SIMT pipeline)
+  void apply(const double *r, double *z, int nrhs, const lag::KrylovScalars *sc, cudaStream_t s,
+             bool rscale = false);
 };
 
 namespace lag {
@@ -209,9 +226,17 @@ namespace lag {
 // ----------------------------------------------------------------- operator and vector kernels
 void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rho_host,
                            cudaStream_t s);
+// cylindrical (r, z) acoustic medium on the kernel grid (rows = radii; see kernel_grid)
+void medium_build_cylindrical(lag_medium &m, const double *c_host, const double *rho_host, cudaStream_t s);
 void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs_host,
                           const double *rho_host, cudaStream_t s);
-// build a medium / a separable preconditioner plan on stream s (blocking)
+// The grid the kernels run on.  Cartesian: the user's grid.  Cylindrical (fields [nr][nz], depth
+// fastest): rows are the radii and the row length the depth nodes, i.e. nx = nz_user,
+// nz = nr, dx = dz_user, dz = dr (the transform runs along z, the tridiagonal systems along r).
+// Throws LAG_EINVAL on an inconsistent grid.
+lag_grid kernel_grid(const lag_grid &g);
+// build a medium / a separable preconditioner plan on stream s (blocking); both take the user's grid
+// and keep the kernel grid
 lag_medium *medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const double *vs,
                        const double *rho, double h, cudaStream_t s);
 // rebuild the tridiagonal factors with another partition count / register-kernel mode tile

@@ -121,6 +121,67 @@ void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rh
   LAG_CUDA_CHECK(cudaStreamSynchronize(s));
 }
 
+// Cylindrical (r, z) medium (Sec. 2.3, Eqs. 17-19, the equation multiplied by r), kernel layout
+// rows = radius i (nr rows), row length = depth k (nzc nodes): ax holds the z faces (a2 = r_i
+// kappa(face) / dz^2, zero on the surface and on the bottom face), az the r faces (a1 = rbar kappa /
+// dr^2 with rbar = i dr: zero on the axis; the outer face to the ghost node takes its node's
+// kappa), rh2 = r rho h^2.  c, rho: [nr][nzc].
+__global__ void cylindrical_coef_kernel(const double *__restrict__ c, const double *__restrict__ rho, int nzc, int nr,
+                                        double dz, double dr, double h2, double *ax, double *az, double *rh2,
+                                        double *kap) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // depth index (fastest)
+  const int i = blockIdx.y;                             // radius index
+  if (k > nzc || i > nr) return;
+  auto K = [&](int ii, int kk) { const size_t o = (size_t)ii * nzc + kk; return rho[o] * c[o] * c[o]; };
+  if (i < nr) {  // z face k of radius i (between depth nodes k-1 and k)
+    const double ri = (i + 0.5) * dr;
+    const double v = (k == 0 || k == nzc) ? 0.0 : ri * 0.5 * (K(i, k - 1) + K(i, k));
+    ax[(size_t)i * (nzc + 1) + k] = v / (dz * dz);
+  }
+  if (k < nzc) {  // r face i of depth k (between radii i-1 and i), rbar = i dr
+    const double rb = i * dr;
+    const double v = (i == 0) ? 0.0 : rb * (i == nr ? K(nr - 1, k) : 0.5 * (K(i - 1, k) + K(i, k)));
+    az[(size_t)i * nzc + k] = v / (dr * dr);
+  }
+  if (i < nr && k < nzc) {
+    const size_t o = (size_t)i * nzc + k;
+    rh2[o] = (i + 0.5) * dr * rho[o] * h2;
+    kap[o] = K(i, k);
+  }
+}
+
+void medium_build_cylindrical(lag_medium &m, const double *c_host, const double *rho_host, cudaStream_t s) {
+  const int nzc = m.grid.nx, nr = m.grid.nz;  // kernel layout: rows = radii
+  const size_t n = (size_t)nzc * nr;
+  const size_t nax = (size_t)nr * (nzc + 1), naz = (size_t)(nr + 1) * nzc;
+  m.ncoef = nax + naz + 2 * n;
+  m.coef.alloc(m.ctx, m.ncoef * sizeof(double));
+  m.rho_h2.alloc(m.ctx, n * sizeof(double));
+  DevBuf tmp;
+  tmp.alloc(m.ctx, (2 * n + 4) * sizeof(double));
+  double *dc = tmp.as<double>(), *drho = dc + n, *mm = drho + n;
+  LAG_CUDA_CHECK(cudaMemcpyAsync(dc, c_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  LAG_CUDA_CHECK(cudaMemcpyAsync(drho, rho_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  double *ax = m.coef.as<double>(), *az = ax + nax, *dg = az + naz, *kap = dg + n;
+  dim3 g((nzc + 1 + 127) / 128, nr + 1);
+  cylindrical_coef_kernel<<<g, 128, 0, s>>>(dc, drho, nzc, nr, m.grid.dx, m.grid.dz, m.h * m.h, ax, az,
+                                            m.rho_h2.as<double>(), kap);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  dim3 g2((nzc + 127) / 128, nr);
+  acoustic_diag_kernel<<<g2, 128, 0, s>>>(ax, az, m.rho_h2.as<double>(), nzc, nr, dg);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+  // whole-medium midranges kappa~ and rho~ (footnote to Eq. 21; the r weights enter the plan)
+  midrange_device(kap, n, mm, s);
+  midrange_device(drho, n, mm + 2, s);
+  double h_mm[4];
+  LAG_CUDA_CHECK(cudaMemcpyAsync(h_mm, mm, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LAG_CUDA_CHECK(cudaStreamSynchronize(s));
+  m.mid[0] = 0.5 * (h_mm[0] + h_mm[1]);
+  m.mid[1] = 0.5 * (h_mm[2] + h_mm[3]);
+}
+
 // ------------------------------------------------------------------------------ acoustic apply
 // 32 x 8 point tiles walked grid-stride by a bounded number of blocks per rhs (the partial sums of
 // (p, q) stay few, so the last block's deterministic sum is short).  mode 1: also alpha = rz / pq.

@@ -64,7 +64,7 @@ int lag_precond_apply_static(lag_precond *p, const double *r, double *z, int nrh
     const int rows = nrhs * p->grid.nz;
     dst_apply_f64_simt(p->dst, r, spec, rows, p->grid.nz, nullptr, ctx->stream);
     tri_solve_f64(p->tri64, spec, spec, nrhs, nullptr, ctx->stream);
-    dst_apply_f64_simt(p->dst, spec, z, rows, p->grid.nz, nullptr, ctx->stream);
+    dst_inverse_f64_simt(p->dst, spec, z, rows, p->grid.nz, nullptr, ctx->stream);
     return LAG_OK;
   } catch (const Error &e) {
     ctx->last_error = e.what();

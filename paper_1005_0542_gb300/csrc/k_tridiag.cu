@@ -88,17 +88,19 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt, 
 
 // ------------------------------------------------------------------------------ factors
 // Matrix of mode j: sub a_k, diag b_k, super c_k (rows >= nz: identity).  Constant coefficients
-// (Toeplitz in z): a = c = off, b = diag0 + ax lambda_j (+ top0 on row 0).  Layered coefficients
+// (Toeplitz in z): a = c = off, b = diag0 + ax lambda_j (+ top0 on row 0).  General coefficients
 // (zf != null): a_k = -zf[k], c_k = -zf[k+1], b_k = zf[k] + zf[k+1] + zax[k] lambda_j + zd[k], with
-// zf the z-face coefficients over dz^2 (zf[0] = 0 under a free surface).
+// zf the face coefficients over dz^2 (layered: zf[0] = 0 under a free surface; cylindrical: the
+// r-faces, zf[0] = 0 on the axis).  lambda_j: DST-I eigenvalues, or DCT-II ones for dct plans.
 struct TriMatrix {
   double off, diag0, ax, dx2inv, nxp1;
   double top0;  // added to row 0's diagonal: off (= -az/dz^2) under a free surface, else 0
   const double *zf, *zax, *zd;
   int nz, perm_ku;
+  int dct;  // modes of the DCT-II (zero-flux faces): lambda_j = 4/dx^2 sin^2(pi j / (2 nx))
   __device__ double sin2(int c) const {
     const int j = (perm_ku > 0) ? (c < perm_ku ? 2 * c : 2 * (c - perm_ku) + 1) : c;  // mode at column c
-    const double s = sinpi((double)(j + 1) / (2.0 * nxp1));
+    const double s = dct ? sinpi((double)j / (2.0 * (nxp1 - 1.0))) : sinpi((double)(j + 1) / (2.0 * nxp1));
     return s * s;
   }
   // per-mode value handed to row(): the diagonal (constant) or lambda_j (layered)
@@ -265,6 +267,8 @@ void tri_build_factors(TriFactors &tf, DevBuf &store, const TriCoef &k, double d
   M.zd = k.zrows ? k.zrows + 2 * tf.nz + 1 : nullptr;
   M.nz = tf.nz;
   M.perm_ku = perm_ku;
+  M.dct = k.dct ? 1 : 0;
+  if (k.dct && !k.zrows) throw Error(LAG_EINVAL, "DCT-II modes need general coefficients");
   const int gen = tf.gen ? 1 : 0;
   dim3 g1((tf.nx + 127) / 128, tf.ncls);
   tri_factor_kernel<<<g1, 128, 0, s>>>(M, tf.nx, tf.P, tf.L, gen, (double *)tf.fm, (double *)tf.fc,

@@ -39,8 +39,8 @@ void check_solver(const lag_solver &s, bool elastic) {
 
 void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, double *z, int nrhs, int ncomp,
                          const KrylovScalars *sc, cudaStream_t s) {
-  if (ncomp == 1) {
-    p1->apply(r, z, nrhs, sc, s);
+  if (ncomp == 1) {  // PCG: r is the residual whose norm sc[b].rr holds
+    p1->apply(r, z, nrhs, sc, s, true);
     return;
   }
   // two components share the DST (same nx); the tridiagonal factors differ per component
@@ -53,7 +53,7 @@ void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, doub
     dst_apply_f64(p1->dst, r, w, rows, rpr, sc, s);
     tri_solve_f64(p1->tri64, w, w, nrhs, sc, s, ncomp, 0, ncomp);
     tri_solve_f64(p2->tri64, w, w, nrhs, sc, s, ncomp, 1, ncomp);
-    dst_apply_f64(p1->dst, w, z, rows, rpr, sc, s);
+    dst_inverse_f64(p1->dst, w, z, rows, rpr, sc, s);
   } else {
     float *w = p1->scratch.as<float>();
     if (p1->use_tc) dst_apply_tc_d2f(p1->dst, r, w, rows, rpr, sc, s);
@@ -61,7 +61,7 @@ void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, doub
     tri_solve_f32(p1->tri32, w, w, nrhs, sc, s, ncomp, 0, ncomp);
     tri_solve_f32(p2->tri32, w, w, nrhs, sc, s, ncomp, 1, ncomp);
     if (p1->use_tc) dst_apply_tc_f2d(p1->dst, w, z, rows, rpr, sc, s);
-    else dst_apply_f32_f2d(p1->dst, w, z, rows, rpr, sc, s);
+    else dst_inverse_f32_f2d(p1->dst, w, z, rows, rpr, sc, s);
   }
 }
 

@@ -65,6 +65,7 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
   cudaStream_t st = sh->stream;
   sh->medium = medium_new(ctx, g, c, vs, rho, lag.h, st);
   const double *mid = sh->medium->mid;
+  if (g.cylindrical && s.layered) throw Error(LAG_EINVAL, "the layered preconditioner is Cartesian only");
   if (!elastic && s.layered) {
     // per-row midranges kappa~(z), rho~(z): ax = az = kappa~(z), d = rho~(z) h^2 / 4
     const int nz = g.nz;
@@ -101,8 +102,10 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
   sh->tables.alloc(ctx, ntab * sizeof(double), true);
   sh->idx.alloc(ctx, (size_t)(nsrc + nrcv + 1) * sizeof(int));
   std::vector<int> hidx(nsrc + nrcv + 1, 0);
-  for (int i = 0; i < nsrc; ++i) hidx[i] = src[i].iz * g.nx + src[i].ix;
-  for (int i = 0; i < nrcv; ++i) hidx[nsrc + i] = rcv[i].iz * g.nx + rcv[i].ix;
+  // node offsets in the field layout: [nz][nx] (Cartesian) or [nx][nz] (cylindrical)
+  auto offset = [&](const lag_point &q) { return g.cylindrical ? q.ix * g.nz + q.iz : q.iz * g.nx + q.ix; };
+  for (int i = 0; i < nsrc; ++i) hidx[i] = offset(src[i]);
+  for (int i = 0; i < nrcv; ++i) hidx[nsrc + i] = offset(rcv[i]);
   LAG_CUDA_CHECK(cudaMemcpyAsync(sh->idx.ptr, hidx.data(), hidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   source_coeffs_device(lag, w, sh->fm(), sh->fm_scratch, ctx, st);
   if (nt > 0) {
@@ -133,8 +136,11 @@ int lag_shot::pump(bool block) {
     if (failed) return 1;
     if (m >= lag.n_harm) return 1;
     if (phase == 0) {
+      // point source per unit cell: 1/(dx dz); cylindrical: 1/(2 pi dr dz) (Eq. 1's delta / (2 pi r)
+      // in the r-weighted equation)
+      const double inv_cell = grid.cylindrical ? 1.0 / (2.0 * M_PI * grid.dx * grid.dz) : 1.0 / (grid.dx * grid.dz);
       laguerre_rhs(medium->rho_h2.as<double>(), S, cm[m], fm(), m, src_idx, elastic ? 1 : 0,
-                   1.0 / (grid.dx * grid.dz), ncomp, nplane, nsrc, wk.r(), wk.x(), solver.tol, wk.sc(),
+                   inv_cell, ncomp, nplane, nsrc, wk.r(), wk.x(), solver.tol, wk.sc(),
                    wk.red.get(), stream);
       wk.start_from_r();
       wk.enqueue_chunk();

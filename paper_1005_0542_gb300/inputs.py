@@ -97,6 +97,28 @@ def random_layered(nx=2048, nz=1024, hx=5.0, n_harm=512, seed=SEED_BASE + 2, f0=
                 t_out=np.linspace(0.002, 1.0, 500))
 
 
+def cylindrical(nr=2048, nz=2048, h=None, n_harm=3000, layered=False, seed=SEED_BASE + 5, f0=30.0):
+    """The paper's axisymmetric acoustic experiment (Sec. 3.2): a point source on the axis at the
+    free surface, the Gaussian-modulated sine of Eq. 23 (f0 = 30 Hz, t0 = 0.2 s, gamma = 4),
+    alpha = 9, Laguerre h = 400, mesh step lambda/40, receivers on the surface row.  Homogeneous
+    (c = 2000 m/s, rho = 1000 kg/m^3) as in the paper, or a random layered medium (the layers
+    along z, the generator of the Cartesian workload) for the iterative behaviour.  Fields are
+    [nr][nz] (depth fastest); sources / receivers are (radius index, depth index)."""
+    c0 = 2000.0
+    if h is None:
+        h = c0 / f0 / 40.0
+    if layered:
+        rng = np.random.default_rng(seed)
+        c = np.ascontiguousarray(random_layered_velocity(nr, nz, rng).T)   # layers along z, [nr][nz]
+    else:
+        c = np.full((nr, nz), c0)
+    rho = gardner_density(c) if layered else np.full((nr, nz), 1000.0)
+    rcv = [(i, 0) for i in range(0, nr, max(1, nr // 64))][:64]
+    return Shot(f"cylindrical_{'layered' if layered else 'homogeneous'}_{nr}x{nz}", nr, nz, h, h, c, rho, None,
+                400.0, 9, n_harm, f0, 0.2, sources=[(0, 0)], receivers=rcv,
+                t_out=np.linspace(0.002, 1.0, 500))
+
+
 def surface_line_sources(nx, count, iz=2):
     """count sources at ix = round((s + 1/2) nx / count), depth row iz."""
     return [(int(round((s + 0.5) * nx / count)), iz) for s in range(count)]

@@ -21,8 +21,8 @@ LAG_WAVELET_RICKER, LAG_WAVELET_PAPER = 0, 1
 
 
 class lag_grid(C.Structure):
-    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dz", C.c_double),
-                ("free_surface", C.c_int)]
+    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dz", C.c_double), ("free_surface", C.c_int),
+                ("cylindrical", C.c_int)]
 
 
 class lag_laguerre(C.Structure):
@@ -88,6 +88,7 @@ _PROTOS = {
     "lag_precond_destroy": (None, [VP]),
     "lag_precond_apply": (I, [VP, VP, VP, I]),
     "lag_precond_dst": (I, [VP, VP, VP, I]),
+    "lag_precond_dst_inverse": (I, [VP, VP, VP, I]),
     "lag_precond_dst_f32": (I, [VP, VP, VP, I]),
     "lag_precond_tridiag": (I, [VP, VP, VP, I]),
     "lag_precond_tridiag_f32": (I, [VP, VP, VP, I]),
@@ -183,8 +184,12 @@ def points(pts):
     return arr
 
 
-def grid(nx, nz, dx, dz, free_surface=False):
-    return lag_grid(int(nx), int(nz), float(dx), float(dz), 1 if free_surface else 0)
+def grid(nx, nz, dx, dz, free_surface=False, cylindrical=False):
+    """Cartesian grid, or with cylindrical=True the axisymmetric (r, z) grid of nx radii and nz
+    depths (fields [nx][nz], depth fastest; a free surface on top by construction)."""
+    if cylindrical:
+        free_surface = True
+    return lag_grid(int(nx), int(nz), float(dx), float(dz), 1 if free_surface else 0, 1 if cylindrical else 0)
 
 
 def solver(tol=1e-10, max_iter=2000, restart_k=20, prec=LAG_FP64, partitions=0, tune=0, layered=0):
