@@ -102,10 +102,13 @@ def assemble_A(a1, a2, w, hr, hz):
 
 
 def dct_matrix(n):
-    """Orthonormal DCT-II basis V[k][q] = c_q cos(pi q (k + 1/2) / n) (columns: z-modes)."""
-    k = np.arange(n)[:, None] + 0.5
-    q = np.arange(n)[None, :]
-    V = np.sqrt(2.0 / n) * np.cos(np.pi * q * k / n)
+    """Orthonormal DCT-II basis V[k][q] = c_q cos(pi q (k + 1/2) / n) (columns: z-modes), by its
+    definition.  The integer product q (2k + 1) is reduced modulo 4n before the cosine, so that
+    the angle pi q (2k + 1) / (2n) is exact to one rounding (the cosine is 2 pi-periodic)."""
+    k = np.arange(n, dtype=np.int64)[:, None]
+    q = np.arange(n, dtype=np.int64)[None, :]
+    m = (q * (2 * k + 1)) % (4 * n)
+    V = np.sqrt(2.0 / n) * np.cos(np.pi * m.astype(np.float64) / (2.0 * n))
     V[:, 0] = np.sqrt(1.0 / n)
     return V
 
