@@ -177,9 +177,9 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     p->zrows.alloc(ctx, zr.size() * sizeof(double));
     LAG_CUDA_CHECK(cudaMemcpyAsync(p->zrows.ptr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  // the DCT-II of cylindrical plans runs on the SIMT pipes (no tensor-core variant)
+  // the mixed-path DCT-II of cylindrical plans runs on the SIMT pipes (no split-bf16 variant)
   p->use_tc = (prec == LAG_MIXED) && !g.cylindrical && dst_tc_supported(g.nx) && !tc_disabled();
-  const bool oz = (prec == LAG_FP64) && !g.cylindrical && dst_oz_supported(g.nx) && !tc_disabled();
+  const bool oz = (prec == LAG_FP64) && dst_oz_supported(g.nx) && !tc_disabled();
   dst_build(p->dst, p->dst_store, g.nx, p->use_tc ? 1 : (oz ? 2 : 0), s, g.cylindrical ? 1 : 0);
   if (p->use_tc || p->dst.oz) {
     p->dst.tc_err = reinterpret_cast<int *>(p->dst_store.as<uint8_t>() + p->dst_store.bytes - 256);

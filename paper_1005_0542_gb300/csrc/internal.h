@@ -131,6 +131,7 @@ struct DstPlan {
   // float64 path on the tensor cores (exact slices): packed B slices [2][9][n tile][k stage]
   bool oz = false;
   uint8_t *oz_b = nullptr;
+  uint8_t *oz_bi = nullptr;   // DCT-II inverse operands (kind 1): [2][9][n tile][k stage]
   size_t oz_slice_bytes = 0;
   int oz_eB = 0;              // |S| < 2^oz_eB
 };
@@ -156,8 +157,10 @@ void dst_apply_f64_simt(const DstPlan &dp, const double *x, double *y, int rows,
 bool dst_oz_supported(int n);
 int dst_oz_products();  // bf16 slice products per float64 product
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows);
+// inverse (DCT-II plans only): gather the even / odd modes, GEMM with the inverse operands into
+// E / O sums (plan scratch), butterfly into y
 void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
-                  const KrylovScalars *sc, cudaStream_t s);
+                  const KrylovScalars *sc, cudaStream_t s, bool inverse = false);
 // mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
                        const KrylovScalars *sc, cudaStream_t s, bool rscale = false);

@@ -43,7 +43,7 @@ __global__ void dst_matrix_kernel(int n, int ku, int kv, double *su, double *sv,
 void dst_build_tc(DstPlan &dp, DevBuf &store, size_t offset_bytes, cudaStream_t s);
 size_t dst_tc_bytes(int n);
 void dst_build_oz(DstPlan &dp, DevBuf &store, size_t offset_bytes, cudaStream_t s);
-size_t dst_oz_bytes(int n);
+size_t dst_oz_bytes(int n, int kind);
 
 // DCT-II halves: su[j'][k'] = V[j'][2k'] (ku x ku), sv[j'][k'] = V[j'][2k'+1] (kv x kv), and the
 // inverse operands ie[q'][k] = V[k][2q'] (ku x ku), io[q'][k] = V[k][2q'+1] (kv x ku).  Angles are
@@ -79,7 +79,7 @@ __global__ void dct_matrix_kernel(int n, int ku, int kv, double *su, double *sv,
 }
 
 void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s, int kind) {
-  if (kind != 0 && tc_mode != 0) throw Error(LAG_EINVAL, "the DCT-II plan has no tensor-core variant");
+  if (kind != 0 && tc_mode == 1) throw Error(LAG_EINVAL, "the DCT-II plan has no split-bf16 variant");
   dp.kind = kind;
   dp.n = n;
   dp.ku = (n + 1) / 2;
@@ -89,7 +89,7 @@ void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s, i
   size_t bytes = (nu + nv + ninv) * (sizeof(double) + sizeof(float)) + 256;
   const size_t tc_off = (bytes + 1023) & ~(size_t)1023;
   if (tc_mode == 1) bytes = tc_off + dst_tc_bytes(n) + 256;  // + error word at the end
-  if (tc_mode == 2) bytes = tc_off + dst_oz_bytes(n) + 256;
+  if (tc_mode == 2) bytes = tc_off + dst_oz_bytes(n, kind) + 256;
   store.alloc(store.ctx, bytes, true);
   char *base = store.as<char>();
   dp.su = reinterpret_cast<double *>(base);
@@ -351,7 +351,8 @@ void dst_inverse_f64_simt(const DstPlan &dp, const double *x, double *y, int row
 }
 void dst_inverse_f64(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
                      cudaStream_t s) {
-  if (dp.kind == 1) dct_inv_launch<double, double, double>(dp, x, y, rows, rpr, dp.ie, dp.io, sc, s, KC_DST64);
+  if (dp.kind == 1 && dp.oz) dst_apply_oz(dp, x, y, rows, rpr, sc, s, true);
+  else if (dp.kind == 1) dct_inv_launch<double, double, double>(dp, x, y, rows, rpr, dp.ie, dp.io, sc, s, KC_DST64);
   else dst_apply_f64(dp, x, y, rows, rpr, sc, s);
 }
 void dst_inverse_f32_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rpr, const KrylovScalars *sc,

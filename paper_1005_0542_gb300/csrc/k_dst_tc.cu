@@ -703,16 +703,19 @@ __device__ __forceinline__ uint16_t oz_slice_bits(unsigned long long T, int i, b
   return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127 - OZ_B * (i - 1)) << 7) | mant);
 }
 
-// B slices, once per plan: [mat 0 = S even columns, 1 = S odd columns][slice][n tile][k stage][TN x TK]
-__global__ void oz_pack_b_kernel(const double *su, const double *sv, int ku, int kv, int nks, int nnt, int eB,
-                                 uint8_t *out, size_t slice_bytes) {
+// B slices, once per plan: [mat 0, mat 1][slice][n tile][k stage][TN x TK].  Mat w is the row-major
+// matrix m_w [K_w][ld_w] (contraction index k, output column n < N_w); zero beyond it.  Forward
+// transforms: m0 = su (even output modes), m1 = sv (odd ones); DCT-II inverse: m0 = ie (even input
+// modes), m1 = io (odd ones), both with ceil(n/2) output columns.
+__global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, const double *m1, int k1n, int n1n,
+                                 int ld1, int nks, int nnt, int eB, uint8_t *out, size_t slice_bytes) {
   const int which = blockIdx.z;
   const int n = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nnt * OZ_TN || k >= nks * TK) return;
   double v = 0.0;
-  if (which == 0) { if (n < ku && k < ku) v = su[(size_t)k * ku + n]; }
-  else if (n < kv && k < kv) v = sv[(size_t)k * kv + n];
+  if (which == 0) { if (n < n0n && k < k0n) v = m0[(size_t)k * ld0 + n]; }
+  else if (n < n1n && k < k1n) v = m1[(size_t)k * ld1 + n];
   const unsigned long long T = oz_fixed(v, eB);
   const size_t tile = (size_t)(n / OZ_TN) * nks + (k / TK);
   const uint32_t off = swz(n % OZ_TN, k % TK);
@@ -730,11 +733,13 @@ __global__ void oz_pack_b_kernel(const double *su, const double *sv, int ku, int
 // Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r with |values| < 2^e_r.
 constexpr int OZ_PACK_THREADS = 256;
 constexpr int OZ_PACK_MAXK = 4224;  // ceil(n / 2) bound of the exact-slice path (K pad <= 4224)
+// gather (DCT-II inverse): u = the even entries x[2j], v = the odd ones x[2j+1] instead of the fold.
 __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n,
                                                                     int ku, int kv, int nks, int nmt,
                                                                     uint8_t *__restrict__ out, size_t slice_bytes,
                                                                     int *__restrict__ erow,
-                                                                    const KrylovScalars *__restrict__ sc, int rpr) {
+                                                                    const KrylovScalars *__restrict__ sc, int rpr,
+                                                                    int gather) {
   extern __shared__ double fold_sm[];  // [2][nks * TK]: u then v
   const int row = blockIdx.x;
   // rows of finished right-hand sides and the padding rows of the last tile pack as zeros (exact
@@ -747,7 +752,10 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
   unsigned long long b0 = 0, b1 = 0;
   for (int j = threadIdx.x; j < kp; j += blockDim.x) {
     double a = 0.0, b = 0.0;
-    if (live && j < kv) {
+    if (gather) {
+      if (live && j < ku) a = __ldg(xr + 2 * j);
+      if (live && j < kv) b = __ldg(xr + 2 * j + 1);
+    } else if (live && j < kv) {
       const double x1 = __ldg(xr + j), x2 = __ldg(xr + n - 1 - j);
       a = x1 + x2;
       b = x1 - x2;
@@ -817,7 +825,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
                                                          const int *__restrict__ erow, int eB, int nks, int nmt,
                                                          int nnt, int rows, double *__restrict__ y, int ld, int ku,
                                                          int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
-                                                         int rpr, int *__restrict__ err) {
+                                                         int rpr, int *__restrict__ err, int inv) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -859,7 +867,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
     par = t / (nnt * nmt);
   };
   auto wanted = [&](int par, int mt, int nt) -> bool {
-    if (nt * OZ_TN >= (par ? kv : ku)) return false;
+    if (nt * OZ_TN >= ((par && !inv) ? kv : ku)) return false;
     if (sc == nullptr) return true;
     const int m0 = mt * TM;
     const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
@@ -989,11 +997,18 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
       if (stop) break;
       if (rok) {
         const int c0 = nt * OZ_TN + h * 64;
-        const int ncols = min(64, (par ? kv : ku) - c0);
-        double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+        const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
+        if (inv) {  // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]
+          double *yp = y + ((size_t)par * rows + row) * ku + c0;
 #pragma unroll
-        for (int q = 0; q < 64; ++q)
-          if (q < ncols) yp[2 * q] = acc64[q];
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) yp[q] = acc64[q];
+        } else {
+          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) yp[2 * q] = acc64[q];
+        }
       }
     }
   }
@@ -1043,9 +1058,9 @@ bool dst_oz_supported(int n) {
   return n >= 16 && 63LL * 63LL * kpad <= (1LL << 24);  // one pair per accumulator at least
 }
 
-size_t dst_oz_bytes(int n) {
+size_t dst_oz_bytes(int n, int kind) {
   const int ku = (n + 1) / 2;
-  return 2 * (size_t)OZ_S * div_up(ku, OZ_TN) * div_up(ku, TK) * OZ_BT;
+  return (kind == 1 ? 2 : 1) * 2 * (size_t)OZ_S * div_up(ku, OZ_TN) * div_up(ku, TK) * OZ_BT;
 }
 
 void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
@@ -1055,22 +1070,47 @@ void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
   dp.oz_slice_bytes = (size_t)nnt * nks * OZ_BT;
   dp.oz_b = store.as<uint8_t>() + off;
   int eB = 0;
-  frexp(std::sqrt(2.0 / (double)(dp.n + 1)), &eB);  // every |S| <= sqrt(2 / (n + 1)) < 2^eB
+  // every |S| <= sqrt(2 / (n + 1)) < 2^eB (DST-I); every |V| <= sqrt(2 / n) < 2^eB (DCT-II)
+  frexp(std::sqrt(2.0 / (double)(dp.kind == 1 ? dp.n : dp.n + 1)), &eB);
   dp.oz_eB = eB;
   dim3 g(div_up(nks * TK, 128), nnt * OZ_TN, 2);
-  oz_pack_b_kernel<<<g, 128, 0, s>>>(dp.su, dp.sv, dp.ku, dp.kv, nks, nnt, eB, dp.oz_b, dp.oz_slice_bytes);
+  oz_pack_b_kernel<<<g, 128, 0, s>>>(dp.su, dp.ku, dp.ku, dp.ku, dp.sv, dp.kv, dp.kv, dp.kv, nks, nnt, eB, dp.oz_b,
+                                     dp.oz_slice_bytes);
   count_launch();
   LAG_LAUNCH_CHECK();
+  if (dp.kind == 1) {  // inverse operands: even / odd input modes x ceil(n/2) output columns
+    dp.oz_bi = dp.oz_b + 2 * (size_t)OZ_S * dp.oz_slice_bytes;
+    oz_pack_b_kernel<<<g, 128, 0, s>>>(dp.ie, dp.ku, dp.ku, dp.ku, dp.io, dp.kv, dp.ku, dp.ku, nks, nnt, eB, dp.oz_bi,
+                                       dp.oz_slice_bytes);
+    count_launch();
+    LAG_LAUNCH_CHECK();
+  }
   dp.oz = true;
 }
 
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows) {
   const size_t nmt = div_up(rows, TM);
-  return 2 * (size_t)OZ_S * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256;
+  const size_t eo = (dp.kind == 1) ? 2 * (size_t)rows * dp.ku * sizeof(double) + 256 : 0;  // DCT-II E / O sums
+  return 2 * (size_t)OZ_S * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256 + eo;
+}
+
+// DCT-II inverse butterfly: x[k] = E[k] + O[k], x[n-1-k] = E[k] - O[k] (k < ceil(n/2)); rows of
+// finished right-hand sides are left as they are (their GEMM tiles were skipped).
+__global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__restrict__ x, int rows, int n, int ku,
+                                    const KrylovScalars *__restrict__ sc, int rpr) {
+  const int row = blockIdx.x;  // one block per row
+  if (row >= rows || (sc != nullptr && sc[row / rpr].state != ST_RUN)) return;
+  const double *E = eo + (size_t)row * ku, *O = eo + ((size_t)rows + row) * ku;
+  double *xr = x + (size_t)row * n;
+  for (int k = threadIdx.x; k < ku; k += blockDim.x) {
+    const double e = E[k], o = O[k];
+    xr[k] = e + o;
+    if (n - 1 - k != k) xr[n - 1 - k] = e - o;
+  }
 }
 
 void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool inverse) {
   if (rows <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -1089,17 +1129,27 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
                                         2 * OZ_PACK_MAXK * (int)sizeof(double)));
     pack_attr = true;
   }
+  const int inv = (inverse && dp.kind == 1) ? 1 : 0;
   oz_pack_a_kernel<<<nmt * TM, OZ_PACK_THREADS, pack_smem, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack, a_slice,
-                                                                 erow, sc, rpr);
+                                                                 erow, sc, rpr, inv);
   count_launch();
   LAG_LAUNCH_CHECK();
   const OzSched sch = oz_schedule(nks * TK);
   const int ntiles = 2 * nmt * nnt;
   const int grid = std::min(ntiles, 152);
-  oz_gemm_kernel<<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, dp.oz_b, dp.oz_slice_bytes, erow, dp.oz_eB, nks, nmt, nnt,
-                                            rows, y, dp.n, dp.ku, dp.kv, sch, sc, rpr, dp.tc_err);
+  // E / O sums of the inverse: after the packed A slices and the row exponents, 256-byte aligned
+  double *eo = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(erow + 2 * (size_t)nmt * TM) + 255) & ~(uintptr_t)255);
+  oz_gemm_kernel<<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes, erow,
+                                            dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku, dp.kv, sch, sc,
+                                            rpr, dp.tc_err, inv);
   count_launch();
   LAG_LAUNCH_CHECK();
+  if (inv) {
+    oz_butterfly_kernel<<<rows, 256, 0, s>>>(eo, y, rows, dp.n, dp.ku, sc, rpr);
+    count_launch();
+    LAG_LAUNCH_CHECK();
+  }
 }
 
 }  // namespace lag

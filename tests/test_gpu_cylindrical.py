@@ -82,7 +82,8 @@ def test_precond_apply_cylindrical(ctx, prec, tol, nr, nz):
     p = C.c_void_p()
     g = L.grid(nr, nz, hr, hz, cylindrical=True)
     L.check(L.lag_precond_create(ctx, C.byref(g), kt, dt * 4.0 / h ** 2, h, prec, C.byref(p)), ctx)
-    assert L.lag_precond_uses_tensor_cores(p) == 0
+    # float64: the exact-slice tcgen05 DCT from 16 depth nodes on; mixed: SIMT float32
+    assert L.lag_precond_uses_tensor_cores(p) == (1 if prec == L.LAG_FP64 and nz >= 16 else 0)
     r = RNG.standard_normal((2, nr, nz))
     rd, zd = dev(r), empty(r.shape)
     L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
@@ -105,13 +106,36 @@ def test_operator_cylindrical(ctx, nr, nz):
 
 
 def test_static_apply_equals_plan_apply(ctx):
-    nr, nz = 96, 80
-    p = cyl_plan(ctx, nr, nz, 5.0, 5.0, 3e9, 1e7)
+    # the no-allocation entry point runs the SIMT DCT; the plan the exact-slice tensor-core one
+    nr, nz, hr, hz, kt, dt = 96, 80, 5.0, 5.0, 3e9, 1e7
+    p = cyl_plan(ctx, nr, nz, hr, hz, kt, dt)
     r = RNG.standard_normal((2, nr, nz))
     rd, z1, z2 = dev(r), empty(r.shape), empty(r.shape)
     L.check(L.lag_precond_apply(p, ptr(rd), ptr(z1), 2), ctx)
     L.check(L.lag_precond_apply_static(p, ptr(rd), ptr(z2), 2), ctx)
-    assert np.array_equal(host(z1), host(z2))
+    ref = cyl.apply_inverse(r, hr, hz, kt, dt)
+    assert rel(host(z1), ref) < 1e-12 and rel(host(z2), ref) < 1e-12
+    assert rel(host(z1), host(z2)) < 1e-13
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nr,nz", [(40, 2048), (3, 4097)])
+def test_dct_exact_slices_large(ctx, nr, nz):
+    # long rows: several K stages and N tiles of the exact-slice GEMM, odd length with a middle mode
+    p = cyl_plan(ctx, nr, nz, 5.0, 4.0, 3e9, 1e7)
+    assert L.lag_precond_uses_tensor_cores(p) == (1 if nz <= 8448 else 0)
+    V = cyl.dct_matrix(nz)
+    x = RNG.standard_normal((1, nr, nz)) * np.logspace(-100, 100, nr)[None, :, None]
+    xd, yd, zd = dev(x), empty(x.shape), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(yd), 1), ctx)
+    y = host(yd)
+    ref = x @ V
+    for i in range(nr):  # row by row: every row keeps its own scale
+        assert rel(y[0, i], ref[0, i]) < 1e-13
+    L.check(L.lag_precond_dst_inverse(p, ptr(yd), ptr(zd), 1), ctx)
+    z = host(zd)
+    for i in range(nr):
+        assert rel(z[0, i], x[0, i]) < 1e-13
     L.lag_precond_destroy(p)
 
 
