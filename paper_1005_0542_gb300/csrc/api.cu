@@ -86,10 +86,10 @@ void lag_precond::apply(const double *r, double *z, int nrhs, const KrylovScalar
     dst_inverse_f64(dst, w, z, rows, grid.nz, sc, s);
   } else {
     float *w = scratch.as<float>();
-    if (use_tc) dst_apply_tc_d2f(dst, r, w, rows, grid.nz, sc, s);
+    if (use_tc) dst_apply_tc_d2f(dst, r, w, rows, grid.nz, sc, s, rscale);
     else dst_apply_f32_d2f(dst, r, w, rows, grid.nz, sc, s, rscale);
     tri_solve_f32(tri32, w, w, nrhs, sc, s);
-    if (use_tc) dst_apply_tc_f2d(dst, w, z, rows, grid.nz, sc, s);
+    if (use_tc) dst_apply_tc_f2d(dst, w, z, rows, grid.nz, sc, s, rscale);
     else dst_inverse_f32_f2d(dst, w, z, rows, grid.nz, sc, s, rscale);
   }
 }
@@ -177,8 +177,8 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     p->zrows.alloc(ctx, zr.size() * sizeof(double));
     LAG_CUDA_CHECK(cudaMemcpyAsync(p->zrows.ptr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  // the mixed-path DCT-II of cylindrical plans runs on the SIMT pipes (no split-bf16 variant)
-  p->use_tc = (prec == LAG_MIXED) && !g.cylindrical && dst_tc_supported(g.nx) && !tc_disabled();
+  // DCT-II plans share the tensor-core paths: same fold, inverse operands su^T / sv^T = ie / io
+  p->use_tc = (prec == LAG_MIXED) && dst_tc_supported(g.nx) && !tc_disabled();
   const bool oz = (prec == LAG_FP64) && dst_oz_supported(g.nx) && !tc_disabled();
   dst_build(p->dst, p->dst_store, g.nx, p->use_tc ? 1 : (oz ? 2 : 0), s, g.cylindrical ? 1 : 0);
   if (p->use_tc || p->dst.oz) {

@@ -56,6 +56,17 @@ struct KrylovScalars {
 };
 static_assert(sizeof(KrylovScalars) == 80, "layout");
 
+// Residual scaling of the float32 / bf16 preconditioner pipelines inside PCG: the right-hand side of
+// system b enters them multiplied by 2^-e, e = the binary exponent of ||r_b|| (KrylovScalars::rr),
+// and the float64 output is multiplied by 2^e again.  Power-of-two scaling is exact; it keeps
+// residuals that are tiny in absolute terms (a weak source, a late iterate) away from float32
+// underflow, the preconditioner being linear.
+__device__ __forceinline__ int residual_exponent(const KrylovScalars *sc, int b) {
+  const double rr = sc[b].rr;
+  if (!(rr > 0.0) || !isfinite(rr)) return 0;
+  return ilogb(sqrt(rr));
+}
+
 // ST_MET (GMRES only): the residual estimate met the tolerance inside an open cycle; the true
 // residual at the next cycle start turns it into ST_CONV or back into ST_RUN.
 enum { ST_RUN = 0, ST_CONV = 1, ST_NAN = 2, ST_STOP = 3, ST_MET = 4 };

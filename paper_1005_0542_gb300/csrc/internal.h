@@ -135,8 +135,8 @@ struct DstPlan {
   size_t oz_slice_bytes = 0;
   int oz_eB = 0;              // |S| < 2^oz_eB
 };
-// tc_mode: 0 none, 1 split-bf16 operands (mixed path), 2 exact slices (float64 path); kind 1
-// (DCT-II) takes tc_mode 0 only
+// tc_mode: 0 none, 1 split-bf16 operands (mixed path), 2 exact slices (float64 path); kind 0 = DST-I,
+// 1 = DCT-II (both fold alike; the DCT-II adds inverse operands, see k_dst.cu)
 void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s, int kind = 0);
 // the inverse transform: the forward one again for DST-I (S^2 = I), the transpose for DCT-II
 void dst_inverse_f64(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
@@ -167,10 +167,11 @@ void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, i
 void dst_apply_f32_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
                        const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
 // mixed path: float64 in -> float32 out, and float32 in -> float64 out (tensor cores)
+// rscale: PCG residual scaling (see dst_inverse_f32_f2d); the fused _beta variant always scales
 void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
-                      const KrylovScalars *sc, cudaStream_t s);
+                      const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
 void dst_apply_tc_f2d(const DstPlan &dp, const float *x, double *y, int rows, int rows_per_rhs,
-                      const KrylovScalars *sc, cudaStream_t s);
+                      const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
 bool dst_tc_supported(int n);
 // inverse tensor-core DST fused with the CG beta of the next step (per rhs: rpr rows)
 void dst_apply_tc_f2d_beta(const DstPlan &dp, const float *y, double *z, int nrhs, int rpr, const double *r,

@@ -79,7 +79,6 @@ __global__ void dct_matrix_kernel(int n, int ku, int kv, double *su, double *sv,
 }
 
 void dst_build(DstPlan &dp, DevBuf &store, int n, int tc_mode, cudaStream_t s, int kind) {
-  if (kind != 0 && tc_mode == 1) throw Error(LAG_EINVAL, "the DCT-II plan has no split-bf16 variant");
   dp.kind = kind;
   dp.n = n;
   dp.ku = (n + 1) / 2;
@@ -129,17 +128,6 @@ __device__ __forceinline__ bool tile_all_done(const KrylovScalars *sc, int m0, i
   for (int r = r0; r <= r1; ++r)
     if (sc[r].state == ST_RUN) return false;
   return true;
-}
-
-// Residual scaling of the float32 transforms inside PCG: the right-hand side of system b enters the
-// float32 pipeline multiplied by 2^-e, e = the binary exponent of ||r_b|| (KrylovScalars::rr), and
-// the float64 output is multiplied by 2^e again.  Power-of-two scaling is exact; it keeps residuals
-// that are tiny in absolute terms (a weak source, a late iterate) away from float32 underflow,
-// since the preconditioner is linear.
-__device__ __forceinline__ int residual_exponent(const KrylovScalars *sc, int b) {
-  const double rr = sc[b].rr;
-  if (!(rr > 0.0) || !isfinite(rr)) return 0;
-  return ilogb(sqrt(rr));
 }
 
 template <typename TI, typename TO, typename TA, int BM, int BN>

@@ -168,13 +168,15 @@ __global__ void pack_b_kernel(const double *su, const double *sv, int ku, int kv
 template <typename TI>
 __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ x, int rows, int n, int ku, int kv,
                                                          int nks, int nmt, uint8_t *__restrict__ out,
-                                                         const KrylovScalars *__restrict__ sc, int rpr) {
+                                                         const KrylovScalars *__restrict__ sc, int rpr, int rscale) {
   const int chunks = nks * (TK / 8);
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)nmt * TM * chunks) return;
   const int row = (int)(t / chunks), ch = (int)(t % chunks);
   const int k0 = ch * 8;
   const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
+  // PCG residuals enter scaled by 2^-e (residual_exponent), undone by the inverse butterfly
+  const double is = (live && rscale && sc != nullptr) ? ldexp(1.0, -residual_exponent(sc, row / rpr)) : 1.0;
   alignas(16) uint16_t uh[8], ul[8], vh[8], vl[8];
   const TI *xr = x + (size_t)(live ? row : 0) * n;
 #pragma unroll
@@ -183,11 +185,11 @@ __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ 
     float u = 0.f, w = 0.f;
     if (live) {
       if (j < kv) {
-        const float a = (float)xr[j], b = (float)xr[n - 1 - j];
+        const float a = (float)((double)xr[j] * is), b = (float)((double)xr[n - 1 - j] * is);
         u = a + b;
         w = a - b;
       } else if (j < ku) {
-        u = (float)xr[j];  // middle element of an odd-length row
+        u = (float)((double)xr[j] * is);  // middle element of an odd-length row
       }
     }
     split2f(u, uh[e], ul[e]);
@@ -424,13 +426,14 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
 // z[k] = E[k] + O[k], z[n-1-k] = E[k] - O[k]   (eo rows: [E (ku) | O (ku)])
 __global__ void __launch_bounds__(256) butterfly_kernel(const float *__restrict__ eo, double *__restrict__ z, int rows,
                                                         int n, int ku, int kv, const KrylovScalars *__restrict__ sc,
-                                                        int rpr) {
+                                                        int rpr, int rscale) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * ku) return;
   const int row = (int)(t / ku), k = (int)(t % ku);
   if (sc != nullptr && sc[row / rpr].state != ST_RUN) return;
   const float *er = eo + (size_t)row * 2 * ku;
-  const double e = (double)er[k], o = (double)er[ku + k];
+  const double os = (rscale && sc != nullptr) ? ldexp(1.0, residual_exponent(sc, row / rpr)) : 1.0;
+  const double e = (double)er[k] * os, o = (double)er[ku + k] * os;
   double *zr = z + (size_t)row * n;
   zr[k] = e + o;
   if (k < kv) zr[n - 1 - k] = e - o;
@@ -447,12 +450,13 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
   if (sc[rhs].state != ST_RUN) return;
   const long long per = (long long)rpr * ku;
   const size_t row0 = (size_t)rhs * rpr;
+  const double os = ldexp(1.0, residual_exponent(sc, rhs));  // the forward pack scaled r by 2^-e
   double a0 = 0.0, a1 = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per; t += (long long)gridDim.x * blockDim.x) {
     const size_t row = row0 + (size_t)(t / ku);
     const int k = (int)(t % ku);
     const float *er = eo + row * 2 * ku;
-    const double e = (double)er[k], o = (double)er[ku + k];
+    const double e = (double)er[k] * os, o = (double)er[ku + k] * os;
     const size_t i1 = row * n + k;
     const double z1 = e + o;
     z[i1] = z1;
@@ -553,7 +557,7 @@ size_t dst_tc_scratch_bytes(const DstPlan &dp, int rows) {
 }
 
 void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rpr, const KrylovScalars *sc,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool rscale) {
   if (rows <= 0) return;
   uint8_t *apack = dp.tc_scratch;
   const int nks = dp.kpad_u, nmt = div_up(rows, TM);
@@ -561,7 +565,7 @@ void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, in
     ProfScope prof(KC_DSTTC_FWD, s);
     const long long threads = (long long)nmt * TM * nks * (TK / 8);
     pack_a_fwd_kernel<double><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt,
-                                                                                apack, sc, rpr);
+                                                                                apack, sc, rpr, rscale ? 1 : 0);
     count_launch();
     LAG_LAUNCH_CHECK();
     gemm_launch(dp, apack, dp.tc_b, rows, y, dp.n, dp.ku, dp.kv, sc, rpr, dp.tc_err, s);
@@ -569,7 +573,7 @@ void dst_apply_tc_d2f(const DstPlan &dp, const double *x, float *y, int rows, in
 }
 
 void dst_apply_tc_f2d(const DstPlan &dp, const float *y, double *z, int rows, int rpr, const KrylovScalars *sc,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool rscale) {
   if (rows <= 0) return;
   uint8_t *apack = dp.tc_scratch;
   float *eo = reinterpret_cast<float *>(apack + 2 * (size_t)div_up(rows, TM) * dp.kpad_u * 2 * A_TILE);
@@ -583,7 +587,8 @@ void dst_apply_tc_f2d(const DstPlan &dp, const float *y, double *z, int rows, in
     LAG_LAUNCH_CHECK();
     gemm_launch(dp, apack, dp.tc_b + 2 * dp.tc_bmat_bytes, rows, eo, 2 * dp.ku, dp.ku, dp.ku, sc, rpr, dp.tc_err, s);
     const long long t = (long long)rows * dp.ku;
-    butterfly_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(eo, z, rows, dp.n, dp.ku, dp.kv, sc, rpr);
+    butterfly_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(eo, z, rows, dp.n, dp.ku, dp.kv, sc, rpr,
+                                                                 rscale ? 1 : 0);
     count_launch();
     LAG_LAUNCH_CHECK();
   }

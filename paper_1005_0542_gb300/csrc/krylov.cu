@@ -155,7 +155,7 @@ void KrylovWork::pcg_iteration() {
     const int rows = nrhs * p1->grid.nz;
     p1->ensure_scratch(nrhs);
     float *w = p1->scratch.as<float>();
-    dst_apply_tc_d2f(p1->dst, r(), w, rows, p1->grid.nz, sc(), stream);
+    dst_apply_tc_d2f(p1->dst, r(), w, rows, p1->grid.nz, sc(), stream, true);
     tri_solve_f32(p1->tri32, w, w, nrhs, sc(), stream);
     dst_apply_tc_f2d_beta(p1->dst, w, z, nrhs, p1->grid.nz, r(), q, flexible, sc(), rd, stream);
   } else {

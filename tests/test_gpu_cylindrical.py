@@ -82,8 +82,8 @@ def test_precond_apply_cylindrical(ctx, prec, tol, nr, nz):
     p = C.c_void_p()
     g = L.grid(nr, nz, hr, hz, cylindrical=True)
     L.check(L.lag_precond_create(ctx, C.byref(g), kt, dt * 4.0 / h ** 2, h, prec, C.byref(p)), ctx)
-    # float64: the exact-slice tcgen05 DCT from 16 depth nodes on; mixed: SIMT float32
-    assert L.lag_precond_uses_tensor_cores(p) == (1 if prec == L.LAG_FP64 and nz >= 16 else 0)
+    # tensor cores from 16 depth nodes on (float64: exact slices; mixed: split bf16)
+    assert L.lag_precond_uses_tensor_cores(p) == (1 if nz >= 16 else 0)
     r = RNG.standard_normal((2, nr, nz))
     rd, zd = dev(r), empty(r.shape)
     L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
@@ -156,7 +156,8 @@ def test_cylindrical_layouts_and_autotune(ctx, prec, tol):
     Pt, mtt, prod, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
     L.check(L.lag_precond_autotune(p, 4, C.byref(Pt), C.byref(mtt), C.byref(prod), C.byref(ms)), ctx)
     L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 4), ctx)
-    assert rel(host(zd), ref) < tol
+    # the tuner may drop bf16 products of the mixed transform (a coarser preconditioner)
+    assert rel(host(zd), ref) < (tol if prec == L.LAG_FP64 or prod.value == 3 else 2e-2)
     L.lag_precond_destroy(p)
 
 
