@@ -135,7 +135,12 @@ const char *lag_profile_class_name(int cls);
  * factored once into partition-local eliminations, spike vectors and the reduced (interface)
  * system.  Acoustic B (Eq. 21): ax = az = kappa~, d = rho~ h^2/4 with f~ = (min f + max f)/2.
  * Elastic K = diag(B1, B2) (Eq. 22): B1 (ax, az) = ((lambda+2mu)~, mu~), B2 = (mu~, (lambda+2mu)~).
- * prec = LAG_FP64 or LAG_MIXED.  partitions = 0 picks the partition count automatically. */
+ * prec = LAG_FP64 or LAG_MIXED.  partitions = 0 picks the partition count automatically.
+ * Cylindrical grids (lag_grid.cylindrical): B of Eq. 21 with the paper's coefficients a1 = rbar ax,
+ * a2 = r az, d(r) = r d; the transform is the orthonormal DCT-II along z (zero-flux faces,
+ * mu_q = (4/dz^2) sin^2(pi q / (2 nz))) and each z-mode q leaves one general tridiagonal system
+ * along r with rows (-ax i/dr, ax (2i+1)/dr + r_i az mu_q + r_i d, -ax (i+1)/dr),
+ * r_i = (i + 1/2) dr.  Both paths run on the tensor cores as for Cartesian plans. */
 int  lag_precond_create(lag_ctx *ctx, const lag_grid *grid, double kappa_t, double rho_t,
                         double h_lag, int prec, lag_precond **out);
 int  lag_precond_create_sep(lag_ctx *ctx, const lag_grid *grid, double ax_t, double az_t,
@@ -156,11 +161,13 @@ int  lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double
                                 lag_precond **out);
 int  lag_precond_is_layered(const lag_precond *p);   /* 1 for plans of lag_precond_create_layered */
 void lag_precond_destroy(lag_precond *p);
-/* z = B^{-1} r for nrhs fields [nrhs][nz][nx] (device, float64).  Stream-ordered.  r and z may
- * not overlap.  Steps: forward DST-I along x, one tridiagonal solve along z per mode, DST-I. */
+/* z = B^{-1} r for nrhs fields [nrhs][nz][nx] (device, float64; cylindrical: [nrhs][nx][nz]).
+ * Stream-ordered.  r and z may not overlap.  Steps: forward DST-I along x, one tridiagonal solve
+ * along z per mode, DST-I (cylindrical: DCT-II along z, systems along r, inverse DCT-II). */
 int  lag_precond_apply(lag_precond *p, const double *r_dev, double *z_dev, int nrhs);
 /* The steps alone (parity and roofline of each kernel).  Stream-ordered.
- * dst:      y[b][k][:] = S x[b][k][:] (orthonormal DST-I, S^2 = I); in the plan's precision.
+ * dst:      y[b][k][:] = S x[b][k][:] (orthonormal DST-I, S^2 = I); in the plan's precision
+ *           (cylindrical plans: y = V^T x along z, the forward DCT-II).
  * tridiag:  for every rhs b and mode j solve T_j y[b][:][j] = d[b][:][j] along z (float64 plan).
  * tridiag_f32: the same on float32 data (LAG_MIXED plan). */
 int  lag_precond_dst(lag_precond *p, const double *x_dev, double *y_dev, int nrhs);
@@ -174,7 +181,7 @@ int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, i
  * float32 in, float64 out).  lag_precond_dst on a mixed plan runs the forward kernel (float64 in,
  * float32 spectrum) and widens its result to float64. */
 int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int nrhs);
-/* 1 if the plan's DST runs on the tcgen05 tensor cores, else 0.  Mixed plans: split-bf16 operands,
+/* 1 if the plan's DST (cylindrical: DCT-II) runs on the tcgen05 tensor cores, else 0.  Mixed plans: split-bf16 operands,
  * FP32 accumulation.  Float64 plans (n >= 16, ceil(n/2) <= 4224): exact slices -- each folded row
  * and S are cut into 9 six-bit integer slices on a power-of-two grid (54 bits), the slice products
  * are summed exactly in FP32 tensor memory (integers below 2^24) and combined in float64, so the

@@ -5,7 +5,8 @@
 // that owns all device memory through its own allocator and forbids others, or a real-time loop
 // that must not block in cudaMalloc / cudaFree (cudaFree synchronises the device).  For them,
 // lag_precond_apply_static runs the three steps (DST-I along x, partitioned tridiagonal solve
-// along z, DST-I back) with the spectrum in the file-scope device array below, whose size is
+// along z, DST-I back; cylindrical plans: DCT-II along z, systems along r, inverse DCT-II) with the
+// spectrum in the file-scope device array below, whose size is
 // fixed when the library is loaded; the DST runs on the FP64 SIMT pipes (the tensor-core float64
 // DST keeps its operand slices in plan scratch that lag_precond_apply allocates on demand).  The plan itself is created beforehand (lag_precond_create
 // allocates its factors once).
