@@ -401,18 +401,26 @@ def cylindrical_leg(ctx, args):
         stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        L.lag_profile_enable(ctx, 1)
         e0.record(stream)
         for _ in range(K):
             L.check(L.lag_shot_step(sh, 1), ctx)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        nk = L.lag_profile_num_classes()
+        cnt = (C.c_longlong * nk)()
+        kms = (C.c_double * nk)()
+        L.check(L.lag_profile_read(ctx, nk, cnt, kms), ctx)
+        L.lag_profile_enable(ctx, 0)
         its = np.zeros((1, s.n_harm), dtype=np.int32)
         st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
         L.lag_shot_stats(sh, C.byref(st))
         L.lag_shot_destroy(sh)
         out[key] = {"grid_r_z": [nr, nz], "h_m": s.hx, "value": K / (ms / 1e3), "unit": UNIT, "steps": K,
-                    "ms_per_step": ms / K, "pcg_iters_per_step": float(its[0, W:W + K].mean())}
+                    "ms_per_step": ms / K, "pcg_iters_per_step": float(its[0, W:W + K].mean()),
+                    "kernel_ms": {L.lag_profile_class_name(i).decode(): {"launches": cnt[i], "ms": round(kms[i], 3)}
+                                  for i in range(nk) if cnt[i]}}
     out["config"] = ("2.5D axisymmetric acoustic half space (r, z), source on the axis, Eq. 23 wavelet 30 Hz, "
                      "mesh lambda/40; homogeneous (Sec. 3.2) and random layered media")
     return out
@@ -688,6 +696,41 @@ def capture_kernels(args):
     print(json.dumps({"capture": "ok"}))
 
 
+def capture_extensions(args):
+    """One launch of the kernels of the layered and cylindrical plans through the C ABI, 1024 x 1024
+    x 16 RHS float64 (134 MB > L2): the general tridiagonal solve (one factor set per partition)
+    of a layered plan, then the forward and the inverse DCT-II of a cylindrical float64 plan
+    (exact slices; the inverse gathers even / odd modes and ends in the E/O butterfly), for
+    `ncu -k ... -c N` captures."""
+    import torch
+    from paper_1005_0542_gb300 import lagwave as L
+    ctx = L.create(0, stream=torch.cuda.current_stream().cuda_stream)
+    n, nrhs = 1024, 16
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    r = torch.randn((nrhs, n, n), dtype=torch.float64, device="cuda", generator=gen)
+    z = torch.empty_like(r)
+    P = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    rng = np.random.default_rng(3)
+    ax = 3e10 * rng.uniform(0.3, 1.0, n)
+    d = 2.2e7 * rng.uniform(0.5, 1.0, n)
+    a_, pa = L.f64(ax)
+    d_, pd = L.f64(d)
+    pl = C.c_void_p()
+    L.check(L.lag_precond_create_layered(ctx, C.byref(L.grid(n, n, 5.0, 5.0)), pa, pa, pd, L.LAG_FP64, 0,
+                                         C.byref(pl)), ctx)
+    pc = C.c_void_p()
+    L.check(L.lag_precond_create_sep(ctx, C.byref(L.grid(n, n, 5.0, 5.0, cylindrical=True)), 3e10, 3e10, 2.2e7,
+                                     L.LAG_FP64, 0, C.byref(pc)), ctx)
+    torch.cuda.synchronize()
+    L.check(L.lag_precond_tridiag(pl, P(r), P(z), nrhs), ctx)        # general tridiagonal solve (layered)
+    L.check(L.lag_precond_dst(pc, P(r), P(z), nrhs), ctx)            # forward DCT-II (fold + exact slices)
+    L.check(L.lag_precond_dst_inverse(pc, P(z), P(r), nrhs), ctx)    # inverse DCT-II (gather + GEMM + E/O)
+    L.check(L.lag_precond_tridiag(pc, P(r), P(z), nrhs), ctx)        # systems along r (cylindrical)
+    torch.cuda.synchronize()
+    L.lag_destroy(ctx)
+    print(json.dumps({"capture": "ok"}))
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def reference_arm(args):
     from paper_1005_0542_gb300 import inputs
@@ -725,6 +768,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-active", type=int, default=8)
     ap.add_argument("--serve-nharm", type=int, nargs=2, default=[4, 16])
+    ap.add_argument("--capture-extensions", action="store_true",
+                    help="launch the layered / cylindrical plan kernels once (1024 x 1024 x 16 RHS) for ncu, then exit")
     ap.add_argument("--capture-kernels", action="store_true",
                     help="launch each hot kernel once (1024 x 1024 x 16 RHS) for ncu captures, then exit")
     args = ap.parse_args()
@@ -735,6 +780,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.capture_kernels:
         capture_kernels(args)
+        return
+    if args.capture_extensions:
+        capture_extensions(args)
         return
     if args.impl == "reference":
         if rank != 0:
