@@ -67,6 +67,21 @@ __device__ __forceinline__ int residual_exponent(const KrylovScalars *sc, int b)
   return ilogb(sqrt(rr));
 }
 
+// x * 2^e by an add to the exponent field (integer ops: the FP64 pipe of this part is narrow).
+// Zero stays zero, Inf / NaN pass through, results below the normal range become signed zero and
+// above it signed Inf; subnormal inputs count as zero.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const long long sign = b & (long long)0x8000000000000000ull;
+  if (ex == 0x7ff) return x;
+  if (ex == 0) return __longlong_as_double(sign);
+  const int ne = ex + e;
+  if (ne <= 0) return __longlong_as_double(sign);
+  if (ne >= 0x7ff) return __longlong_as_double(sign | 0x7ff0000000000000ll);
+  return __longlong_as_double(b + ((long long)e << 52));
+}
+
 // ST_MET (GMRES only): the residual estimate met the tolerance inside an open cycle; the true
 // residual at the next cycle start turns it into ST_CONV or back into ST_RUN.
 enum { ST_RUN = 0, ST_CONV = 1, ST_NAN = 2, ST_STOP = 3, ST_MET = 4 };

@@ -144,11 +144,11 @@ __global__ void __launch_bounds__(256) dst_simt_kernel(const TI *__restrict__ X,
   if (n0 >= K || tile_all_done<BM>(sc, m0, rows, rpr)) return;
   // rscale 1: scale the input rows by 2^-e (float64 in); 2: the output rows by 2^e (float64 out)
   const bool scaled = rscale != 0 && sc != nullptr;
-  double in_scale[LA];
+  int in_exp[LA];
 #pragma unroll
   for (int e = 0; e < LA; ++e) {
     const int row = m0 + (threadIdx.x + e * 256) / BK;
-    in_scale[e] = (scaled && rscale == 1 && row < rows) ? ldexp(1.0, -residual_exponent(sc, row / rpr)) : 1.0;
+    in_exp[e] = (scaled && rscale == 1 && row < rows) ? -residual_exponent(sc, row / rpr) : 0;
   }
   __shared__ __align__(16) TA As[BK][BM + 4];
   __shared__ __align__(16) TA Bs[BK][BN + 4];
@@ -168,8 +168,9 @@ __global__ void __launch_bounds__(256) dst_simt_kernel(const TI *__restrict__ X,
       TA v = TA(0);
       if (row < rows && j < K) {
         const TI *xr = X + (size_t)row * n;
-        const TA x1 = (TA)(xr[j] * in_scale[e]);
-        const TA x2 = (TA)(xr[n - 1 - j] * in_scale[e]);
+        const double d1 = (double)xr[j], d2 = (double)xr[n - 1 - j];
+        const TA x1 = (TA)(in_exp[e] != 0 ? scale_pow2(d1, in_exp[e]) : d1);
+        const TA x2 = (TA)(in_exp[e] != 0 ? scale_pow2(d2, in_exp[e]) : d2);
         if (parity == 0) v = (odd_n && j == K - 1) ? x1 : x1 + x2;
         else v = x1 - x2;
       }
@@ -200,11 +201,11 @@ __global__ void __launch_bounds__(256) dst_simt_kernel(const TI *__restrict__ X,
   for (int i = 0; i < UM; ++i) {
     const int row = m0 + ty * UM + i;
     if (row >= rows) continue;
-    const double os = (scaled && rscale == 2) ? ldexp(1.0, residual_exponent(sc, row / rpr)) : 1.0;
+    const int oe = (scaled && rscale == 2) ? residual_exponent(sc, row / rpr) : 0;
 #pragma unroll
     for (int j = 0; j < UN; ++j) {
       const int col = n0 + tx * UN + j;
-      if (col < K) Y[(size_t)row * n + 2 * col + parity] = (TO)((double)acc[i][j] * os);
+      if (col < K) Y[(size_t)row * n + 2 * col + parity] = (TO)(oe != 0 ? scale_pow2((double)acc[i][j], oe) : (double)acc[i][j]);
     }
   }
 }
@@ -301,14 +302,15 @@ __global__ void __launch_bounds__(256) dct_inv_simt_kernel(const TI *__restrict_
   for (int i = 0; i < UM; ++i) {
     const int row = m0 + ty * UM + i;
     if (row >= rows) continue;
-    const double os = (rscale == 2 && sc != nullptr) ? ldexp(1.0, residual_exponent(sc, row / rpr)) : 1.0;
+    const int oe = (rscale == 2 && sc != nullptr) ? residual_exponent(sc, row / rpr) : 0;
 #pragma unroll
     for (int j = 0; j < UN; ++j) {
       const int col = n0 + tx * UN + j;
       if (col >= ku) continue;
       const TA e = acc[0][i][j], o = acc[1][i][j];
-      X[(size_t)row * n + col] = (TO)((double)(e + o) * os);
-      if (n - 1 - col != col) X[(size_t)row * n + n - 1 - col] = (TO)((double)(e - o) * os);
+      const double p1 = (double)(e + o), p2 = (double)(e - o);
+      X[(size_t)row * n + col] = (TO)(oe != 0 ? scale_pow2(p1, oe) : p1);
+      if (n - 1 - col != col) X[(size_t)row * n + n - 1 - col] = (TO)(oe != 0 ? scale_pow2(p2, oe) : p2);
     }
   }
 }

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ 
   const int k0 = ch * 8;
   const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
   // PCG residuals enter scaled by 2^-e (residual_exponent), undone by the inverse butterfly
-  const double is = (live && rscale && sc != nullptr) ? ldexp(1.0, -residual_exponent(sc, row / rpr)) : 1.0;
+  const int es = (live && rscale && sc != nullptr) ? -residual_exponent(sc, row / rpr) : 0;
   alignas(16) uint16_t uh[8], ul[8], vh[8], vl[8];
   const TI *xr = x + (size_t)(live ? row : 0) * n;
 #pragma unroll
@@ -185,11 +185,17 @@ __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ 
     float u = 0.f, w = 0.f;
     if (live) {
       if (j < kv) {
-        const float a = (float)((double)xr[j] * is), b = (float)((double)xr[n - 1 - j] * is);
+        double xa = (double)xr[j], xb = (double)xr[n - 1 - j];
+        if (es != 0) {
+          xa = scale_pow2(xa, es);
+          xb = scale_pow2(xb, es);
+        }
+        const float a = (float)xa, b = (float)xb;
         u = a + b;
         w = a - b;
       } else if (j < ku) {
-        u = (float)((double)xr[j] * is);  // middle element of an odd-length row
+        const double xm = (double)xr[j];
+        u = (float)(es != 0 ? scale_pow2(xm, es) : xm);  // middle element of an odd-length row
       }
     }
     split2f(u, uh[e], ul[e]);
@@ -432,8 +438,12 @@ __global__ void __launch_bounds__(256) butterfly_kernel(const float *__restrict_
   const int row = (int)(t / ku), k = (int)(t % ku);
   if (sc != nullptr && sc[row / rpr].state != ST_RUN) return;
   const float *er = eo + (size_t)row * 2 * ku;
-  const double os = (rscale && sc != nullptr) ? ldexp(1.0, residual_exponent(sc, row / rpr)) : 1.0;
-  const double e = (double)er[k] * os, o = (double)er[ku + k] * os;
+  const int es = (rscale && sc != nullptr) ? residual_exponent(sc, row / rpr) : 0;
+  double e = (double)er[k], o = (double)er[ku + k];
+  if (es != 0) {
+    e = scale_pow2(e, es);
+    o = scale_pow2(o, es);
+  }
   double *zr = z + (size_t)row * n;
   zr[k] = e + o;
   if (k < kv) zr[n - 1 - k] = e - o;
@@ -450,13 +460,17 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
   if (sc[rhs].state != ST_RUN) return;
   const long long per = (long long)rpr * ku;
   const size_t row0 = (size_t)rhs * rpr;
-  const double os = ldexp(1.0, residual_exponent(sc, rhs));  // the forward pack scaled r by 2^-e
+  const int es = residual_exponent(sc, rhs);  // the forward pack scaled r by 2^-e
   double a0 = 0.0, a1 = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per; t += (long long)gridDim.x * blockDim.x) {
     const size_t row = row0 + (size_t)(t / ku);
     const int k = (int)(t % ku);
     const float *er = eo + row * 2 * ku;
-    const double e = (double)er[k] * os, o = (double)er[ku + k] * os;
+    double e = (double)er[k], o = (double)er[ku + k];
+    if (es != 0) {
+      e = scale_pow2(e, es);
+      o = scale_pow2(o, es);
+    }
     const size_t i1 = row * n + k;
     const double z1 = e + o;
     z[i1] = z1;
