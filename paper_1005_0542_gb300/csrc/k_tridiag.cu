@@ -70,7 +70,9 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt, 
     tf.threads = threads(mt);
     // constant coefficients: the 3 factor classes are staged in shared memory; general systems
     // (one factor set per partition) read theirs from global memory (L2)
-    tf.smem = (size_t)((general ? 0 : 5 * 3 * L * mt) + (3 * 32 + 33) * mt) * elem_bytes;
+    // + the reduced-system multipliers of the CTA's modes ([mt][nf][32]) when a CTA solves several
+    // right-hand sides (read in the dependent PCR chain: shared memory instead of L2)
+    tf.smem = (size_t)((general ? 0 : 5 * 3 * L * mt) + (3 * 32 + 33) * mt + mt * tf.nf * 32) * elem_bytes;
     return;
   }
   // shared-memory tile kernel: modes per CTA power of two <= 32, threads <= 1024,
@@ -410,71 +412,6 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
 }
 
 
-// One right-hand side of the partitioned solve for the CTA's MT modes, thread (c, p) holding the L
-// values of rows p L .. p L + L - 1 of mode j0 + c in v: block sweeps (v = T_I^{-1} d_I), the
-// separators by parallel cyclic reduction (one warp per mode, shuffles, precomputed multipliers),
-// then the spike correction, whose value y of row i (the separator row of p >= 1 included) goes to
-// store(i, y).  Called by every thread of the CTA (two barriers); gF / gL / ds / xi are CTA shared
-// memory.
-template <typename T, int L, int MT, typename Store>
-__device__ __forceinline__ void tri_plane_solve(T (&v)[L], bool live, int c, int p, int i0, int P, int nx, int j0,
-                                                int levels, int nf, const T *__restrict__ red, const T *Fm,
-                                                const T *Fa, const T *Fc, const T *Sv, const T *Sw, int FS, T *gF,
-                                                T *gL, T *ds, T *xi, Store &&store) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
-  const int n = P - 1;
-  const T dsep = v[0];  // separator row value (p >= 1)
-  if (live) {
-    // forward elimination over the block rows i0..L-1, then back substitution: v = T_I^{-1} d_I
-    T prev = T(0);
-#pragma unroll
-    for (int i = 0; i < L; ++i) {
-      if (i < i0) continue;
-      const T m = Fm[i * FS];
-      v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * FS] * prev) * m;
-      prev = v[i];
-    }
-#pragma unroll
-    for (int i = L - 2; i >= 0; --i) {
-      if (i < i0) continue;
-      v[i] = v[i] - Fc[i * FS] * v[i + 1];
-    }
-    gF[c * 32 + p] = (i0 == 0) ? v[0] : v[1];
-    gL[c * 32 + p] = v[L - 1];
-    ds[c * 32 + p] = (p >= 1) ? dsep : T(0);
-  }
-  __syncthreads();
-  for (int cc = warp; n > 0 && cc < MT; cc += nwarp) {
-    const int jj = j0 + cc;
-    if (jj >= nx) continue;  // warp-uniform
-    const T *R = red + (size_t)jj * nf * 32;
-    const bool act = lane < n;
-    T rq = T(0);
-    if (act) {
-      const int pp = lane + 1;
-      rq = (ds[cc * 32 + pp] - R[lane] * gL[cc * 32 + pp - 1] - R[32 + lane] * gF[cc * 32 + pp]) * R[64 + lane];
-    }
-    for (int l = 0; l < levels; ++l) {
-      const int s = 1 << l;
-      T rm = __shfl_up_sync(0xffffffffu, rq, s);
-      T rp = __shfl_down_sync(0xffffffffu, rq, s);
-      if (lane < s) rm = T(0);
-      if (lane + s >= n) rp = T(0);
-      if (act) rq = (rq - R[(3 + 3 * l) * 32 + lane] * rm - R[(4 + 3 * l) * 32 + lane] * rp) * R[(5 + 3 * l) * 32 + lane];
-    }
-    xi[cc * 33 + lane + 1] = act ? rq : T(0);
-    if (lane == 0) xi[cc * 33] = T(0);
-  }
-  if (n == 0 && tid < MT) xi[tid * 33] = T(0);
-  __syncthreads();
-  if (live) {
-    const T xa = xi[c * 33 + p];
-    const T xb = (p + 1 <= P - 1) ? xi[c * 33 + p + 1] : T(0);
-#pragma unroll
-    for (int i = 0; i < L; ++i) store(i, (i < i0) ? xa : v[i] - xa * Sv[i * FS] - xb * Sw[i * FS]);
-  }
-}
-
 // Register-resident variant (partition length L a compile-time power of two): thread (c, p) keeps
 // the L values of its partition in registers, loaded straight from global memory (a warp reads
 // rows of MT consecutive modes: whole 32-byte sectors, 64 bytes per row for float32) and stored
@@ -509,8 +446,13 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T
   T *gL = gF + MT * 32;
   T *ds = gL + MT * 32;
   T *xi = ds + MT * 32;                      // [MT][33]
+  T *Rs = xi + MT * 33;                      // [MT][nf][32]: reduced systems of the CTA's modes
   const int j0 = blockIdx.x * MT;
   const int tid = threadIdx.x, nth = blockDim.x;
+  const bool stage_red = per_cta > 1;        // staging pays off over several right-hand sides
+  if (stage_red)
+    for (int idx = tid; idx < MT * nf * 32; idx += nth)  // one contiguous block of red
+      Rs[idx] = (j0 + idx / (nf * 32) < nx) ? red[(size_t)j0 * nf * 32 + idx] : T(0);
   // stage the factors of this CTA's modes: row-major [row][MT], MT a power of two
   if constexpr (!GEN) {
     const int cm = tid % MT, r0 = tid / MT, rstep = nth / MT;
@@ -579,7 +521,7 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T
     for (int cc = warp; n > 0 && cc < MT; cc += nwarp) {
       const int jj = j0 + cc;
       if (jj >= nx) continue;  // warp-uniform
-      const T *R = red + (size_t)jj * nf * 32;
+      const T *R = stage_red ? Rs + (size_t)cc * nf * 32 : red + (size_t)jj * nf * 32;
       const bool act = lane < n;
       T rq = T(0);
       if (act) {
