@@ -433,20 +433,20 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
 __global__ void __launch_bounds__(256) butterfly_kernel(const float *__restrict__ eo, double *__restrict__ z, int rows,
                                                         int n, int ku, int kv, const KrylovScalars *__restrict__ sc,
                                                         int rpr, int rscale) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)rows * ku) return;
-  const int row = (int)(t / ku), k = (int)(t % ku);
-  if (sc != nullptr && sc[row / rpr].state != ST_RUN) return;
+  const int row = blockIdx.x;  // one block per row, its modes over the threads
+  if (row >= rows || (sc != nullptr && sc[row / rpr].state != ST_RUN)) return;
   const float *er = eo + (size_t)row * 2 * ku;
   const int es = (rscale && sc != nullptr) ? residual_exponent(sc, row / rpr) : 0;
-  double e = (double)er[k], o = (double)er[ku + k];
-  if (es != 0) {
-    e = scale_pow2(e, es);
-    o = scale_pow2(o, es);
-  }
   double *zr = z + (size_t)row * n;
-  zr[k] = e + o;
-  if (k < kv) zr[n - 1 - k] = e - o;
+  for (int k = threadIdx.x; k < ku; k += blockDim.x) {
+    double e = (double)er[k], o = (double)er[ku + k];
+    if (es != 0) {
+      e = scale_pow2(e, es);
+      o = scale_pow2(o, es);
+    }
+    zr[k] = e + o;
+    if (k < kv) zr[n - 1 - k] = e - o;
+  }
 }
 
 // The butterfly fused with the CG update of the next step: per right-hand side (rpr rows each),
@@ -458,13 +458,13 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
                                                              KrylovScalars *sc, Reduce red) {
   const int rhs = blockIdx.y;
   if (sc[rhs].state != ST_RUN) return;
-  const long long per = (long long)rpr * ku;
   const size_t row0 = (size_t)rhs * rpr;
   const int es = residual_exponent(sc, rhs);  // the forward pack scaled r by 2^-e
   double a0 = 0.0, a1 = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per; t += (long long)gridDim.x * blockDim.x) {
-    const size_t row = row0 + (size_t)(t / ku);
-    const int k = (int)(t % ku);
+  // rows round-robin over the blocks, a row's modes over the threads (no 64-bit index division)
+  for (int rl = blockIdx.x; rl < rpr; rl += gridDim.x)
+  for (int k = threadIdx.x; k < ku; k += blockDim.x) {
+    const size_t row = row0 + (size_t)rl;
     const float *er = eo + row * 2 * ku;
     double e = (double)er[k], o = (double)er[ku + k];
     if (es != 0) {
@@ -600,9 +600,7 @@ void dst_apply_tc_f2d(const DstPlan &dp, const float *y, double *z, int rows, in
     count_launch();
     LAG_LAUNCH_CHECK();
     gemm_launch(dp, apack, dp.tc_b + 2 * dp.tc_bmat_bytes, rows, eo, 2 * dp.ku, dp.ku, dp.ku, sc, rpr, dp.tc_err, s);
-    const long long t = (long long)rows * dp.ku;
-    butterfly_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(eo, z, rows, dp.n, dp.ku, dp.kv, sc, rpr,
-                                                                 rscale ? 1 : 0);
+    butterfly_kernel<<<rows, 256, 0, s>>>(eo, z, rows, dp.n, dp.ku, dp.kv, sc, rpr, rscale ? 1 : 0);
     count_launch();
     LAG_LAUNCH_CHECK();
   }
@@ -622,8 +620,8 @@ void dst_apply_tc_f2d_beta(const DstPlan &dp, const float *y, double *z, int nrh
   count_launch();
   LAG_LAUNCH_CHECK();
   gemm_launch(dp, apack, dp.tc_b + 2 * dp.tc_bmat_bytes, rows, eo, 2 * dp.ku, dp.ku, dp.ku, sc, rpr, dp.tc_err, s);
-  const long long per = (long long)rpr * dp.ku;
-  int blocks = (int)std::min<long long>((per + 1023) / 1024, 1216);
+  // rows per right-hand side over at most min(1216, the reduction's block capacity) blocks
+  int blocks = std::min(std::min(rpr, 1216), red.nblk);
   if (blocks < 1) blocks = 1;
   dim3 g(blocks, nrhs);
   butterfly_beta_kernel<<<g, 256, 0, s>>>(eo, z, r, q, dp.n, dp.ku, dp.kv, rpr, flexible, sc, red);
