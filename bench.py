@@ -40,7 +40,8 @@ WORKLOAD = ("random_layered_2048x1024 acoustic FP64 single shot: 5 m, 20 layers 
 NCU_TRAFFIC = {
     # oz_pack_a_kernel (16.8 MB) + oz_gemm_kernel (78.8 MB), one 2048-mode x 1024-row launch each
     # (bench.py --capture-kernels; profiles/launches_dst_f64_random_layered_2048x1024.md)
-    "dst_f64_oz": {"bytes": 95.6e6, "sha1": "b88daea6e09e"},
+    "dst_f64_oz": {"bytes": 95.6e6, "sha1": "12d01cd0fb46",
+                   "section": "// ============================================================================ exact-slice FP64 DST"},
 }
 
 
@@ -49,11 +50,22 @@ def sha1_of(path):
         return hashlib.sha1(f.read()).hexdigest()[:12]
 
 
+def section_sha1(path, marker):
+    """sha1 of the source from the line holding `marker` to the end of the file (the kernels the
+    counters were taken on; edits elsewhere in the file do not void them)."""
+    with open(path, "rb") as f:
+        data = f.read()
+    i = data.find(marker.encode())
+    return hashlib.sha1(data[i:] if i >= 0 else data).hexdigest()[:12]
+
+
 def traffic_for(kernel_file, key):
     rec = NCU_TRAFFIC.get(key)
     if not rec:
         return None
-    if sha1_of(os.path.join(ROOT, "paper_1005_0542_gb300", "csrc", kernel_file)) != rec["sha1"]:
+    path = os.path.join(ROOT, "paper_1005_0542_gb300", "csrc", kernel_file)
+    digest = section_sha1(path, rec["section"]) if "section" in rec else sha1_of(path)
+    if digest != rec["sha1"]:
         return None
     return rec["bytes"]
 
