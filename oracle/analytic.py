@@ -15,6 +15,14 @@
   Eq. 1; a free surface at z = 0 adds the mirror source at -z0 (the paper's exact solution of
   Sec. 3.2, f(t - r/c) / (2 pi r) with kappa = 1, is the case z0 = 0 seen on the surface).
 
+* ``point_force_3d``: homogeneous isotropic elastic medium, rho u_tt = div sigma + e_z delta_3(x - x0)
+  f(t) (a vertical point force), zero initial data.  Stokes' solution (the classical elastodynamic
+  Green's function, near, intermediate and far field), with R = |x - x0|, gamma = (x - x0) / R,
+  alpha / beta the P / S speeds:
+      u_i = (3 g_i g_z - d_iz) / (4 pi rho R^3) int_{R/alpha}^{R/beta} tau f(t - tau) d tau
+          + g_i g_z / (4 pi rho alpha^2 R) f(t - R/alpha) - (g_i g_z - d_iz) / (4 pi rho beta^2 R) f(t - R/beta).
+  Returned as the radial (i = r, d_rz = 0) and vertical (i = z) components about the force axis.
+
 * ``oscillator``: one mode of the semi-discrete problem, rho u'' + q u = f(t), u(0)=u'(0)=0:
       u(t) = 1/(rho w) int_0^t sin(w (t - tau)) f(tau) d tau,  w = sqrt(q/rho).
   Its Laguerre coefficients must satisfy the scalar form of the spectral recurrence (Eq. 9):
@@ -54,6 +62,27 @@ def point_source_3d(R, t, kappa, rho, fun):
     c = math.sqrt(kappa / rho)
     t = np.atleast_1d(np.asarray(t, dtype=np.float64))
     return np.where(t > R / c, fun(t - R / c), 0.0) / (4.0 * math.pi * kappa * R)
+
+
+def point_force_3d(r, dz, t, lam, mu, rho, fun, order=24, panels=16):
+    """(u_r, u_z) at horizontal distance r >= 0 and height dz = z - z0 (R > 0) for an array of t."""
+    a = math.sqrt((lam + 2.0 * mu) / rho)
+    b = math.sqrt(mu / rho)
+    R = math.hypot(r, dz)
+    gr, gz = r / R, dz / R
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    near = np.zeros_like(t)
+    edges = np.linspace(R / a, R / b, panels + 1)
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        tau, w = _gl(lo, hi, order)
+        near += np.sum(w[None, :] * tau[None, :] * fun(t[:, None] - tau[None, :]), axis=1)
+    fa = fun(t - R / a)
+    fb = fun(t - R / b)
+    c = 1.0 / (4.0 * math.pi * rho)
+    ur = c * (3.0 * gr * gz) / R ** 3 * near + c * gr * gz / (a * a * R) * fa - c * gr * gz / (b * b * R) * fb
+    uz = (c * (3.0 * gz * gz - 1.0) / R ** 3 * near + c * gz * gz / (a * a * R) * fa
+          - c * (gz * gz - 1.0) / (b * b * R) * fb)
+    return ur, uz
 
 
 def oscillator(t, q, rho, fun, panels=256, order=16):
