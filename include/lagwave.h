@@ -70,18 +70,28 @@ typedef struct lag_shot    lag_shot;
 
 /* Interior nodes nx x nz with spacing dx, dz (m); u = 0 on the ghost nodes around them, except
  * that free_surface = 1 puts a free surface on top (Sec. 2.1, Eq. 3: du/dz = 0 at z = 0), read
- * as a top face of node row 0 that carries no flux (acoustic problems only; elastic media return
- * LAG_EINVAL).  The surface lies half a cell above row 0.  Fields are [nz][nx], x fastest.
+ * as a top face of node row 0 that carries no flux (on Cartesian grids acoustic problems only;
+ * elastic media return LAG_EINVAL).  The surface lies half a cell above row 0.  Fields are
+ * [nz][nx], x fastest.
  *
  * cylindrical = 1: the paper's own 2.5D axisymmetric problem (Sec. 2.1 Eqs. 1-5, the scheme of
- * Sec. 2.3 Eqs. 17-19), acoustic only.  x is then the radius r: nodes r_i = (i + 1/2) dx from the
- * axis (the axis face carries no flux, Eq. 5), u = 0 on the ghost node r = (nx + 1/2) dx; z_k =
+ * Sec. 2.3 Eqs. 17-19; elastic media: Sec. 2.2, below).  x is then the radius r: nodes
+ * r_i = (i + 1/2) dx from the axis (the axis face carries no flux, Eq. 5), u = 0 on the ghost
+ * node r = (nx + 1/2) dx; z_k =
  * (k + 1/2) dz with zero-flux faces at z = 0 (the free surface, Eq. 3) and at z = nz dz (the
  * auxiliary boundary).  free_surface must be 1.  Every term carries the factor r (a1 = rbar
  * kappa, a2 = r kappa, w = r rho h^2/4; the source f_m / (2 pi dx dz) at its node, the history
  * term r rho h^2).  Fields of cylindrical grids are [nx][nz]: radius index slow, depth index
  * fastest (the DCT-II along z runs over contiguous rows, the general tridiagonal systems along r
- * over columns); lag_point (ix, iz) is still (radius index, depth index). */
+ * over columns); lag_point (ix, iz) is still (radius index, depth index).
+ *
+ * Elastic media on a cylindrical grid (Sec. 2.2, Eqs. 10-12): u = (u_r, u_z) = (Q, U), fields
+ * [rhs][comp][nx][nz] (comp 0 = u_r); the operator is the gradient of a discrete strain energy
+ * (symmetric; each strain term sampled at r-faces, z-faces, nodes or cell corners), so the
+ * traction-free surface sigma_zz = sigma_rz = 0 (the paper's condition with Q and U put back in
+ * place) is its natural condition at z = 0 and at the bottom; a vertical point force on the axis
+ * (delta(r) delta(z - d) / (2 pi r)) enters the u_z equation as f_m / (2 pi dx dz); K = diag(B1, B2)
+ * with the cylindrical coefficients of Eq. 22 (B1's d includes (l+2m)~ / r). */
 typedef struct { int nx, nz; double dx, dz; int free_surface; int cylindrical; } lag_grid;
 typedef struct { double h; int alpha; int n_harm; } lag_laguerre; /* Sec. 2.1: h (1/s), alpha >= 2 */
 typedef struct {
@@ -160,6 +170,11 @@ int  lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double
                                 const double *az_z, const double *d_z, int prec, int partitions,
                                 lag_precond **out);
 int  lag_precond_is_layered(const lag_precond *p);   /* 1 for plans of lag_precond_create_layered */
+/* Cylindrical grids only: B of Eq. 21 / Eq. 22 with a1 = rbar ax_t, a2 = r az_t and
+ * d(r) = r d_t + hoop_t / r (B1 of the elastic K: ax_t = (l+2m)~, az_t = mu~, hoop_t = (l+2m)~;
+ * B2: ax_t = mu~, az_t = (l+2m)~, hoop_t = 0).  LAG_EINVAL on a Cartesian grid. */
+int  lag_precond_create_cyl(lag_ctx *ctx, const lag_grid *grid, double ax_t, double az_t, double d_t,
+                            double hoop_t, int prec, int partitions, lag_precond **out);
 void lag_precond_destroy(lag_precond *p);
 /* z = B^{-1} r for nrhs fields [nrhs][nz][nx] (device, float64; cylindrical: [nrhs][nx][nz]).
  * Stream-ordered.  r and z may not overlap.  Steps: forward DST-I along x, one tridiagonal solve

@@ -122,7 +122,7 @@ lag_grid lag::kernel_grid(const lag_grid &g) {
 }
 
 lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, double az, double d, int prec,
-                              int partitions, cudaStream_t s, const double *layered) {
+                              int partitions, cudaStream_t s, const double *layered, double hoop) {
   const lag_grid g = kernel_grid(gu);
   std::vector<double> zr;
   if (g.cylindrical) {
@@ -130,7 +130,8 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     // DCT-II along z, per z-mode q the system along r has the rows
     //   (-ax i/dr, ax (2i+1)/dr + r_i az mu_q + r_i d, -ax (i+1)/dr)   (r_i = (i + 1/2) dr)
     if (layered != nullptr) throw Error(LAG_EINVAL, "the layered preconditioner is Cartesian only");
-    if (!(ax > 0) || !(az > 0) || !(d >= 0)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+    if (!(ax > 0) || !(az > 0) || !(d >= 0) || !(hoop >= 0))
+      throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
     const int nr = g.nz;
     const double dr = g.dz;
     zr.resize(3 * (size_t)nr + 1);
@@ -138,8 +139,10 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     for (int i = 0; i < nr; ++i) {
       const double ri = (i + 0.5) * dr;
       zr[nr + 1 + i] = ri * az;
-      zr[2 * nr + 1 + i] = ri * d;
+      zr[2 * nr + 1 + i] = ri * d + hoop / ri;
     }
+  } else if (hoop != 0.0) {
+    throw Error(LAG_EINVAL, "the hoop term belongs to cylindrical grids");
   } else if (layered != nullptr) {
     // per-row coefficients -> z faces (mean of the two rows; a boundary face takes its row's value,
     // the top face carries no flux under a free surface), each over dz^2
@@ -231,7 +234,11 @@ lag_medium *lag::medium_new(lag_ctx *ctx, const lag_grid &gu, const double *c, c
     if (g.cylindrical) medium_build_cylindrical(*m, c, rho, s);
     else medium_build_acoustic(*m, c, rho, s);
   } else {
-    if (g.cylindrical) throw Error(LAG_EINVAL, "cylindrical grids are acoustic only (the elastic 2.5D problem is not built)");
+    if (g.cylindrical) {  // the axisymmetric elastic operator (k_elastic_cyl.cu)
+      m->elastic = true;
+      medium_build_elastic_cylindrical(*m, c, vs, rho, s);
+      return m.release();
+    }
     if (g.free_surface)
       throw Error(LAG_EINVAL, "free_surface applies to acoustic media only (the elastic traction-free surface is not built)");
     m->elastic = true;
@@ -360,6 +367,18 @@ int lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double 
     std::copy(az_z, az_z + grid->nz, rows.begin() + grid->nz);
     std::copy(d_z, d_z + grid->nz, rows.begin() + 2 * (size_t)grid->nz);
     *out = precond_new(ctx, *grid, 0.0, 0.0, 0.0, prec, partitions, ctx->stream, rows.data());
+  });
+}
+
+int lag_precond_create_cyl(lag_ctx *ctx, const lag_grid *grid, double ax_t, double az_t, double d_t, double hoop_t,
+                           int prec, int partitions, lag_precond **out) {
+  if (!ctx || !grid || !out) return LAG_EINVAL;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    if (!grid->cylindrical) throw Error(LAG_EINVAL, "lag_precond_create_cyl needs a cylindrical grid");
+    if (partitions < 0 || partitions > 32) throw Error(LAG_EINVAL, "partitions must be 0..32");
+    *out = precond_new(ctx, *grid, ax_t, az_t, d_t, prec, partitions, ctx->stream, nullptr, hoop_t);
   });
 }
 

@@ -232,6 +232,11 @@ void medium_build_acoustic(lag_medium &m, const double *c_host, const double *rh
                            cudaStream_t s);
 // cylindrical (r, z) acoustic medium on the kernel grid (rows = radii; see kernel_grid)
 void medium_build_cylindrical(lag_medium &m, const double *c_host, const double *rho_host, cudaStream_t s);
+// cylindrical (r, z) elastic medium: energy-derived axisymmetric operator (k_elastic_cyl.cu)
+void medium_build_elastic_cylindrical(lag_medium &m, const double *vp_host, const double *vs_host,
+                                      const double *rho_host, cudaStream_t s);
+void elastic_cyl_apply(const lag_medium &m, const double *p, double *q, int nrhs, const KrylovScalars *sc,
+                       int mode, cudaStream_t s);
 void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs_host,
                           const double *rho_host, cudaStream_t s);
 // The grid the kernels run on.  Cartesian: the user's grid.  Cylindrical (fields [nr][nz], depth
@@ -248,8 +253,9 @@ lag_medium *medium_new(lag_ctx *ctx, const lag_grid &g, const double *c, const d
 void precond_rebuild_tri(lag_precond *p, int want_P, int want_mt, cudaStream_t s);
 // layered (nullable, host): [ax(z): nz | az(z): nz | d(z): nz] per-row coefficients; then ax, az, d
 // are unused
+// hoop (cylindrical grids only): d(r) = r d + hoop / r (the (l+2m)~/r term of B1, Eq. 22)
 lag_precond *precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, double d, int prec,
-                         int partitions, cudaStream_t s, const double *layered = nullptr);
+                         int partitions, cudaStream_t s, const double *layered = nullptr, double hoop = 0.0);
 // mode 0: q = Ap only; mode 1: also (p,q) -> alpha = rz/pq  (PCG)
 void acoustic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
                     const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s);

@@ -181,6 +181,10 @@ __global__ void __launch_bounds__(256) elastic_apply_kernel(const double *__rest
 
 void elastic_apply(const lag_medium &m, const double *p, double *q, int nrhs, const KrylovScalars *sc,
                    const Reduce *, int mode, cudaStream_t s) {
+  if (m.grid.cylindrical) {
+    elastic_cyl_apply(m, p, q, nrhs, sc, mode, s);
+    return;
+  }
   dim3 g((m.grid.nx + 31) / 32, (m.grid.nz + 7) / 8, nrhs);
   ProfScope prof(KC_STENCIL_E, s);
   elastic_apply_kernel<<<g, 256, 0, s>>>(p, q, m.grid.nx, m.grid.nz, elastic_coef(m), sc, mode);

@@ -84,7 +84,8 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
     sh->p1 = precond_new(ctx, g, mid[0], mid[0], mid[1] * lag.h * lag.h / 4.0, s.prec, s.partitions, st);
   } else {  // K = diag(B1, B2), Eq. (22): B1 (ax, az) = ((l+2m)~, mu~), B2 = (mu~, (l+2m)~)
     const double d = mid[2] * lag.h * lag.h / 4.0;
-    sh->p1 = precond_new(ctx, g, mid[0], mid[1], d, s.prec, s.partitions, st);
+    // cylindrical grids: B1 also holds the hoop term (l+2m)~/r (Eq. 22)
+    sh->p1 = precond_new(ctx, g, mid[0], mid[1], d, s.prec, s.partitions, st, nullptr, g.cylindrical ? mid[0] : 0.0);
     sh->p2 = precond_new(ctx, g, mid[1], mid[0], d, s.prec, s.partitions, st);
   }
   if (s.tune) {  // the autotuner issues on the context stream: the plans are complete already

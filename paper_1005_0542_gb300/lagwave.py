@@ -85,6 +85,7 @@ _PROTOS = {
     "lag_precond_create_sep": (I, [VP, C.POINTER(lag_grid), D, D, D, I, I, C.POINTER(VP)]),
     "lag_precond_create_layered": (I, [VP, C.POINTER(lag_grid), PD, PD, PD, I, I, C.POINTER(VP)]),
     "lag_precond_is_layered": (I, [VP]),
+    "lag_precond_create_cyl": (I, [VP, C.POINTER(lag_grid), D, D, D, D, I, I, C.POINTER(VP)]),
     "lag_precond_destroy": (None, [VP]),
     "lag_precond_apply": (I, [VP, VP, VP, I]),
     "lag_precond_dst": (I, [VP, VP, VP, I]),

@@ -215,10 +215,6 @@ def test_cylindrical_rejections(ctx):
     rc, _, _ = _shot(ctx, s, L.LAG_FP64, 1e-8, layered=1)               # layered is Cartesian only
     assert rc == L.LAG_EINVAL
     g = L.grid(16, 12, 5.0, 5.0, cylindrical=True)
-    m = C.c_void_p()
-    c_, pc = L.f64(s.c)
-    r_, pr = L.f64(s.rho)
-    assert L.lag_medium_create_elastic(ctx, C.byref(g), pc, pc, pr, s.h, C.byref(m)) == L.LAG_EINVAL
     p = C.c_void_p()
     a_, pa = L.f64(np.ones(12))
     assert L.lag_precond_create_layered(ctx, C.byref(g), pa, pa, pa, L.LAG_FP64, 0, C.byref(p)) == L.LAG_EINVAL
