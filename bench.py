@@ -402,24 +402,28 @@ def cylindrical_leg(ctx, args):
     wavelet of Eq. 23 (30 Hz, t0 = 0.2 s, gamma = 4), alpha = 9, h = 400, mesh step lambda/40, on
     2^k x 2^k nodes; here 2048 x 2048 (the paper's smallest mesh is 4096^2), FP64 path, where A == B
     and PCG takes one iteration; plus a random layered half space (layers along z) at 2048 x 1024
-    for the iterative case.  step = one harmonic."""
+    for the iterative case, and the same model as an elastic half space (Sec. 2.2: Vs = Vp / 1.73,
+    a vertical force on the axis, FGMRES(20) with K = diag(B1, B2), B1 with its hoop term).
+    step = one harmonic."""
     import torch
     from paper_1005_0542_gb300 import inputs
     from paper_1005_0542_gb300 import lagwave as L
     out = {}
-    for key, nr, nz, layered, prec in (("homogeneous_fp64", 2048, 2048, False, L.LAG_FP64),
-                                       ("layered_fp64", 2048, 1024, True, L.LAG_FP64),
-                                       ("layered_mixed", 2048, 1024, True, L.LAG_MIXED)):
-        s = inputs.cylindrical(nr=nr, nz=nz, n_harm=64, layered=layered)
+    for key, nr, nz, layered, prec, elastic in (("homogeneous_fp64", 2048, 2048, False, L.LAG_FP64, False),
+                                                ("layered_fp64", 2048, 1024, True, L.LAG_FP64, False),
+                                                ("layered_mixed", 2048, 1024, True, L.LAG_MIXED, False),
+                                                ("elastic_layered_mixed", 2048, 1024, True, L.LAG_MIXED, True)):
+        s = inputs.cylindrical(nr=nr, nz=nz, n_harm=64, layered=layered, elastic=elastic)
         g = L.grid(s.nx, s.nz, s.hx, s.hz, cylindrical=True)
         lag = L.laguerre(s.h, s.alpha, s.n_harm)
-        sv = L.solver(tol=1e-10, prec=prec)
+        sv = L.solver(tol=1e-10, prec=prec, restart_k=s.restart)
         w = L.wavelet(s.f0, s.t0, 4.0, L.LAG_WAVELET_PAPER)
         c_, pc = L.f64(s.c)
         r_, pr = L.f64(s.rho)
         t_, pt = L.f64(s.t_out)
+        v_, pv = L.f64(s.vs) if elastic else (None, None)
         sh = C.c_void_p()
-        L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+        L.check(L.lag_shot_create(ctx, C.byref(g), pc, pv, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
                                   L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
                                   C.byref(sh)), ctx)
         W, K = 3, args.cyl_steps
@@ -448,11 +452,14 @@ def cylindrical_leg(ctx, args):
         L.lag_shot_stats(sh, C.byref(st))
         L.lag_shot_destroy(sh)
         out[key] = {"grid_r_z": [nr, nz], "h_m": s.hx, "value": K / (ms / 1e3), "unit": UNIT, "steps": K,
-                    "ms_per_step": ms / K, "pcg_iters_per_step": float(its[0, W:W + K].mean()),
+                    "ms_per_step": ms / K,
+                    ("fgmres_iters_per_step" if elastic else "pcg_iters_per_step"): float(its[0, W:W + K].mean()),
                     "kernel_ms": {L.lag_profile_class_name(i).decode(): {"launches": cnt[i], "ms": round(kms[i], 3)}
                                   for i in range(nk) if cnt[i]}}
-    out["config"] = ("2.5D axisymmetric acoustic half space (r, z), source on the axis, Eq. 23 wavelet 30 Hz, "
-                     "mesh lambda/40; homogeneous (Sec. 3.2) and random layered media")
+    out["config"] = ("2.5D axisymmetric half space (r, z), source on the axis, Eq. 23 wavelet 30 Hz, "
+                     "mesh lambda/40; acoustic: homogeneous (Sec. 3.2) and random layered media; elastic "
+                     "(Sec. 2.2): the layered medium as Vp, Vs = Vp / 1.73, vertical force, FGMRES(20) with "
+                     "K = diag(B1, B2) of Eq. 22")
     return out
 
 

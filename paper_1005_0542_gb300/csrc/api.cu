@@ -214,8 +214,9 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
 
 // ------------------------------------------------------------------------------ medium
 void lag_medium::apply(const double *p, double *q, int nrhs, const KrylovScalars *sc, const Reduce *red, int mode,
-                       cudaStream_t s) {
-  if (elastic) elastic_apply(*this, p, q, nrhs, sc, red, mode, s);
+                       cudaStream_t s, const double *sub) {
+  if (elastic) elastic_apply(*this, p, q, nrhs, sc, red, mode, s, sub);
+  else if (sub != nullptr) throw Error(LAG_EINVAL, "acoustic operator: no subtrahend");
   else acoustic_apply(*this, p, q, nrhs, sc, red, mode, s);
 }
 

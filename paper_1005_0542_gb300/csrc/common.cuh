@@ -52,7 +52,7 @@ struct KrylovScalars {
   int state;      // ST_* below
   int iters;
   int jdone;      // GMRES: steps taken in the open cycle
-  int pad;
+  int reorth;     // GMRES: 1 if this step's second Gram-Schmidt pass runs (set by the first pass)
 };
 static_assert(sizeof(KrylovScalars) == 80, "layout");
 

@@ -222,8 +222,9 @@ struct lag_medium {
   lag::DevBuf rho_h2;          // rho h^2 at nodes (right-hand side history term)
   lag::DevBuf rowmm;           // acoustic: per-row [kappa | rho][nz][min, max] (layered preconditioner)
   size_t ncoef = 0;
+  // q = C p (elastic) or A p; sub (elastic only, nullable): q = C p - sub, same layout as q
   void apply(const double *p, double *q, int nrhs, const lag::KrylovScalars *sc,
-             const lag::Reduce *red, int mode, cudaStream_t s);
+             const lag::Reduce *red, int mode, cudaStream_t s, const double *sub = nullptr);
 };
 
 namespace lag {
@@ -236,7 +237,7 @@ void medium_build_cylindrical(lag_medium &m, const double *c_host, const double 
 void medium_build_elastic_cylindrical(lag_medium &m, const double *vp_host, const double *vs_host,
                                       const double *rho_host, cudaStream_t s);
 void elastic_cyl_apply(const lag_medium &m, const double *p, double *q, int nrhs, const KrylovScalars *sc,
-                       int mode, cudaStream_t s);
+                       int mode, cudaStream_t s, const double *sub);
 void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs_host,
                           const double *rho_host, cudaStream_t s);
 // The grid the kernels run on.  Cartesian: the user's grid.  Cylindrical (fields [nr][nz], depth
@@ -260,7 +261,8 @@ lag_precond *precond_new(lag_ctx *ctx, const lag_grid &g, double ax, double az, 
 void acoustic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
                     const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s);
 void elastic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
-                   const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s);
+                   const KrylovScalars *sc, const Reduce *red, int mode, cudaStream_t s,
+                   const double *sub = nullptr);
 
 int reduce_blocks(size_t n);  // blocks per rhs of the vector kernels for n values per rhs
 
@@ -285,8 +287,9 @@ struct GmresDev {
 void gm_start(const double *b, const double *cx, double *v0, size_t n, int nrhs, int first,
               double tol, int max_iter, KrylovScalars *sc, GmresDev &g, const Reduce &red,
               cudaStream_t s);
+// shifted: w holds C z_j - V_j (the shifted Arnoldi step); h_jj gets the 1 back
 void gm_orthogonalize(double *w, const double *V, int j, size_t n, int nrhs, size_t vstride,
-                      const KrylovScalars *sc, GmresDev &g, const Reduce &red, int pass,
+                      KrylovScalars *sc, GmresDev &g, const Reduce &red, int pass, bool shifted,
                       cudaStream_t s);
 void gm_normalize(double *w, double *vnext, int j, size_t n, int nrhs, KrylovScalars *sc,
                   GmresDev &g, const Reduce &red, int max_iter, cudaStream_t s);

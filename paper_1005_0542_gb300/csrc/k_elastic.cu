@@ -133,7 +133,8 @@ void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs
 // mode 0: every rhs (or those running when sc is given); mode 2: rhs running or ST_MET
 __global__ void __launch_bounds__(256) elastic_apply_kernel(const double *__restrict__ U, double *__restrict__ Q,
                                                             int nx, int nz, ElasticCoef c,
-                                                            const KrylovScalars *__restrict__ sc, int mode) {
+                                                            const KrylovScalars *__restrict__ sc, int mode,
+                                                            const double *__restrict__ sub) {
   const int b = blockIdx.z;
   if (sc != nullptr) {
     const int st = sc[b].state;
@@ -169,25 +170,26 @@ __global__ void __launch_bounds__(256) elastic_apply_kernel(const double *__rest
   vu = fma(-c.mz[o + nx], us, vu);
   vu = fma(-c.mz[o], un, vu);
   const double mixu = l4e * (wpp - wmp) - l4w * (wpm - wmm) + m4s * (wpp - wpm) - m4n * (wmp - wmm);
-  qu[o] = vu - mixu;
+  const double *su = sub ? sub + (size_t)b * 2 * plane : nullptr;
+  qu[o] = su ? (vu - mixu) - su[o] : vu - mixu;
   double vw = c.dw[o] * wc;
   vw = fma(-c.mx[fx + 1], we, vw);
   vw = fma(-c.mx[fx], ww, vw);
   vw = fma(-c.pz[o + nx], ws, vw);
   vw = fma(-c.pz[o], wn, vw);
   const double mixw = m4e * (upp - ump) - m4w * (upm - umm) + l4s * (upp - upm) - l4n * (ump - umm);
-  qw[o] = vw - mixw;
+  qw[o] = su ? (vw - mixw) - su[plane + o] : vw - mixw;
 }
 
 void elastic_apply(const lag_medium &m, const double *p, double *q, int nrhs, const KrylovScalars *sc,
-                   const Reduce *, int mode, cudaStream_t s) {
+                   const Reduce *, int mode, cudaStream_t s, const double *sub) {
   if (m.grid.cylindrical) {
-    elastic_cyl_apply(m, p, q, nrhs, sc, mode, s);
+    elastic_cyl_apply(m, p, q, nrhs, sc, mode, s, sub);
     return;
   }
   dim3 g((m.grid.nx + 31) / 32, (m.grid.nz + 7) / 8, nrhs);
   ProfScope prof(KC_STENCIL_E, s);
-  elastic_apply_kernel<<<g, 256, 0, s>>>(p, q, m.grid.nx, m.grid.nz, elastic_coef(m), sc, mode);
+  elastic_apply_kernel<<<g, 256, 0, s>>>(p, q, m.grid.nx, m.grid.nz, elastic_coef(m), sc, mode, sub);
   count_launch();
   LAG_LAUNCH_CHECK();
 }
@@ -255,21 +257,60 @@ void gm_start(const double *b, const double *cx, double *v0, size_t n, int nrhs,
   LAG_LAUNCH_CHECK();
 }
 
-// h_i = (w, V_i), i <= j: partials per block, the last block finishes all j+1 sums
+// Warp sum of eight per-thread values, scattered: lane l ends with the warp total of value l >> 2
+// (recursive halving: each butterfly step keeps half of the values and adds the partner's copy of
+// them, 4 + 2 + 1 + 1 + 1 = 9 FP64 adds instead of 40 for eight full butterflies; the FP64 pipe,
+// not HBM, bounds the Gram-Schmidt kernels on this part).  Fixed order: deterministic.
+__device__ __forceinline__ double warp_sum8_scatter(const double (&a)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  double h4[4], h2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double keep = b4 ? a[4 + i] : a[i], send = b4 ? a[i] : a[4 + i];
+    h4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double keep = b3 ? h4[2 + i] : h4[i], send = b3 ? h4[i] : h4[2 + i];
+    h2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  double h1 = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? h2[0] : h2[1], 4);
+  h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
+  h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
+  return h1;
+}
+
+// blocks per rhs of the Gram-Schmidt dot kernel: four per SM, so that each thread sums many
+// elements before the (FP64) block reduction
+static int dots_blocks(size_t n) { return std::min(reduce_blocks(n), 4 * 152); }
+
+// h_i = (w, V_i), i <= j: partials per block, the last block finishes all j+1 sums.
+// Pass 0 also sums (w, w) and decides whether the second pass runs (selective reorthogonalisation,
+// the criterion of Daniel, Gragg, Kaufman and Stewart, 1976, with eta = 1/sqrt(2)): the projected
+// norm ||w - V h||^2 = (w, w) - sum h_i^2 (V orthonormal); when more than half of (w, w) remains,
+// little cancellation took place, the estimate is accurate and one pass leaves w orthogonal to
+// working precision; otherwise (or for a non-finite estimate) the second pass runs as in CGS2.
+// shifted: w = C Z_j - V_j, so the Hessenberg entry h_jj is the dot plus one.
 __global__ void __launch_bounds__(256) gm_dots_kernel(const double *__restrict__ w, const double *__restrict__ V,
-                                                      int j, size_t n, size_t vstride, const KrylovScalars *sc,
-                                                      GmresDev g, Reduce red, int pass) {
+                                                      int j, size_t n, size_t vstride, KrylovScalars *sc,
+                                                      GmresDev g, Reduce red, int pass, int shifted) {
   const int rhs = blockIdx.y;
   if (sc[rhs].state != ST_RUN) return;
+  if (pass == 1 && sc[rhs].reorth == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // 8 warps
   const size_t off = (size_t)rhs * n;
-  __shared__ double sh[32 * 8];
+  __shared__ double sh[9 * 8];
+  __shared__ double tot[72];
   __shared__ bool is_last;
   double *part = red.part + (size_t)rhs * red.rstride;
   // eight basis vectors per sweep: w is read once per eight dots instead of once per dot (w does
-  // not stay in L2 across a batch of right-hand sides); each dot keeps its own summation order
+  // not stay in L2 across a batch of right-hand sides); each dot keeps its own summation order.
+  // The first sweep of pass 0 also sums (w, w), stored as value j + 1.
   for (int i0 = 0; i0 <= j; i0 += 8) {
     const int cnt = min(8, j + 1 - i0);
-    double acc[8];
+    const bool ww = pass == 0 && i0 == 0;
+    double acc[8], aw = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -277,10 +318,24 @@ __global__ void __launch_bounds__(256) gm_dots_kernel(const double *__restrict__
 #pragma unroll
       for (int q = 0; q < 8; ++q)
         if (q < cnt) acc[q] = fma(we, V[(size_t)(i0 + q) * vstride + off + e], acc[q]);
+      if (ww) aw = fma(we, we, aw);
     }
-    block_sum<8>(acc, sh);
-    if (threadIdx.x == 0)
-      for (int q = 0; q < cnt; ++q) part[(size_t)(i0 + q) * red.nblk + blockIdx.x] = acc[q];
+    const double sv = warp_sum8_scatter(acc);
+    if ((lane & 3) == 0) sh[(lane >> 2) * 8 + warp] = sv;
+    if (ww) {
+      aw = warp_sum(aw);
+      if (lane == 0) sh[64 + warp] = aw;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+      const int q = threadIdx.x;
+      if (q < cnt || (q == 8 && ww)) {
+        double t = 0.0;
+        for (int u = 0; u < 8; ++u) t += sh[q * 8 + u];
+        part[(size_t)(q < 8 ? i0 + q : j + 1) * red.nblk + blockIdx.x] = t;
+      }
+    }
+    __syncthreads();  // sh is reused by the next sweep
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -290,28 +345,41 @@ __global__ void __launch_bounds__(256) gm_dots_kernel(const double *__restrict__
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int k = g.k;
-  double *hc = g.hcol + (size_t)rhs * (k + 1);
-  double *tmp = g.y + (size_t)rhs * k;  // this pass's coefficients
-  for (int i = 0; i <= j; ++i) {
-    double acc = 0.0;
-    for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) acc += __ldcg(part + (size_t)i * red.nblk + bb);
-    double v1[1] = {acc};
-    block_sum<1>(v1, sh);
-    if (threadIdx.x == 0) {
-      tmp[i] = v1[0];
-      hc[i] = pass == 0 ? v1[0] : hc[i] + v1[0];
-    }
-    __syncthreads();
+  // the last block: warp v sums value v (then v + 8, ...) over the blocks, lanes strided
+  const int nsum = pass == 0 ? j + 2 : j + 1;
+  for (int v = warp; v < nsum; v += 8) {
+    double a = 0.0;
+    for (int bb = lane; bb < (int)gridDim.x; bb += 32) a += __ldcg(part + (size_t)v * red.nblk + bb);
+    a = warp_sum(a);
+    if (lane == 0) tot[v] = a;
   }
-  if (threadIdx.x == 0) red.count[rhs] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int k = g.k;
+    double *hc = g.hcol + (size_t)rhs * (k + 1);
+    double *tmp = g.y + (size_t)rhs * k;  // this pass's coefficients
+    double hsum = 0.0;
+    for (int i = 0; i <= j; ++i) {
+      const double h = tot[i];
+      tmp[i] = h;
+      hc[i] = pass == 0 ? (shifted && i == j ? h + 1.0 : h) : hc[i] + h;
+      hsum = fma(h, h, hsum);
+    }
+    if (pass == 0) {
+      const double wnorm2 = tot[j + 1], rest = wnorm2 - hsum;
+      sc[rhs].reorth = (rest > 0.5 * wnorm2 && isfinite(rest)) ? 0 : 1;
+    }
+    red.count[rhs] = 0u;
+  }
 }
 
 // w -= sum_i tmp_i V_i
 __global__ void __launch_bounds__(256) gm_axpy_kernel(double *__restrict__ w, const double *__restrict__ V, int j,
-                                                      size_t n, size_t vstride, const KrylovScalars *sc, GmresDev g) {
+                                                      size_t n, size_t vstride, const KrylovScalars *sc, GmresDev g,
+                                                      int pass) {
   const int rhs = blockIdx.y;
   if (sc[rhs].state != ST_RUN) return;
+  if (pass == 1 && sc[rhs].reorth == 0) return;
   const size_t off = (size_t)rhs * n;
   const double *tmp = g.y + (size_t)rhs * g.k;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -321,14 +389,15 @@ __global__ void __launch_bounds__(256) gm_axpy_kernel(double *__restrict__ w, co
   }
 }
 
-void gm_orthogonalize(double *w, const double *V, int j, size_t n, int nrhs, size_t vstride, const KrylovScalars *sc,
-                      GmresDev &g, const Reduce &red, int pass, cudaStream_t s) {
+void gm_orthogonalize(double *w, const double *V, int j, size_t n, int nrhs, size_t vstride, KrylovScalars *sc,
+                      GmresDev &g, const Reduce &red, int pass, bool shifted, cudaStream_t s) {
   ProfScope prof(KC_GMRES, s);
-  dim3 grid(reduce_blocks(n), nrhs);
-  gm_dots_kernel<<<grid, 256, 0, s>>>(w, V, j, n, vstride, sc, g, red, pass);
+  if (j + 2 > 72) throw Error(LAG_EINVAL, "GMRES restart length above 70");
+  dim3 gd(dots_blocks(n), nrhs), grid(reduce_blocks(n), nrhs);
+  gm_dots_kernel<<<gd, 256, 0, s>>>(w, V, j, n, vstride, sc, g, red, pass, shifted ? 1 : 0);
   count_launch();
   LAG_LAUNCH_CHECK();
-  gm_axpy_kernel<<<grid, 256, 0, s>>>(w, V, j, n, vstride, sc, g);
+  gm_axpy_kernel<<<grid, 256, 0, s>>>(w, V, j, n, vstride, sc, g, pass);
   count_launch();
   LAG_LAUNCH_CHECK();
 }

@@ -1,89 +1,136 @@
 // Axisymmetric elastic operator (Sec. 2.2 Eqs. 10-12 in cylindrical coordinates (r, z)), the
-// gradient of a discrete strain energy, so that C is symmetric and the traction-free surface is the
+// Hessian of a discrete strain energy, so that C is symmetric and the traction-free surface is the
 // energy's natural condition.  Kernel layout: rows = radii i (nr), row length = depth nodes k (nzc);
 // fields [rhs][comp][nr][nzc], comp 0 = Q (u_r), comp 1 = U (u_z).  With r_i = (i + 1/2) hr and
-// rbar_i = (i + 1) hr (the face between radii i and i + 1):
+// rbar_i = (i + 1) hr (the face between radii i and i + 1), the energy per unit area is
 //   r-faces (i+1/2, k), weight rbar: (l+2m) e_rr^2 + m U_r^2 + 2 l e_rr <e_tt>,
 //   z-faces (i, k+1/2), weight r:    (l+2m) e_zz^2 + m Q_z^2 + 2 l e_zz <e_tt>,
 //   nodes, weight r:                 (l+2m) e_tt^2 (e_tt = Q / r),
 //   corners (i+1/2, k+1/2), weight rbar: 2 l <e_rr> <e_zz> + 2 m <Q_z> <U_r>,
-// with <.> the mean of the two neighbouring values, e_rr = dQ/dr and U_r across r-faces, e_zz = dU/dz
-// and Q_z across z-faces; Q = U = 0 on the ghost radius nr; no faces on the axis (rbar = 0), at
-// z = 0 or at the bottom.  Each thread forms the two components of one node from the quadrature
-// points around it (2 r-faces, 2 z-faces, 4 corners, the node), plus the mass r rho h^2/4.
+// (one half in front of the sum), <.> the mean of the two neighbouring values, e_rr = dQ/dr and U_r
+// across r-faces, e_zz = dU/dz and Q_z across z-faces; Q = U = 0 on the ghost radius nr; no faces on
+// the axis (rbar = 0), at z = 0 or at the bottom; face coefficients are node means (the ghost radius
+// repeats the last node), corner coefficients means of the two r-face means.
+//
+// The energy is quadratic, so C is a fixed stencil: at the medium's creation one thread per node
+// differentiates the energy terms around its node twice and stores the node's row of C,
+//   Q-Q: diagonal dq, r-neighbour wqr (node i with i + 1), z-neighbour wqz (k with k + 1),
+//   U-U: du, wur, wuz,
+//   Q-U: x[9], the weights of U at (i + di, k + dk), di, dk in {-1, 0, 1} (index 3 (di+1) + dk+1),
+// the mass r rho h^2/4 in both diagonals.  The U-Q block is the transpose (C is symmetric): the
+// weight of Q(i + di, k + dk) in row U(i, k) is x[3 (1-di) + 1-dk] of node (i + di, k + dk).  The
+// apply is then 28 FP64 multiply-adds per node, the least the stencil's 28 couplings allow (FP64
+// throughput, not HBM, bounds this kernel on this part: about two FP64 FMAs per clock per SM).
 #include "internal.h"
 
 namespace lag {
 
-// coef layout (each [nr][nzc]): p_r, m_r, l_r | p_z, m_z, l_z | p_n | l_c, m_c
-struct CylElasticCoef {
-  const double *p_r, *m_r, *l_r, *p_z, *m_z, *l_z, *p_n, *l_c, *m_c;
-};
+// coef layout (each [nr][nzc]): dq, du, wqr, wur, wqz, wuz, x0..x8
+enum { CE_DQ = 0, CE_DU, CE_WQR, CE_WUR, CE_WQZ, CE_WUZ, CE_X0, CE_NARRAYS = CE_X0 + 9 };
 
-static CylElasticCoef cyl_elastic_coef(const lag_medium &m) {
-  const size_t n = (size_t)m.grid.nx * m.grid.nz;
-  const double *b = m.coef.as<double>();
-  CylElasticCoef c;
-  c.p_r = b;
-  c.m_r = b + n;
-  c.l_r = b + 2 * n;
-  c.p_z = b + 3 * n;
-  c.m_z = b + 4 * n;
-  c.l_z = b + 5 * n;
-  c.p_n = b + 6 * n;
-  c.l_c = b + 7 * n;
-  c.m_c = b + 8 * n;
-  return c;
-}
-
-// face / corner means of the nodal lambda, mu (the ghost radius takes the last node's values)
-__global__ void cyl_elastic_coef_kernel(const double *__restrict__ vp, const double *__restrict__ vs,
-                                        const double *__restrict__ rho, int nzc, int nr, double hr, double h2,
-                                        double *out, double *rh2, double *p2m, double *mu_n) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (k >= nzc || i >= nr) return;
+// one node's row of C from the energy terms around it (Hessian entries, see the file header)
+__global__ void cyl_elastic_stencil_kernel(const double *__restrict__ vp, const double *__restrict__ vs,
+                                           const double *__restrict__ rho, int nzc, int nr, double hr, double hz,
+                                           double h2, double *out, double *rh2, double *p2m, double *mu_n) {
   const size_t n = (size_t)nr * nzc;
-  auto LM = [&](int ii, int kk, double &l, double &m) {
-    ii = min(ii, nr - 1);
-    const size_t o = (size_t)ii * nzc + kk;
-    const double r = rho[o], a = vp[o], b = vs[o];
-    m = r * b * b;
-    l = r * (a * a - 2.0 * b * b);
-  };
-  double l0, m0, l1, m1;
-  LM(i, k, l0, m0);
-  LM(i + 1, k, l1, m1);  // the ghost radius repeats the last node
-  const size_t o = (size_t)i * nzc + k;
-  const double lr = 0.5 * (l0 + l1), mr = 0.5 * (m0 + m1);
-  out[o] = lr + 2.0 * mr;           // p_r
-  out[n + o] = mr;                  // m_r
-  out[2 * n + o] = lr;              // l_r
-  out[6 * n + o] = l0 + 2.0 * m0;   // p_n
-  if (k + 1 < nzc) {
-    double l2, m2, l3, m3;
-    LM(i, k + 1, l2, m2);
-    LM(i + 1, k + 1, l3, m3);
-    const double lz = 0.5 * (l0 + l2), mz = 0.5 * (m0 + m2);
-    out[3 * n + o] = lz + 2.0 * mz;                         // p_z
-    out[4 * n + o] = mz;                                    // m_z
-    out[5 * n + o] = lz;                                    // l_z
-    out[7 * n + o] = 0.5 * (lr + 0.5 * (l2 + l3));          // l_c: mean of the two r-face means
-    out[8 * n + o] = 0.5 * (mr + 0.5 * (m2 + m3));          // m_c
-  } else {
-    out[3 * n + o] = out[4 * n + o] = out[5 * n + o] = out[7 * n + o] = out[8 * n + o] = 0.0;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = (int)(t / nzc), k = (int)(t % nzc);
+  // lambda, mu, l+2m on the 3 x 3 neighbourhood (the ghost radius repeats the last node; entries
+  // outside the grid are never used)
+  double Lm[3][3], Mu[3][3], Pn[3][3];
+  for (int di = -1; di <= 1; ++di)
+    for (int dk = -1; dk <= 1; ++dk) {
+      const int ii = min(i + di, nr - 1), kk = k + dk;
+      double l = 0.0, m = 0.0;
+      if (ii >= 0 && kk >= 0 && kk < nzc) {
+        const size_t o = (size_t)ii * nzc + kk;
+        const double r = rho[o], a = vp[o], b = vs[o];
+        m = r * b * b;
+        l = r * (a * a - 2.0 * b * b);
+      }
+      Lm[di + 1][dk + 1] = l;
+      Mu[di + 1][dk + 1] = m;
+      Pn[di + 1][dk + 1] = l + 2.0 * m;
+    }
+  // face and corner means; di, dk are offsets of the face's / corner's lower node from (i, k)
+  auto rf = [&](const double (&f)[3][3], int di, int dk) { return 0.5 * (f[di + 1][dk + 1] + f[di + 2][dk + 1]); };
+  auto zf = [&](const double (&f)[3][3], int dk) { return 0.5 * (f[1][dk + 1] + f[1][dk + 2]); };
+  auto cf = [&](const double (&f)[3][3], int di, int dk) { return 0.5 * (rf(f, di, dk) + rf(f, di, dk + 1)); };
+  const double a = 1.0 / hr, c = 1.0 / hz;
+  const double r_i = (i + 0.5) * hr, b0 = 0.5 / r_i;
+  double dq = 0.0, du = 0.0, wqr = 0.0, wur = 0.0, wqz = 0.0, wuz = 0.0, x[9];
+  for (int j = 0; j < 9; ++j) x[j] = 0.0;
+  {  // r-face i: the node is its inner side
+    const double p = rf(Pn, 0, 0), l = rf(Lm, 0, 0), m = rf(Mu, 0, 0), rb = (i + 1.0) * hr;
+    dq += rb * (p * a * a - 2.0 * l * a * b0);
+    du += rb * m * a * a;
+    if (i + 1 < nr) {
+      const double b1 = 0.5 / ((i + 1.5) * hr);
+      wqr = rb * (-p * a * a + l * a * (b0 - b1));
+      wur = -rb * m * a * a;
+    }
   }
-  const double r_i = (i + 0.5) * hr;
+  if (i >= 1) {  // r-face i-1: the node is its outer side
+    const double p = rf(Pn, -1, 0), l = rf(Lm, -1, 0), m = rf(Mu, -1, 0), rb = i * hr;
+    dq += rb * (p * a * a + 2.0 * l * a * b0);
+    du += rb * m * a * a;
+  }
+  if (k + 1 < nzc) {  // z-face k: the node is its upper side
+    const double p = zf(Pn, 0), l = zf(Lm, 0), m = zf(Mu, 0);
+    dq += r_i * m * c * c;
+    du += r_i * p * c * c;
+    wqz = -r_i * m * c * c;
+    wuz = -r_i * p * c * c;
+    x[4] -= 0.5 * l * c;   // U(i, k)
+    x[5] += 0.5 * l * c;   // U(i, k+1)
+  }
+  if (k >= 1) {  // z-face k-1: the node is its lower side
+    const double p = zf(Pn, -1), l = zf(Lm, -1), m = zf(Mu, -1);
+    dq += r_i * m * c * c;
+    du += r_i * p * c * c;
+    x[3] -= 0.5 * l * c;   // U(i, k-1)
+    x[4] += 0.5 * l * c;   // U(i, k)
+  }
+  dq += Pn[1][1] / r_i;  // node term (l+2m) e_tt^2
+  const size_t o = (size_t)i * nzc + k;
+  const double mass = 0.25 * r_i * rho[o] * h2;
+  dq += mass;
+  du += mass;
+  // corners (ci + 1/2, ck + 1/2) around the node: l <e_rr><e_zz> + m <Q_z><U_r> with weight rbar
+  for (int ci = i - 1; ci <= i; ++ci) {
+    if (ci < 0) continue;
+    for (int ck = k - 1; ck <= k; ++ck) {
+      if (ck < 0 || ck + 1 >= nzc) continue;
+      const double lc = cf(Lm, ci - i, ck - k), mc = cf(Mu, ci - i, ck - k);
+      const double sc = (ci + 1.0) * hr * a * c * 0.25;
+      const double srA = (ci == i - 1) ? 1.0 : -1.0, szA = (ck == k - 1) ? 1.0 : -1.0;
+      for (int bi = ci; bi <= ci + 1; ++bi) {
+        if (bi >= nr) continue;  // ghost radius
+        for (int bk = ck; bk <= ck + 1; ++bk) {
+          const double srB = (bi == ci + 1) ? 1.0 : -1.0, szB = (bk == ck + 1) ? 1.0 : -1.0;
+          x[3 * (bi - i + 1) + (bk - k + 1)] += sc * (lc * srA * szB + mc * szA * srB);
+        }
+      }
+    }
+  }
+  out[CE_DQ * n + o] = dq;
+  out[CE_DU * n + o] = du;
+  out[CE_WQR * n + o] = wqr;
+  out[CE_WUR * n + o] = wur;
+  out[CE_WQZ * n + o] = wqz;
+  out[CE_WUZ * n + o] = wuz;
+  for (int j = 0; j < 9; ++j) out[(CE_X0 + j) * n + o] = x[j];
   rh2[o] = r_i * rho[o] * h2;
-  p2m[o] = l0 + 2.0 * m0;
-  mu_n[o] = m0;
+  p2m[o] = Pn[1][1];
+  mu_n[o] = Mu[1][1];
 }
 
 // mode 0: every rhs (or those running when sc is given); mode 2: rhs running or ST_MET
 __global__ void __launch_bounds__(256) cyl_elastic_apply_kernel(const double *__restrict__ X, double *__restrict__ Y,
-                                                                int nzc, int nr, double hr, double hz,
-                                                                CylElasticCoef c, const double *__restrict__ rh2,
-                                                                const KrylovScalars *__restrict__ sc, int mode) {
+                                                                int nzc, int nr, const double *__restrict__ cf,
+                                                                const KrylovScalars *__restrict__ sc, int mode,
+                                                                const double *__restrict__ sub) {
   const int b = blockIdx.z;
   if (sc != nullptr) {
     const int st = sc[b].state;
@@ -92,92 +139,58 @@ __global__ void __launch_bounds__(256) cyl_elastic_apply_kernel(const double *__
   const int k = blockIdx.x * 32 + (threadIdx.x & 31);
   const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (k >= nzc || i >= nr) return;
-  const size_t plane = (size_t)nr * nzc;
-  const double *Qf = X + (size_t)b * 2 * plane, *Uf = Qf + plane;
-  double *yq = Y + (size_t)b * 2 * plane, *yu = yq + plane;
-  auto Q = [&](int ii, int kk) -> double { return (ii < nr && kk >= 0 && kk < nzc) ? Qf[(size_t)ii * nzc + kk] : 0.0; };
-  auto U = [&](int ii, int kk) -> double { return (ii < nr && kk >= 0 && kk < nzc) ? Uf[(size_t)ii * nzc + kk] : 0.0; };
-  auto rr = [&](int ii) { return (ii + 0.5) * hr; };
-  const double ihr = 1.0 / hr, ihz = 1.0 / hz;
-  // r-face (ii+1/2, k): s_rr, s_tt, s_ur (0 outside 0 <= ii < nr)
-  auto rface = [&](int ii, double &srr, double &stt, double &sur) {
-    srr = stt = sur = 0.0;
-    if (ii < 0 || ii >= nr) return;
-    const size_t o = (size_t)ii * nzc + k;
-    const double qa = Q(ii, k), qb = Q(ii + 1, k), ua = U(ii, k), ub = U(ii + 1, k);
-    const double err = (qb - qa) * ihr;
-    const double ett = 0.5 * (qa / rr(ii) + qb / rr(ii + 1));
-    const double rb = (ii + 1.0) * hr;
-    srr = rb * (c.p_r[o] * err + c.l_r[o] * ett);
-    stt = rb * c.l_r[o] * err;
-    sur = rb * c.m_r[o] * (ub - ua) * ihr;
-  };
-  // z-face (i, kk+1/2): s_zz, s_tz, s_qz (0 outside 0 <= kk < nzc - 1)
-  auto zface = [&](int kk, double &szz, double &stz, double &sqz) {
-    szz = stz = sqz = 0.0;
-    if (kk < 0 || kk + 1 >= nzc) return;
-    const size_t o = (size_t)i * nzc + kk;
-    const double qa = Q(i, kk), qb = Q(i, kk + 1), ua = U(i, kk), ub = U(i, kk + 1);
-    const double ezz = (ub - ua) * ihz;
-    const double ett = 0.5 * (qa + qb) / rr(i);
-    const double r = rr(i);
-    szz = r * (c.p_z[o] * ezz + c.l_z[o] * ett);
-    stz = r * c.l_z[o] * ezz;
-    sqz = r * c.m_z[o] * (qb - qa) * ihz;
-  };
-  // corner (ii+1/2, kk+1/2): X = rbar l <e_zz>, X2 = rbar l <e_rr>, Y = rbar m <U_r>, Y2 = rbar m <Q_z>
-  auto corner = [&](int ii, int kk, double &x1, double &x2, double &y1, double &y2) {
-    x1 = x2 = y1 = y2 = 0.0;
-    if (ii < 0 || ii >= nr || kk < 0 || kk + 1 >= nzc) return;
-    const size_t o = (size_t)ii * nzc + kk;
-    const double q00 = Q(ii, kk), q10 = Q(ii + 1, kk), q01 = Q(ii, kk + 1), q11 = Q(ii + 1, kk + 1);
-    const double u00 = U(ii, kk), u10 = U(ii + 1, kk), u01 = U(ii, kk + 1), u11 = U(ii + 1, kk + 1);
-    const double err = 0.5 * ((q10 - q00) + (q11 - q01)) * ihr;
-    const double ezz = 0.5 * ((u01 - u00) + (u11 - u10)) * ihz;
-    const double qz = 0.5 * ((q01 - q00) + (q11 - q10)) * ihz;
-    const double ur = 0.5 * ((u10 - u00) + (u11 - u01)) * ihr;
-    const double rb = (ii + 1.0) * hr;
-    const double lc = rb * c.l_c[o], mc = rb * c.m_c[o];
-    x1 = lc * ezz;
-    x2 = lc * err;
-    y1 = mc * ur;
-    y2 = mc * qz;
-  };
-  const double ri = rr(i);
-  double srr0, stt0, sur0, srr1, stt1, sur1;
-  rface(i - 1, srr0, stt0, sur0);
-  rface(i, srr1, stt1, sur1);
-  double szz0, stz0, sqz0, szz1, stz1, sqz1;
-  zface(k - 1, szz0, stz0, sqz0);
-  zface(k, szz1, stz1, sqz1);
-  // corners around the node: (i-1, k-1), (i-1, k), (i, k-1), (i, k)
-  double xa[4], xb[4], ya[4], yb[4];
-  corner(i - 1, k - 1, xa[0], xb[0], ya[0], yb[0]);
-  corner(i - 1, k, xa[1], xb[1], ya[1], yb[1]);
-  corner(i, k - 1, xa[2], xb[2], ya[2], yb[2]);
-  corner(i, k, xa[3], xb[3], ya[3], yb[3]);
+  const size_t n = (size_t)nr * nzc;
   const size_t o = (size_t)i * nzc + k;
-  const double q = Qf[o], u = Uf[o];
-  const double w = 0.25 * rh2[o];
-  double gq = (srr0 - srr1) * ihr + 0.5 * (stt1 + stt0) / ri;
-  gq += 0.5 * (stz0 + stz1) / ri + (sqz0 - sqz1) * ihz;
-  gq += c.p_n[o] * q / ri;
-  // dr^T(avz^T(X)) and dz^T(avr^T(Y))
-  gq += (0.5 * (xa[0] + xa[1]) - 0.5 * (xa[2] + xa[3])) * ihr;
-  gq += (0.5 * (ya[2] + ya[0]) - 0.5 * (ya[3] + ya[1])) * ihz;
-  double gu = (sur0 - sur1) * ihr + (szz0 - szz1) * ihz;
-  // dz^T(avr^T(X2)) and dr^T(avz^T(Y2))
-  gu += (0.5 * (xb[2] + xb[0]) - 0.5 * (xb[3] + xb[1])) * ihz;
-  gu += (0.5 * (yb[0] + yb[1]) - 0.5 * (yb[2] + yb[3])) * ihr;
-  yq[o] = gq + w * q;
-  yu[o] = gu + w * u;
+  const double *Qf = X + (size_t)b * 2 * n, *Uf = Qf + n;
+  const bool im = i >= 1, ip = i + 1 < nr, km = k >= 1, kp = k + 1 < nzc;
+  const int s = nzc;
+  double gq = __ldg(cf + CE_DQ * n + o) * __ldg(Qf + o);
+  double gu = __ldg(cf + CE_DU * n + o) * __ldg(Uf + o);
+  if (ip) {
+    gq = fma(__ldg(cf + CE_WQR * n + o), __ldg(Qf + o + s), gq);
+    gu = fma(__ldg(cf + CE_WUR * n + o), __ldg(Uf + o + s), gu);
+  }
+  if (im) {
+    gq = fma(__ldg(cf + CE_WQR * n + o - s), __ldg(Qf + o - s), gq);
+    gu = fma(__ldg(cf + CE_WUR * n + o - s), __ldg(Uf + o - s), gu);
+  }
+  if (kp) {
+    gq = fma(__ldg(cf + CE_WQZ * n + o), __ldg(Qf + o + 1), gq);
+    gu = fma(__ldg(cf + CE_WUZ * n + o), __ldg(Uf + o + 1), gu);
+  }
+  if (km) {
+    gq = fma(__ldg(cf + CE_WQZ * n + o - 1), __ldg(Qf + o - 1), gq);
+    gu = fma(__ldg(cf + CE_WUZ * n + o - 1), __ldg(Uf + o - 1), gu);
+  }
+  // Q-U block (row Q(i, k): x of this node) and its transpose (row U(i, k): x of the neighbour)
+#pragma unroll
+  for (int di = -1; di <= 1; ++di) {
+    const bool vi = di < 0 ? im : (di > 0 ? ip : true);
+#pragma unroll
+    for (int dk = -1; dk <= 1; ++dk) {
+      const bool vk = dk < 0 ? km : (dk > 0 ? kp : true);
+      if (vi && vk) {
+        const long long off = (long long)di * s + dk;
+        gq = fma(__ldg(cf + (CE_X0 + 3 * (di + 1) + dk + 1) * n + o), __ldg(Uf + o + off), gq);
+        gu = fma(__ldg(cf + (CE_X0 + 3 * (1 - di) + 1 - dk) * n + o + off), __ldg(Qf + o + off), gu);
+      }
+    }
+  }
+  double *yq = Y + (size_t)b * 2 * n;
+  if (sub != nullptr) {
+    const double *sq = sub + (size_t)b * 2 * n;
+    gq -= sq[o];
+    gu -= sq[n + o];
+  }
+  yq[o] = gq;
+  yq[n + o] = gu;
 }
 
 void medium_build_elastic_cylindrical(lag_medium &m, const double *vp_host, const double *vs_host,
                                       const double *rho_host, cudaStream_t s) {
   const int nzc = m.grid.nx, nr = m.grid.nz;  // kernel layout: rows = radii
   const size_t n = (size_t)nzc * nr;
-  m.ncoef = 9 * n;
+  m.ncoef = CE_NARRAYS * n;
   m.coef.alloc(m.ctx, m.ncoef * sizeof(double));
   m.rho_h2.alloc(m.ctx, n * sizeof(double));
   DevBuf tmp;
@@ -186,9 +199,9 @@ void medium_build_elastic_cylindrical(lag_medium &m, const double *vp_host, cons
   LAG_CUDA_CHECK(cudaMemcpyAsync(dvp, vp_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
   LAG_CUDA_CHECK(cudaMemcpyAsync(dvs, vs_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
   LAG_CUDA_CHECK(cudaMemcpyAsync(drho, rho_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
-  dim3 g((nzc + 127) / 128, nr);
-  cyl_elastic_coef_kernel<<<g, 128, 0, s>>>(dvp, dvs, drho, nzc, nr, m.grid.dz, m.h * m.h, m.coef.as<double>(),
-                                            m.rho_h2.as<double>(), p2m, mun);
+  if ((nr + 7) / 8 > 65535) throw Error(LAG_EINVAL, "cylindrical elastic grid: at most 524280 radii");
+  cyl_elastic_stencil_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(dvp, dvs, drho, nzc, nr, m.grid.dz, m.grid.dx,
+                                               m.h * m.h, m.coef.as<double>(), m.rho_h2.as<double>(), p2m, mun);
   count_launch();
   LAG_LAUNCH_CHECK();
   // whole-medium midranges (l+2m)~, m~, rho~ (footnote to Eq. 21; Eq. 22 puts the r weights in the plan)
@@ -204,12 +217,11 @@ void medium_build_elastic_cylindrical(lag_medium &m, const double *vp_host, cons
 }
 
 void elastic_cyl_apply(const lag_medium &m, const double *p, double *q, int nrhs, const KrylovScalars *sc, int mode,
-                       cudaStream_t s) {
+                       cudaStream_t s, const double *sub) {
   const int nzc = m.grid.nx, nr = m.grid.nz;
   dim3 g((nzc + 31) / 32, (nr + 7) / 8, nrhs);
   ProfScope prof(KC_STENCIL_E, s);
-  cyl_elastic_apply_kernel<<<g, 256, 0, s>>>(p, q, nzc, nr, m.grid.dz, m.grid.dx, cyl_elastic_coef(m),
-                                             m.rho_h2.as<double>(), sc, mode);
+  cyl_elastic_apply_kernel<<<g, 256, 0, s>>>(p, q, nzc, nr, m.coef.as<double>(), sc, mode, sub);
   count_launch();
   LAG_LAUNCH_CHECK();
 }

@@ -331,9 +331,13 @@ void KrylovWork::gmres_step() {
   const size_t vs = n * (size_t)nrhs;
   Reduce rd = red.get();
   precond(V + (size_t)j * vs, Z + (size_t)j * vs);               // Z_j = K^{-1} V_j
-  m->apply(Z + (size_t)j * vs, w, nrhs, sc(), nullptr, 0, stream);  // w = C Z_j
-  gm_orthogonalize(w, V, j, n, nrhs, vs, sc(), gdev, rd, 0, stream);
-  gm_orthogonalize(w, V, j, n, nrhs, vs, sc(), gdev, rd, 1, stream);
+  // shifted Arnoldi step: w = C Z_j - V_j spans the same Krylov space (C K^{-1} - I has the
+  // Hessenberg matrix H - I), but for a good preconditioner C K^{-1} V_j lies close to V_j and the
+  // shift removes that component before the projections, so the first Gram-Schmidt pass cancels
+  // less and the second one (selective) is often skipped
+  m->apply(Z + (size_t)j * vs, w, nrhs, sc(), nullptr, 0, stream, V + (size_t)j * vs);
+  gm_orthogonalize(w, V, j, n, nrhs, vs, sc(), gdev, rd, 0, true, stream);
+  gm_orthogonalize(w, V, j, n, nrhs, vs, sc(), gdev, rd, 1, true, stream);
   gm_normalize(w, V + (size_t)(j + 1) * vs, j, n, nrhs, sc(), gdev, rd, s.max_iter, stream);
   gj = j + 1;
 }

@@ -97,13 +97,16 @@ def random_layered(nx=2048, nz=1024, hx=5.0, n_harm=512, seed=SEED_BASE + 2, f0=
                 t_out=np.linspace(0.002, 1.0, 500))
 
 
-def cylindrical(nr=2048, nz=2048, h=None, n_harm=3000, layered=False, seed=SEED_BASE + 5, f0=30.0):
+def cylindrical(nr=2048, nz=2048, h=None, n_harm=3000, layered=False, seed=SEED_BASE + 5, f0=30.0,
+                elastic=False):
     """The paper's axisymmetric acoustic experiment (Sec. 3.2): a point source on the axis at the
     free surface, the Gaussian-modulated sine of Eq. 23 (f0 = 30 Hz, t0 = 0.2 s, gamma = 4),
     alpha = 9, Laguerre h = 400, mesh step lambda/40, receivers on the surface row.  Homogeneous
     (c = 2000 m/s, rho = 1000 kg/m^3) as in the paper, or a random layered medium (the layers
     along z, the generator of the Cartesian workload) for the iterative behaviour.  Fields are
-    [nr][nz] (depth fastest); sources / receivers are (radius index, depth index)."""
+    [nr][nz] (depth fastest); sources / receivers are (radius index, depth index).
+    elastic=True: the same model read as Vp with Vs = Vp / 1.73 (Sec. 2.2's axisymmetric elastic
+    problem; the source becomes a vertical force on the axis)."""
     c0 = 2000.0
     if h is None:
         h = c0 / f0 / 40.0
@@ -114,7 +117,9 @@ def cylindrical(nr=2048, nz=2048, h=None, n_harm=3000, layered=False, seed=SEED_
         c = np.full((nr, nz), c0)
     rho = gardner_density(c) if layered else np.full((nr, nz), 1000.0)
     rcv = [(i, 0) for i in range(0, nr, max(1, nr // 64))][:64]
-    return Shot(f"cylindrical_{'layered' if layered else 'homogeneous'}_{nr}x{nz}", nr, nz, h, h, c, rho, None,
+    vs = c / 1.73 if elastic else None
+    kind = ("elastic_" if elastic else "") + ("layered" if layered else "homogeneous")
+    return Shot(f"cylindrical_{kind}_{nr}x{nz}", nr, nz, h, h, c, rho, vs,
                 400.0, 9, n_harm, f0, 0.2, sources=[(0, 0)], receivers=rcv,
                 t_out=np.linspace(0.002, 1.0, 500))
 
