@@ -244,9 +244,9 @@ def gpu_arm(args, rank, world, local_rank):
     L.lag_precond_destroy(probe)
     fp64_equiv = (real * flops_launch) / (ms_dst / 1e3) / 1e12 if ms_dst > 0 else None
     if on_tc:
-        # exact-slice DST on the bf16 tensor cores: 45 bf16 slice products per float64 product;
-        # timed inside a long step -> the sustained bf16 peak
-        npair = L.lag_dst_f64_slice_products()
+        # exact-slice DST on the bf16 tensor cores: 36 bf16 slice products per float64 product at
+        # this length (45 above 2048); timed inside a long step -> the sustained bf16 peak
+        npair = L.lag_dst_f64_slice_products(s.nx)
         achieved = fp64_equiv * npair if fp64_equiv else None
         peak = peaks["bf16_tflops_sustained"]
         roofline = {"bound": "tensor",

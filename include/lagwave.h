@@ -203,8 +203,10 @@ int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int 
  * result carries float64 rounding only (relative error < 1e-14 per row in the tests).  The
  * environment variable LAGWAVE_DST_KERNEL=simt at plan creation selects the SIMT kernels. */
 int  lag_precond_uses_tensor_cores(const lag_precond *p);
-/* bf16 slice products the float64 tensor-core DST forms per float64 multiply-add (45) */
-int  lag_dst_f64_slice_products(void);
+/* bf16 slice products the float64 tensor-core DST of length n forms per float64 multiply-add:
+ * 36 (8 seven-bit slices) for ceil(n/2) <= 1024, 45 (9 six-bit slices) above; 0 where the
+ * exact-slice path does not apply (n < 16 or ceil(n/2) > 4224). */
+int  lag_dst_f64_slice_products(int n);
 /* Tensor-core DST of a mixed plan: number of bf16 products per K step (3: split hi*hi + hi*lo +
  * lo*hi, relative error ~1e-5; 2: hi*hi + lo*hi with S rounded to bf16, ~2e-3; 1: hi*hi, ~4e-3).
  * Default 3 (or the environment variable LAGWAVE_DST_PRODUCTS at plan creation).  The flexible

@@ -500,7 +500,10 @@ int lag_precond_info(const lag_precond *p, int *P, int *L, int *mt) {
   return LAG_OK;
 }
 
-int lag_dst_f64_slice_products(void) { return dst_oz_products(); }
+int lag_dst_f64_slice_products(int n) {
+  if (!dst_oz_supported(n)) return 0;
+  return dst_oz_products(n);
+}
 
 int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? ((p->use_tc || p->dst.oz) ? 1 : 0) : 0; }
 

@@ -134,6 +134,7 @@ struct DstPlan {
   uint8_t *oz_bi = nullptr;   // DCT-II inverse operands (kind 1): [2][9][n tile][k stage]
   size_t oz_slice_bytes = 0;
   int oz_eB = 0;              // |S| < 2^oz_eB
+  int oz_nb = 6, oz_ns = 9;   // exact slices: bits per slice, slices per operand
 };
 // tc_mode: 0 none, 1 split-bf16 operands (mixed path), 2 exact slices (float64 path); kind 0 = DST-I,
 // 1 = DCT-II (both fold alike; the DCT-II adds inverse operands, see k_dst.cu)
@@ -155,7 +156,7 @@ void dst_apply_f64_simt(const DstPlan &dp, const double *x, double *y, int rows,
                         const KrylovScalars *sc, cudaStream_t s);
 // exact-slice tensor-core float64 DST (dp.oz); scratch dp.tc_scratch of dst_oz_scratch_bytes
 bool dst_oz_supported(int n);
-int dst_oz_products();  // bf16 slice products per float64 product
+int dst_oz_products(int n);  // bf16 slice products per float64 product of a length-n transform
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows);
 // inverse (DCT-II plans only): gather the even / odd modes, GEMM with the inverse operands into
 // E / O sums (plan scratch), butterfly into y

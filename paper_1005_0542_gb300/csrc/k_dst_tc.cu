@@ -28,6 +28,9 @@
 
 #include "internal.h"
 
+#include <utility>
+#include <vector>
+
 namespace lag {
 
 namespace {
@@ -648,17 +651,25 @@ void spectrum_unpermute_widen(const float *in, double *out, int rows, int n, int
 // The float64 path's transform on the same tensor cores, without rounding anything beyond what a
 // float64 GEMM rounds (the Ozaki splitting idea: exact products of short slices, summed in float64).
 //   * Every folded input row is scaled by a power of two 2^-e_r with |row| < 2^e_r and cut into
-//     OZ_S slices of OZ_B bits of its fixed-point expansion: u = 2^e_r sum_i q_i 2^(-OZ_B i) up to
-//     a truncation below 2^(e_r - OZ_S OZ_B) (54 bits); the q_i are integers |q_i| < 2^OZ_B, exact
-//     in bf16.  S is sliced the same way with one scale 2^e_B.
-//   * A pair (i, j) gives G_ij = sum_k q_i p_j: integers of magnitude < 2^(2 OZ_B) K, exactly summed
-//     by the FP32 accumulator while the total stays below 2^24.  Pairs of the same weight i + j
-//     share one accumulator in groups of at most floor(2^24 / (63^2 K)) (4 at K = 1024).
-//   * Pairs with i + j <= OZ_S + 1 are kept (the dropped ones weigh < 2^-54 of the row scale), and
-//     the epilogue adds each group as y += 2^(e_r + e_B - OZ_B (i + j)) G in float64, largest weight
-//     first, straight into the float64 output (natural mode order, as the SIMT kernel writes it).
-constexpr int OZ_B = 6;   // bits per slice
-constexpr int OZ_S = 9;   // slices per operand
+//     NS slices of NB bits of its fixed-point expansion: u = 2^e_r sum_i q_i 2^(-NB i) up to a
+//     truncation below 2^(e_r - NS NB) (54 or 56 bits); the q_i are integers |q_i| < 2^NB, exact
+//     in bf16 (8-bit significand).  S is sliced the same way with one scale 2^e_B.
+//   * A pair (i, j) gives G_ij = sum_k q_i p_j: integers of magnitude < (2^NB - 1)^2 K, exactly
+//     summed by the FP32 accumulator while the total stays below 2^24.  Pairs of the same weight
+//     i + j share one accumulator in groups of at most floor(2^24 / ((2^NB - 1)^2 K)) (at most 4).
+//   * Pairs with i + j <= NS + 1 are kept (the dropped ones weigh < 2^-54 of the row scale), and
+//     the epilogue adds each group as y += 2^(e_r + e_B - 2 NB) G' in float64 (G' the pre-scaled
+//     group sum), straight into the float64 output (natural mode order, as the SIMT kernel writes
+//     it).  Groups are scheduled in an order that keeps the tensor pipe busy (see oz_schedule).
+//   * Slice width: 7 bits (8 slices, 36 pairs) while one pair's exact sum fits the FP32
+//     accumulator (127^2 K <= 2^24: K <= 1024), else 6 bits (9 slices, 45 pairs).  The GEMM streams
+//     one A and one B slice tile per pair and K step, so fewer pairs mean proportionally fewer
+//     operand bytes into each SM, the limit of this kernel.
+constexpr int OZ_SMAX = 9;  // slices per operand at most (storage bound)
+struct OzFmt {
+  int nb, ns;  // bits per slice, slices per operand
+};
+static OzFmt oz_format(int kpad) { return (127LL * 127LL * kpad <= (1LL << 24)) ? OzFmt{7, 8} : OzFmt{6, 9}; }
 constexpr int OZ_TN = 128;                 // output columns per tile
 constexpr int OZ_BT = OZ_TN * TK * 2;      // B stage tile, 16 KB
 constexpr int OZ_KT = 2;                   // 64-wide K tiles per pipeline stage
@@ -668,10 +679,13 @@ constexpr int OZ_NACC = 4;                 // tensor-memory accumulators of 128 
 constexpr int OZ_SMEM = OZ_NST * OZ_STAGE + 1024 + 256;
 constexpr int OZ_EXP_NAN = 0x7fffffff;     // row exponent marking a non-finite row
 // pairs of weight i + j >= tail share one accumulator with FP32 rounding: together they weigh
-// < 2^-(OZ_B (tail - 2)) of the leading products (2^-36 at tail = 8), so that rounding stays below
-// 2^-50 of the row scale, under the float64 rounding of the product itself; lighter weights are
-// exact.  tail = 8 up to K = 1024 and one weight later per doubling of K (the rounding grows with K).
-constexpr int OZ_TAIL = 8;
+// < 2^-(NB (tail - 2)) of the leading products (2^-36 at tail = 8 with 6-bit slices, 2^-42 with
+// 7-bit ones), so that the roundings of the K / 16 accumulating MMAs (directed, not random, in the
+// tensor cores' adder: they add up linearly) stay near 2^-50 of the row scale or below, under the
+// float64 rounding of the product itself; lighter weights are exact.  6-bit slices: tail = 8 up to
+// K = 1024 and one weight later per doubling of K (the rounding grows with K); 7-bit slices
+// (K <= 1024): tail = 8 as well (a tail from weight 7, 2^-35, measured 1.3e-14 relative row error at
+// K = 1024 against 1e-15 for a float64 GEMM).
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -683,8 +697,9 @@ __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint6
 }
 
 // float -> double for the group sums, with integer operations only (the FP64 pipe does the
-// accumulation): a sum is an integer of magnitude <= 2^24, i.e. zero or a normal float, whose double
-// has the same sign and significand and the exponent rebiased by 1023 - 127
+// accumulation): a sum is zero or a normal float (exact groups: integer multiples of 2^-(NB (w - 2))
+// below 2^24 of them; the tail: a rounded float32), whose double has the same sign and
+// significand and the exponent rebiased by 1023 - 127
 __device__ __forceinline__ double oz_exact_f2d(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t mag = u & 0x7fffffffu;
@@ -698,32 +713,37 @@ struct OzSched {
   int8_t gd[48];                               // weight i + j of each group
 };
 
-// |v| < 2^e: 54-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
+// |v| < 2^e: NBITS-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
+template <int NBITS>
 __device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
+  static_assert(NBITS >= 53 && NBITS <= 63, "fixed-point width");
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
   const int E = (int)(bits >> 52);
   const unsigned long long M = (bits & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
-  const int s = (E ? E : 1) - 1075 + 54 - e;  // |v| = M 2^((E ? E : 1) - 1075)
-  if (s >= 0) return M << s;                   // s <= 1 since |v| < 2^e
+  const int s = (E ? E : 1) - 1075 + NBITS - e;  // |v| = M 2^((E ? E : 1) - 1075)
+  if (s >= 0) return M << s;                      // s <= NBITS - 52 since |v| < 2^e
   return (s <= -64) ? 0ull : (M >> (-s));
 }
-// slice i (1-based) of a fixed-point value as bf16 bits, built with integer operations and stored
-// pre-scaled by 2^-(OZ_B (i - 1)): the integer 1 <= q < 2^OZ_B is 1.f x 2^p with p = 31 - clz(q),
-// exactly representable in bf16's 8-bit significand, and the scale only moves the exponent.  A
-// product of slices i and j then carries 2^-(OZ_B (i + j - 2)) already, so products of different
-// weights can share an accumulator.
+// slice i (1-based) of an NB*NS-bit fixed-point value as bf16 bits, built with integer operations
+// and stored pre-scaled by 2^-(NB (i - 1)): the integer 1 <= q < 2^NB is 1.f x 2^p with
+// p = 31 - clz(q), exactly representable in bf16's 8-bit significand (NB <= 8), and the scale only
+// moves the exponent.  A product of slices i and j then carries 2^-(NB (i + j - 2)) already, so
+// products of different weights can share an accumulator.
+template <int NB, int NS>
 __device__ __forceinline__ uint16_t oz_slice_bits(unsigned long long T, int i, bool neg) {
-  const uint32_t q = (uint32_t)(T >> (54 - OZ_B * i)) & ((1u << OZ_B) - 1u);
+  static_assert(NB <= 8, "bf16 holds 8 significant bits");
+  const uint32_t q = (uint32_t)(T >> (NB * NS - NB * i)) & ((1u << NB) - 1u);
   if (q == 0) return 0;
   const int pw = 31 - __clz(q);
   const uint32_t mant = (q << (7 - pw)) & 0x7fu;
-  return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127 - OZ_B * (i - 1)) << 7) | mant);
+  return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127 - NB * (i - 1)) << 7) | mant);
 }
 
 // B slices, once per plan: [mat 0, mat 1][slice][n tile][k stage][TN x TK].  Mat w is the row-major
 // matrix m_w [K_w][ld_w] (contraction index k, output column n < N_w); zero beyond it.  Forward
 // transforms: m0 = su (even output modes), m1 = sv (odd ones); DCT-II inverse: m0 = ie (even input
 // modes), m1 = io (odd ones), both with ceil(n/2) output columns.
+template <int NB, int NS>
 __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, const double *m1, int k1n, int n1n,
                                  int ld1, int nks, int nnt, int eB, uint8_t *out, size_t slice_bytes) {
   const int which = blockIdx.z;
@@ -733,12 +753,12 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
   double v = 0.0;
   if (which == 0) { if (n < n0n && k < k0n) v = m0[(size_t)k * ld0 + n]; }
   else if (n < n1n && k < k1n) v = m1[(size_t)k * ld1 + n];
-  const unsigned long long T = oz_fixed(v, eB);
+  const unsigned long long T = oz_fixed<NB * NS>(v, eB);
   const size_t tile = (size_t)(n / OZ_TN) * nks + (k / TK);
   const uint32_t off = swz(n % OZ_TN, k % TK);
-  for (int i = 1; i <= OZ_S; ++i) {
-    uint8_t *base = out + ((size_t)which * OZ_S + (i - 1)) * slice_bytes + tile * OZ_BT;
-    *reinterpret_cast<uint16_t *>(base + off) = oz_slice_bits(T, i, v < 0.0);
+  for (int i = 1; i <= NS; ++i) {
+    uint8_t *base = out + ((size_t)which * NS + (i - 1)) * slice_bytes + tile * OZ_BT;
+    *reinterpret_cast<uint16_t *>(base + off) = oz_slice_bits<NB, NS>(T, i, v < 0.0);
   }
 }
 
@@ -751,6 +771,7 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
 constexpr int OZ_PACK_THREADS = 256;
 constexpr int OZ_PACK_MAXK = 4224;  // ceil(n / 2) bound of the exact-slice path (K pad <= 4224)
 // gather (DCT-II inverse): u = the even entries x[2j], v = the odd ones x[2j+1] instead of the fold.
+template <int NB, int NS>
 __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n,
                                                                     int ku, int kv, int nks, int nmt,
                                                                     uint8_t *__restrict__ out, size_t slice_bytes,
@@ -818,16 +839,16 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const double val = src[q];
-      T[q] = bad ? 0ull : oz_fixed(val, e);
+      T[q] = bad ? 0ull : oz_fixed<NB * NS>(val, e);
       negm |= (__double_as_longlong(val) < 0 ? 1u : 0u) << q;
     }
     const uint32_t off = swz(r, kk);
-    uint8_t *tile0 = out + (size_t)par * OZ_S * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
+    uint8_t *tile0 = out + (size_t)par * NS * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
 #pragma unroll
-    for (int i = 1; i <= OZ_S; ++i) {
+    for (int i = 1; i <= NS; ++i) {
       alignas(16) uint16_t hv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) hv[q] = oz_slice_bits(T[q], i, (negm >> q) & 1u);
+      for (int q = 0; q < 8; ++q) hv[q] = oz_slice_bits<NB, NS>(T[q], i, (negm >> q) & 1u);
       *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = *reinterpret_cast<const uint4 *>(hv);
     }
   }
@@ -837,6 +858,7 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
 // schedule: warp 0 streams A_i / B_j stages, warp 1 issues the MMAs of a group into one of four
 // tensor-memory accumulators, warps 2-9 add finished groups into float64 sums held in registers
 // (warp w: rows 32 (w % 4).., columns 64 ((w - 2) / 4)..) and store the tile once at its end.
+template <int NB, int NS>
 __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restrict__ apack, size_t a_slice_bytes,
                                                          const uint8_t *__restrict__ bpack, size_t b_slice_bytes,
                                                          const int *__restrict__ erow, int eB, int nks, int nmt,
@@ -901,8 +923,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         decode(t, par, mt, nt);
         if (!wanted(par, mt, nt)) continue;
         for (int pr = 0; pr < sch.npairs && !*abort_flag; ++pr) {
-          const uint8_t *at = apack + ((size_t)par * OZ_S + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
-          const uint8_t *bt = bpack + ((size_t)par * OZ_S + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+          const uint8_t *at = apack + ((size_t)par * NS + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
+          const uint8_t *bt = bpack + ((size_t)par * NS + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
           for (int kk = 0; kk < nks; kk += OZ_KT, ++it) {
             const int kt = min(OZ_KT, nks - kk);  // K tiles in this stage
             const int s = it % OZ_NST, use = it / OZ_NST;
@@ -993,7 +1015,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
-                                               : ldexp(1.0, e + eB - 2 * OZ_B);
+                                               : ldexp(1.0, e + eB - 2 * NB);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           float v[32];
@@ -1034,40 +1056,65 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_NACC * OZ_TN) : "memory");
 }
 
+// Pair schedule of one output tile.  Exact groups: pairs of one weight d < tail, at most gmax per
+// accumulator.  The tail (d >= tail, FP32-rounded) is cut into chunks of at most 3 pairs, each in
+// its own accumulator, and the chunks are spread between the exact groups: every group costs the
+// epilogue one float64 multiply-add per output (about as long as one pair's MMAs), so runs of
+// one-pair groups alone would hold the MMA issuer waiting for accumulators, while the tail's
+// longer groups give the epilogue time to catch up.
 static OzSched oz_schedule(int kpad) {
   OzSched s{};
-  const long long cap = (1LL << 24) / (63LL * 63LL * kpad);  // pairs per exact FP32 accumulation
+  const OzFmt f = oz_format(kpad);
+  const long long qmax = (1LL << f.nb) - 1;
+  const long long cap = (1LL << 24) / (qmax * qmax * kpad);  // pairs per exact FP32 accumulation
   const int gmax = (int)std::max(1LL, std::min(4LL, cap));
-  int tail_d = OZ_TAIL;
+  int tail_d = 8;
   for (long long k = 1024; k < kpad; k *= 2) ++tail_d;
-  int np = 0, ng = 0;
-  for (int d = 2; d <= OZ_S + 1; ++d) {
-    int in_group = 0;
-    const bool tail = d >= tail_d;
-    for (int i = 1; i <= OZ_S; ++i) {
+  struct Group {
+    int d;
+    std::vector<std::pair<int, int>> pairs;
+  };
+  std::vector<Group> exact, tail;
+  for (int d = 2; d <= f.ns + 1; ++d) {
+    for (int i = 1; i <= f.ns; ++i) {
       const int j = d - i;
-      if (j < 1 || j > OZ_S) continue;
-      s.si[np] = (int8_t)i;
-      s.sj[np] = (int8_t)j;
-      const bool starts = tail ? (d == tail_d && in_group == 0) : (in_group == 0);
-      s.first[np] = starts;
-      if (starts) s.gd[ng++] = (int8_t)d;
-      ++in_group;
-      ++np;
-      if (!tail && in_group == gmax) {
-        s.last[np - 1] = 1;
-        in_group = 0;
+      if (j < 1 || j > f.ns) continue;
+      if (d < tail_d) {
+        if (exact.empty() || exact.back().d != d || (int)exact.back().pairs.size() == gmax) exact.push_back({d, {}});
+        exact.back().pairs.push_back({i, j});
+      } else {
+        if (tail.empty() || (int)tail.back().pairs.size() == 3) tail.push_back({tail_d, {}});
+        tail.back().pairs.push_back({i, j});
       }
     }
-    if (!tail && in_group > 0) s.last[np - 1] = 1;
   }
-  s.last[np - 1] = 1;  // the tail group ends with the last pair
+  std::vector<const Group *> order;
+  const size_t ne = exact.size(), nt = tail.size();
+  size_t ie = 0;
+  for (size_t it = 0; it < nt; ++it) {  // spread: exact groups, a tail chunk, exact groups, ...
+    const size_t upto = (it + 1) * ne / (nt + 1);
+    for (; ie < upto; ++ie) order.push_back(&exact[ie]);
+    order.push_back(&tail[it]);
+  }
+  for (; ie < ne; ++ie) order.push_back(&exact[ie]);
+  int np = 0, ng = 0;
+  for (const Group *g : order) {
+    for (size_t q = 0; q < g->pairs.size(); ++q) {
+      if (np >= (int)sizeof(s.si)) throw Error(LAG_EINVAL, "exact-slice schedule: too many pairs");
+      s.si[np] = (int8_t)g->pairs[q].first;
+      s.sj[np] = (int8_t)g->pairs[q].second;
+      s.first[np] = (q == 0);
+      s.last[np] = (q + 1 == g->pairs.size());
+      ++np;
+    }
+    s.gd[ng++] = (int8_t)g->d;
+  }
   s.npairs = np;
   s.ngroups = ng;
   return s;
 }
 
-int dst_oz_products() { return oz_schedule(TK).npairs; }
+int dst_oz_products(int n) { return oz_schedule(div_up((n + 1) / 2, TK) * TK).npairs; }
 
 bool dst_oz_supported(int n) {
   const int ku = (n + 1) / 2;
@@ -1077,7 +1124,7 @@ bool dst_oz_supported(int n) {
 
 size_t dst_oz_bytes(int n, int kind) {
   const int ku = (n + 1) / 2;
-  return (kind == 1 ? 2 : 1) * 2 * (size_t)OZ_S * div_up(ku, OZ_TN) * div_up(ku, TK) * OZ_BT;
+  return (kind == 1 ? 2 : 1) * 2 * (size_t)OZ_SMAX * div_up(ku, OZ_TN) * div_up(ku, TK) * OZ_BT;
 }
 
 void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
@@ -1090,17 +1137,25 @@ void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
   // every |S| <= sqrt(2 / (n + 1)) < 2^eB (DST-I); every |V| <= sqrt(2 / n) < 2^eB (DCT-II)
   frexp(std::sqrt(2.0 / (double)(dp.kind == 1 ? dp.n : dp.n + 1)), &eB);
   dp.oz_eB = eB;
+  const OzFmt f = oz_format(nks * TK);
+  dp.oz_nb = f.nb;
+  dp.oz_ns = f.ns;
   dim3 g(div_up(nks * TK, 128), nnt * OZ_TN, 2);
-  oz_pack_b_kernel<<<g, 128, 0, s>>>(dp.su, dp.ku, dp.ku, dp.ku, dp.sv, dp.kv, dp.kv, dp.kv, nks, nnt, eB, dp.oz_b,
-                                     dp.oz_slice_bytes);
-  count_launch();
-  LAG_LAUNCH_CHECK();
-  if (dp.kind == 1) {  // inverse operands: even / odd input modes x ceil(n/2) output columns
-    dp.oz_bi = dp.oz_b + 2 * (size_t)OZ_S * dp.oz_slice_bytes;
-    oz_pack_b_kernel<<<g, 128, 0, s>>>(dp.ie, dp.ku, dp.ku, dp.ku, dp.io, dp.kv, dp.ku, dp.ku, nks, nnt, eB, dp.oz_bi,
-                                       dp.oz_slice_bytes);
+  auto pack_b = [&](const double *m0, int k0n, int n0n, int ld0, const double *m1, int k1n, int n1n, int ld1,
+                    uint8_t *out) {
+    if (f.nb == 7)
+      oz_pack_b_kernel<7, 8><<<g, 128, 0, s>>>(m0, k0n, n0n, ld0, m1, k1n, n1n, ld1, nks, nnt, eB, out,
+                                               dp.oz_slice_bytes);
+    else
+      oz_pack_b_kernel<6, 9><<<g, 128, 0, s>>>(m0, k0n, n0n, ld0, m1, k1n, n1n, ld1, nks, nnt, eB, out,
+                                               dp.oz_slice_bytes);
     count_launch();
     LAG_LAUNCH_CHECK();
+  };
+  pack_b(dp.su, dp.ku, dp.ku, dp.ku, dp.sv, dp.kv, dp.kv, dp.kv, dp.oz_b);
+  if (dp.kind == 1) {  // inverse operands: even / odd input modes x ceil(n/2) output columns
+    dp.oz_bi = dp.oz_b + 2 * (size_t)f.ns * dp.oz_slice_bytes;
+    pack_b(dp.ie, dp.ku, dp.ku, dp.ku, dp.io, dp.kv, dp.ku, dp.ku, dp.oz_bi);
   }
   dp.oz = true;
 }
@@ -1108,7 +1163,7 @@ void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows) {
   const size_t nmt = div_up(rows, TM);
   const size_t eo = (dp.kind == 1) ? 2 * (size_t)rows * dp.ku * sizeof(double) + 256 : 0;  // DCT-II E / O sums
-  return 2 * (size_t)OZ_S * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256 + eo;
+  return 2 * (size_t)OZ_SMAX * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256 + eo;
 }
 
 // DCT-II inverse butterfly: x[k] = E[k] + O[k], x[n-1-k] = E[k] - O[k] (k < ceil(n/2)); rows of
@@ -1126,29 +1181,23 @@ __global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__res
   }
 }
 
-void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
-                  cudaStream_t s, bool inverse) {
-  if (rows <= 0) return;
+template <int NB, int NS>
+static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
+                         cudaStream_t s, int inv) {
   static bool attr = false;
   if (!attr) {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        2 * OZ_PACK_MAXK * (int)sizeof(double)));
     attr = true;
   }
-  ProfScope prof(KC_DST64, s);
   const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
   const size_t a_slice = (size_t)nmt * nks * A_TILE;
   uint8_t *apack = dp.tc_scratch;
-  int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)OZ_S * a_slice);
+  int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)NS * a_slice);
   const size_t pack_smem = 2 * (size_t)nks * TK * sizeof(double);
-  static bool pack_attr = false;
-  if (!pack_attr) {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        2 * OZ_PACK_MAXK * (int)sizeof(double)));
-    pack_attr = true;
-  }
-  const int inv = (inverse && dp.kind == 1) ? 1 : 0;
-  oz_pack_a_kernel<<<nmt * TM, OZ_PACK_THREADS, pack_smem, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack, a_slice,
-                                                                 erow, sc, rpr, inv);
+  oz_pack_a_kernel<NB, NS><<<nmt * TM, OZ_PACK_THREADS, pack_smem, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack,
+                                                                         a_slice, erow, sc, rpr, inv);
   count_launch();
   LAG_LAUNCH_CHECK();
   const OzSched sch = oz_schedule(nks * TK);
@@ -1157,9 +1206,9 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
   // E / O sums of the inverse: after the packed A slices and the row exponents, 256-byte aligned
   double *eo = reinterpret_cast<double *>(
       (reinterpret_cast<uintptr_t>(erow + 2 * (size_t)nmt * TM) + 255) & ~(uintptr_t)255);
-  oz_gemm_kernel<<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes, erow,
-                                            dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku, dp.kv, sch, sc,
-                                            rpr, dp.tc_err, inv);
+  oz_gemm_kernel<NB, NS><<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
+                                                    erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,
+                                                    dp.kv, sch, sc, rpr, dp.tc_err, inv);
   count_launch();
   LAG_LAUNCH_CHECK();
   if (inv) {
@@ -1167,6 +1216,15 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
     count_launch();
     LAG_LAUNCH_CHECK();
   }
+}
+
+void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
+                  cudaStream_t s, bool inverse) {
+  if (rows <= 0) return;
+  ProfScope prof(KC_DST64, s);
+  const int inv = (inverse && dp.kind == 1) ? 1 : 0;
+  if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, inv);
+  else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, inv);
 }
 
 }  // namespace lag

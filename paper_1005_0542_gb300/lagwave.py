@@ -122,7 +122,7 @@ _PROTOS = {
     "lag_shot_copy_field": (I, [VP, VP]),
     "lag_shot_stats": (I, [VP, C.POINTER(lag_stats)]),
     "lag_precond_status": (I, [VP]),
-    "lag_dst_f64_slice_products": (I, []),
+    "lag_dst_f64_slice_products": (I, [I]),
     "lag_shot_checkpoint_size": (C.c_size_t, [VP]),
     "lag_shot_checkpoint": (I, [VP, VP, C.c_size_t]),
     "lag_shot_restore": (I, [VP, VP, C.c_size_t]),
