@@ -724,19 +724,24 @@ __device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
   if (s >= 0) return M << s;                      // s <= NBITS - 52 since |v| < 2^e
   return (s <= -64) ? 0ull : (M >> (-s));
 }
-// slice i (1-based) of an NB*NS-bit fixed-point value as bf16 bits, built with integer operations
-// and stored pre-scaled by 2^-(NB (i - 1)): the integer 1 <= q < 2^NB is 1.f x 2^p with
-// p = 31 - clz(q), exactly representable in bf16's 8-bit significand (NB <= 8), and the scale only
-// moves the exponent.  A product of slices i and j then carries 2^-(NB (i + j - 2)) already, so
-// products of different weights can share an accumulator.
+// slice i (1-based) of an NB*NS-bit fixed-point value, pre-scaled by 2^-(NB (i - 1)) and signed, as
+// a float whose upper half is the bf16 operand: the integer 0 <= q < 2^NB becomes a float by the
+// 2^23 magic-number trick, and one FMA scales it exactly (q has at most 8 significant bits, so the
+// low half of the float is zero and its upper half is q 2^-(NB (i - 1)) in bf16; 0 stays +0).
+// A product of slices i and j then carries 2^-(NB (i + j - 2)) already, so products of different
+// weights can share an accumulator.
 template <int NB, int NS>
-__device__ __forceinline__ uint16_t oz_slice_bits(unsigned long long T, int i, bool neg) {
+__device__ __forceinline__ float oz_slice_f(unsigned long long T, int i, bool neg) {
   static_assert(NB <= 8, "bf16 holds 8 significant bits");
   const uint32_t q = (uint32_t)(T >> (NB * NS - NB * i)) & ((1u << NB) - 1u);
-  if (q == 0) return 0;
-  const int pw = 31 - __clz(q);
-  const uint32_t mant = (q << (7 - pw)) & 0x7fu;
-  return (uint16_t)((neg ? 0x8000u : 0u) | ((uint32_t)(pw + 127 - NB * (i - 1)) << 7) | mant);
+  const float c = __uint_as_float((uint32_t)(127 - NB * (i - 1)) << 23);  // 2^-(NB (i - 1))
+  const float cs = neg ? -c : c;
+  return fmaf(__uint_as_float(0x4B000000u | q), cs, -8388608.0f * cs);
+}
+__device__ __forceinline__ uint16_t oz_bf16_of(float f) { return (uint16_t)(__float_as_uint(f) >> 16); }
+// two slice values as one 32-bit word of bf16 operands (f0 at the lower address)
+__device__ __forceinline__ uint32_t oz_pack2(float f0, float f1) {
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
 }
 
 // B slices, once per plan: [mat 0, mat 1][slice][n tile][k stage][TN x TK].  Mat w is the row-major
@@ -758,7 +763,7 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
   const uint32_t off = swz(n % OZ_TN, k % TK);
   for (int i = 1; i <= NS; ++i) {
     uint8_t *base = out + ((size_t)which * NS + (i - 1)) * slice_bytes + tile * OZ_BT;
-    *reinterpret_cast<uint16_t *>(base + off) = oz_slice_bits<NB, NS>(T, i, v < 0.0);
+    *reinterpret_cast<uint16_t *>(base + off) = oz_bf16_of(oz_slice_f<NB, NS>(T, i, v < 0.0));
   }
 }
 
@@ -788,6 +793,7 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
   const int kp = nks * TK;
   double *su = fold_sm, *sv = fold_sm + kp;
   unsigned long long b0 = 0, b1 = 0;
+#pragma unroll 4
   for (int j = threadIdx.x; j < kp; j += blockDim.x) {
     double a = 0.0, b = 0.0;
     if (gather) {
@@ -846,10 +852,12 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
     uint8_t *tile0 = out + (size_t)par * NS * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
 #pragma unroll
     for (int i = 1; i <= NS; ++i) {
-      alignas(16) uint16_t hv[8];
+      uint32_t hw[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) hv[q] = oz_slice_bits<NB, NS>(T[q], i, (negm >> q) & 1u);
-      *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = *reinterpret_cast<const uint4 *>(hv);
+      for (int q = 0; q < 4; ++q)
+        hw[q] = oz_pack2(oz_slice_f<NB, NS>(T[2 * q], i, (negm >> (2 * q)) & 1u),
+                         oz_slice_f<NB, NS>(T[2 * q + 1], i, (negm >> (2 * q + 1)) & 1u));
+      *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     }
   }
 }
