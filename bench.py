@@ -746,8 +746,9 @@ def capture_extensions(args):
     """One launch of the kernels of the layered and cylindrical plans through the C ABI, 1024 x 1024
     x 16 RHS float64 (134 MB > L2): the general tridiagonal solve (one factor set per partition)
     of a layered plan, then the forward and the inverse DCT-II of a cylindrical float64 plan
-    (exact slices; the inverse gathers even / odd modes and ends in the E/O butterfly), for
-    `ncu -k ... -c N` captures."""
+    (exact slices; the inverse gathers even / odd modes and ends in the E/O butterfly); then a
+    two-harmonic cylindrical elastic shot of 1024 x 512 (the axisymmetric elastic stencil and the
+    FGMRES kernels), for `ncu -k ... -c N` captures."""
     import torch
     from paper_1005_0542_gb300 import lagwave as L
     ctx = L.create(0, stream=torch.cuda.current_stream().cuda_stream)
@@ -773,6 +774,22 @@ def capture_extensions(args):
     L.check(L.lag_precond_dst_inverse(pc, P(z), P(r), nrhs), ctx)    # inverse DCT-II (gather + GEMM + E/O)
     L.check(L.lag_precond_tridiag(pc, P(r), P(z), nrhs), ctx)        # systems along r (cylindrical)
     torch.cuda.synchronize()
+    # a cylindrical elastic shot, 1024 x 512 (r x z), 2 harmonics, mixed path: the axisymmetric
+    # elastic stencil and the FGMRES Gram-Schmidt kernels (basis vectors 8.4 MB each, 176 MB > L2)
+    from paper_1005_0542_gb300 import inputs
+    se = inputs.cylindrical(nr=1024, nz=512, n_harm=2, layered=True, elastic=True)
+    ge = L.grid(se.nx, se.nz, se.hx, se.hz, cylindrical=True)
+    lag = L.laguerre(se.h, se.alpha, se.n_harm)
+    sv = L.solver(tol=1e-10, prec=L.LAG_MIXED, restart_k=se.restart)
+    w = L.wavelet(se.f0, se.t0, 4.0, L.LAG_WAVELET_PAPER)
+    c_, pcv = L.f64(se.c)
+    v_, pvs = L.f64(se.vs)
+    r_, prh = L.f64(se.rho)
+    t_, pt = L.f64(se.t_out)
+    tr = np.zeros((1, 2, len(se.receivers), se.t_out.size))
+    L.check(L.lag_solve_elastic(ctx, C.byref(ge), pcv, pvs, prh, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                                L.points(se.sources), len(se.receivers), L.points(se.receivers), se.t_out.size, pt,
+                                tr.ctypes.data_as(L.PD), None), ctx)
     L.lag_destroy(ctx)
     print(json.dumps({"capture": "ok"}))
 

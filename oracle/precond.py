@@ -109,6 +109,16 @@ def acoustic_params_layered(kappa, rho, h_lag):
     return kz, kz.copy(), row_midranges(rho) * h_lag ** 2 / 4.0
 
 
+def elastic_params_layered(lam, mu, rho, h_lag):
+    """((ax~(z), az~(z), d~(z)) of B1, the same of B2) of the layered elastic preconditioner:
+    Eq. (22)'s K = diag(B1, B2) with each tilde taken over a node row (B1: ax = (lambda+2mu)~(z),
+    az = mu~(z); B2: ax = mu~(z), az = (lambda+2mu)~(z); d = rho~(z) h^2/4)."""
+    pz = row_midranges(np.asarray(lam) + 2.0 * np.asarray(mu))
+    mz = row_midranges(mu)
+    dz = row_midranges(rho) * h_lag ** 2 / 4.0
+    return (pz, mz, dz), (mz.copy(), pz.copy(), dz.copy())
+
+
 def _z_faces(az_z, free_surface):
     nz = az_z.shape[0]
     f = np.empty(nz + 1)

@@ -84,14 +84,20 @@ def elastic_lame(vp, vs, rho):
 
 def elastic_shot(vp, vs, rho, hx, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
                  tol=1e-10, restart=20, max_iter=4000, keep_fields=False, fm=None,
-                 wavelet="ricker"):
+                 wavelet="ricker", layered=False):
     """One elastic shot with a vertical point force.  Returns dict(R_rcv [n, 2, nrcv],
-    traces [2, nrcv, nt], iters [n], fm, fields (optional: [n, 2, nz, nx]))."""
+    traces [2, nrcv, nt], iters [n], fm, fields (optional: [n, 2, nz, nx])).
+    layered: K = diag(B1, B2) with per-row midranges (precond.elastic_params_layered)."""
     lam, mu = elastic_lame(vp, vs, rho)
     rho = np.asarray(rho, dtype=np.float64)
     nz, nx = lam.shape
     n = nz * nx
-    p1, p2 = precond.elastic_params(lam, mu, rho, h)
+    if layered:
+        p1, p2 = precond.elastic_params_layered(lam, mu, rho, h)
+        inv = precond.apply_inverse_layered
+    else:
+        p1, p2 = precond.elastic_params(lam, mu, rho, h)
+        inv = precond.apply_inverse
     if fm is None:
         fm = source_coeffs(n_harm, h, alpha, f0, t0, kind=wavelet)
 
@@ -100,8 +106,8 @@ def elastic_shot(vp, vs, rho, hx, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
         return np.concatenate([cu.ravel(), cw.ravel()])
 
     def Kinv(v):
-        yu = precond.apply_inverse(v[:n].reshape(nz, nx), hx, hz, *p1)
-        yw = precond.apply_inverse(v[n:].reshape(nz, nx), hx, hz, *p2)
+        yu = inv(v[:n].reshape(nz, nx), hx, hz, *p1)
+        yw = inv(v[n:].reshape(nz, nx), hx, hz, *p2)
         return np.concatenate([yu.ravel(), yw.ravel()])
 
     R = []

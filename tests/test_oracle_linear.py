@@ -323,3 +323,56 @@ def test_layered_precond_needs_fewer_iterations_on_layers():
     assert it_l < it_c / 2
     M = fd.assemble_A(kappa, rho, h, hx, hx)
     assert np.linalg.norm(M @ xl - b) / np.linalg.norm(b) < 1e-9
+
+
+def test_layered_elastic_blocks_equal_the_diagonal_blocks_of_C_for_a_z_only_medium():
+    # lambda, mu, rho depending on z only: the layered B1 is the u-u block of C and B2 the w-w
+    # block (the face rule of the elastic operator is the layered preconditioner's), so K differs
+    # from C by the mixed u-w terms alone
+    nz, nx, hx, hz, h = 13, 10, 2.5, 3.0, 300.0
+    lam = np.repeat(RNG.uniform(2e9, 9e9, nz)[:, None], nx, axis=1)
+    mu = np.repeat(RNG.uniform(1e9, 5e9, nz)[:, None], nx, axis=1)
+    rho = np.repeat(RNG.uniform(1800.0, 2600.0, nz)[:, None], nx, axis=1)
+    p1, p2 = precond.elastic_params_layered(lam, mu, rho, h)
+    y = RNG.standard_normal((nz, nx))
+    zero = np.zeros_like(y)
+    cu, _ = fd.apply_C(y, zero, lam, mu, rho, h, hx, hz)
+    _, cw = fd.apply_C(zero, y, lam, mu, rho, h, hx, hz)
+    # the mixed terms of a field in one component only land in the other component
+    assert np.abs(cu - precond.apply_separable_layered(y, hx, hz, *p1)).max() < 1e-12 * np.abs(cu).max()
+    assert np.abs(cw - precond.apply_separable_layered(y, hx, hz, *p2)).max() < 1e-12 * np.abs(cw).max()
+    # constant rows: the layered blocks are Eq. 22's constant ones
+    c1, c2 = precond.elastic_params(lam[:1].repeat(nz, 0), mu[:1].repeat(nz, 0), rho[:1].repeat(nz, 0), h)
+    l1, l2 = precond.elastic_params_layered(lam[:1].repeat(nz, 0), mu[:1].repeat(nz, 0), rho[:1].repeat(nz, 0), h)
+    r = RNG.standard_normal((nz, nx))
+    for c, l in ((c1, l1), (c2, l2)):
+        a = precond.apply_inverse_layered(r, hx, hz, *l)
+        b = precond.apply_inverse(r, hx, hz, *c)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
+
+
+def test_layered_elastic_precond_needs_fewer_iterations_on_layers():
+    # FGMRES(20) on a layered elastic model with lateral noise: per-row midranges beat Eq. 22's
+    # whole-medium ones, and the solution satisfies the dense system
+    nz, nx, hx, h = 36, 30, 5.0, 300.0
+    layers = (np.arange(nz) * 5) // nz
+    vp = RNG.uniform(2000, 5000, 5)[layers][:, None] * (1 + 0.02 * RNG.standard_normal((nz, nx)))
+    vs = vp / 1.8
+    rho = RNG.uniform(1800, 2600, 5)[layers][:, None] * np.ones((1, nx))
+    from oracle.solve import elastic_lame
+    lam, mu = elastic_lame(vp, vs, rho)
+    n = nz * nx
+
+    def C(v):
+        a, b = fd.apply_C(v[:n].reshape(nz, nx), v[n:].reshape(nz, nx), lam, mu, rho, h, hx, hx)
+        return np.concatenate([a.ravel(), b.ravel()])
+
+    def K(params, inv):
+        return lambda v: np.concatenate([inv(v[:n].reshape(nz, nx), hx, hx, *params[0]).ravel(),
+                                         inv(v[n:].reshape(nz, nx), hx, hx, *params[1]).ravel()])
+    b = RNG.standard_normal(2 * n)
+    _, it_c, _ = krylov.gmres(C, K(precond.elastic_params(lam, mu, rho, h), precond.apply_inverse), b, 20, 1e-10, 2000)
+    x, it_l, _ = krylov.gmres(C, K(precond.elastic_params_layered(lam, mu, rho, h), precond.apply_inverse_layered),
+                              b, 20, 1e-10, 2000)
+    assert it_l < 0.75 * it_c
+    assert np.linalg.norm(C(x) - b) / np.linalg.norm(b) < 1e-9
