@@ -101,8 +101,10 @@ typedef struct {
   int prec;         /* LAG_FP64 or LAG_MIXED                                                       */
   int partitions;   /* z-partitions of the tridiagonal solve; 0 = automatic                        */
   int tune;         /* 1: shots run lag_precond_autotune on their plans at creation                */
-  int layered;      /* 1: acoustic shots precondition with per-row midranges (lag_precond_create_
-                       layered) instead of the whole-medium midranges of Eq. 21; elastic: 0 only  */
+  int layered;      /* 1: shots on Cartesian grids precondition with per-row midranges
+                       (lag_precond_create_layered) instead of the whole-medium midranges of
+                       Eq. 21 (acoustic) or Eq. 22 (elastic: B1, B2 with (l+2m)~(z), mu~(z),
+                       rho~(z)); cylindrical grids: 0 only                                       */
 } lag_solver;
 typedef struct { int ix, iz; } lag_point;                          /* 0-based interior node        */
 typedef struct { double f0, t0, gamma; int kind; } lag_wavelet;

@@ -221,7 +221,8 @@ struct lag_medium {
   double mid[3] = {0, 0, 0};   // kappa~, rho~ | (l+2m)~, mu~, rho~
   lag::DevBuf coef;            // operator coefficients (see k_ops.cu)
   lag::DevBuf rho_h2;          // rho h^2 at nodes (right-hand side history term)
-  lag::DevBuf rowmm;           // acoustic: per-row [kappa | rho][nz][min, max] (layered preconditioner)
+  lag::DevBuf rowmm;           // per-row [nz][min, max] of [kappa | rho] (acoustic) or [lambda+2mu | mu |
+                               // rho] (Cartesian elastic), for the layered preconditioner
   size_t ncoef = 0;
   // q = C p (elastic) or A p; sub (elastic only, nullable): q = C p - sub, same layout as q
   void apply(const double *p, double *q, int nrhs, const lag::KrylovScalars *sc,

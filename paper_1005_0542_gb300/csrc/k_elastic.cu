@@ -122,6 +122,11 @@ void medium_build_elastic(lag_medium &m, const double *vp_host, const double *vs
   midrange_device(p2m, n, mm, s);
   midrange_device(mu, n, mm + 2, s);
   midrange_device(drho, n, mm + 4, s);
+  // per-row extremes (layered K): [lambda+2mu | mu | rho][nz][min, max]
+  m.rowmm.alloc(m.ctx, 6 * (size_t)nz * sizeof(double));
+  row_minmax_device(p2m, nx, nz, m.rowmm.as<double>(), s);
+  row_minmax_device(mu, nx, nz, m.rowmm.as<double>() + 2 * (size_t)nz, s);
+  row_minmax_device(drho, nx, nz, m.rowmm.as<double>() + 4 * (size_t)nz, s);
   double h_mm[6];
   LAG_CUDA_CHECK(cudaMemcpyAsync(h_mm, mm, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
   LAG_CUDA_CHECK(cudaStreamSynchronize(s));

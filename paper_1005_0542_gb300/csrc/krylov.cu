@@ -34,7 +34,6 @@ void check_solver(const lag_solver &s, bool elastic) {
   if (s.partitions < 0 || s.partitions > 32) throw Error(LAG_EINVAL, "partitions must be 0..32");
   if (s.tune != 0 && s.tune != 1) throw Error(LAG_EINVAL, "tune must be 0 or 1");
   if (s.layered != 0 && s.layered != 1) throw Error(LAG_EINVAL, "layered must be 0 or 1");
-  if (elastic && s.layered) throw Error(LAG_EINVAL, "the layered preconditioner is acoustic only");
 }
 
 void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, double *z, int nrhs, int ncomp,

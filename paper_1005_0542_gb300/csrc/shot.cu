@@ -82,6 +82,26 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
     sh->p1 = precond_new(ctx, g, 0.0, 0.0, 0.0, s.prec, s.partitions, st, rows.data());
   } else if (!elastic) {
     sh->p1 = precond_new(ctx, g, mid[0], mid[0], mid[1] * lag.h * lag.h / 4.0, s.prec, s.partitions, st);
+  } else if (s.layered) {
+    // Eq. (22)'s K with per-row midranges: B1 (ax, az) = ((l+2m)~(z), mu~(z)), B2 = (mu~(z),
+    // (l+2m)~(z)), d = rho~(z) h^2 / 4
+    const int nz = g.nz;
+    std::vector<double> mm(6 * (size_t)nz), r1(3 * (size_t)nz), r2(3 * (size_t)nz);
+    LAG_CUDA_CHECK(cudaMemcpyAsync(mm.data(), sh->medium->rowmm.ptr, mm.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+    LAG_CUDA_CHECK(cudaStreamSynchronize(st));
+    for (int k = 0; k < nz; ++k) {
+      const double pz = 0.5 * (mm[2 * k] + mm[2 * k + 1]);
+      const double uz = 0.5 * (mm[2 * (nz + k)] + mm[2 * (nz + k) + 1]);
+      const double rz = 0.5 * (mm[2 * (2 * nz + k)] + mm[2 * (2 * nz + k) + 1]);
+      r1[k] = pz;
+      r1[nz + k] = uz;
+      r2[k] = uz;
+      r2[nz + k] = pz;
+      r1[2 * nz + k] = r2[2 * nz + k] = rz * lag.h * lag.h / 4.0;
+    }
+    sh->p1 = precond_new(ctx, g, 0.0, 0.0, 0.0, s.prec, s.partitions, st, r1.data());
+    sh->p2 = precond_new(ctx, g, 0.0, 0.0, 0.0, s.prec, s.partitions, st, r2.data());
   } else {  // K = diag(B1, B2), Eq. (22): B1 (ax, az) = ((l+2m)~, mu~), B2 = (mu~, (l+2m)~)
     const double d = mid[2] * lag.h * lag.h / 4.0;
     // cylindrical grids: B1 also holds the hoop term (l+2m)~/r (Eq. 22)

@@ -184,9 +184,44 @@ def test_layered_shot_one_iteration_on_a_z_only_medium(ctx):
     assert np.all(its == 1), its
 
 
-def test_layered_elastic_rejected(ctx):
-    s = inputs.elastic_layered(nx=16, nz=12, hx=2.5, n_harm=2, nsrc=1)
+def _elastic_shot(ctx, s, prec, tol, layered):
     g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=tol, prec=prec, restart_k=s.restart, layered=layered)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    v_, pv = L.f64(s.vs)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    traces = np.zeros((1, 2, len(s.receivers), s.t_out.size))
+    its = np.zeros((1, s.n_harm), dtype=np.int32)
+    st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+    L.check(L.lag_solve_elastic(ctx, C.byref(g), pc, pv, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                                L.points(s.sources[:1]), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                                traces.ctypes.data_as(L.PD), C.byref(st)), ctx)
+    return traces[0], its[0]
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, 1e-13, 1e-10), (L.LAG_MIXED, 1e-11, 1e-8)])
+def test_layered_elastic_shot_matches_oracle(ctx, prec, tol, gate):
+    # Eq. 22's K with per-row midranges (B1: (l+2m)~(z), mu~(z); B2 swapped) on the layered elastic
+    # model with its dipping interface: the traces of the oracle's layered FGMRES, fewer iterations
+    # than with the whole-medium K
+    s = inputs.elastic_layered(nx=64, nz=40, hx=2.5, n_harm=6, nsrc=1)
+    s.receivers = s.receivers[:8]
+    tr, its = _elastic_shot(ctx, s, prec, tol, 1)
+    ref = solve.elastic_shot(s.c, s.vs, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, s.sources[0], s.receivers,
+                             s.t_out, s.f0, s.t0, tol=tol, restart=s.restart, layered=True)
+    assert rel_l2(tr, ref["traces"]) < gate
+    if prec == L.LAG_FP64:
+        assert np.abs(its - ref["iters"]).max() <= 1
+        _, its_c = _elastic_shot(ctx, s, prec, tol, 0)
+        assert its.sum() < its_c.sum(), (its, its_c)
+
+
+def test_layered_cylindrical_elastic_rejected(ctx):
+    s = inputs.cylindrical(nr=16, nz=12, h=10.0, n_harm=2, elastic=True)
+    g = L.grid(s.nx, s.nz, s.hx, s.hz, cylindrical=True)
     lag = L.laguerre(s.h, s.alpha, s.n_harm)
     sv = L.solver(tol=1e-8, layered=1)
     w = L.wavelet(s.f0, s.t0)
