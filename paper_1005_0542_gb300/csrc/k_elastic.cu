@@ -286,6 +286,18 @@ __device__ __forceinline__ double warp_sum8_scatter(const double (&a)[8]) {
   return h1;
 }
 
+// acc[q] += (w, V_q) over this thread's elements for q < C (and aw += (w, w) when W)
+template <int C, int W>
+__device__ __forceinline__ void gm_dots_sweep(const double *__restrict__ w, const double *__restrict__ V,
+                                              size_t vstride, size_t n, double (&acc)[8], double &aw) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double we = w[e];
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = fma(we, V[(size_t)q * vstride + e], acc[q]);
+    if (W) aw = fma(we, we, aw);
+  }
+}
+
 // blocks per rhs of the Gram-Schmidt dot kernel: four per SM, so that each thread sums many
 // elements before the (FP64) block reduction
 static int dots_blocks(size_t n) { return std::min(reduce_blocks(n), 4 * 152); }
@@ -318,12 +330,19 @@ __global__ void __launch_bounds__(256) gm_dots_kernel(const double *__restrict__
     double acc[8], aw = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-      const double we = w[off + e];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < cnt) acc[q] = fma(we, V[(size_t)(i0 + q) * vstride + off + e], acc[q]);
-      if (ww) aw = fma(we, we, aw);
+    // one instantiation per basis count and (w, w) flag: predicated-off FMAs would still take
+    // FP64 issue slots, the limit of this kernel
+    const double *Vi = V + (size_t)i0 * vstride + off;
+    const double *wp = w + off;
+    switch (cnt * 2 + (ww ? 1 : 0)) {
+#define LAG_GM_SWEEP(C, W) \
+      case C * 2 + W: gm_dots_sweep<C, W>(wp, Vi, vstride, n, acc, aw); break;
+      LAG_GM_SWEEP(1, 0) LAG_GM_SWEEP(1, 1) LAG_GM_SWEEP(2, 0) LAG_GM_SWEEP(2, 1)
+      LAG_GM_SWEEP(3, 0) LAG_GM_SWEEP(3, 1) LAG_GM_SWEEP(4, 0) LAG_GM_SWEEP(4, 1)
+      LAG_GM_SWEEP(5, 0) LAG_GM_SWEEP(5, 1) LAG_GM_SWEEP(6, 0) LAG_GM_SWEEP(6, 1)
+      LAG_GM_SWEEP(7, 0) LAG_GM_SWEEP(7, 1) LAG_GM_SWEEP(8, 0) LAG_GM_SWEEP(8, 1)
+#undef LAG_GM_SWEEP
+      default: break;
     }
     const double sv = warp_sum8_scatter(acc);
     if ((lane & 3) == 0) sh[(lane >> 2) * 8 + warp] = sv;
