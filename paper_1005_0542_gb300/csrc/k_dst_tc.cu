@@ -137,6 +137,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 16 consecutive columns of a lane's row (fewer live registers than 32 in register-tight epilogues)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 }  // namespace
 
@@ -658,9 +670,10 @@ void spectrum_unpermute_widen(const float *in, double *out, int rows, int n, int
 //     summed by the FP32 accumulator while the total stays below 2^24.  Pairs of the same weight
 //     i + j share one accumulator in groups of at most floor(2^24 / ((2^NB - 1)^2 K)) (at most 4).
 //   * Pairs with i + j <= NS + 1 are kept (the dropped ones weigh < 2^-54 of the row scale), and
-//     the epilogue adds each group as y += 2^(e_r + e_B - 2 NB) G' in float64 (G' the pre-scaled
-//     group sum), straight into the float64 output (natural mode order, as the SIMT kernel writes
-//     it).  Groups are scheduled in an order that keeps the tensor pipe busy (see oz_schedule).
+//     the epilogue adds the groups as int64 fixed-point numbers (units of 2^-38 of the pre-scaled
+//     domain, see OZ_FIX) and rounds once to float64, y = 2^(e_r + e_B - 2 NB) 2^-38 I, straight
+//     into the float64 output (natural mode order, as the SIMT kernel writes it).  Groups are
+//     scheduled in an order that keeps the tensor pipe busy (see oz_schedule).
 //   * Slice width: 7 bits (8 slices, 36 pairs) while one pair's exact sum fits the FP32
 //     accumulator (127^2 K <= 2^24: K <= 1024), else 6 bits (9 slices, 45 pairs).  The GEMM streams
 //     one A and one B slice tile per pair and K step, so fewer pairs mean proportionally fewer
@@ -696,22 +709,24 @@ __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint6
       : "memory");
 }
 
-// float -> double for the group sums, with integer operations only (the FP64 pipe does the
-// accumulation): a sum is zero or a normal float (exact groups: integer multiples of 2^-(NB (w - 2))
-// below 2^24 of them; the tail: a rounded float32), whose double has the same sign and
-// significand and the exponent rebiased by 1023 - 127
-__device__ __forceinline__ double oz_exact_f2d(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t mag = u & 0x7fffffffu;
-  const uint32_t hi = (u & 0x80000000u) | (mag ? ((((mag >> 23) + 896u) << 20) | ((mag >> 3) & 0xfffffu)) : 0u);
-  return __hiloint2double((int)hi, (int)(mag ? (u << 29) : 0u));
-}
-
 struct OzSched {
   int npairs, ngroups;
   int8_t si[48], sj[48], first[48], last[48];  // slice indices (1-based), group start / end flags
-  int8_t gd[48];                               // weight i + j of each group
+  int8_t gd[48];                               // weight i + j of each group (the tail: its lightest)
+  int8_t gsh[48];  // per group: s >= 0 if its sum is an exact integer G with value G 2^-(38 - s) (the
+                   // int64 epilogue adds G << s), -1 for a rounded group (added as rn(v 2^38))
 };
+
+// The epilogue's accumulator: a signed fixed-point integer in units of 2^-38 of the pre-scaled
+// domain (where weight-2 products have unit 1), in int64.  An exact group of weight w holds
+// G 2^-(NB (w - 2)) with G an integer below 2^24: F2I of v 2^(NB (w - 2)) is exact and G << s,
+// s = 38 - NB (w - 2) >= 0, places it (w <= 7 for both formats).  A tail chunk (FP32-rounded, or
+// an exact group too light for a non-negative s) is below 2^-10 in that domain and is added as
+// rn(v 2^38), below 2^31: a rounding at 2^-39, under the float64 rounding of the product.  The sum
+// stays below 2^62.1 (the leading group < 2^24).  One I2F and one DMUL per output at the end; the
+// per-group work is a float multiply, a conversion and integer adds instead of one DFMA on the
+// narrow FP64 pipe.
+constexpr int OZ_FIX = 38;
 
 // |v| < 2^e: NBITS-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
 template <int NBITS>
@@ -1009,7 +1024,9 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
       const int row = mt * TM + lg * 32 + lane;
       const bool rok = row < rows;
       const int e = rok ? erow[par * (nmt * TM) + row] : 0;
-      double acc64[64];
+      long long acci[64];
+#pragma unroll
+      for (int q = 0; q < 64; ++q) acci[q] = 0;
       bool stop = false;
       for (int g = 0; g < sch.ngroups; ++g) {
         const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
@@ -1022,18 +1039,19 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
-                                               : ldexp(1.0, e + eB - 2 * NB);
+        const int gs = sch.gsh[g];
+        // exact: G = v 2^(38 - s) exactly (a power-of-two multiply), then G << s; rounded: rn(v 2^38)
+        const float up = __uint_as_float((uint32_t)(127 + (gs >= 0 ? OZ_FIX - gs : OZ_FIX)) << 23);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 32), v);
-          if (g == 0) {
+        for (int c = 0; c < 4; ++c) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 16), v);
+          if (gs >= 0) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = scale * oz_exact_f2d(v[q]);
+            for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rz(v[q] * up) << gs;
           } else {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc64[c * 32 + q] = fma(scale, oz_exact_f2d(v[q]), acc64[c * 32 + q]);
+            for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rn(v[q] * up);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1043,18 +1061,24 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
       }
       if (stop) break;
       if (rok) {
+        // the one float64 rounding of the product: int64 -> double, then exact power-of-two scales
+        // (2^-38 first, so that a row near the bottom of the float64 range meets the same
+        // subnormal rounding as its float64 product would)
+        const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
+                                               : ldexp(1.0, e + eB - 2 * NB);
+        const double unit = 1.0 / (double)(1LL << OZ_FIX);
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
         if (inv) {  // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]
           double *yp = y + ((size_t)par * rows + row) * ku + c0;
 #pragma unroll
           for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[q] = acc64[q];
+            if (q < ncols) yp[q] = scale * (unit * __ll2double_rn(acci[q]));
         } else {
           double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
 #pragma unroll
           for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[2 * q] = acc64[q];
+            if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
         }
       }
     }
@@ -1107,6 +1131,9 @@ static OzSched oz_schedule(int kpad) {
   for (; ie < ne; ++ie) order.push_back(&exact[ie]);
   int np = 0, ng = 0;
   for (const Group *g : order) {
+    const bool exact = g->d < tail_d;
+    const int sh = OZ_FIX - f.nb * (g->d - 2);
+    s.gsh[ng] = (int8_t)((exact && sh >= 0) ? sh : -1);
     for (size_t q = 0; q < g->pairs.size(); ++q) {
       if (np >= (int)sizeof(s.si)) throw Error(LAG_EINVAL, "exact-slice schedule: too many pairs");
       s.si[np] = (int8_t)g->pairs[q].first;
