@@ -143,8 +143,47 @@ def apply_inverse(rhs, hr, hz, kt, dt):
     return np.moveaxis(yt, 0, -2) @ V.T
 
 
+# Radial variant (a design extension beyond the paper, the counterpart of the Cartesian layered
+# preconditioner): kappa~(r), rho~(r), each the midrange over the depths of one radius.  The
+# coefficients stay independent of z, so the DCT-II along z still separates the variables; the
+# r-systems take a1 = rbar kappa~_face(r) (face mean of the two radii, the outer face its node's
+# value), a2 = r kappa~(r), d = r rho~(r) h^2/4.  For a medium that varies with r only, B is A.
+def precond_params_radial(kappa, rho, h):
+    """(kappa~(r), d~(r) = rho~(r) h^2 / 4), shapes [nr]: per-radius midranges over z."""
+    kappa = np.asarray(kappa, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.float64)
+    kr = 0.5 * (kappa.min(axis=1) + kappa.max(axis=1))
+    dr = 0.5 * (rho.min(axis=1) + rho.max(axis=1)) * h ** 2 / 4.0
+    return kr, dr
+
+
+def apply_inverse_radial(rhs, hr, hz, kr, dr):
+    """y = B^{-1} rhs for the radial preconditioner; rhs [..., nr, nz]."""
+    rhs = np.asarray(rhs, dtype=np.float64)
+    nr, nz = rhs.shape[-2:]
+    kr = np.asarray(kr, dtype=np.float64)
+    dr = np.asarray(dr, dtype=np.float64)
+    V = dct_matrix(nz)
+    mu = neumann_eigenvalues(nz, hz)
+    r, _ = mesh(nr, nz, hr, hz)
+    kf = np.empty(nr + 1)                                   # face values; the axis face has rbar = 0
+    kf[0] = 0.0
+    kf[1:nr] = 0.5 * (kr[:-1] + kr[1:])
+    kf[nr] = kr[nr - 1]
+    a1 = np.arange(nr + 1) * hr * kf / hr ** 2               # rbar kappa~_face / hr^2
+    extra = (1,) * (rhs.ndim - 2)
+    sub = (-a1[:nr]).reshape((nr,) + extra + (1,))
+    sup = (-a1[1:]).reshape((nr,) + extra + (1,))
+    diag = (a1[:nr] + a1[1:])[:, None] + (r * kr)[:, None] * mu[None, :] + (r * dr)[:, None]
+    diag = diag.reshape((nr,) + extra + (nz,))
+    yh = rhs @ V
+    col = np.moveaxis(yh, -2, 0)
+    yt = thomas(sub, diag, sup, col)
+    return np.moveaxis(yt, 0, -2) @ V.T
+
+
 def acoustic_shot(c, rho, hr, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
-                  tol=1e-10, max_iter=2000, keep_fields=False, fm=None, wavelet="ricker"):
+                  tol=1e-10, max_iter=2000, keep_fields=False, fm=None, wavelet="ricker", radial=False):
     """One axisymmetric acoustic shot.  c, rho: [nr, nz]; src = (ir, iz); rcv = [(ir, iz), ...].
 
     Returns dict(R_rcv [n, nrcv], traces [nrcv, nt], iters [n], fm [n], fields (optional))."""
@@ -155,7 +194,12 @@ def acoustic_shot(c, rho, hr, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
     a1, a2, w = coefficients(kappa, rho, hr, hz, h)
     r, _ = mesh(nr, nz, hr, hz)
     rrho = r[:, None] * rho                                 # C3: the history term carries r
-    kt, dt = precond_params(kappa, rho, h)
+    if radial:
+        kt, dt = precond_params_radial(kappa, rho, h)
+        inv = apply_inverse_radial
+    else:
+        kt, dt = precond_params(kappa, rho, h)
+        inv = apply_inverse
     if fm is None:
         fm = source_coeffs(n_harm, h, alpha, f0, t0, kind=wavelet)
 
@@ -163,7 +207,7 @@ def acoustic_shot(c, rho, hr, hz, h, alpha, n_harm, src, rcv, t_out, f0, t0,
         return apply_A(v.reshape(nr, nz), a1, a2, w, hr, hz).ravel()
 
     def Minv(v):
-        return apply_inverse(v.reshape(nr, nz), hr, hz, kt, dt).ravel()
+        return inv(v.reshape(nr, nz), hr, hz, kt, dt).ravel()
 
     R, iters = [], []
     for m in range(n_harm):

@@ -130,3 +130,20 @@ def test_shot_matches_3d_point_source_with_image_at_second_order():
     assert np.all(it10 == 1) and np.all(it5 == 1)       # homogeneous: A == B
     assert e5 < 0.04
     assert 3.3 < e10 / e5 < 5.0                           # O(h^2)
+
+
+def test_radial_preconditioner_is_A_for_an_r_only_medium():
+    # kappa, rho depending on r only: the radial B equals A (PCG takes one iteration); constant
+    # radii give the whole-medium B
+    nr, nz, hr, hz, h = 11, 9, 5.0, 4.0, 400.0
+    kappa = np.repeat(RNG.uniform(2e9, 9e9, nr)[:, None], nz, axis=1)
+    rho = np.repeat(RNG.uniform(1000, 2600, nr)[:, None], nz, axis=1)
+    a1, a2, w = cyl.coefficients(kappa, rho, hr, hz, h)
+    kr, dr = cyl.precond_params_radial(kappa, rho, h)
+    y = RNG.standard_normal((nr, nz))
+    assert np.abs(cyl.apply_inverse_radial(cyl.apply_A(y, a1, a2, w, hr, hz), hr, hz, kr, dr) - y).max() < 1e-11
+    kt, dt = 4e9, 3e7
+    r = RNG.standard_normal((2, nr, nz))
+    a = cyl.apply_inverse_radial(r, hr, hz, np.full(nr, kt), np.full(nr, dt))
+    b = cyl.apply_inverse(r, hr, hz, kt, dt)
+    assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
