@@ -104,7 +104,9 @@ typedef struct {
   int layered;      /* 1: shots on Cartesian grids precondition with per-row midranges
                        (lag_precond_create_layered) instead of the whole-medium midranges of
                        Eq. 21 (acoustic) or Eq. 22 (elastic: B1, B2 with (l+2m)~(z), mu~(z),
-                       rho~(z)); cylindrical grids: 0 only                                       */
+                       rho~(z)); acoustic shots on cylindrical grids with per-radius midranges
+                       kappa~(r), rho~(r) (the DCT along z still separates); cylindrical
+                       elastic: 0 only                                                           */
 } lag_solver;
 typedef struct { int ix, iz; } lag_point;                          /* 0-based interior node        */
 typedef struct { double f0, t0, gamma; int kind; } lag_wavelet;
@@ -167,7 +169,11 @@ int  lag_precond_create_sep(lag_ctx *ctx, const lag_grid *grid, double ax_t, dou
  * top face carries no flux under a free surface).  For a medium whose kappa and rho depend on z
  * only, this operator equals A.  The factors are stored per partition (nz x nx values of each of
  * five factor arrays instead of 3 L x nx).  Everything else (apply, steps, layout, autotune) is
- * as for the other plans. */
+ * as for the other plans.
+ * Cylindrical grids (the radial variant): coefficients that vary with r only, arrays of nx values
+ * (one per radius): the r faces take a1 = rbar ax~_face (mean of the two radii, the outer face its
+ * radius's value), a2 = r az~(r), d(r) = r d~(r); the DCT-II along z still separates, and for a
+ * medium whose kappa and rho depend on r only the operator equals A. */
 int  lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double *ax_z,
                                 const double *az_z, const double *d_z, int prec, int partitions,
                                 lag_precond **out);

@@ -129,17 +129,31 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     // Eq. 21 with the cylindrical coefficients a1 = rbar ax, a2 = r az, d(r) = r d: after the
     // DCT-II along z, per z-mode q the system along r has the rows
     //   (-ax i/dr, ax (2i+1)/dr + r_i az mu_q + r_i d, -ax (i+1)/dr)   (r_i = (i + 1/2) dr)
-    if (layered != nullptr) throw Error(LAG_EINVAL, "the layered preconditioner is Cartesian only");
-    if (!(ax > 0) || !(az > 0) || !(d >= 0) || !(hoop >= 0))
-      throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+    // With per-radius rows (the radial variant: coefficients independent of z keep the DCT's
+    // separation) ax, az, d come from layered = [ax(r) | az(r) | d(r)], the r faces taking the
+    // mean of their two radii (the outer face its radius's value).
     const int nr = g.nz;
     const double dr = g.dz;
+    if (!(hoop >= 0)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+    if (layered == nullptr && (!(ax > 0) || !(az > 0) || !(d >= 0)))
+      throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+    auto AX = [&](int i) { return layered ? layered[i] : ax; };
+    auto AZ = [&](int i) { return layered ? layered[nr + i] : az; };
+    auto D = [&](int i) { return layered ? layered[2 * (size_t)nr + i] : d; };
+    if (layered)
+      for (int i = 0; i < nr; ++i)
+        if (!(AX(i) > 0) || !(AZ(i) > 0) || !(D(i) >= 0))
+          throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
     zr.resize(3 * (size_t)nr + 1);
-    for (int i = 0; i <= nr; ++i) zr[i] = ax * (double)i / dr;   // rbar ax / dr^2 with rbar = i dr
+    zr[0] = 0.0;  // the axis face: rbar = 0
+    for (int i = 1; i <= nr; ++i) {  // rbar a_face / dr^2 with rbar = i dr
+      const double af = (i < nr) ? 0.5 * (AX(i - 1) + AX(i)) : AX(nr - 1);
+      zr[i] = af * (double)i / dr;
+    }
     for (int i = 0; i < nr; ++i) {
       const double ri = (i + 0.5) * dr;
-      zr[nr + 1 + i] = ri * az;
-      zr[2 * nr + 1 + i] = ri * d + hoop / ri;
+      zr[nr + 1 + i] = ri * AZ(i);
+      zr[2 * nr + 1 + i] = ri * D(i) + hoop / ri;
     }
   } else if (hoop != 0.0) {
     throw Error(LAG_EINVAL, "the hoop term belongs to cylindrical grids");
@@ -362,11 +376,13 @@ int lag_precond_create_layered(lag_ctx *ctx, const lag_grid *grid, const double 
   return guarded(ctx, [&] {
     set_device(ctx);
     if (partitions < 0 || partitions > 32) throw Error(LAG_EINVAL, "partitions must be 0..32");
-    if (grid->nz < 1) throw Error(LAG_EINVAL, "bad grid");
-    std::vector<double> rows(3 * (size_t)grid->nz);
-    std::copy(ax_z, ax_z + grid->nz, rows.begin());
-    std::copy(az_z, az_z + grid->nz, rows.begin() + grid->nz);
-    std::copy(d_z, d_z + grid->nz, rows.begin() + 2 * (size_t)grid->nz);
+    // rows: depths of a Cartesian grid, radii (grid->nx) of a cylindrical one
+    const int nrow = grid->cylindrical ? grid->nx : grid->nz;
+    if (nrow < 1) throw Error(LAG_EINVAL, "bad grid");
+    std::vector<double> rows(3 * (size_t)nrow);
+    std::copy(ax_z, ax_z + nrow, rows.begin());
+    std::copy(az_z, az_z + nrow, rows.begin() + nrow);
+    std::copy(d_z, d_z + nrow, rows.begin() + 2 * (size_t)nrow);
     *out = precond_new(ctx, *grid, 0.0, 0.0, 0.0, prec, partitions, ctx->stream, rows.data());
   });
 }

@@ -175,6 +175,10 @@ void medium_build_cylindrical(lag_medium &m, const double *c_host, const double 
   // whole-medium midranges kappa~ and rho~ (footnote to Eq. 21; the r weights enter the plan)
   midrange_device(kap, n, mm, s);
   midrange_device(drho, n, mm + 2, s);
+  // per-radius extremes (the radial preconditioner): [kappa | rho][nr][min, max]
+  m.rowmm.alloc(m.ctx, 4 * (size_t)nr * sizeof(double));
+  row_minmax_device(kap, nzc, nr, m.rowmm.as<double>(), s);
+  row_minmax_device(drho, nzc, nr, m.rowmm.as<double>() + 2 * (size_t)nr, s);
   double h_mm[4];
   LAG_CUDA_CHECK(cudaMemcpyAsync(h_mm, mm, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   LAG_CUDA_CHECK(cudaStreamSynchronize(s));

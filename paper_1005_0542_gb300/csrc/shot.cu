@@ -65,10 +65,12 @@ lag_shot *shot_new(lag_ctx *ctx, const lag_grid &g, const double *c, const doubl
   cudaStream_t st = sh->stream;
   sh->medium = medium_new(ctx, g, c, vs, rho, lag.h, st);
   const double *mid = sh->medium->mid;
-  if (g.cylindrical && s.layered) throw Error(LAG_EINVAL, "the layered preconditioner is Cartesian only");
+  if (g.cylindrical && elastic && s.layered)
+    throw Error(LAG_EINVAL, "the layered preconditioner is acoustic only on cylindrical grids");
   if (!elastic && s.layered) {
-    // per-row midranges kappa~(z), rho~(z): ax = az = kappa~(z), d = rho~(z) h^2 / 4
-    const int nz = g.nz;
+    // per-row midranges kappa~(z), rho~(z): ax = az = kappa~(z), d = rho~(z) h^2 / 4 (cylindrical
+    // grids: per radius, the rows of the kernel grid)
+    const int nz = g.cylindrical ? g.nx : g.nz;
     std::vector<double> mm(4 * (size_t)nz), rows(3 * (size_t)nz);
     LAG_CUDA_CHECK(cudaMemcpyAsync(mm.data(), sh->medium->rowmm.ptr, mm.size() * sizeof(double),
                                    cudaMemcpyDeviceToHost, st));

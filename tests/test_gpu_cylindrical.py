@@ -212,9 +212,65 @@ def test_cylindrical_rejections(ctx):
     s = inputs.cylindrical(nr=16, nz=12, h=10.0, n_harm=2)
     rc, _, _ = _shot(ctx, s, L.LAG_FP64, 1e-8, free_surface=False)      # the half space has a surface
     assert rc == L.LAG_EINVAL
-    rc, _, _ = _shot(ctx, s, L.LAG_FP64, 1e-8, layered=1)               # layered is Cartesian only
-    assert rc == L.LAG_EINVAL
     g = L.grid(16, 12, 5.0, 5.0, cylindrical=True)
     p = C.c_void_p()
-    a_, pa = L.f64(np.ones(12))
-    assert L.lag_precond_create_layered(ctx, C.byref(g), pa, pa, pa, L.LAG_FP64, 0, C.byref(p)) == L.LAG_EINVAL
+    a_, pa = L.f64(np.ones(16))
+    z_, pz = L.f64(np.zeros(16))
+    # radial rows must be positive (d >= 0)
+    assert L.lag_precond_create_layered(ctx, C.byref(g), pz, pa, pa, L.LAG_FP64, 0, C.byref(p)) == L.LAG_EINVAL
+    assert L.lag_precond_create_layered(ctx, C.byref(g), pa, pz, pa, L.LAG_FP64, 0, C.byref(p)) == L.LAG_EINVAL
+
+
+@pytest.mark.parametrize("prec,tol", [(L.LAG_FP64, 1e-12), (L.LAG_MIXED, 2e-4)])
+@pytest.mark.parametrize("nr,nz", [(1, 1), (7, 2), (33, 17), (300, 257)])
+def test_radial_precond_apply(ctx, prec, tol, nr, nz):
+    # per-radius coefficients (the radial variant of the layered plan): against the oracle
+    hr, hz, h = 5.0, 4.0, 400.0
+    kappa = RNG.uniform(2e9, 9e9, (nr, nz))
+    rho = RNG.uniform(1000, 2600, (nr, nz))
+    kr, dr = cyl.precond_params_radial(kappa, rho, h)
+    g = L.grid(nr, nz, hr, hz, cylindrical=True)
+    p = C.c_void_p()
+    k_, pk = L.f64(kr)
+    d_, pd = L.f64(dr)
+    L.check(L.lag_precond_create_layered(ctx, C.byref(g), pk, pk, pd, prec, 0, C.byref(p)), ctx)
+    assert L.lag_precond_is_layered(p) == 1
+    r = RNG.standard_normal((2, nr, nz))
+    rd, zd = dev(r), empty(r.shape)
+    L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
+    assert rel(host(zd), cyl.apply_inverse_radial(r, hr, hz, kr, dr)) < tol
+    L.lag_precond_destroy(p)
+
+
+def _radial_model(nr, nz, h, n_harm, noise):
+    # velocity layered along r (the radial preconditioner's case) with optional lateral noise
+    s = inputs.cylindrical(nr=nr, nz=nz, h=h, n_harm=n_harm, layered=True)
+    rng = np.random.default_rng(77)
+    layers = (np.arange(nr) * 8) // nr
+    cr = rng.uniform(1500, 4500, 8)[layers]
+    s.c = np.repeat(cr[:, None], nz, axis=1) * (1 + noise * rng.standard_normal((nr, nz)))
+    s.rho = 310.0 * s.c ** 0.25
+    return s
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, 1e-13, 1e-10), (L.LAG_MIXED, 1e-11, 1e-8)])
+def test_radial_shot_matches_oracle(ctx, prec, tol, gate):
+    s = _radial_model(96, 64, 10.0, 8, 0.02)
+    s.sources = [(0, 3)]
+    s.receivers = [(i, 3) for i in range(0, 96, 8)]
+    rc, tr, its = _shot(ctx, s, prec, tol, layered=1)
+    L.check(rc, ctx)
+    ref = cyl.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, s.sources[0], s.receivers, s.t_out,
+                            s.f0, s.t0, tol=tol, wavelet="paper", radial=True)
+    assert rel_l2(tr, ref["traces"]) < gate
+    if prec == L.LAG_FP64:
+        assert np.abs(its - ref["iters"]).max() <= 1
+        _, _, its_c = _shot(ctx, s, prec, tol)
+        assert its.sum() < its_c.sum(), (its, its_c)
+
+
+def test_radial_shot_r_only_medium_one_iteration(ctx):
+    s = _radial_model(80, 48, 10.0, 6, 0.0)
+    rc, tr, its = _shot(ctx, s, L.LAG_FP64, 1e-10, layered=1)
+    L.check(rc, ctx)
+    assert np.all(its == 1), its
