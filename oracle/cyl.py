@@ -157,12 +157,15 @@ def precond_params_radial(kappa, rho, h):
     return kr, dr
 
 
-def apply_inverse_radial(rhs, hr, hz, kr, dr):
-    """y = B^{-1} rhs for the radial preconditioner; rhs [..., nr, nz]."""
+def apply_inverse_radial(rhs, hr, hz, kr, dr, kz=None):
+    """y = B^{-1} rhs for the radial preconditioner; rhs [..., nr, nz].  kr(r) gives the r faces
+    (a1 = rbar kr_face), kz(r) the z part (a2 = r kz; kz = kr when omitted, as Eq. 21 has one
+    kappa~), dr(r) the mass term (d = r dr)."""
     rhs = np.asarray(rhs, dtype=np.float64)
     nr, nz = rhs.shape[-2:]
     kr = np.asarray(kr, dtype=np.float64)
     dr = np.asarray(dr, dtype=np.float64)
+    kz = kr if kz is None else np.asarray(kz, dtype=np.float64)
     V = dct_matrix(nz)
     mu = neumann_eigenvalues(nz, hz)
     r, _ = mesh(nr, nz, hr, hz)
@@ -174,7 +177,7 @@ def apply_inverse_radial(rhs, hr, hz, kr, dr):
     extra = (1,) * (rhs.ndim - 2)
     sub = (-a1[:nr]).reshape((nr,) + extra + (1,))
     sup = (-a1[1:]).reshape((nr,) + extra + (1,))
-    diag = (a1[:nr] + a1[1:])[:, None] + (r * kr)[:, None] * mu[None, :] + (r * dr)[:, None]
+    diag = (a1[:nr] + a1[1:])[:, None] + (r * kz)[:, None] * mu[None, :] + (r * dr)[:, None]
     diag = diag.reshape((nr,) + extra + (nz,))
     yh = rhs @ V
     col = np.moveaxis(yh, -2, 0)

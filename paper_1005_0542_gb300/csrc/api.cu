@@ -134,16 +134,16 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     // mean of their two radii (the outer face its radius's value).
     const int nr = g.nz;
     const double dr = g.dz;
-    if (!(hoop >= 0)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
-    if (layered == nullptr && (!(ax > 0) || !(az > 0) || !(d >= 0)))
-      throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+    if (!(hoop >= 0) || !std::isfinite(hoop)) throw Error(LAG_EINVAL, "preconditioner coefficients must be positive and finite");
+    if (layered == nullptr && (!(ax > 0) || !(az > 0) || !(d >= 0) || !std::isfinite(ax + az + d)))
+      throw Error(LAG_EINVAL, "preconditioner coefficients must be positive and finite");
     auto AX = [&](int i) { return layered ? layered[i] : ax; };
     auto AZ = [&](int i) { return layered ? layered[nr + i] : az; };
     auto D = [&](int i) { return layered ? layered[2 * (size_t)nr + i] : d; };
     if (layered)
       for (int i = 0; i < nr; ++i)
-        if (!(AX(i) > 0) || !(AZ(i) > 0) || !(D(i) >= 0))
-          throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+        if (!(AX(i) > 0) || !(AZ(i) > 0) || !(D(i) >= 0) || !std::isfinite(AX(i) + AZ(i) + D(i)))
+          throw Error(LAG_EINVAL, "per-radius preconditioner coefficients must be positive and finite");
     zr.resize(3 * (size_t)nr + 1);
     zr[0] = 0.0;  // the axis face: rbar = 0
     for (int i = 1; i <= nr; ++i) {  // rbar a_face / dr^2 with rbar = i dr
@@ -176,8 +176,8 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
     }
     ax = az = d = 0.0;
   }
-  if (!g.cylindrical && layered == nullptr && (!(ax > 0) || !(az > 0) || !(d >= 0))) {
-    throw Error(LAG_EINVAL, "preconditioner coefficients must be positive");
+  if (!g.cylindrical && layered == nullptr && (!(ax > 0) || !(az > 0) || !(d >= 0) || !std::isfinite(ax + az + d))) {
+    throw Error(LAG_EINVAL, "preconditioner coefficients must be positive and finite");
   }
   if (prec != LAG_FP64 && prec != LAG_MIXED) throw Error(LAG_EINVAL, "prec must be LAG_FP64 or LAG_MIXED");
   std::unique_ptr<lag_precond> p(new lag_precond());
@@ -189,6 +189,7 @@ lag_precond *lag::precond_new(lag_ctx *ctx, const lag_grid &gu, double ax, doubl
   p->d = d;
   p->dst_store.ctx = p->tri_store.ctx = p->tri32_store.ctx = p->scratch.ctx = p->tc_scratch.ctx = ctx;
   p->zrows.ctx = ctx;
+  p->layered = layered != nullptr;
   const bool gen = !zr.empty();
   if (gen) {
     p->zrows.alloc(ctx, zr.size() * sizeof(double));
@@ -399,7 +400,7 @@ int lag_precond_create_cyl(lag_ctx *ctx, const lag_grid *grid, double ax_t, doub
   });
 }
 
-int lag_precond_is_layered(const lag_precond *p) { return (p && p->zrows.ptr) ? 1 : 0; }
+int lag_precond_is_layered(const lag_precond *p) { return (p && p->layered) ? 1 : 0; }
 
 void lag_precond_destroy(lag_precond *p) {
   if (!p) return;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 
@@ -26,6 +27,25 @@ struct Error : public std::runtime_error {
   } while (0)
 
 #define LAG_LAUNCH_CHECK() LAG_CUDA_CHECK(cudaGetLastError())
+
+// One-time set-up that belongs to a device (kernel attributes, constant memory): runs f once per
+// device, on the device current at the call, under a mutex (several host threads may make the first
+// calls).  f throws on failure and is then retried by the next call.
+struct PerDeviceOnce {
+  std::mutex mu;
+  uint64_t done[4] = {0, 0, 0, 0};  // one bit per device ordinal (256 devices)
+  template <typename F>
+  void run(F &&f) {
+    int dev = 0;
+    LAG_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) throw Error(-5, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done[dev >> 6] & bit) return;
+    f();
+    done[dev >> 6] |= bit;
+  }
+};
 
 // Count of the library's kernel launches (process-wide, for launch accounting).
 // While a thread captures a CUDA graph its launches are not counted (the graph's kernel nodes

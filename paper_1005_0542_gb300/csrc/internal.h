@@ -190,7 +190,8 @@ struct lag_precond {
   lag_grid grid{};
   int prec = LAG_FP64;
   double ax = 0, az = 0, d = 0;
-  lag::DevBuf zrows;        // layered plans: z-face / per-row coefficients (see lag::TriCoef)
+  lag::DevBuf zrows;        // general z-systems: z-face / per-row coefficients (see lag::TriCoef)
+  bool layered = false;     // built from per-row (or per-radius) midranges, not the whole medium's
   lag::TriCoef coef() const;
   lag::DstPlan dst;
   lag::TriFactors tri64, tri32;

@@ -556,12 +556,11 @@ void dst_build_tc(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
 template <int NPROD>
 static void gemm_launch_n(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
                           int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(dst_tc_gemm_kernel<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         TcCfg<NPROD>::SMEM));
-    attr = true;
-  }
+  });
   const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
   const int ntiles = 2 * nmt * nnt;
   const int grid = std::min(ntiles, 152);
@@ -1219,13 +1218,12 @@ __global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__res
 template <int NB, int NS>
 static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
                          cudaStream_t s, int inv) {
-  static bool attr = false;
-  if (!attr) {
+  static PerDeviceOnce attr;
+  attr.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         2 * OZ_PACK_MAXK * (int)sizeof(double)));
-    attr = true;
-  }
+  });
   const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
   const size_t a_slice = (size_t)nmt * nks * A_TILE;
   uint8_t *apack = dp.tc_scratch;

@@ -630,14 +630,13 @@ static void gauss_legendre16(double *x, double *w) {
 
 void source_coeffs_device(const lag_laguerre &lag, const lag_wavelet &w, double *fm_dev, DevBuf &scratch,
                           lag_ctx *ctx, cudaStream_t s) {
-  static bool gl_done = false;
-  if (!gl_done) {
+  static PerDeviceOnce gl_done;  // constant memory belongs to each device
+  gl_done.run([] {
     double x[16], wt[16];
     gauss_legendre16(x, wt);
     LAG_CUDA_CHECK(cudaMemcpyToSymbol(c_gl_x, x, sizeof(x)));
     LAG_CUDA_CHECK(cudaMemcpyToSymbol(c_gl_w, wt, sizeof(wt)));
-    gl_done = true;
-  }
+  });
   const int n = lag.n_harm;
   const double t_end = (w.kind == LAG_WAVELET_PAPER) ? w.t0 + 2.0 * w.gamma / w.f0 : w.t0 + 4.0 / w.f0;
   int panels = 4 * n + (int)(8.0 * lag.h * t_end / 16.0) + 64;

@@ -559,12 +559,11 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T
 template <typename T, int L, int MT, bool GEN>
 static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
                               cudaStream_t s, int pstride, int poff, int ncomp) {
-  static bool attr_done = false;
-  if (!attr_done) {
+  static PerDeviceOnce attr_done;
+  attr_done.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT, GEN>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_done = true;
-  }
+  });
   // several right-hand sides per CTA when there are plenty of CTAs anyway (factor reuse)
   const int ctas_x = (tf.nx + MT - 1) / MT;
   int per_cta = 1;
@@ -603,11 +602,10 @@ template <typename T>
 static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
                        cudaStream_t s, int pstride, int poff, int ncomp) {
   if (nrhs <= 0) return;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static PerDeviceOnce attr_done;
+  attr_done.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_done = true;
-  }
+  });
   ProfScope prof(sizeof(T) == 8 ? KC_TRI64 : KC_TRI32, s);
   if (tf.reg) {
     switch (tf.L) {

@@ -229,17 +229,42 @@ def test_radial_precond_apply(ctx, prec, tol, nr, nz):
     kappa = RNG.uniform(2e9, 9e9, (nr, nz))
     rho = RNG.uniform(1000, 2600, (nr, nz))
     kr, dr = cyl.precond_params_radial(kappa, rho, h)
+    kz = kr * RNG.uniform(0.5, 2.0, nr)   # a z coefficient apart from the r-face one
     g = L.grid(nr, nz, hr, hz, cylindrical=True)
     p = C.c_void_p()
     k_, pk = L.f64(kr)
+    kz_, pkz = L.f64(kz)
     d_, pd = L.f64(dr)
-    L.check(L.lag_precond_create_layered(ctx, C.byref(g), pk, pk, pd, prec, 0, C.byref(p)), ctx)
+    L.check(L.lag_precond_create_layered(ctx, C.byref(g), pk, pkz, pd, prec, 0, C.byref(p)), ctx)
     assert L.lag_precond_is_layered(p) == 1
     r = RNG.standard_normal((2, nr, nz))
     rd, zd = dev(r), empty(r.shape)
     L.check(L.lag_precond_apply(p, ptr(rd), ptr(zd), 2), ctx)
-    assert rel(host(zd), cyl.apply_inverse_radial(r, hr, hz, kr, dr)) < tol
+    assert rel(host(zd), cyl.apply_inverse_radial(r, hr, hz, kr, dr, kz=kz)) < tol
     L.lag_precond_destroy(p)
+
+
+def test_whole_medium_cylindrical_plans_are_not_layered(ctx):
+    # only lag_precond_create_layered plans report themselves as layered
+    g = L.grid(24, 16, 5.0, 4.0, cylindrical=True)
+    p = C.c_void_p()
+    L.check(L.lag_precond_create(ctx, C.byref(g), 4e9, 1500.0, 400.0, L.LAG_FP64, C.byref(p)), ctx)
+    assert L.lag_precond_is_layered(p) == 0
+    L.lag_precond_destroy(p)
+    L.check(L.lag_precond_create_cyl(ctx, C.byref(g), 9e9, 3e9, 1500.0 * 400.0 ** 2 / 4, 9e9, L.LAG_FP64, 0,
+                                     C.byref(p)), ctx)
+    assert L.lag_precond_is_layered(p) == 0
+    L.lag_precond_destroy(p)
+    gc = L.grid(24, 16, 5.0, 4.0)
+    L.check(L.lag_precond_create(ctx, C.byref(gc), 4e9, 1500.0, 400.0, L.LAG_FP64, C.byref(p)), ctx)
+    assert L.lag_precond_is_layered(p) == 0
+    L.lag_precond_destroy(p)
+    # a non-finite per-radius coefficient is rejected like the Cartesian layered rows
+    a_, pa = L.f64(np.full(24, 4e9))
+    i_ = np.full(24, 4e9)
+    i_[5] = np.inf
+    ib_, pi = L.f64(i_)
+    assert L.lag_precond_create_layered(ctx, C.byref(g), pi, pa, pa, L.LAG_FP64, 0, C.byref(p)) == L.LAG_EINVAL
 
 
 def _radial_model(nr, nz, h, n_harm, noise):

@@ -147,3 +147,25 @@ def test_radial_preconditioner_is_A_for_an_r_only_medium():
     a = cyl.apply_inverse_radial(r, hr, hz, np.full(nr, kt), np.full(nr, dt))
     b = cyl.apply_inverse(r, hr, hz, kt, dt)
     assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
+
+
+def test_radial_preconditioner_keeps_the_r_and_z_coefficients_apart():
+    # separate per-radius coefficients for the r faces (a1 = rbar ax~, mean of the two radii at a
+    # face, the outer face its radius's value) and for the z direction (a2 = r az~, zero-flux
+    # surface and bottom): with nothing depending on z the DCT-II along z separates exactly, so
+    # B^{-1} inverts the operator assembled from those faces; swapping ax~ and az~ does not
+    nr, nz, hr, hz = 13, 10, 5.0, 4.0
+    ax = RNG.uniform(2e9, 9e9, nr)
+    az = RNG.uniform(2e9, 9e9, nr)
+    dd = RNG.uniform(1e6, 5e7, nr)
+    r, _ = cyl.mesh(nr, nz, hr, hz)
+    rbar = np.arange(nr + 1) * hr
+    af = np.concatenate([[0.0], 0.5 * (ax[:-1] + ax[1:]), [ax[-1]]])
+    a1 = np.repeat((rbar * af)[:, None], nz, axis=1)
+    a2 = np.zeros((nr, nz + 1))
+    a2[:, 1:nz] = (r * az)[:, None]
+    w = np.repeat((r * dd)[:, None], nz, axis=1)
+    y = RNG.standard_normal((2, nr, nz))
+    Ay = cyl.apply_A(y, a1, a2, w, hr, hz)
+    assert np.abs(cyl.apply_inverse_radial(Ay, hr, hz, ax, dd, kz=az) - y).max() < 1e-11
+    assert np.abs(cyl.apply_inverse_radial(Ay, hr, hz, az, dd, kz=ax) - y).max() > 1e-3

@@ -12,6 +12,7 @@ import os
 
 import numpy as np
 import pytest
+import torch
 
 from paper_1005_0542_gb300 import lagwave as L
 
@@ -43,7 +44,16 @@ def test_static_apply_matches_regular_apply_twice():
             rd, z_tc, z_simt, z_sta = dev(r), empty(r.shape), empty(r.shape), empty(r.shape)
             L.check(L.lag_precond_apply(p, ptr(rd), ptr(z_tc), nrhs), ctx)
             L.check(L.lag_precond_apply(q, ptr(rd), ptr(z_simt), nrhs), ctx)
+            torch.cuda.synchronize()
+            held = L.lag_bytes_in_use(ctx)
+            free0 = torch.cuda.mem_get_info()[0]
             L.check(L.lag_precond_apply_static(p, ptr(rd), ptr(z_sta), nrhs), ctx)
+            torch.cuda.synchronize()
+            # nothing allocated: the library's ledger is unchanged, and after the first call's
+            # one-time set-up the device's free memory is too
+            assert L.lag_bytes_in_use(ctx) == held
+            if call > 0:
+                assert torch.cuda.mem_get_info()[0] == free0
             a = host(z_sta)
             assert np.array_equal(a, host(z_simt))   # same kernels, same order: identical bits
             assert rel(a, host(z_tc)) < TOL64
