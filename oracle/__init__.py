@@ -14,7 +14,9 @@ Modules and what they follow (paper sections / equations):
 
 * ``fd``        -- Sec. 2.3, Eqs. (15)-(18): conservative 5-point operator A (Cartesian reading),
                    Eq. (19) elastic operator C (plane-strain reading: the paper only says
-                   "finite volume, second order"; parity unpinned beyond symmetry/limits).
+                   "finite volume, second order"); pinned by symmetry, positivity, an O(h^2)
+                   manufactured solution, and through whole elastic shots that converge at O(h^2)
+                   to the plane-strain line-force solution (``analytic.line_force_2d``).
 * ``dst``       -- Sec. 2.4 variable separation along x: orthonormal DST-I by its definition.
 * ``tridiag``   -- Thomas algorithm (the sequential reference for the Dichotomy solve, Sec. 1).
 * ``precond``   -- Sec. 2.4, Eqs. (21)-(22): Laplace preconditioner B with midrange coefficients
@@ -23,7 +25,8 @@ Modules and what they follow (paper sections / equations):
 * ``laguerre``  -- Sec. 2.1, Eqs. (7)-(9): Laguerre functions, forward transform of the source,
                    the spectral recurrence, inverse summation.
 * ``solve``     -- Sec. 2.1-2.2: whole harmonic loop for one shot (acoustic, elastic).
-* ``analytic``  -- closed-form solutions used as pins (2D point source, scalar oscillator).
+* ``analytic``  -- closed-form solutions used as pins (2D point source, 3D point source and point
+                   force, 2D line force in plane strain, scalar oscillator).
 
 Readings of silent / garbled passages are stated in each function's docstring.
 """

@@ -23,6 +23,21 @@
           + g_i g_z / (4 pi rho alpha^2 R) f(t - R/alpha) - (g_i g_z - d_iz) / (4 pi rho beta^2 R) f(t - R/beta).
   Returned as the radial (i = r, d_rz = 0) and vertical (i = z) components about the force axis.
 
+* ``line_force_2d``: homogeneous isotropic elastic medium in plane strain,
+  rho u_tt = div sigma + e_z delta(x - x0) f(t) (a vertical line force, the Cartesian source of
+  Eq. 12), zero initial data.  Derived here (the paper prints no Cartesian elastic solution): split
+  the force as e_z delta = grad div(e_z G0) - curl curl(e_z G0) with Lap G0 = delta; each part
+  propagates with its own speed, u = (1/rho) [grad div(e_z (h_P - h_S)) + e_z g_S], where g_c is
+  the 2D wave Green's function (g_tt - c^2 Lap g = delta(x) delta(t): g = H(ct - r) / (2 pi c
+  sqrt(c^2 t^2 - r^2))) and Lap h_c = g_c.  For radial h, the Hessian is
+  h'' g_i g_j + (h'/r)(d_ij - g_i g_j) with (r h')' = r g, which gives, with
+  gamma = (x - x0)/r, alpha / beta the P / S speeds,
+      rho u_i = g_i g_z (g_P * f) + (d_iz - g_i g_z) (g_S * f) + (d_iz - 2 g_i g_z) (K * f),
+      K(r, t) = [H(beta t - r) sqrt(t^2 - r^2/beta^2) - H(alpha t - r) sqrt(t^2 - r^2/alpha^2)] / (2 pi r^2)
+  (* a convolution in time).  (1/rho) g_c * f is point_source_2d with kappa = rho c^2; the K terms
+  take the same substitution tau = t - r/c - s^2, under which sqrt((t - tau)^2 - r^2/c^2) d tau
+  becomes 2 s^2 sqrt(2r/c + s^2) ds.
+
 * ``oscillator``: one mode of the semi-discrete problem, rho u'' + q u = f(t), u(0)=u'(0)=0:
       u(t) = 1/(rho w) int_0^t sin(w (t - tau)) f(tau) d tau,  w = sqrt(q/rho).
   Its Laguerre coefficients must satisfy the scalar form of the spectral recurrence (Eq. 9):
@@ -83,6 +98,39 @@ def point_force_3d(r, dz, t, lam, mu, rho, fun, order=24, panels=16):
     uz = (c * (3.0 * gz * gz - 1.0) / R ** 3 * near + c * gz * gz / (a * a * R) * fa
           - c * (gz * gz - 1.0) / (b * b * R) * fb)
     return ur, uz
+
+
+def _wake_integral(r, t, c, fun, panels=64, order=8):
+    """int_0^{t - r/c} sqrt((t - tau)^2 - r^2/c^2) f(tau) d tau for scalar r > 0 and an array of t."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    out = np.zeros_like(t)
+    for j, tj in enumerate(t):
+        smax2 = tj - r / c
+        if smax2 <= 0.0:
+            continue
+        edges = np.linspace(0.0, math.sqrt(smax2), panels + 1)
+        acc = 0.0
+        for a, b in zip(edges[:-1], edges[1:]):
+            s, w = _gl(a, b, order)
+            acc += np.sum(w * 2.0 * s * s * np.sqrt(2.0 * r / c + s * s) * fun(tj - r / c - s * s))
+        out[j] = acc
+    return out
+
+
+def line_force_2d(dx, dz, t, lam, mu, rho, fun, panels=64, order=8):
+    """(u_x, u_z) at the offset (dx, dz) from a vertical line force (r > 0), array t."""
+    a = math.sqrt((lam + 2.0 * mu) / rho)
+    b = math.sqrt(mu / rho)
+    r = math.hypot(dx, dz)
+    gx, gz = dx / r, dz / r
+    nodes = panels * order
+    gp = point_source_2d(r, t, lam + 2.0 * mu, rho, fun, nodes=nodes, panels=panels)   # (1/rho) g_P * f
+    gs = point_source_2d(r, t, mu, rho, fun, nodes=nodes, panels=panels)               # (1/rho) g_S * f
+    kf = (_wake_integral(r, t, b, fun, panels, order) - _wake_integral(r, t, a, fun, panels, order)) / (
+        2.0 * math.pi * r * r * rho)                                                     # (1/rho) K * f
+    ux = gx * gz * gp - gx * gz * gs - 2.0 * gx * gz * kf
+    uz = gz * gz * gp + (1.0 - gz * gz) * gs + (1.0 - 2.0 * gz * gz) * kf
+    return ux, uz
 
 
 def oscillator(t, q, rho, fun, panels=256, order=16):
