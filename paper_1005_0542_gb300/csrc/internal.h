@@ -162,6 +162,13 @@ size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows);
 // E / O sums (plan scratch), butterfly into y
 void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
                   const KrylovScalars *sc, cudaStream_t s, bool inverse = false);
+// DST-I plans (S^2 = I): y = S x as above for nrhs systems of rpr rows, and PCG's (r, y) with beta
+// (Fletcher-Reeves, 0 on a solve's first iteration) into sc; rzpart: scratch of
+// nrhs * rpr * dst_oz_rz_parts(dp) doubles
+bool dst_oz_rz_fusable(const DstPlan &dp);
+size_t dst_oz_rz_parts(const DstPlan &dp);
+void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, int rpr, KrylovScalars *sc,
+                     const double *r, double *rzpart, cudaStream_t s);
 // mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
                        const KrylovScalars *sc, cudaStream_t s, bool rscale = false);
@@ -269,17 +276,19 @@ void elastic_apply(const lag_medium &m, const double *p, double *q, int nrhs,
 
 int reduce_blocks(size_t n);  // blocks per rhs of the vector kernels for n values per rhs
 
-// PCG pieces (per rhs, n values each)
-void pcg_start(const double *b, double *x, double *r, size_t n, int nrhs, double tol,
+// p_new = z + beta p_old, q = A p_new, (p_new, q) -> alpha (PCG's direction update and operator in
+// one pass; p_new and p_old are different buffers)
+void acoustic_apply_dir(const lag_medium &m, const double *z, const double *pold, double *pnew, double *q,
+                        int nrhs, const KrylovScalars *sc, const Reduce &red, cudaStream_t s);
+
+// PCG pieces (per rhs, n values each).  One iteration: z = B^{-1} r and beta (0 on the first), the
+// direction update with q = A p and alpha, then x, r and the convergence test.
+void pcg_start(const double *b, double *x, double *r, double *p, size_t n, int nrhs, double tol,
                KrylovScalars *sc, const Reduce &red, cudaStream_t s);
-void pcg_rz_p(const double *r, const double *z, double *p, size_t n, int nrhs,
-              KrylovScalars *sc, const Reduce &red, cudaStream_t s);
 void pcg_update_xr(double *x, double *r, const double *p, const double *q, size_t n, int nrhs,
                    int max_iter, KrylovScalars *sc, const Reduce &red, cudaStream_t s);
 void pcg_beta(const double *r, const double *z, const double *q, size_t n, int nrhs, int flexible,
               KrylovScalars *sc, const Reduce &red, cudaStream_t s);
-void pcg_update_p(double *p, const double *z, size_t n, int nrhs, const KrylovScalars *sc,
-                  cudaStream_t s);
 
 // FGMRES pieces: vectors of n values per rhs; V, Z: [k+1][nrhs][n] bases; H: [nrhs][(k+1)*k]
 struct GmresDev {
@@ -304,10 +313,11 @@ void source_coeffs_device(const lag_laguerre &lag, const lag_wavelet &w, double 
                           DevBuf &scratch, lag_ctx *ctx, cudaStream_t s);
 void laguerre_table_device(const lag_laguerre &lag, int nt, const double *t_dev, double *tab_dev,
                            cudaStream_t s);
-// r = -c_m rho h^2 S (+ f_m/(dx dz) at each source), x = 0, ||r||^2 -> sc.bb; per rhs/comp.
+// r = -c_m rho h^2 S (+ f_m/(dx dz) at each source), x = 0, p = 0 (p nullable), ||r||^2 -> sc.bb;
+// per rhs/comp.
 void laguerre_rhs(const double *rho_h2, const double *S, double cm, const double *fm, int m,
                   const int *src_idx, int src_comp, double inv_cell, int ncomp, size_t nplane,
-                  int nrhs, double *r, double *x, double tol, KrylovScalars *sc,
+                  int nrhs, double *r, double *x, double *p, double tol, KrylovScalars *sc,
                   const Reduce &red, cudaStream_t s);
 void laguerre_accumulate(const double *x, double *T, double *S, double chat, size_t n, int nrhs,
                          cudaStream_t s);

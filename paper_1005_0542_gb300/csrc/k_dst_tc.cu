@@ -506,9 +506,10 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
     KrylovScalars &S = sc[rhs];
     const double rz_new = tot[0];
     S.zq = tot[1];
-    S.beta = flexible ? (-S.alpha * tot[1] / S.rz) : (rz_new / S.rz);
+    // the first direction of a solve is z itself (beta = 0)
+    S.beta = (S.iters == 0) ? 0.0 : (flexible ? (-S.alpha * tot[1] / S.rz) : (rz_new / S.rz));
     S.rz = rz_new;
-    if (!isfinite(S.beta)) S.state = ST_NAN;
+    if (!isfinite(S.beta) || !isfinite(rz_new) || !isfinite(tot[1])) S.state = ST_NAN;
   }
 }
 
@@ -799,9 +800,12 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
                                                                     int gather) {
   extern __shared__ double fold_sm[];  // [2][nks * TK]: u then v
   const int row = blockIdx.x;
-  // rows of finished right-hand sides and the padding rows of the last tile pack as zeros (exact
-  // zero outputs; the GEMM may still cover them in a tile shared with running rows)
-  const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
+  // rows of finished right-hand sides keep whatever slices they had: the GEMM may still cover them
+  // in a tile shared with running rows, but nothing reads those rows' outputs any more (their
+  // values stay finite: slices are bounded integers)
+  if (row < rows && sc != nullptr && sc[row / rpr].state != ST_RUN) return;
+  // the padding rows of the last tile pack as zeros
+  const bool live = row < rows;
   const double *xr = x + (size_t)(row < rows ? row : 0) * n;
   const bool odd_n = (n & 1) != 0;
   const int kp = nks * TK;
@@ -886,7 +890,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
                                                          const int *__restrict__ erow, int eB, int nks, int nmt,
                                                          int nnt, int rows, double *__restrict__ y, int ld, int ku,
                                                          int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
-                                                         int rpr, int *__restrict__ err, int inv) {
+                                                         int rpr, int *__restrict__ err, int inv,
+                                                         const double *__restrict__ rdot, double *__restrict__ rzpart) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -1073,11 +1078,25 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
 #pragma unroll
           for (int q = 0; q < 64; ++q)
             if (q < ncols) yp[q] = scale * (unit * __ll2double_rn(acci[q]));
-        } else {
+        } else if (rzpart == nullptr) {
           double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
 #pragma unroll
           for (int q = 0; q < 64; ++q)
             if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
+        } else {
+          // the CG dot (r, z) of the values just formed, one partial per (row, parity, column tile,
+          // half): PCG's beta without another sweep over r and z
+          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+          const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
+          double dacc = 0.0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) {
+              const double v = scale * (unit * __ll2double_rn(acci[q]));
+              yp[2 * q] = v;
+              dacc = fma(__ldg(rp + 2 * q), v, dacc);
+            }
+          rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dacc;
         }
       }
     }
@@ -1215,9 +1234,37 @@ __global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__res
   }
 }
 
+// PCG's (r, z) and beta from the exact-slice GEMM's partials: one block per right-hand side sums its
+// rows' partials of the column tiles that exist (fixed order: deterministic, and the same alone or
+// in a batch); beta = rz_new / rz (Fletcher-Reeves), 0 on the first iteration of a solve.
+__global__ void __launch_bounds__(256) oz_rz_beta_kernel(const double *__restrict__ part, int rpr, int nnt, int ku,
+                                                         int kv, KrylovScalars *sc) {
+  const int rhs = blockIdx.x;
+  if (sc[rhs].state != ST_RUN) return;
+  const int np = 4 * nnt;
+  const double *pr = part + (size_t)rhs * rpr * np;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < rpr * np; e += blockDim.x) {
+    const int rl = e / np, sl = e - rl * np;
+    const int h = sl & 1, tile = sl >> 1;
+    const int par = tile / nnt, nt = tile - par * nnt;
+    if (nt * OZ_TN + h * 64 < (par ? kv : ku)) acc += pr[(size_t)rl * np + sl];
+  }
+  double v1[1] = {acc};
+  __shared__ double sh[32];
+  block_sum<1>(v1, sh);
+  if (threadIdx.x == 0) {
+    KrylovScalars &S = sc[rhs];
+    const double rz_new = v1[0];
+    S.beta = (S.iters == 0) ? 0.0 : rz_new / S.rz;
+    S.rz = rz_new;
+    if (!isfinite(S.beta) || !isfinite(rz_new)) S.state = ST_NAN;
+  }
+}
+
 template <int NB, int NS>
 static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
-                         cudaStream_t s, int inv) {
+                         cudaStream_t s, int inv, const double *rdot = nullptr, double *rzpart = nullptr) {
   static PerDeviceOnce attr;
   attr.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
@@ -1241,7 +1288,7 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
       (reinterpret_cast<uintptr_t>(erow + 2 * (size_t)nmt * TM) + 255) & ~(uintptr_t)255);
   oz_gemm_kernel<NB, NS><<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
                                                     erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,
-                                                    dp.kv, sch, sc, rpr, dp.tc_err, inv);
+                                                    dp.kv, sch, sc, rpr, dp.tc_err, inv, rdot, rzpart);
   count_launch();
   LAG_LAUNCH_CHECK();
   if (inv) {
@@ -1258,6 +1305,24 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
   const int inv = (inverse && dp.kind == 1) ? 1 : 0;
   if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, inv);
   else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, inv);
+}
+
+bool dst_oz_rz_fusable(const DstPlan &dp) { return dp.oz && dp.kind == 0; }
+size_t dst_oz_rz_parts(const DstPlan &dp) { return 4 * (size_t)dp.npad_u; }
+
+void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, int rpr, KrylovScalars *sc,
+                     const double *r, double *rzpart, cudaStream_t s) {
+  const int rows = nrhs * rpr;
+  if (rows <= 0) return;
+  {
+    ProfScope prof(KC_DST64, s);
+    if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
+    else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
+  }
+  ProfScope prof(KC_VEC, s);
+  oz_rz_beta_kernel<<<nrhs, 256, 0, s>>>(rzpart, rpr, dp.npad_u, dp.ku, dp.kv, sc);
+  count_launch();
+  LAG_LAUNCH_CHECK();
 }
 
 }  // namespace lag

@@ -234,6 +234,69 @@ __global__ void __launch_bounds__(256) acoustic_apply_kernel(const double *__res
   }
 }
 
+// The CG direction update fused with the operator (Sec. 2.3): p_new = z + beta p_old (beta of the
+// right-hand side's record, 0 on its first iteration), q = A p_new and (p_new, q) -> alpha = rz / pq.
+// p_new goes to a buffer of its own because neighbouring tiles still read p_old for their halos.
+// 32 x 8 point tiles as above; a tile's p_new with its one-point halo is formed in shared memory
+// (the same fma(beta, p_old, z) per point as a separate update would take, and the same stencil
+// arithmetic in the same order), so the results equal those of the two separate passes bit for bit.
+__global__ void __launch_bounds__(256) acoustic_apply_dir_kernel(const double *__restrict__ z,
+                                                                 const double *__restrict__ pold,
+                                                                 double *__restrict__ pnew, double *__restrict__ q,
+                                                                 int nx, int nz, const double *__restrict__ ax,
+                                                                 const double *__restrict__ az,
+                                                                 const double *__restrict__ dg, KrylovScalars *sc,
+                                                                 Reduce red) {
+  const int b = blockIdx.y;
+  if (sc[b].state != ST_RUN) return;
+  const double beta = sc[b].beta;
+  const int tx = (nx + 31) / 32, tz = (nz + 7) / 8;
+  const size_t plane = (size_t)nx * nz;
+  const double *zb = z + (size_t)b * plane, *pob = pold + (size_t)b * plane;
+  double *pnb = pnew + (size_t)b * plane, *qb = q + (size_t)b * plane;
+  __shared__ double sp[10][34];
+  const int lx = threadIdx.x & 31, lz = threadIdx.x >> 5;
+  double dot = 0.0;
+  for (int t = blockIdx.x; t < tx * tz; t += gridDim.x) {
+    const int i0 = (t % tx) * 32, k0 = (t / tx) * 8;
+    __syncthreads();  // the previous tile is finished with sp
+    for (int e = threadIdx.x; e < 10 * 34; e += 256) {
+      const int hz = e / 34, hx = e - hz * 34;
+      const int i = i0 + hx - 1, k = k0 + hz - 1;
+      double v = 0.0;  // Dirichlet: p = 0 outside the grid
+      if (i >= 0 && i < nx && k >= 0 && k < nz) {
+        const size_t o = (size_t)k * nx + i;
+        v = fma(beta, pob[o], zb[o]);
+      }
+      sp[hz][hx] = v;
+    }
+    __syncthreads();
+    const int i = i0 + lx, k = k0 + lz;
+    if (i < nx && k < nz) {
+      const size_t o = (size_t)k * nx + i;
+      const size_t fx = (size_t)k * (nx + 1) + i;
+      const double pc = sp[lz + 1][lx + 1];
+      double v = dg[o] * pc;
+      v = fma(-ax[fx], sp[lz + 1][lx], v);
+      v = fma(-ax[fx + 1], sp[lz + 1][lx + 2], v);
+      v = fma(-az[o], sp[lz][lx + 1], v);
+      v = fma(-az[o + nx], sp[lz + 2][lx + 1], v);
+      pnb[o] = pc;
+      qb[o] = v;
+      dot = fma(pc, v, dot);
+    }
+  }
+  double v1[1] = {dot}, tot[1];
+  __shared__ double sh[32];
+  block_sum<1>(v1, sh);
+  if (publish_partials<1>(red, b, blockIdx.x, gridDim.x, v1, tot)) {
+    const double pq = tot[0];
+    sc[b].pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) sc[b].state = ST_NAN;
+    else sc[b].alpha = sc[b].rz / pq;
+  }
+}
+
 int stencil_blocks_per_rhs(int nx, int nz) {
   const int tiles = ((nx + 31) / 32) * ((nz + 7) / 8);
   return tiles < 1216 ? tiles : 1216;
@@ -252,15 +315,29 @@ void acoustic_apply(const lag_medium &m, const double *p, double *q, int nrhs, c
   LAG_LAUNCH_CHECK();
 }
 
+void acoustic_apply_dir(const lag_medium &m, const double *z, const double *pold, double *pnew, double *q, int nrhs,
+                        const KrylovScalars *sc, const Reduce &red, cudaStream_t s) {
+  const int nx = m.grid.nx, nz = m.grid.nz;
+  const size_t nax = (size_t)nz * (nx + 1), naz = (size_t)(nz + 1) * nx;
+  const double *ax = m.coef.as<double>(), *az = ax + nax, *dg = az + naz;
+  dim3 g(stencil_blocks_per_rhs(nx, nz), nrhs);
+  ProfScope prof(KC_STENCIL_A, s);
+  acoustic_apply_dir_kernel<<<g, 256, 0, s>>>(z, pold, pnew, q, nx, nz, ax, az, dg, const_cast<KrylovScalars *>(sc),
+                                              red);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------------------ vector kernels
 int reduce_blocks(size_t n) {
   const size_t b = (n + 1023) / 1024;
   return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
 }
 
+// r = b, x = 0, p = 0 (the first direction update takes beta = 0 and reads p), ||b||^2
 __global__ void __launch_bounds__(256) pcg_start_kernel(const double *__restrict__ b, double *__restrict__ x,
-                                                        double *__restrict__ r, size_t n, double tol2,
-                                                        KrylovScalars *sc, Reduce red) {
+                                                        double *__restrict__ r, double *__restrict__ p, size_t n,
+                                                        double tol2, KrylovScalars *sc, Reduce red) {
   const int rhs = blockIdx.y;
   const size_t off = (size_t)rhs * n;
   double acc = 0.0;
@@ -268,6 +345,7 @@ __global__ void __launch_bounds__(256) pcg_start_kernel(const double *__restrict
     const double v = b[off + i];
     r[off + i] = v;
     x[off + i] = 0.0;
+    p[off + i] = 0.0;
     acc = fma(v, v, acc);
   }
   double v1[1] = {acc}, tot[1];
@@ -284,42 +362,11 @@ __global__ void __launch_bounds__(256) pcg_start_kernel(const double *__restrict
   }
 }
 
-void pcg_start(const double *b, double *x, double *r, size_t n, int nrhs, double tol, KrylovScalars *sc,
+void pcg_start(const double *b, double *x, double *r, double *p, size_t n, int nrhs, double tol, KrylovScalars *sc,
                const Reduce &red, cudaStream_t s) {
   dim3 g(reduce_blocks(n), nrhs);
   ProfScope prof(KC_VEC, s);
-  pcg_start_kernel<<<g, 256, 0, s>>>(b, x, r, n, tol * tol, sc, red);
-  count_launch();
-  LAG_LAUNCH_CHECK();
-}
-
-// p = z, rz = (r, z)
-__global__ void __launch_bounds__(256) pcg_rz_p_kernel(const double *__restrict__ r, const double *__restrict__ z,
-                                                       double *__restrict__ p, size_t n, KrylovScalars *sc,
-                                                       Reduce red) {
-  const int rhs = blockIdx.y;
-  if (sc[rhs].state != ST_RUN) return;
-  const size_t off = (size_t)rhs * n;
-  double acc = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double zv = z[off + i];
-    p[off + i] = zv;
-    acc = fma(r[off + i], zv, acc);
-  }
-  double v1[1] = {acc}, tot[1];
-  __shared__ double sh[32];
-  block_sum<1>(v1, sh);
-  if (publish_partials<1>(red, rhs, blockIdx.x, gridDim.x, v1, tot)) {
-    sc[rhs].rz = tot[0];
-    if (!isfinite(tot[0])) sc[rhs].state = ST_NAN;
-  }
-}
-
-void pcg_rz_p(const double *r, const double *z, double *p, size_t n, int nrhs, KrylovScalars *sc,
-              const Reduce &red, cudaStream_t s) {
-  dim3 g(reduce_blocks(n), nrhs);
-  ProfScope prof(KC_VEC, s);
-  pcg_rz_p_kernel<<<g, 256, 0, s>>>(r, z, p, n, sc, red);
+  pcg_start_kernel<<<g, 256, 0, s>>>(b, x, r, p, n, tol * tol, sc, red);
   count_launch();
   LAG_LAUNCH_CHECK();
 }
@@ -362,7 +409,8 @@ void pcg_update_xr(double *x, double *r, const double *p, const double *q, size_
   LAG_LAUNCH_CHECK();
 }
 
-// rz_new = (r, z), zq = (z, q); beta = rz_new / rz (Fletcher-Reeves) or -alpha zq / rz (Polak-Ribiere)
+// rz_new = (r, z), zq = (z, q); beta = rz_new / rz (Fletcher-Reeves) or -alpha zq / rz (Polak-Ribiere),
+// 0 on the first iteration of a solve
 __global__ void __launch_bounds__(256) pcg_beta_kernel(const double *__restrict__ r, const double *__restrict__ z,
                                                        const double *__restrict__ q, size_t n, int flexible,
                                                        KrylovScalars *sc, Reduce red) {
@@ -382,9 +430,10 @@ __global__ void __launch_bounds__(256) pcg_beta_kernel(const double *__restrict_
     KrylovScalars &S = sc[rhs];
     const double rz_new = tot[0];
     S.zq = tot[1];
-    S.beta = flexible ? (-S.alpha * tot[1] / S.rz) : (rz_new / S.rz);
+    // the first direction of a solve is z itself (beta = 0)
+    S.beta = (S.iters == 0) ? 0.0 : (flexible ? (-S.alpha * tot[1] / S.rz) : (rz_new / S.rz));
     S.rz = rz_new;
-    if (!isfinite(S.beta)) S.state = ST_NAN;
+    if (!isfinite(S.beta) || !isfinite(rz_new) || !isfinite(tot[1])) S.state = ST_NAN;
   }
 }
 
@@ -397,24 +446,6 @@ void pcg_beta(const double *r, const double *z, const double *q, size_t n, int n
   LAG_LAUNCH_CHECK();
 }
 
-__global__ void __launch_bounds__(256) pcg_update_p_kernel(double *__restrict__ p, const double *__restrict__ z,
-                                                           size_t n, const KrylovScalars *sc) {
-  const int rhs = blockIdx.y;
-  if (sc[rhs].state != ST_RUN) return;
-  const double be = sc[rhs].beta;
-  const size_t off = (size_t)rhs * n;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    p[off + i] = fma(be, p[off + i], z[off + i]);
-}
-
-void pcg_update_p(double *p, const double *z, size_t n, int nrhs, const KrylovScalars *sc, cudaStream_t s) {
-  dim3 g(reduce_blocks(n), nrhs);
-  ProfScope prof(KC_VEC, s);
-  pcg_update_p_kernel<<<g, 256, 0, s>>>(p, z, n, sc);
-  count_launch();
-  LAG_LAUNCH_CHECK();
-}
-
 // ------------------------------------------------------------------------------ Laguerre series
 // Right-hand side of harmonic m (Eq. 9 in SPD form), per rhs b and component c:
 //   r = -c_m rho h^2 S + (f_m / (dx dz)) at the source node of component src_comp;  x = 0.
@@ -423,7 +454,8 @@ __global__ void __launch_bounds__(256) laguerre_rhs_kernel(const double *__restr
                                                            const int *__restrict__ src_idx,
                                                            int src_comp, double inv_cell, int ncomp, size_t nplane,
                                                            double *__restrict__ r, double *__restrict__ x,
-                                                           double tol2, KrylovScalars *sc, Reduce red) {
+                                                           double *__restrict__ p, double tol2, KrylovScalars *sc,
+                                                           Reduce red) {
   const int rhs = blockIdx.y;
   const size_t n = nplane * ncomp;
   const size_t off = (size_t)rhs * n;
@@ -436,6 +468,7 @@ __global__ void __launch_bounds__(256) laguerre_rhs_kernel(const double *__restr
     if (i == sidx) v += fmv * inv_cell;
     r[off + i] = v;
     x[off + i] = 0.0;
+    if (p != nullptr) p[off + i] = 0.0;
     acc = fma(v, v, acc);
   }
   double v1[1] = {acc}, tot[1];
@@ -454,10 +487,10 @@ __global__ void __launch_bounds__(256) laguerre_rhs_kernel(const double *__restr
 
 void laguerre_rhs(const double *rho_h2, const double *S, double cm, const double *fm, int m, const int *src_idx,
                   int src_comp, double inv_cell, int ncomp, size_t nplane, int nrhs, double *r, double *x,
-                  double tol, KrylovScalars *sc, const Reduce &red, cudaStream_t s) {
+                  double *p, double tol, KrylovScalars *sc, const Reduce &red, cudaStream_t s) {
   dim3 g(reduce_blocks(nplane * ncomp), nrhs);
   ProfScope prof(KC_LAGUERRE, s);
-  laguerre_rhs_kernel<<<g, 256, 0, s>>>(rho_h2, S, cm, fm, m, src_idx, src_comp, inv_cell, ncomp, nplane, r, x,
+  laguerre_rhs_kernel<<<g, 256, 0, s>>>(rho_h2, S, cm, fm, m, src_idx, src_comp, inv_cell, ncomp, nplane, r, x, p,
                                         tol * tol, sc, red);
   count_launch();
   LAG_LAUNCH_CHECK();

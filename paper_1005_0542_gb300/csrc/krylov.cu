@@ -1,7 +1,9 @@
 // Krylov drivers: preconditioned CG (acoustic) and right-preconditioned flexible GMRES(k)
-// (elastic), Sec. 2.3.  Every scalar stays on the device; the host enqueues chunks of iterations
-// and looks at a pinned copy of the per-system state between chunks.  Systems that have
-// converged are skipped by every kernel, so a chunk that overshoots costs only launches.
+// (elastic), Sec. 2.3.  Every scalar stays on the device.  PCG runs as one CUDA graph per solve
+// whose conditional WHILE node repeats the iterations until every system has stopped (eager chunks
+// of iterations where a graph cannot be used); GMRES is enqueued in chunks of steps.  The host looks
+// at a pinned copy of the per-system state after each launch.  Systems that have converged are
+// skipped by every kernel, so iterations past a system's convergence cost only launches.
 #include <cstdlib>
 #include <cstring>
 
@@ -66,19 +68,18 @@ void precond_apply_multi(lag_precond *p1, lag_precond *p2, const double *r, doub
 
 KrylovWork::~KrylovWork() {
   if (hsc) cudaFreeHost(hsc);
-  for (auto &g : gexec)
-    if (g) cudaGraphExecDestroy(g);
+  if (wexec) cudaGraphExecDestroy(wexec);
   if (ev) cudaEventDestroy(ev);
 }
 
 void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond *q2, const lag_solver &sol,
                        int nr, cudaStream_t st) {
-  for (auto &g : gexec)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  if (wexec) {
+    cudaGraphExecDestroy(wexec);
+    wexec = nullptr;
+  }
   eager_done = false;
+  pcur = 0;
   ctx = c;
   m = med;
   p1 = q1;
@@ -90,8 +91,8 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
   ncomp = elastic ? 2 : 1;
   nplane = (size_t)med->grid.nx * med->grid.nz;
   n = nplane * ncomp;
-  vecs.ctx = scal.ctx = gm.ctx = red.part.ctx = red.count.ctx = ctx;
-  const int nvec = elastic ? (3 + (s.restart_k + 1) + s.restart_k) : 6;
+  vecs.ctx = scal.ctx = gm.ctx = red.part.ctx = red.count.ctx = wcount.ctx = rzpart.ctx = ctx;
+  const int nvec = elastic ? (3 + (s.restart_k + 1) + s.restart_k) : 7;
   vecs.alloc(ctx, (size_t)nvec * n * nrhs * sizeof(double));
   scal.alloc(ctx, (size_t)nrhs * sizeof(KrylovScalars), true);
   const int cap = std::max(std::max(reduce_blocks(n), stencil_blocks(med->grid)), 1);
@@ -110,6 +111,13 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
     gdev.y = gdev.g + (size_t)nrhs * (k + 1);
     gdev.hcol = gdev.y + (size_t)nrhs * k;
   }
+  if (!elastic) {
+    wcount.alloc(ctx, sizeof(unsigned int), true);
+    if (p1->prec == LAG_FP64 && dst_oz_rz_fusable(p1->dst))
+      rzpart.alloc(ctx, (size_t)nrhs * p1->grid.nz * dst_oz_rz_parts(p1->dst) * sizeof(double));
+    else
+      rzpart.release();
+  }
   // pinned mirror: the scalars, then the error words of the two plans' tensor-core kernels
   LAG_CUDA_CHECK(cudaMallocHost(&hsc, (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int)));
   std::memset(hsc, 0, (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int));
@@ -124,7 +132,7 @@ void KrylovWork::start_from_b() {
     gmres_begin_cycle(true);
     return;
   }
-  pcg_start(b(), x(), r(), n, nrhs, s.tol, sc(), red.get(), stream);
+  pcg_start(b(), x(), r(), vec(3), n, nrhs, s.tol, sc(), red.get(), stream);
   start_from_r();
 }
 
@@ -137,31 +145,43 @@ void KrylovWork::start_from_r() {
     gmres_begin_cycle(true);
     return;
   }
-  double *z = vec(5), *p = vec(3);
-  precond(r(), z);
-  pcg_rz_p(r(), z, p, n, nrhs, sc(), red.get(), stream);
+  // PCG: x = 0, r = b and p = 0 were set by the right-hand side kernel; the first iteration takes
+  // beta = 0, so its direction is z = B^{-1} r
+  pcur = 0;
 }
 
+// One PCG iteration (Sec. 2.3), in the order z = B^{-1} r, beta, p = z + beta p with q = A p and
+// alpha = (r, z) / (p, q), then x += alpha p, r -= alpha q and the convergence test; beta is 0 on a
+// system's first iteration.  The direction alternates between two buffers (vec 3 and vec 6).
 void KrylovWork::pcg_iteration() {
-  double *p = vec(3), *q = vec(4), *z = vec(5);
+  double *q = vec(4), *z = vec(5);
+  double *pold = vec(pcur ? 6 : 3), *pnew = vec(pcur ? 3 : 6);
   Reduce rd = red.get();
   const int flexible = s.prec == LAG_MIXED ? 1 : 0;
-  m->apply(p, q, nrhs, sc(), &rd, 1, stream);                        // q = A p, alpha
-  pcg_update_xr(x(), r(), p, q, n, nrhs, s.max_iter, sc(), rd, stream);  // x, r, ||r||, state
+  const int rpr = p1->grid.nz;
   if (p1->use_tc) {
     // mixed path: forward DST, tridiagonal solve, then the inverse DST whose butterfly also forms
     // (r, z), (z, q) and beta
-    const int rows = nrhs * p1->grid.nz;
+    const int rows = nrhs * rpr;
     p1->ensure_scratch(nrhs);
     float *w = p1->scratch.as<float>();
-    dst_apply_tc_d2f(p1->dst, r(), w, rows, p1->grid.nz, sc(), stream, true);
+    dst_apply_tc_d2f(p1->dst, r(), w, rows, rpr, sc(), stream, true);
     tri_solve_f32(p1->tri32, w, w, nrhs, sc(), stream);
-    dst_apply_tc_f2d_beta(p1->dst, w, z, nrhs, p1->grid.nz, r(), q, flexible, sc(), rd, stream);
+    dst_apply_tc_f2d_beta(p1->dst, w, z, nrhs, rpr, r(), q, flexible, sc(), rd, stream);
+  } else if (p1->prec == LAG_FP64 && rzpart.ptr != nullptr) {
+    // float64 path on the exact-slice transform: its epilogue also forms (r, z) for beta
+    p1->ensure_scratch(nrhs);
+    double *w = p1->scratch.as<double>();
+    dst_apply_f64(p1->dst, r(), w, nrhs * rpr, rpr, sc(), stream);
+    tri_solve_f64(p1->tri64, w, w, nrhs, sc(), stream);
+    dst_apply_oz_rz(p1->dst, w, z, nrhs, rpr, sc(), r(), rzpart.as<double>(), stream);
   } else {
     precond(r(), z);                                                 // z = B^{-1} r
     pcg_beta(r(), z, q, n, nrhs, flexible, sc(), rd, stream);
   }
-  pcg_update_p(p, z, n, nrhs, sc(), stream);                         // p = z + beta p
+  acoustic_apply_dir(*m, z, pold, pnew, q, nrhs, sc(), rd, stream);   // p = z + beta p, q = A p, alpha
+  pcg_update_xr(x(), r(), pnew, q, n, nrhs, s.max_iter, sc(), rd, stream);  // x, r, ||r||, state
+  pcur ^= 1;
 }
 
 static bool graphs_disabled() {
@@ -170,55 +190,105 @@ static bool graphs_disabled() {
 }
 
 void KrylovWork::pcg_chunk(int iters) {
-  int idx = 0;
-  while ((1 << idx) < iters && idx < 4) ++idx;
-  // the first chunk runs eagerly: it also performs the one-time kernel attribute setup, which
-  // must not happen inside a capture
-  // (the legacy default stream cannot be captured)
-  const bool capturable = stream != nullptr && stream != cudaStreamLegacy && stream != cudaStreamPerThread;
-  if (!eager_done || (1 << idx) != iters || !capturable || profiling_on() || graphs_disabled()) {
-    for (int i = 0; i < iters; ++i) pcg_iteration();
-    eager_done = true;
-    return;
+  for (int i = 0; i < iters; ++i) pcg_iteration();
+}
+
+// Condition of the WHILE node: repeat while a system still runs, no tensor-core kernel reported
+// a pipeline timeout, and this launch has repeated the body fewer than `cap` times (a bound on one
+// launch; the host launches again if a system is still running then).  The counter is reset when
+// the loop ends, for the next launch.
+__global__ void pcg_loop_kernel(const KrylovScalars *sc, int nrhs, const int *err0, const int *err1,
+                                unsigned int *count, unsigned int cap, cudaGraphConditionalHandle handle) {
+  bool run = false;
+  for (int b = threadIdx.x; b < nrhs; b += blockDim.x) run |= (sc[b].state == ST_RUN);
+  run = __any_sync(0xffffffffu, run);
+  if (threadIdx.x == 0) {
+    const unsigned int c = *count + 1;
+    if ((err0 != nullptr && *err0 != 0) || (err1 != nullptr && *err1 != 0) || c >= cap) run = false;
+    *count = run ? c : 0u;
+    cudaGraphSetConditional(handle, run ? 1u : 0u);
   }
+}
+
+void KrylovWork::pcg_loop_condition(unsigned long long handle) {
+  const int *e0 = (p1 != nullptr && (p1->use_tc || p1->dst.oz)) ? p1->dst.tc_err : nullptr;
+  pcg_loop_kernel<<<1, 32, 0, stream>>>(sc(), nrhs, e0, nullptr, wcount.as<unsigned int>(), 1024u,
+                                        (cudaGraphConditionalHandle)handle);
+  count_launch();
+  LAG_LAUNCH_CHECK();
+}
+
+void KrylovWork::pcg_while() {
   p1->ensure_scratch(nrhs);
-  const void *key[3] = {p1->scratch.ptr, p1->tc_scratch.ptr, vecs.ptr};
+  const void *key[4] = {p1->scratch.ptr, p1->tc_scratch.ptr, vecs.ptr, rzpart.ptr};
   const int prod = p1->dst.tc_products;
-  if (gexec[idx] != nullptr && (std::memcmp(key, gkey[idx], sizeof(key)) != 0 || prod != gprod[idx])) {
-    cudaGraphExecDestroy(gexec[idx]);
-    gexec[idx] = nullptr;
+  if (wexec != nullptr && (std::memcmp(key, wkey, sizeof(key)) != 0 || prod != wprod)) {
+    cudaGraphExecDestroy(wexec);
+    wexec = nullptr;
   }
-  if (gexec[idx] == nullptr) {
+  if (wexec == nullptr) {
     cudaGraph_t g = nullptr;
-    LAG_CUDA_CHECK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-    g_capturing = true;
+    LAG_CUDA_CHECK(cudaGraphCreate(&g, 0));
     try {
-      for (int i = 0; i < iters; ++i) pcg_iteration();
-    } catch (...) {
+      cudaGraphConditionalHandle h;
+      LAG_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      LAG_CUDA_CHECK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      LAG_CUDA_CHECK(cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      g_capturing = true;
+      const int pc = pcur;
+      try {
+        pcur = 0;
+        pcg_iteration();
+        pcg_iteration();
+        pcg_loop_condition((unsigned long long)h);
+      } catch (...) {
+        g_capturing = false;
+        pcur = pc;
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(stream, &dummy);
+        throw;
+      }
       g_capturing = false;
-      cudaStreamEndCapture(stream, &g);
-      if (g) cudaGraphDestroy(g);
+      pcur = pc;
+      cudaGraph_t captured = nullptr;
+      LAG_CUDA_CHECK(cudaStreamEndCapture(stream, &captured));
+      size_t nodes = 0;
+      LAG_CUDA_CHECK(cudaGraphGetNodes(body, nullptr, &nodes));
+      LAG_CUDA_CHECK(cudaGraphInstantiate(&wexec, g, 0));
+      wnodes = nodes;
+    } catch (...) {
+      cudaGraphDestroy(g);
       throw;
     }
-    g_capturing = false;
-    LAG_CUDA_CHECK(cudaStreamEndCapture(stream, &g));
-    size_t nodes = 0;
-    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nodes);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec[idx], g, 0);
     cudaGraphDestroy(g);
-    LAG_CUDA_CHECK(e);
-    gnodes[idx] = nodes;
-    std::memcpy(gkey[idx], key, sizeof(key));
-    gprod[idx] = prod;
+    std::memcpy(wkey, key, sizeof(key));
+    wprod = prod;
   }
-  LAG_CUDA_CHECK(cudaGraphLaunch(gexec[idx], stream));
-  count_launch((int)gnodes[idx]);
+  if (pcur != 0) throw Error(LAG_ECUDA, "PCG graph: the direction buffers are out of step");
+  LAG_CUDA_CHECK(cudaGraphLaunch(wexec, stream));
+  count_launch();  // the body's kernels run a data-dependent number of times
 }
 
 void KrylovWork::enqueue_chunk() {
   if (!elastic) {
-    pcg_chunk(chunk);
-    iters_this_solve += chunk;
+    // the legacy default stream cannot be captured; the first iterations on a stream run eagerly:
+    // they also perform the one-time kernel attribute setup, which must not happen inside a capture
+    const bool capturable = stream != nullptr && stream != cudaStreamLegacy && stream != cudaStreamPerThread;
+    if (!eager_done || !capturable || profiling_on() || graphs_disabled()) {
+      pcg_chunk(chunk);  // an even count: the graph's body starts from the first direction buffer
+      iters_this_solve += chunk;
+      eager_done = true;
+    } else {
+      pcg_while();
+      iters_this_solve += 2;
+    }
   } else {
     for (int i = 0; i < chunk; ++i) {
       if (!cycle_open) gmres_begin_cycle(false);

@@ -163,7 +163,7 @@ int lag_shot::pump(bool block) {
       // in the r-weighted equation)
       const double inv_cell = grid.cylindrical ? 1.0 / (2.0 * M_PI * grid.dx * grid.dz) : 1.0 / (grid.dx * grid.dz);
       laguerre_rhs(medium->rho_h2.as<double>(), S, cm[m], fm(), m, src_idx, elastic ? 1 : 0,
-                   inv_cell, ncomp, nplane, nsrc, wk.r(), wk.x(), solver.tol, wk.sc(),
+                   inv_cell, ncomp, nplane, nsrc, wk.r(), wk.x(), elastic ? nullptr : wk.vec(3), solver.tol, wk.sc(),
                    wk.red.get(), stream);
       wk.start_from_r();
       wk.enqueue_chunk();

@@ -42,19 +42,25 @@ struct KrylovWork {
   int gj = 0, gk = 0;
   bool cycle_open = false;
   GmresDev gdev{};
-  // CUDA graphs of PCG chunks (1, 2, 4, 8, 16 iterations), replayed instead of launching each
-  // kernel; captured again when a pointer or the DST product count they baked in changes
-  cudaGraphExec_t gexec[5] = {};
-  unsigned long long gnodes[5] = {};
-  const void *gkey[5][3] = {};
-  int gprod[5] = {};
+  // PCG on the device: one CUDA graph whose conditional WHILE node repeats a body of two iterations
+  // until no system runs (pcg_loop_kernel sets the condition from the systems' states), so a solve is
+  // one graph launch with no host round trip and at most one iteration past convergence (whose
+  // kernels skip the finished systems).  Captured again when a pointer or the DST product count
+  // it baked in changes.
+  cudaGraphExec_t wexec = nullptr;
+  unsigned long long wnodes = 0;
+  const void *wkey[4] = {};
+  int wprod = 0;
+  DevBuf wcount;             // the loop's iteration counter (a bound on one launch's body repeats)
   bool eager_done = false;
+  int pcur = 0;              // which of the two direction buffers holds the current p
+  DevBuf rzpart;             // float64 PCG: partial (r, z) sums of the exact-slice GEMM's epilogue
 
   ~KrylovWork();
   void setup(lag_ctx *ctx, lag_medium *m, lag_precond *p1, lag_precond *p2, const lag_solver &s, int nrhs,
              cudaStream_t stream);
   double *vec(int i) const { return vecs.as<double>() + (size_t)i * n * nrhs; }
-  // acoustic: 0 b, 1 x, 2 r, 3 p, 4 q, 5 z
+  // acoustic: 0 b, 1 x, 2 r, 3 p (even iterations' old direction), 4 q, 5 z, 6 p (odd ones')
   // elastic:  0 b, 1 x, 2 r (= w work), 3..3+k V_0..V_k, 4+k.. Z_0..Z_{k-1}
   double *b() const { return vec(0); }
   double *x() const { return vec(1); }
@@ -73,7 +79,9 @@ struct KrylovWork {
 
  private:
   void pcg_iteration();
-  void pcg_chunk(int iters);  // iters PCG iterations, through a replayed graph where possible
+  void pcg_chunk(int iters);  // iters PCG iterations, launched one kernel at a time
+  void pcg_while();           // iterate until every system stops, as one graph launch
+  void pcg_loop_condition(unsigned long long handle);  // the WHILE node's condition kernel
   void mirror_state();        // async copy of the scalars and the plans' error words + event
   void gmres_begin_cycle(bool first);
   void gmres_step();

@@ -164,33 +164,77 @@ def test_elastic_shot_small(ctx, prec, tol, gate):
         assert rel_l2(traces[i], ref["traces"]) < gate
 
 
-def test_shot_full_size_first_harmonics(ctx):
-    # the 2048 x 1024 random layered workload in its launch configuration (FP64 path): the first
-    # two harmonics' fields against the oracle, every value
+@pytest.fixture(scope="module")
+def full_size_oracle():
+    # the oracle's first two harmonics of the 2048 x 1024 random layered shot, every field value
     s = inputs.random_layered()
     n = 2
+    ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, n, s.sources[0], s.receivers, s.t_out, s.f0,
+                              s.t0, tol=TOL64, keep_fields=True,
+                              fm=laguerre.forward_coeffs(laguerre.ricker(s.f0, s.t0), s.n_harm, s.h, s.alpha,
+                                                         s.t0 + 4 / s.f0)[:n])
+    return s, ref["fields"]
+
+
+def _shot_fields(ctx, s, prec, tol, n, layered=0, tune=0):
     g = L.grid(s.nx, s.nz, s.hx, s.hz)
     lag = L.laguerre(s.h, s.alpha, s.n_harm)
-    sv = L.solver(tol=TOL64, prec=L.LAG_FP64)
+    sv = L.solver(tol=tol, prec=prec, layered=layered, tune=tune)
     w = L.wavelet(s.f0, s.t0)
     c_, pc = L.f64(s.c)
     r_, pr = L.f64(s.rho)
     t_, pt = L.f64(s.t_out)
     sh = C.c_void_p()
-    L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
-                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
-                              C.byref(sh)), ctx)
-    ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, n, s.sources[0], s.receivers, s.t_out, s.f0,
-                              s.t0, tol=TOL64, keep_fields=True,
-                              fm=laguerre.forward_coeffs(laguerre.ricker(s.f0, s.t0), s.n_harm, s.h, s.alpha,
-                                                         s.t0 + 4 / s.f0)[:n])
-    field = empty((s.nz, s.nx))
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w),
+                              len(s.sources), L.points(s.sources), len(s.receivers), L.points(s.receivers),
+                              s.t_out.size, pt, C.byref(sh)), ctx)
+    field = empty((len(s.sources), s.nz, s.nx))
+    out = []
     for m in range(n):
         L.check(L.lag_shot_step(sh, 1), ctx)
         assert L.lag_shot_harmonic(sh) == m + 1
         L.check(L.lag_shot_copy_field(sh, ptr(field)), ctx)
-        assert rel_l2(host(field), ref["fields"][m]) < GATE64
+        out.append(host(field).copy())
     L.lag_shot_destroy(sh)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, TOL64, GATE64), (L.LAG_MIXED, TOLMX, GATEMX)])
+def test_shot_full_size_first_harmonics(ctx, full_size_oracle, prec, tol, gate):
+    # the 2048 x 1024 random layered workload in its launch configuration (the float64 path with
+    # the exact-slice DST, the mixed path with the split-bf16 one): the first two harmonics' fields
+    # against the oracle, every value
+    s, ref = full_size_oracle
+    got = _shot_fields(ctx, s, prec, tol, 2)
+    for m in range(2):
+        assert rel_l2(got[m, 0], ref[m]) < gate
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(L.LAG_FP64, TOL64, GATE64), (L.LAG_MIXED, TOLMX, GATEMX)])
+def test_batched_sources_match_oracle_per_source(ctx, prec, tol, gate):
+    # eight sources on a surface line (the batched workload's geometry on a mid-size grid) solved in
+    # one shot, every source's harmonic fields against its own oracle shot; the mixed case with the
+    # autotuned plan
+    nx, nz, ns = 192, 112, 8
+    srcs = [(int(round((i + 0.5) * nx / ns)), 2) for i in range(ns)]
+    s = inputs.random_layered(nx=nx, nz=nz, hx=10.0, n_harm=5, sources=srcs, f0=12.0)
+    got = _shot_fields(ctx, s, prec, tol, s.n_harm, tune=1 if prec == L.LAG_MIXED else 0)
+    for i, src in enumerate(srcs):
+        ref = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, s.n_harm, src, s.receivers[:2], s.t_out,
+                                  s.f0, s.t0, tol=tol, keep_fields=True)["fields"]
+        assert rel_l2(got[:, i], ref) < gate, i
+
+
+def test_graph_and_eager_pcg_identical(ctx, monkeypatch):
+    # the PCG loop as one graph launch (conditional WHILE node) and as eagerly launched iterations
+    # run the same kernels in the same order: identical fields and iteration counts, on both paths
+    s = inputs.random_layered(nx=128, nz=80, hx=10.0, n_harm=4, sources=[(30, 3), (90, 20)], f0=12.0)
+    for prec, tol in ((L.LAG_FP64, 1e-10), (L.LAG_MIXED, 1e-10)):
+        a = _shot_fields(ctx, s, prec, tol, s.n_harm)
+        monkeypatch.setenv("LAGWAVE_GRAPHS", "0")
+        b = _shot_fields(ctx, s, prec, tol, s.n_harm)
+        monkeypatch.delenv("LAGWAVE_GRAPHS")
+        assert np.array_equal(a, b), prec
 
 
 def test_elastic_full_size_first_harmonic_true_residual(ctx):
