@@ -79,6 +79,145 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# The metric's accuracy gate: the first ACC_HARM harmonics of every leg (fields at every node)
+# against the oracle's fields, the oracle solving to ACC_TOL (two solutions that each meet
+# ||r|| <= tol ||b|| differ by up to cond(A) tol, so the reference is solved well below the legs'
+# 1e-10); relative L2 at most GATE (the float64 legs are flagged against 1e-10 as well).
+ACC_HARM = 2
+ACC_TOL = 1e-13
+GATE = 1e-8
+GATE64 = 1e-10
+
+
+def shot_fields(ctx, sh, nsrc, ncomp, shape, picks):
+    """Host copies of the current harmonic's fields of the sources `picks` of a shot."""
+    import torch
+    from paper_1005_0542_gb300 import lagwave as L
+    buf = torch.empty((nsrc, ncomp) + tuple(shape), dtype=torch.float64, device="cuda")
+    L.check(L.lag_shot_copy_field(sh, C.c_void_p(buf.data_ptr())), ctx)
+    torch.cuda.synchronize()
+    out = [buf[i].cpu().numpy().copy() for i in picks]
+    del buf
+    return [o[0] if ncomp == 1 else o for o in out]
+
+
+class OracleRefs:
+    """Oracle solutions of the benchmark's problems, computed on demand (CPU, float64)."""
+
+    def __init__(self, s):
+        self.s = s
+        self.cache = {}
+        self.seconds = 0.0
+
+    def _fm(self, s, wavelet="ricker"):
+        from oracle import laguerre
+        if wavelet == "paper":
+            fun, t_end = laguerre.paper_wavelet(s.f0, s.t0, 4.0), s.t0 + 8.0 / s.f0
+        else:
+            fun, t_end = laguerre.ricker(s.f0, s.t0), s.t0 + 4.0 / s.f0
+        # the coefficients of the whole series, as the shot computes them, then the first few
+        return laguerre.forward_coeffs(fun, s.n_harm, s.h, s.alpha, t_end)[:ACC_HARM]
+
+    def cartesian(self, src=None, free_surface=False):
+        from oracle import solve
+        s = self.s
+        src = tuple(src or s.sources[0])
+        key = ("cart", src, free_surface)
+        if key not in self.cache:
+            t0 = time.perf_counter()
+            out = solve.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, ACC_HARM, src, s.receivers[:1],
+                                      s.t_out[:2], s.f0, s.t0, tol=ACC_TOL, keep_fields=True, fm=self._fm(s),
+                                      free_surface=free_surface)
+            self.seconds += time.perf_counter() - t0
+            self.cache[key] = out["fields"]
+        return self.cache[key]
+
+    def cylindrical(self, s):
+        from oracle import cyl
+        key = ("cyl", s.name)
+        if key not in self.cache:
+            t0 = time.perf_counter()
+            out = cyl.acoustic_shot(s.c, s.rho, s.hx, s.hz, s.h, s.alpha, ACC_HARM, s.sources[0], s.receivers[:1],
+                                    s.t_out[:2], s.f0, s.t0, tol=ACC_TOL, keep_fields=True,
+                                    fm=self._fm(s, "paper"), wavelet="paper")
+            self.seconds += time.perf_counter() - t0
+            self.cache[key] = out["fields"]
+        return self.cache[key]
+
+    def elastic_residual(self, s, fields, srcs):
+        """||b - C R_0|| / ||b|| with the oracle's plane-strain operator for harmonic 0 (no history)."""
+        from oracle import fd, solve
+        t0 = time.perf_counter()
+        lam, mu = solve.elastic_lame(s.c, s.vs, s.rho)
+        f0m = self._fm(s)[0]
+        res = []
+        for R, (ix, iz) in zip(fields, srcs):
+            cu, cw = fd.apply_C(R[0], R[1], lam, mu, s.rho, s.h, s.hx, s.hz)
+            bz = f0m / (s.hx * s.hz)
+            cw[iz, ix] -= bz
+            res.append(float(np.sqrt(np.sum(cu * cu) + np.sum(cw * cw)) / abs(bz)))
+        self.seconds += time.perf_counter() - t0
+        return res
+
+    def cyl_elastic_residual(self, s, R):
+        """The same for the axisymmetric elastic operator (vertical force on the axis)."""
+        from oracle import cyl_elastic, solve
+        t0 = time.perf_counter()
+        lam, mu = solve.elastic_lame(s.c, s.vs, s.rho)
+        co = cyl_elastic.coefficients(lam, mu, s.hx, s.hz)
+        cq, cu = cyl_elastic.apply_C(R[0], R[1], co, s.rho, s.h, s.hx, s.hz)
+        ir, iz = s.sources[0]
+        b = self._fm(s, "paper")[0] / (2.0 * np.pi * s.hx * s.hz)
+        cu[ir, iz] -= b
+        self.seconds += time.perf_counter() - t0
+        return float(np.sqrt(np.sum(cq * cq) + np.sum(cu * cu)) / abs(b))
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def accuracy_report(acc, refs):
+    """Every leg's first harmonics against the oracle: relative L2 over every node."""
+    rep = {"gate": GATE, "harmonics": list(range(ACC_HARM)), "oracle_tol": ACC_TOL,
+           "measure": ("relative L2 error over every node of each harmonic's field R_m, the leg's own shot "
+                       "(its warm-up harmonics, solved at the leg's tolerance 1e-10) against the oracle's "
+                       "field (PCG to 1e-13); elastic legs: the oracle operator's relative residual "
+                       "||b - C R_0|| / ||b|| of harmonic 0 (the 4096 x 2048 elastic oracle solve does not fit "
+                       "the bench's time)")}
+    ok = True
+    for leg, item in acc.items():
+        kind, fields = item[0], item[1]
+        try:
+            if kind in ("cart", "cart_fs", "cart_src", "cyl"):
+                if kind == "cyl":
+                    ref = refs.cylindrical(item[2])
+                elif kind == "cart_src":
+                    ref = refs.cartesian(src=item[2])
+                else:
+                    ref = refs.cartesian(free_surface=(kind == "cart_fs"))
+                errs = [_rel_l2(f, r) for f, r in zip(fields, ref)]
+                e = {"rel_l2": errs, "max": max(errs), "pass": max(errs) <= GATE}
+                if leg in ("headline_fp64", "layered", "free_surface") or leg.endswith("_fp64"):
+                    e["pass_1e-10"] = max(errs) <= GATE64
+            elif kind == "cart_elastic":
+                res = refs.elastic_residual(item[2], fields, item[3])
+                e = {"oracle_operator_residual": res, "max": max(res), "pass": max(res) <= 2e-10,
+                     "solver_tol": 1e-10}
+            elif kind == "cyl_elastic":
+                res = refs.cyl_elastic_residual(item[2], fields[0])
+                e = {"oracle_operator_residual": [res], "max": res, "pass": res <= 2e-10, "solver_tol": 1e-10}
+            else:
+                continue
+        except Exception as exc:  # a failed reference is reported, not hidden
+            e = {"error": f"{type(exc).__name__}: {exc}", "pass": False}
+        ok = ok and e["pass"]
+        rep[leg] = e
+    rep["all_pass"] = ok
+    rep["oracle_seconds"] = refs.seconds
+    return rep
+
+
 # FP64 ALU peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
 # (1.25 TFLOP/s nominal; the DFMA probe measured 1.20 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -171,13 +310,16 @@ def gpu_arm(args, rank, world, local_rank):
                                   C.byref(sh)), ctx)
         return sh
 
-    def timed_steps(sh, W, K, sampler=None):
+    def timed_steps(sh, W, K, keep=None):
         """W warm-up harmonics, then the timed region: K harmonics in the production configuration
-        (PCG chunks replayed as CUDA graphs).  Then the kernel-class times: the next K harmonics of
-        the same shot with a CUDA event pair per launch on the shot's stream (a replayed graph
-        cannot bracket its kernels with events, so this pass launches eagerly; it is not timed)."""
-        for _ in range(W):
+        (each harmonic's PCG solve is one graph launch).  Then the kernel-class times: the next K
+        harmonics of the same shot with a CUDA event pair per launch on the shot's stream (a graph
+        cannot bracket its kernels with events, so this pass launches eagerly; it is not timed).
+        keep (a list): the fields of the first ACC_HARM warm-up harmonics are appended to it."""
+        for m in range(W):
             L.check(L.lag_shot_step(sh, 1), ctx, ok=(L.LAG_OK,))
+            if keep is not None and m < ACC_HARM:
+                keep.append(shot_fields(ctx, sh, 1, 1, s.c.shape, [0])[0])
         stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if dist is not None:
@@ -220,10 +362,12 @@ def gpu_arm(args, rank, world, local_rank):
         return tr
 
     W, K = args.warmup, args.steps
+    acc = {}  # leg -> fields of harmonics 0 .. ACC_HARM-1 (the oracle check after the timed legs)
     # ---- headline: FP64 path
     sh = make_shot(L.LAG_FP64)
+    acc["headline_fp64"] = []
     with ClockSampler(local_rank) as clk:
-        ms, launches, prof, ms_prof = timed_steps(sh, W, K)
+        ms, launches, prof, ms_prof = timed_steps(sh, W, K, keep=acc["headline_fp64"])
     clocks = clk.summary()
     its = iters_of(sh, W, W + K)
     its_prof = iters_of(sh, W + K, W + 2 * K)                          # the profiled harmonics
@@ -282,12 +426,16 @@ def gpu_arm(args, rank, world, local_rank):
            "clocks": clocks}
     if rank != 0:
         return None
+    refs = OracleRefs(s)
     if args.no_extras:
+        if not args.no_accuracy:
+            out["accuracy"] = accuracy_report({"headline_fp64": ("cart", acc["headline_fp64"])}, refs)
         return out
 
     # ---- mixed-precision path, same workload, same harmonics
     shm = make_shot(L.LAG_MIXED)
-    msm, launches_m, profm, _ = timed_steps(shm, W, K)
+    acc["mixed"] = []
+    msm, launches_m, profm, _ = timed_steps(shm, W, K, keep=acc["mixed"])
     itsm = iters_of(shm, W, W + K)
     trm = traces_of(shm)
     L.lag_shot_destroy(shm)
@@ -299,7 +447,8 @@ def gpu_arm(args, rank, world, local_rank):
 
     # ---- the same with the autotuned plan (partition count, bf16 product count)
     sht = make_shot(L.LAG_MIXED, tune=1)
-    mst, _, proft, _ = timed_steps(sht, W, K)
+    acc["mixed_tuned"] = []
+    mst, _, proft, _ = timed_steps(sht, W, K, keep=acc["mixed_tuned"])
     trt = traces_of(sht)
     L.lag_shot_destroy(sht)
     out["mixed_tuned"] = {"value": K / (mst / 1e3), "ms_per_step": mst / K,
@@ -309,7 +458,8 @@ def gpu_arm(args, rank, world, local_rank):
     # ---- the same shot with a free surface on top (Sec. 2.1, Eq. 3), float64 path
     shf = make_shot(L.LAG_FP64, free_surface=True)
     Kf = min(K, 16)
-    msf, _, proff, _ = timed_steps(shf, W, Kf)
+    acc["free_surface"] = []
+    msf, _, proff, _ = timed_steps(shf, W, Kf, keep=acc["free_surface"])
     itsf = iters_of(shf, W, W + Kf)
     L.lag_shot_destroy(shf)
     out["free_surface"] = {"config": "the 2048x1024 shot with a free surface at z = 0 (zero-flux top face), FP64",
@@ -319,7 +469,8 @@ def gpu_arm(args, rank, world, local_rank):
     # ---- the same shot with the layered preconditioner (per-row midranges), both paths
     for key, prec in (("layered", L.LAG_FP64), ("layered_mixed", L.LAG_MIXED)):
         shl = make_shot(prec, layered=1)
-        msl, launches_l, profl, _ = timed_steps(shl, W, K)
+        acc[key] = []
+        msl, launches_l, profl, _ = timed_steps(shl, W, K, keep=acc[key])
         itsl = iters_of(shl, W, W + K)
         trl = traces_of(shl)
         L.lag_shot_destroy(shl)
@@ -333,15 +484,21 @@ def gpu_arm(args, rank, world, local_rank):
                     "kernel_ms": {k: {"launches": c, "ms": round(v, 3)} for k, (c, v) in sorted(profl.items())}}
 
     # ---- batched mixed path: 64 sources on the surface line share one shot (one launch set per step)
-    out["batched"] = batched_leg(ctx, args)
+    out["batched"] = batched_leg(ctx, args, acc)
     # ---- elastic 4096 x 2048, 16 sources, FGMRES(20), float32 vector preconditioner
     if args.elastic_sources > 0:
-        out["elastic"] = elastic_leg(ctx, args)
-        out["elastic_layered"] = elastic_leg(ctx, args, layered=1)
+        out["elastic"] = elastic_leg(ctx, args, acc=acc)
+        out["elastic_layered"] = elastic_leg(ctx, args, layered=1, acc=acc)
 
     # ---- the paper's own 2.5D axisymmetric (r, z) acoustic problem
     if args.cyl_steps > 0:
-        out["cylindrical"] = cylindrical_leg(ctx, args)
+        out["cylindrical"] = cylindrical_leg(ctx, args, acc)
+
+    # ---- every leg's first harmonics against the oracle (the metric's "at 1e-8 rel err")
+    if not args.no_accuracy:
+        kinds = {"headline_fp64": "cart", "mixed": "cart", "mixed_tuned": "cart", "free_surface": "cart_fs",
+                 "layered": "cart", "layered_mixed": "cart"}
+        out["accuracy"] = accuracy_report({k: (kinds.get(k, k), v) for k, v in acc.items()}, refs)
 
     # ---- served stream: Poisson arrivals of acoustic / elastic shots, continuous batching
     out["serving"] = serving_leg(ctx, args)
@@ -358,8 +515,9 @@ def gpu_arm(args, rank, world, local_rank):
     return out
 
 
-def batched_leg(ctx, args):
-    """64 sources at ix = round((s + 1/2) 2048 / 64), iz = 2 on the 2048 x 1024 model, mixed path."""
+def batched_leg(ctx, args, acc=None):
+    """64 sources at ix = round((s + 1/2) 2048 / 64), iz = 2 on the 2048 x 1024 model, mixed path.
+    The fields of the middle source in the first two (warm-up) harmonics go to acc["batched"]."""
     import torch
     from paper_1005_0542_gb300 import inputs
     from paper_1005_0542_gb300 import lagwave as L
@@ -376,7 +534,13 @@ def batched_leg(ctx, args):
     L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), nsrc,
                               L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
                               C.byref(sh)), ctx)
-    L.check(L.lag_shot_step(sh, 1), ctx)  # warm-up harmonic
+    pick = nsrc // 2
+    kept = []
+    for _ in range(ACC_HARM):  # warm-up harmonics
+        L.check(L.lag_shot_step(sh, 1), ctx)
+        kept.append(shot_fields(ctx, sh, nsrc, 1, s.c.shape, [pick])[0])
+    if acc is not None:
+        acc["batched"] = ("cart_src", kept, s.sources[pick])
     stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -393,10 +557,10 @@ def batched_leg(ctx, args):
     L.lag_shot_destroy(sh)
     return {"config": f"2048x1024 model, {nsrc} sources on row 2, mixed path, autotuned plan, one shot; "
                       f"step = one harmonic of every source", "value": nsrc * K / (ms / 1e3), "unit": UNIT, "steps": K,
-            "ms_per_step": ms / K, "pcg_iters_per_solve": float(its[:, 1:1 + K].mean())}
+            "ms_per_step": ms / K, "pcg_iters_per_solve": float(its[:, ACC_HARM:ACC_HARM + K].mean())}
 
 
-def cylindrical_leg(ctx, args):
+def cylindrical_leg(ctx, args, acc=None):
     """The paper's own 2.5D axisymmetric acoustic problem (Sec. 2.1, the r-weighted scheme of
     Sec. 2.3, the cylindrical preconditioner: DCT-II along z + general tridiagonal systems along r).
     Sec. 3.2's experiment: homogeneous half space, a point source on the axis at the surface, the
@@ -428,8 +592,13 @@ def cylindrical_leg(ctx, args):
                                   L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
                                   C.byref(sh)), ctx)
         W, K = 3, args.cyl_steps
-        for _ in range(W):
+        kept = []
+        for m in range(W):
             L.check(L.lag_shot_step(sh, 1), ctx)
+            if m < (1 if elastic else ACC_HARM):
+                kept.append(shot_fields(ctx, sh, 1, 2 if elastic else 1, s.c.shape, [0])[0])
+        if acc is not None:
+            acc["cylindrical_" + key] = ("cyl_elastic" if elastic else "cyl", kept, s)
         stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -464,7 +633,7 @@ def cylindrical_leg(ctx, args):
     return out
 
 
-def elastic_leg(ctx, args, layered=0):
+def elastic_leg(ctx, args, layered=0, acc=None):
     """The elastic workload: 4096 x 2048 at 2.5 m, layered Vp / Vs / rho with a dipping interface,
     vertical-force Ricker 20 Hz, sources on the surface line batched in one shot, FGMRES(20) to
     1e-10 with the float32 vector preconditioner (tensor-core DST) and float64 Krylov vectors;
@@ -488,6 +657,10 @@ def elastic_leg(ctx, args, layered=0):
                               C.byref(sh)), ctx)
     held = L.lag_bytes_in_use(ctx)
     L.check(L.lag_shot_step(sh, 1), ctx)  # warm-up harmonic
+    if acc is not None:  # harmonic 0 of two sources, for the oracle operator's residual
+        picks = [0, nsrc // 2]
+        acc["elastic_layered" if layered else "elastic"] = (
+            "cart_elastic", shot_fields(ctx, sh, nsrc, 2, s.c.shape, picks), s, [s.sources[i] for i in picks])
     stream = torch.cuda.ExternalStream(L.lag_shot_stream(sh))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -691,11 +864,51 @@ def oracle_harmonics(s, budget_s, max_harm, min_harm=1):
     return times, iters
 
 
+def oracle_iteration_seconds(budget):
+    """Seconds per oracle PCG iteration on the benchmark shot's first harmonic (run in a child
+    process pinned to one thread for the single-core figure)."""
+    from oracle import fd, krylov, laguerre, precond
+    from paper_1005_0542_gb300 import inputs
+    s = inputs.random_layered()
+    kap = fd.kappa_from_velocity(s.c, s.rho)
+    pr = precond.acoustic_params(kap, s.rho, s.h)
+    nz, nx = s.nz, s.nx
+    fm = laguerre.forward_coeffs(laguerre.ricker(s.f0, s.t0), 1, s.h, s.alpha, s.t0 + 4.0 / s.f0)
+    b = np.zeros((nz, nx))
+    b[s.sources[0][1], s.sources[0][0]] = fm[0] / (s.hx * s.hz)
+    A = lambda v: fd.apply_A(v.reshape(nz, nx), kap, s.rho, s.h, s.hx, s.hz).ravel()  # noqa: E731
+    M = lambda v: precond.apply_inverse(v.reshape(nz, nx), s.hx, s.hz, *pr).ravel()  # noqa: E731
+    k, t = 1, 0.0
+    while True:
+        t0 = time.perf_counter()
+        krylov.pcg(A, M, b.ravel(), 1e-30, max_iter=k)   # exactly k iterations
+        t = time.perf_counter() - t0
+        if t >= budget or k >= 64:
+            return t / k, k
+        k *= 2
+
+
 def cpu_baseline(s, budget):
     times, iters = oracle_harmonics(s, budget, 64)
-    return {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"first {len(times)} harmonics of the same shot (oracle PCG, direct DST, Thomas; "
-                      f"{sum(times):.1f} s, {np.mean(iters):.0f} PCG iterations/harmonic)"}
+    out = {"value": len(times) / sum(times), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"first {len(times)} harmonics of the same shot (oracle PCG, direct DST, Thomas; "
+                     f"{sum(times):.1f} s, {np.mean(iters):.0f} PCG iterations/harmonic)"}
+    # one core: a child process with single-threaded BLAS times PCG iterations of the first harmonic;
+    # the rate is one harmonic per (seconds per iteration x the iterations per harmonic above)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               GOTO_NUM_THREADS="1", PYTHONPATH=ROOT)
+    code = ("import json, bench; t, k = bench.oracle_iteration_seconds(%r); print(json.dumps([t, k]))"
+            % (budget / 2,))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                           timeout=max(120.0, 8 * budget))
+        t_it, k = json.loads(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": 1.0 / (t_it * float(np.mean(iters))), "unit": UNIT, "cores": 1,
+                           "sample": f"{k} PCG iterations of harmonic 0 on one thread ({t_it:.2f} s each), "
+                                     f"x {np.mean(iters):.0f} iterations per harmonic"}
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError) as exc:
+        out["one_core"] = {"error": f"{type(exc).__name__}: {exc}"}
+    return out
 
 
 # ---------------------------------------------------------------------------------- ncu capture
@@ -823,6 +1036,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lagwave", choices=["lagwave", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="headline only (for launch-list captures)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle check of the legs' first harmonics")
     ap.add_argument("--e2e-harmonics", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-sources", type=int, default=64)

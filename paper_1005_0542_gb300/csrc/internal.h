@@ -168,7 +168,7 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
 bool dst_oz_rz_fusable(const DstPlan &dp);
 size_t dst_oz_rz_parts(const DstPlan &dp);
 void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, int rpr, KrylovScalars *sc,
-                     const double *r, double *rzpart, cudaStream_t s);
+                     const double *r, double *rzpart, const Reduce &red, cudaStream_t s);
 // mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
                        const KrylovScalars *sc, cudaStream_t s, bool rscale = false);

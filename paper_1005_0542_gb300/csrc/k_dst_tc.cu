@@ -1234,28 +1234,33 @@ __global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__res
   }
 }
 
-// PCG's (r, z) and beta from the exact-slice GEMM's partials: one block per right-hand side sums its
-// rows' partials of the column tiles that exist (fixed order: deterministic, and the same alone or
-// in a batch); beta = rz_new / rz (Fletcher-Reeves), 0 on the first iteration of a solve.
-__global__ void __launch_bounds__(256) oz_rz_beta_kernel(const double *__restrict__ part, int rpr, int nnt, int ku,
-                                                         int kv, KrylovScalars *sc) {
-  const int rhs = blockIdx.x;
+// PCG's (r, z) and beta from the exact-slice GEMM's partials: grid (blocks, nrhs), one thread per
+// row summing that row's partials of the column tiles that exist, then the block sums combined by
+// the last block in block order (deterministic, and the same alone or in a batch); beta =
+// rz_new / rz (Fletcher-Reeves), 0 on the first iteration of a solve.
+constexpr int OZ_RZ_THREADS = 128;
+__global__ void __launch_bounds__(OZ_RZ_THREADS) oz_rz_beta_kernel(const double *__restrict__ part, int rpr, int nnt,
+                                                                   int ku, int kv, KrylovScalars *sc, Reduce red) {
+  const int rhs = blockIdx.y;
   if (sc[rhs].state != ST_RUN) return;
   const int np = 4 * nnt;
-  const double *pr = part + (size_t)rhs * rpr * np;
+  const int rl = blockIdx.x * OZ_RZ_THREADS + threadIdx.x;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < rpr * np; e += blockDim.x) {
-    const int rl = e / np, sl = e - rl * np;
-    const int h = sl & 1, tile = sl >> 1;
-    const int par = tile / nnt, nt = tile - par * nnt;
-    if (nt * OZ_TN + h * 64 < (par ? kv : ku)) acc += pr[(size_t)rl * np + sl];
+  if (rl < rpr) {
+    const double *pr = part + ((size_t)rhs * rpr + rl) * np;
+#pragma unroll 8
+    for (int sl = 0; sl < np; ++sl) {
+      const int h = sl & 1, tile = sl >> 1;
+      const int par = tile / nnt, nt = tile - par * nnt;
+      if (nt * OZ_TN + h * 64 < (par ? kv : ku)) acc += __ldg(pr + sl);
+    }
   }
-  double v1[1] = {acc};
+  double v1[1] = {acc}, tot[1];
   __shared__ double sh[32];
   block_sum<1>(v1, sh);
-  if (threadIdx.x == 0) {
+  if (publish_partials<1>(red, rhs, blockIdx.x, gridDim.x, v1, tot)) {
     KrylovScalars &S = sc[rhs];
-    const double rz_new = v1[0];
+    const double rz_new = tot[0];
     S.beta = (S.iters == 0) ? 0.0 : rz_new / S.rz;
     S.rz = rz_new;
     if (!isfinite(S.beta) || !isfinite(rz_new)) S.state = ST_NAN;
@@ -1311,7 +1316,7 @@ bool dst_oz_rz_fusable(const DstPlan &dp) { return dp.oz && dp.kind == 0; }
 size_t dst_oz_rz_parts(const DstPlan &dp) { return 4 * (size_t)dp.npad_u; }
 
 void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, int rpr, KrylovScalars *sc,
-                     const double *r, double *rzpart, cudaStream_t s) {
+                     const double *r, double *rzpart, const Reduce &red, cudaStream_t s) {
   const int rows = nrhs * rpr;
   if (rows <= 0) return;
   {
@@ -1320,7 +1325,9 @@ void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, in
     else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
   }
   ProfScope prof(KC_VEC, s);
-  oz_rz_beta_kernel<<<nrhs, 256, 0, s>>>(rzpart, rpr, dp.npad_u, dp.ku, dp.kv, sc);
+  const int nb = div_up(rpr, OZ_RZ_THREADS);
+  if (nb > red.nblk) throw Error(LAG_EINVAL, "exact-slice (r, z): more row blocks than the reduction holds");
+  oz_rz_beta_kernel<<<dim3(nb, nrhs), OZ_RZ_THREADS, 0, s>>>(rzpart, rpr, dp.npad_u, dp.ku, dp.kv, sc, red);
   count_launch();
   LAG_LAUNCH_CHECK();
 }

@@ -112,15 +112,20 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
     gdev.hcol = gdev.y + (size_t)nrhs * k;
   }
   if (!elastic) {
-    wcount.alloc(ctx, sizeof(unsigned int), true);
+    wcount.alloc(ctx, 4 * sizeof(unsigned int), true);  // [0] repeats this launch, [2..3] bodies in total
+    wbodies_seen = 0;
     if (p1->prec == LAG_FP64 && dst_oz_rz_fusable(p1->dst))
       rzpart.alloc(ctx, (size_t)nrhs * p1->grid.nz * dst_oz_rz_parts(p1->dst) * sizeof(double));
     else
       rzpart.release();
   }
-  // pinned mirror: the scalars, then the error words of the two plans' tensor-core kernels
-  LAG_CUDA_CHECK(cudaMallocHost(&hsc, (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int)));
-  std::memset(hsc, 0, (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int));
+  // pinned mirror: the scalars, the error words of the two plans' tensor-core kernels, then the
+  // PCG graph's body count
+  if (hsc) cudaFreeHost(hsc);
+  hsc = nullptr;
+  const size_t mbytes = (size_t)nrhs * sizeof(KrylovScalars) + 2 * sizeof(int) + sizeof(unsigned long long);
+  LAG_CUDA_CHECK(cudaMallocHost(&hsc, mbytes));
+  std::memset(hsc, 0, mbytes);
   LAG_CUDA_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
 }
 
@@ -174,7 +179,7 @@ void KrylovWork::pcg_iteration() {
     double *w = p1->scratch.as<double>();
     dst_apply_f64(p1->dst, r(), w, nrhs * rpr, rpr, sc(), stream);
     tri_solve_f64(p1->tri64, w, w, nrhs, sc(), stream);
-    dst_apply_oz_rz(p1->dst, w, z, nrhs, rpr, sc(), r(), rzpart.as<double>(), stream);
+    dst_apply_oz_rz(p1->dst, w, z, nrhs, rpr, sc(), r(), rzpart.as<double>(), rd, stream);
   } else {
     precond(r(), z);                                                 // z = B^{-1} r
     pcg_beta(r(), z, q, n, nrhs, flexible, sc(), rd, stream);
@@ -203,6 +208,9 @@ __global__ void pcg_loop_kernel(const KrylovScalars *sc, int nrhs, const int *er
   for (int b = threadIdx.x; b < nrhs; b += blockDim.x) run |= (sc[b].state == ST_RUN);
   run = __any_sync(0xffffffffu, run);
   if (threadIdx.x == 0) {
+    // count[1..2]: bodies executed since the work was set up (64-bit), for launch accounting
+    unsigned long long *total = reinterpret_cast<unsigned long long *>(count + 2);
+    *total += 1ull;
     const unsigned int c = *count + 1;
     if ((err0 != nullptr && *err0 != 0) || (err1 != nullptr && *err1 != 0) || c >= cap) run = false;
     *count = run ? c : 0u;
@@ -272,8 +280,7 @@ void KrylovWork::pcg_while() {
     wprod = prod;
   }
   if (pcur != 0) throw Error(LAG_ECUDA, "PCG graph: the direction buffers are out of step");
-  LAG_CUDA_CHECK(cudaGraphLaunch(wexec, stream));
-  count_launch();  // the body's kernels run a data-dependent number of times
+  LAG_CUDA_CHECK(cudaGraphLaunch(wexec, stream));  // its kernels are counted from the body count (poll)
 }
 
 void KrylovWork::enqueue_chunk() {
@@ -308,6 +315,9 @@ void KrylovWork::mirror_state() {
   for (int i = 0; i < 2; ++i)
     if (pl[i] != nullptr && (pl[i]->use_tc || pl[i]->dst.oz) && pl[i]->dst.tc_err != nullptr)
       LAG_CUDA_CHECK(cudaMemcpyAsync(herr + i, pl[i]->dst.tc_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  if (wcount.ptr != nullptr)
+    LAG_CUDA_CHECK(cudaMemcpyAsync(herr + 2, wcount.as<unsigned int>() + 2, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, stream));
   LAG_CUDA_CHECK(cudaEventRecord(ev, stream));
   pending = true;
 }
@@ -323,6 +333,12 @@ int KrylovWork::poll(bool block) {
     }
     pending = false;
     const int *herr = reinterpret_cast<const int *>(hsc + nrhs);
+    if (wcount.ptr != nullptr) {  // kernels the PCG graph ran: its body's nodes per repeat
+      unsigned long long bodies;
+      std::memcpy(&bodies, herr + 2, sizeof(bodies));
+      if (bodies > wbodies_seen) count_launch((int)((bodies - wbodies_seen) * wnodes));
+      wbodies_seen = bodies;
+    }
     if (herr[0] != 0 || herr[1] != 0)
       throw Error(LAG_ETIMEDOUT, "tensor-core DST: a bounded pipeline wait gave up (code " +
                                      std::to_string(herr[0] ? herr[0] : herr[1]) + "); the preconditioner output is invalid");

@@ -51,7 +51,8 @@ struct KrylovWork {
   unsigned long long wnodes = 0;
   const void *wkey[4] = {};
   int wprod = 0;
-  DevBuf wcount;             // the loop's iteration counter (a bound on one launch's body repeats)
+  DevBuf wcount;             // the loop's repeat counter (a bound on one launch) and its body total
+  unsigned long long wbodies_seen = 0;
   bool eager_done = false;
   int pcur = 0;              // which of the two direction buffers holds the current p
   DevBuf rzpart;             // float64 PCG: partial (r, z) sums of the exact-slice GEMM's epilogue
