@@ -208,7 +208,7 @@ def accuracy_report(acc, refs):
                 res = refs.cyl_elastic_residual(item[2], fields[0])
                 e = {"oracle_operator_residual": [res], "max": res, "pass": res <= 2e-10, "solver_tol": 1e-10}
             else:
-                continue
+                raise ValueError(f"unknown accuracy entry kind {kind!r}")
         except Exception as exc:  # a failed reference is reported, not hidden
             e = {"error": f"{type(exc).__name__}: {exc}", "pass": False}
         ok = ok and e["pass"]
@@ -498,7 +498,8 @@ def gpu_arm(args, rank, world, local_rank):
     if not args.no_accuracy:
         kinds = {"headline_fp64": "cart", "mixed": "cart", "mixed_tuned": "cart", "free_surface": "cart_fs",
                  "layered": "cart", "layered_mixed": "cart"}
-        out["accuracy"] = accuracy_report({k: (kinds.get(k, k), v) for k, v in acc.items()}, refs)
+        out["accuracy"] = accuracy_report({k: (v if isinstance(v, tuple) else (kinds[k], v)) for k, v in acc.items()},
+                                          refs)
 
     # ---- served stream: Poisson arrivals of acoustic / elastic shots, continuous batching
     out["serving"] = serving_leg(ctx, args)

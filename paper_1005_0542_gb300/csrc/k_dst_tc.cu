@@ -21,9 +21,13 @@
 // tcgen05.mma from shared-memory descriptors into a 128 x 256 FP32 accumulator in tensor memory,
 // tcgen05.commit releases each stage, and four warps read the accumulator with tcgen05.ld.
 // Every wait is bounded: on expiry the kernel records an error code and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
+#include <cstdlib>
 #include <cstdint>
 
 #include "internal.h"
@@ -671,18 +675,28 @@ void spectrum_unpermute_widen(const float *in, double *out, int rows, int n, int
 //     i + j share one accumulator in groups of at most floor(2^24 / ((2^NB - 1)^2 K)) (at most 4).
 //   * Pairs with i + j <= NS + 1 are kept (the dropped ones weigh < 2^-54 of the row scale), and
 //     the epilogue adds the groups as int64 fixed-point numbers (units of 2^-38 of the pre-scaled
-//     domain, see OZ_FIX) and rounds once to float64, y = 2^(e_r + e_B - 2 NB) 2^-38 I, straight
+//     domain, see oz_fix) and rounds once to float64, y = 2^(e_r + e_B - 2 NB) 2^-FIX I, straight
 //     into the float64 output (natural mode order, as the SIMT kernel writes it).  Groups are
 //     scheduled in an order that keeps the tensor pipe busy (see oz_schedule).
 //   * Slice width: 7 bits (8 slices, 36 pairs) while one pair's exact sum fits the FP32
 //     accumulator (127^2 K <= 2^24: K <= 1024), else 6 bits (9 slices, 45 pairs).  The GEMM streams
 //     one A and one B slice tile per pair and K step, so fewer pairs mean proportionally fewer
 //     operand bytes into each SM, the limit of this kernel.
+//   * 8-bit slices (7 balanced digits in [-128, 128] of a 55-bit expansion, 28 pairs; the default
+//     up to K = 1024): bf16 holds every such digit exactly and one pair's sum over K <= 1024 stays
+//     within 128^2 1024 = 2^24, exact in FP32, so the groups are those of the 7-bit format with
+//     22 % fewer products and operand bytes.  (Plain 8-bit digits, up to 255, would need the exact
+//     pairs cut into K chunks of 256: 65 accumulator groups per tile instead of 20, and the epilogue
+//     then holds the MMA issuer back; the schedule still supports such chunks.)
 constexpr int OZ_SMAX = 9;  // slices per operand at most (storage bound)
 struct OzFmt {
   int nb, ns;  // bits per slice, slices per operand
 };
-static OzFmt oz_format(int kpad) { return (127LL * 127LL * kpad <= (1LL << 24)) ? OzFmt{7, 8} : OzFmt{6, 9}; }
+static OzFmt oz_format(int kpad) {
+  const char *v = std::getenv("LAGWAVE_OZ_BITS");  // "7": the 7-bit / 6-bit formats only
+  if (kpad <= 1024 && !(v != nullptr && v[0] == '7')) return OzFmt{8, 7};
+  return (127LL * 127LL * kpad <= (1LL << 24)) ? OzFmt{7, 8} : OzFmt{6, 9};
+}
 constexpr int OZ_TN = 128;                 // output columns per tile
 constexpr int OZ_BT = OZ_TN * TK * 2;      // B stage tile, 16 KB
 constexpr int OZ_KT = 2;                   // 64-wide K tiles per pipeline stage
@@ -693,12 +707,13 @@ constexpr int OZ_SMEM = OZ_NST * OZ_STAGE + 1024 + 256;
 constexpr int OZ_EXP_NAN = 0x7fffffff;     // row exponent marking a non-finite row
 // pairs of weight i + j >= tail share one accumulator with FP32 rounding: together they weigh
 // < 2^-(NB (tail - 2)) of the leading products (2^-36 at tail = 8 with 6-bit slices, 2^-42 with
-// 7-bit ones), so that the roundings of the K / 16 accumulating MMAs (directed, not random, in the
-// tensor cores' adder: they add up linearly) stay near 2^-50 of the row scale or below, under the
-// float64 rounding of the product itself; lighter weights are exact.  6-bit slices: tail = 8 up to
-// K = 1024 and one weight later per doubling of K (the rounding grows with K); 7-bit slices
-// (K <= 1024): tail = 8 as well (a tail from weight 7, 2^-35, measured 1.3e-14 relative row error at
-// K = 1024 against 1e-15 for a float64 GEMM).
+// 7-bit ones, 2^-40 at tail = 7 with 8-bit ones), so that the roundings of the K / 16 accumulating
+// MMAs (directed, not random, in the tensor cores' adder: they add up linearly) stay near 2^-50 of
+// the row scale or below, under the float64 rounding of the product itself; lighter weights are
+// exact.  6-bit slices: tail = 8 up to K = 1024 and one weight later per doubling of K (the
+// rounding grows with K); 7-bit slices (K <= 1024): tail = 8 as well (a tail from weight 7, 2^-35,
+// measured 1.3e-14 relative row error at K = 1024 against 1e-15 for a float64 GEMM); 8-bit slices
+// (K <= 1024): tail = 7.
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -709,24 +724,33 @@ __device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t a, uint6
       : "memory");
 }
 
+// The schedule of one output tile: a sequence of units (one slice pair over a range of K tiles),
+// cut into groups that each fill one tensor-memory accumulator.
+constexpr int OZ_MAXU = 128;
 struct OzSched {
-  int npairs, ngroups;
-  int8_t si[48], sj[48], first[48], last[48];  // slice indices (1-based), group start / end flags
-  int8_t gd[48];                               // weight i + j of each group (the tail: its lightest)
-  int8_t gsh[48];  // per group: s >= 0 if its sum is an exact integer G with value G 2^-(38 - s) (the
-                   // int64 epilogue adds G << s), -1 for a rounded group (added as rn(v 2^38))
+  int nunits, ngroups, npairs;
+  int8_t si[OZ_MAXU], sj[OZ_MAXU];            // slice indices (1-based) of each unit
+  uint8_t k0[OZ_MAXU], k1[OZ_MAXU];           // the unit's K tiles [k0, k1)
+  int8_t first[OZ_MAXU], last[OZ_MAXU];       // group start / end flags
+  int8_t gsh[OZ_MAXU];  // per group: s >= 0 if its sum is an exact integer G with value G 2^-(FIX - s)
+                        // (the int64 epilogue adds G << s), -1 for a rounded group (rn(v 2^FIX))
 };
 
-// The epilogue's accumulator: a signed fixed-point integer in units of 2^-38 of the pre-scaled
+// The epilogue's accumulator: a signed fixed-point integer in units of 2^-FIX of the pre-scaled
 // domain (where weight-2 products have unit 1), in int64.  An exact group of weight w holds
 // G 2^-(NB (w - 2)) with G an integer below 2^24: F2I of v 2^(NB (w - 2)) is exact and G << s,
-// s = 38 - NB (w - 2) >= 0, places it (w <= 7 for both formats).  A tail chunk (FP32-rounded, or
-// an exact group too light for a non-negative s) is below 2^-10 in that domain and is added as
-// rn(v 2^38), below 2^31: a rounding at 2^-39, under the float64 rounding of the product.  The sum
-// stays below 2^62.1 (the leading group < 2^24).  One I2F and one DMUL per output at the end; the
-// per-group work is a float multiply, a conversion and integer adds instead of one DFMA on the
-// narrow FP64 pipe.
-constexpr int OZ_FIX = 38;
+// s = FIX - NB (w - 2) >= 0, places it.  A tail chunk (FP32-rounded, or an exact group too light for
+// a non-negative s) is added as rn(v 2^FIX), below 2^31: a rounding at 2^-(FIX+1), under the
+// float64 rounding of the product.  FIX = 38: the leading group is at most 2^24 for every format,
+// the sum below 2^62.1, and the lightest exact weight keeps s >= 0 (8-bit slices: weight 6, s = 6).
+// One I2F and one
+// DMUL per output at the end; the per-group work is a float multiply, a conversion and integer adds
+// instead of one DFMA on the narrow FP64 pipe.
+__host__ __device__ constexpr int oz_fix(int) { return 38; }
+// width of the fixed-point expansion of an operand (55 bits for the balanced 8-bit digits, whose top
+// digit must stay <= 128), and the exponent shift of its slices: v = 2^(e - se) sum_i q_i 2^-(NB (i-1))
+__host__ __device__ constexpr int oz_bits(int nb, int ns) { return nb == 8 ? 55 : nb * ns; }
+__host__ __device__ constexpr int oz_se(int nb, int ns) { return oz_bits(nb, ns) - nb * (ns - 1); }
 
 // |v| < 2^e: NBITS-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
 template <int NBITS>
@@ -745,13 +769,25 @@ __device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
 // low half of the float is zero and its upper half is q 2^-(NB (i - 1)) in bf16; 0 stays +0).
 // A product of slices i and j then carries 2^-(NB (i + j - 2)) already, so products of different
 // weights can share an accumulator.
+// 8-bit slices are balanced digits in [-128, 128] (the 7-bit and 6-bit ones are plain digits): the
+// 55-bit value T (below 2^55) plus 128 in each of its six lower byte positions has bytes b_i with
+// T = (b_1) 256^6 + sum_{i >= 2} (b_i - 128) 256^(7 - i), b_1 <= 128; every digit magnitude is at
+// most 128 = 2^7, so one pair's sum over K <= 1024 stays within 2^24, exact in FP32.
 template <int NB, int NS>
 __device__ __forceinline__ float oz_slice_f(unsigned long long T, int i, bool neg) {
   static_assert(NB <= 8, "bf16 holds 8 significant bits");
-  const uint32_t q = (uint32_t)(T >> (NB * NS - NB * i)) & ((1u << NB) - 1u);
   const float c = __uint_as_float((uint32_t)(127 - NB * (i - 1)) << 23);  // 2^-(NB (i - 1))
   const float cs = neg ? -c : c;
-  return fmaf(__uint_as_float(0x4B000000u | q), cs, -8388608.0f * cs);
+  if constexpr (NB == 8) {
+    static_assert(NS == 7, "balanced 8-bit digits of a 55-bit value");
+    const unsigned long long Tb = T + 0x0000808080808080ull;
+    const uint32_t raw = (uint32_t)(Tb >> (8 * (NS - i))) & (i == 1 ? 0x1ffu : 0xffu);
+    const float off = (i == 1) ? 8388608.0f : 8388736.0f;  // 2^23, or 2^23 + 128 for the lower digits
+    return fmaf(__uint_as_float(0x4B000000u | raw), cs, -off * cs);
+  } else {
+    const uint32_t q = (uint32_t)(T >> (NB * NS - NB * i)) & ((1u << NB) - 1u);
+    return fmaf(__uint_as_float(0x4B000000u | q), cs, -8388608.0f * cs);
+  }
 }
 __device__ __forceinline__ uint16_t oz_bf16_of(float f) { return (uint16_t)(__float_as_uint(f) >> 16); }
 // two slice values as one 32-bit word of bf16 operands (f0 at the lower address)
@@ -773,7 +809,7 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
   double v = 0.0;
   if (which == 0) { if (n < n0n && k < k0n) v = m0[(size_t)k * ld0 + n]; }
   else if (n < n1n && k < k1n) v = m1[(size_t)k * ld1 + n];
-  const unsigned long long T = oz_fixed<NB * NS>(v, eB);
+  const unsigned long long T = oz_fixed<oz_bits(NB, NS)>(v, eB);
   const size_t tile = (size_t)(n / OZ_TN) * nks + (k / TK);
   const uint32_t off = swz(n % OZ_TN, k % TK);
   for (int i = 1; i <= NS; ++i) {
@@ -863,7 +899,7 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const double val = src[q];
-      T[q] = bad ? 0ull : oz_fixed<NB * NS>(val, e);
+      T[q] = bad ? 0ull : oz_fixed<oz_bits(NB, NS)>(val, e);
       negm |= (__double_as_longlong(val) < 0 ? 1u : 0u) << q;
     }
     const uint32_t off = swz(r, kk);
@@ -934,6 +970,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   };
   auto wanted = [&](int par, int mt, int nt) -> bool {
     if (nt * OZ_TN >= ((par && !inv) ? kv : ku)) return false;
+    if (mt * TM >= rows) return false;  // the padding m-tile of an odd count (A slices come in pairs)
     if (sc == nullptr) return true;
     const int m0 = mt * TM;
     const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
@@ -949,11 +986,12 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         int par, mt, nt;
         decode(t, par, mt, nt);
         if (!wanted(par, mt, nt)) continue;
-        for (int pr = 0; pr < sch.npairs && !*abort_flag; ++pr) {
+        for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
           const uint8_t *at = apack + ((size_t)par * NS + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
           const uint8_t *bt = bpack + ((size_t)par * NS + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
-          for (int kk = 0; kk < nks; kk += OZ_KT, ++it) {
-            const int kt = min(OZ_KT, nks - kk);  // K tiles in this stage
+          const int ke = sch.k1[pr];
+          for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, ke - kk);  // K tiles in this stage
             const int s = it % OZ_NST, use = it / OZ_NST;
             if (it >= OZ_NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
               atomicExch(err, 11);
@@ -977,7 +1015,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         decode(t, par, mt, nt);
         if (!wanted(par, mt, nt)) continue;
         uint32_t d = 0;
-        for (int pr = 0; pr < sch.npairs && !*abort_flag; ++pr) {
+        for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
           if (sch.first[pr]) {
             const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
             if (gc >= OZ_NACC && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) {
@@ -988,8 +1026,9 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             d = tmem + (uint32_t)(acc * OZ_TN);
           }
-          for (int kk = 0; kk < nks; kk += OZ_KT, ++it) {
-            const int kt = min(OZ_KT, nks - kk);
+          const int kb = sch.k0[pr], ke = sch.k1[pr];
+          for (int kk = kb; kk < ke; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, ke - kk);
             const int s = it % OZ_NST, use = it / OZ_NST;
             if (!mbar_wait(full0 + 8 * s, use & 1)) {
               atomicExch(err, 12);
@@ -1003,7 +1042,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
               for (int sub = 0; sub < TK / 16; ++sub) {
                 const uint32_t o = sub * 32;
                 mma_bf16_n128(d, sdesc(st + t * A_TILE + o), sdesc(st + OZ_KT * A_TILE + t * OZ_BT + o),
-                              (sch.first[pr] && kk == 0 && t == 0 && sub == 0) ? 0u : 1u);
+                              (sch.first[pr] && kk == kb && t == 0 && sub == 0) ? 0u : 1u);
               }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
@@ -1045,7 +1084,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int gs = sch.gsh[g];
         // exact: G = v 2^(38 - s) exactly (a power-of-two multiply), then G << s; rounded: rn(v 2^38)
-        const float up = __uint_as_float((uint32_t)(127 + (gs >= 0 ? OZ_FIX - gs : OZ_FIX)) << 23);
+        constexpr int FIX = oz_fix(NB);
+        const float up = __uint_as_float((uint32_t)(127 + (gs >= 0 ? FIX - gs : FIX)) << 23);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float v[16];
@@ -1069,8 +1109,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         // (2^-38 first, so that a row near the bottom of the float64 range meets the same
         // subnormal rounding as its float64 product would)
         const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
-                                               : ldexp(1.0, e + eB - 2 * NB);
-        const double unit = 1.0 / (double)(1LL << OZ_FIX);
+                                               : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
+        const double unit = 1.0 / (double)(1LL << oz_fix(NB));
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
         if (inv) {  // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]
@@ -1106,35 +1146,352 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_NACC * OZ_TN) : "memory");
 }
 
-// Pair schedule of one output tile.  Exact groups: pairs of one weight d < tail, at most gmax per
-// accumulator.  The tail (d >= tail, FP32-rounded) is cut into chunks of at most 3 pairs, each in
-// its own accumulator, and the chunks are spread between the exact groups: every group costs the
-// epilogue one float64 multiply-add per output (about as long as one pair's MMAs), so runs of
-// one-pair groups alone would hold the MMA issuer waiting for accumulators, while the tail's
-// longer groups give the epilogue time to catch up.
-static OzSched oz_schedule(int kpad) {
+// ---------------------------------------------------------------- two-SM (cta_group::2) variant
+// The same exact-slice GEMM with the MMA spread over a cluster of two CTAs on two SMs: the pair
+// computes a 256 x 128 tile per (pair, K step), each CTA holding its own 128 rows of A and half of
+// the 128 B columns in shared memory; the tensor cores of the pair exchange the B halves, so each
+// SM streams 16 + 8 KB of operands per 128 x 128 x 64 of its own output instead of 16 + 16 KB (the
+// per-SM operand stream is what bounds the one-CTA kernel).  The MMAs are issued by one thread of
+// the even CTA (the leader) into both CTAs' tensor memory; each CTA's epilogue adds its own rows.
+// Synchronisation across the pair: both CTAs' operand copies (TMA tensor copies of the pre-swizzled
+// slice tiles, verbatim rows of 128 bytes) complete on the leader's "full" barrier, whose expected
+// byte count the leader sets for the pair; the leader's commits arrive on both CTAs' "empty" and
+// "tfull" barriers (multicast); the odd CTA's epilogue warps arrive on the leader's "tempty".  Every wait is bounded; both CTAs meet at a cluster barrier before
+// they free their tensor memory and exit, so neither leaves while the other may still use it.
+constexpr int OZ2_BH = (OZ_TN / 2) * TK * 2;            // half a B stage tile: 64 columns x 64 K, 8 KB
+constexpr int OZ2_STAGE = OZ_KT * (A_TILE + OZ2_BH);    // 48 KB: [A k tiles][B half k tiles]
+constexpr int OZ2_NST = 4;                              // pipeline stages
+constexpr int OZ2_NACC = 2;                             // accumulators of 128 columns per CTA
+constexpr int OZ2_SMEM = OZ2_NST * OZ2_STAGE + 1024 + 512;
+// kind::f16, D f32, A / B bf16 K-major, M = 256 (the pair), N = 128
+constexpr uint32_t OZ2_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait with cluster-scope acquire (for barriers that another CTA's threads arrive on)
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (i > 32) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void mma2_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(OZ2_IDESC), "r"(accumulate)
+      : "memory");
+}
+// TMA copy of rows [y, y + box rows) of a 2-D tensor of 128-byte rows into this CTA's shared memory,
+// completing on the mbarrier at cluster address `bar` (this CTA's or its pair leader's)
+__device__ __forceinline__ void tma_rows2(uint32_t dst, const CUtensorMap *tm, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void commit2_both(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+template <int NB, int NS>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
+    oz_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const int *__restrict__ erow, int eB, int nks, int nmt, int nnt, int rows,
+                    double *__restrict__ y, int ld, int ku, int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
+                    int rpr, int *__restrict__ err, const double *__restrict__ rdot, double *__restrict__ rzpart) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + OZ2_NST * OZ2_STAGE;
+  const uint32_t full0 = bars, empty0 = bars + 8 * OZ2_NST;
+  const uint32_t tfull0 = bars + 16 * OZ2_NST, tempty0 = tfull0 + 8 * OZ2_NACC;
+  uint8_t *gtail = gbase + OZ2_NST * OZ2_STAGE + 16 * OZ2_NST + 16 * OZ2_NACC;
+  volatile uint32_t *holder = reinterpret_cast<volatile uint32_t *>(gtail + 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gtail + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int nmtp = nmt >> 1;  // m-tile pairs (nmt is even: the A slices are padded to a pair)
+  const int ntiles = 2 * nmtp * nnt;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)holder)),
+                 "r"(OZ2_NACC * OZ_TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int st = 0; st < OZ2_NST; ++st) {
+      mbar_init(full0 + 8 * st, 1);   // the leader's expect-tx arrive (and both CTAs' bytes)
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    for (int a = 0; a < OZ2_NACC; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 16);  // the eight epilogue warps of both CTAs
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();  // barriers of both CTAs initialised before any remote arrive
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *holder;
+
+  auto decode = [&](int t, int &par, int &mtp, int &nt) {
+    nt = t % nnt;
+    mtp = (t / nnt) % nmtp;
+    par = t / (nnt * nmtp);
+  };
+  // the pair decides together: a tile is skipped only when none of its 256 rows runs
+  auto wanted = [&](int par, int mtp, int nt) -> bool {
+    if (nt * OZ_TN >= (par ? kv : ku)) return false;
+    const int m0 = mtp * 2 * TM;
+    if (m0 >= rows) return false;
+    if (sc == nullptr) return true;
+    const int r0 = m0 / rpr, r1 = (min(m0 + 2 * TM, rows) - 1) / rpr;
+    for (int r = r0; r <= r1; ++r)
+      if (sc[r].state == ST_RUN) return true;
+    return false;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer (both CTAs): own A rows, own half of the B columns
+      const uint32_t lead_full0 = map_rank(full0, 0);
+      int it = 0;
+      for (int t = pair; t < ntiles && !*abort_flag; t += npairs) {
+        int par, mtp, nt;
+        decode(t, par, mtp, nt);
+        if (!wanted(par, mtp, nt)) continue;
+        const int mt = 2 * mtp + (int)rank;
+        for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
+          // 128-byte row index of this K step's A tile / B half in the packed slice buffers
+          const int ya = (((par * NS + (sch.si[pr] - 1)) * nmt + mt) * nks) * TM;
+          const int yb = (((par * NS + (sch.sj[pr] - 1)) * nnt + nt) * nks) * OZ_TN + (int)rank * (OZ_TN / 2);
+          const int ke = sch.k1[pr];
+          for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, ke - kk);
+            const int st = it % OZ2_NST, use = it / OZ2_NST;
+            if (it >= OZ2_NST && !mbar_wait(empty0 + 8 * st, (use - 1) & 1)) {
+              atomicExch(err, 21);
+              *abort_flag = 1;
+              break;
+            }
+            const uint32_t sa = base + st * OZ2_STAGE;
+            if (rank == 0) mbar_expect_tx(full0 + 8 * st, (uint32_t)(2 * kt * (A_TILE + OZ2_BH)));
+            for (int q = 0; q < kt; ++q) {
+              tma_rows2(sa + q * A_TILE, &tmA, ya + (kk + q) * TM, lead_full0 + 8 * st);
+              tma_rows2(sa + OZ_KT * A_TILE + q * OZ2_BH, &tmB, yb + (kk + q) * OZ_TN, lead_full0 + 8 * st);
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {  // the leader: MMA issuer for the pair
+      int it = 0, gc = 0;
+      for (int t = pair; t < ntiles && !*abort_flag; t += npairs) {
+        int par, mtp, nt;
+        decode(t, par, mtp, nt);
+        if (!wanted(par, mtp, nt)) continue;
+        uint32_t d = 0;
+        for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
+          if (sch.first[pr]) {
+            const int acc = gc % OZ2_NACC, ause = gc / OZ2_NACC;
+            if (gc >= OZ2_NACC && !mbar_wait_cluster(tempty0 + 8 * acc, (ause - 1) & 1)) {
+              atomicExch(err, 24);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            d = tmem + (uint32_t)(acc * OZ_TN);
+          }
+          const int kb = sch.k0[pr], ke = sch.k1[pr];
+          for (int kk = kb; kk < ke; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, ke - kk);
+            const int st = it % OZ2_NST, use = it / OZ2_NST;
+            if (!mbar_wait(full0 + 8 * st, use & 1)) {
+              atomicExch(err, 22);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = base + st * OZ2_STAGE;
+            for (int q = 0; q < kt; ++q) {
+#pragma unroll
+              for (int sub = 0; sub < TK / 16; ++sub) {
+                const uint32_t o = sub * 32;
+                mma2_bf16(d, sdesc(sa + q * A_TILE + o), sdesc(sa + OZ_KT * A_TILE + q * OZ2_BH + o),
+                          (sch.first[pr] && kk == kb && q == 0 && sub == 0) ? 0u : 1u);
+              }
+            }
+            commit2_both(empty0 + 8 * st);
+          }
+          if (sch.last[pr]) {
+            commit2_both(tfull0 + 8 * (gc % OZ2_NACC));
+            ++gc;
+          }
+        }
+      }
+    }
+  } else {  // epilogue warps 2..9 of both CTAs: their own 128 rows
+    const int lg = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t my_tempty0 = (rank == 0) ? tempty0 : map_rank(tempty0, 0);
+    int gc = 0;
+    for (int t = pair; t < ntiles; t += npairs) {
+      int par, mtp, nt;
+      decode(t, par, mtp, nt);
+      if (!wanted(par, mtp, nt)) continue;
+      const int mt = 2 * mtp + (int)rank;
+      const int row = mt * TM + lg * 32 + lane;
+      const bool rok = row < rows;
+      const int e = rok ? erow[par * (nmt * TM) + row] : 0;
+      long long acci[64];
+#pragma unroll
+      for (int q = 0; q < 64; ++q) acci[q] = 0;
+      bool stop = false;
+      for (int g = 0; g < sch.ngroups; ++g) {
+        const int acc = gc % OZ2_NACC, ause = gc / OZ2_NACC;
+        const bool ok = mbar_wait(tfull0 + 8 * acc, ause & 1);
+        __syncwarp();
+        if (!ok || *abort_flag) {
+          if (lane == 0 && !ok) atomicExch(err, 23);
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int gs = sch.gsh[g];
+        constexpr int FIX = oz_fix(NB);
+        const float up = __uint_as_float((uint32_t)(127 + (gs >= 0 ? FIX - gs : FIX)) << 23);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 16), v);
+          if (gs >= 0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rz(v[q] * up) << gs;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rn(v[q] * up);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (rank == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(my_tempty0 + 8 * acc) : "memory");
+          else mbar_arrive_remote(my_tempty0 + 8 * acc);
+        }
+        ++gc;
+      }
+      if (stop) break;
+      if (rok) {
+        const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
+                                               : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
+        const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+        const int c0 = nt * OZ_TN + h * 64;
+        const int ncols = min(64, (par ? kv : ku) - c0);
+        double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+        if (rzpart == nullptr) {
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
+        } else {
+          const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
+          double dacc = 0.0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) {
+              const double v = scale * (unit * __ll2double_rn(acci[q]));
+              yp[2 * q] = v;
+              dacc = fma(__ldg(rp + 2 * q), v, dacc);
+            }
+          rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dacc;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // neither CTA frees its tensor memory or leaves while the pair may still use it
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ2_NACC * OZ_TN) : "memory");
+}
+
+// Schedule of one output tile.  Exact groups: units of one weight d < tail over one K chunk (the
+// longest multiple of 64 K values whose sum stays exact, kc), at most gmax units per accumulator.
+// The tail (d >= tail, FP32-rounded) is cut into chunks of at most 3 pairs over the whole K range,
+// each in its own accumulator, and the chunks are spread between the exact groups: every group
+// costs the epilogue a pass over its accumulator, so runs of short exact groups alone would hold
+// the MMA issuer waiting for accumulators, while the tail's longer groups let the epilogue catch up.
+static OzSched oz_schedule(int kpad, OzFmt f) {
   OzSched s{};
-  const OzFmt f = oz_format(kpad);
-  const long long qmax = (1LL << f.nb) - 1;
-  const long long cap = (1LL << 24) / (qmax * qmax * kpad);  // pairs per exact FP32 accumulation
+  const long long qmax = (f.nb == 8) ? 128 : (1LL << f.nb) - 1;  // largest digit magnitude
+  const int nks = kpad / TK;
+  const int kcs = std::max(1, std::min(nks, (int)((1LL << 24) / (qmax * qmax) / TK)));  // K tiles per chunk
+  const long long cap = (1LL << 24) / (qmax * qmax * (long long)kcs * TK);               // units per accumulator
   const int gmax = (int)std::max(1LL, std::min(4LL, cap));
-  int tail_d = 8;
+  int tail_d = (f.nb == 8) ? 7 : 8;
   for (long long k = 1024; k < kpad; k *= 2) ++tail_d;
+  struct Unit {
+    int i, j, k0, k1;
+  };
   struct Group {
     int d;
-    std::vector<std::pair<int, int>> pairs;
+    std::vector<Unit> units;
   };
   std::vector<Group> exact, tail;
+  int npairs = 0;
   for (int d = 2; d <= f.ns + 1; ++d) {
+    std::vector<std::pair<int, int>> pairs;
     for (int i = 1; i <= f.ns; ++i) {
       const int j = d - i;
-      if (j < 1 || j > f.ns) continue;
-      if (d < tail_d) {
-        if (exact.empty() || exact.back().d != d || (int)exact.back().pairs.size() == gmax) exact.push_back({d, {}});
-        exact.back().pairs.push_back({i, j});
-      } else {
-        if (tail.empty() || (int)tail.back().pairs.size() == 3) tail.push_back({tail_d, {}});
-        tail.back().pairs.push_back({i, j});
+      if (j >= 1 && j <= f.ns) pairs.push_back({i, j});
+    }
+    npairs += (int)pairs.size();
+    if (d < tail_d) {
+      for (int c0 = 0; c0 < nks; c0 += kcs) {
+        const int c1 = std::min(nks, c0 + kcs);
+        for (size_t q = 0; q < pairs.size(); ++q) {
+          if (q % gmax == 0) exact.push_back({d, {}});
+          exact.back().units.push_back({pairs[q].first, pairs[q].second, c0, c1});
+        }
+      }
+    } else {
+      for (const auto &pq : pairs) {
+        if (tail.empty() || (int)tail.back().units.size() == 3) tail.push_back({tail_d, {}});
+        tail.back().units.push_back({pq.first, pq.second, 0, nks});
       }
     }
   }
@@ -1147,27 +1504,36 @@ static OzSched oz_schedule(int kpad) {
     order.push_back(&tail[it]);
   }
   for (; ie < ne; ++ie) order.push_back(&exact[ie]);
-  int np = 0, ng = 0;
+  const int fix = oz_fix(f.nb);
+  int nu = 0, ng = 0;
   for (const Group *g : order) {
-    const bool exact = g->d < tail_d;
-    const int sh = OZ_FIX - f.nb * (g->d - 2);
-    s.gsh[ng] = (int8_t)((exact && sh >= 0) ? sh : -1);
-    for (size_t q = 0; q < g->pairs.size(); ++q) {
-      if (np >= (int)sizeof(s.si)) throw Error(LAG_EINVAL, "exact-slice schedule: too many pairs");
-      s.si[np] = (int8_t)g->pairs[q].first;
-      s.sj[np] = (int8_t)g->pairs[q].second;
-      s.first[np] = (q == 0);
-      s.last[np] = (q + 1 == g->pairs.size());
-      ++np;
+    const bool ex = g->d < tail_d;
+    const int sh = fix - f.nb * (g->d - 2);
+    if (ng >= OZ_MAXU) throw Error(LAG_EINVAL, "exact-slice schedule: too many groups");
+    s.gsh[ng] = (int8_t)((ex && sh >= 0) ? sh : -1);
+    for (size_t q = 0; q < g->units.size(); ++q) {
+      if (nu >= OZ_MAXU) throw Error(LAG_EINVAL, "exact-slice schedule: too many units");
+      const Unit &u = g->units[q];
+      s.si[nu] = (int8_t)u.i;
+      s.sj[nu] = (int8_t)u.j;
+      s.k0[nu] = (uint8_t)u.k0;
+      s.k1[nu] = (uint8_t)u.k1;
+      s.first[nu] = (q == 0);
+      s.last[nu] = (q + 1 == g->units.size());
+      ++nu;
     }
-    s.gd[ng++] = (int8_t)g->d;
+    ++ng;
   }
-  s.npairs = np;
+  s.nunits = nu;
   s.ngroups = ng;
+  s.npairs = npairs;
   return s;
 }
 
-int dst_oz_products(int n) { return oz_schedule(div_up((n + 1) / 2, TK) * TK).npairs; }
+int dst_oz_products(int n) {
+  const int kpad = div_up((n + 1) / 2, TK) * TK;
+  return oz_schedule(kpad, oz_format(kpad)).npairs;
+}
 
 bool dst_oz_supported(int n) {
   const int ku = (n + 1) / 2;
@@ -1196,7 +1562,10 @@ void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
   dim3 g(div_up(nks * TK, 128), nnt * OZ_TN, 2);
   auto pack_b = [&](const double *m0, int k0n, int n0n, int ld0, const double *m1, int k1n, int n1n, int ld1,
                     uint8_t *out) {
-    if (f.nb == 7)
+    if (f.nb == 8)
+      oz_pack_b_kernel<8, 7><<<g, 128, 0, s>>>(m0, k0n, n0n, ld0, m1, k1n, n1n, ld1, nks, nnt, eB, out,
+                                               dp.oz_slice_bytes);
+    else if (f.nb == 7)
       oz_pack_b_kernel<7, 8><<<g, 128, 0, s>>>(m0, k0n, n0n, ld0, m1, k1n, n1n, ld1, nks, nnt, eB, out,
                                                dp.oz_slice_bytes);
     else
@@ -1213,8 +1582,54 @@ void dst_build_oz(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
   dp.oz = true;
 }
 
+// 2-D tensor map over `nrows` rows of 128 bytes (64 bf16) at base: TMA copies of box_rows whole
+// rows, verbatim (the tiles are already in the swizzled shared-memory layout)
+// The driver's tensor-map encoder, looked up through the runtime (the library does not link the
+// driver library, so it still loads where no driver is installed)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  if (fn == nullptr) throw Error(LAG_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  return fn;
+}
+
+static CUtensorMap rows_map(const void *base, uint64_t nrows, uint32_t box_rows) {
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {64, (cuuint64_t)nrows};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(LAG_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+// m-tiles of packed A slices: rounded up to a pair for the two-SM GEMM
+static int oz_mtiles(int rows) {
+  const int nmt = div_up(rows, TM);
+  return nmt + (nmt & 1);
+}
+
+// the two-SM variant is opt-in (LAGWAVE_OZ_PAIR=1): it streams a quarter fewer operand bytes per
+// SM but measured slower than the one-SM kernel (the pair's stages complete at the pace of the
+// slower SM)
+static bool oz_pair_enabled() {
+  const char *v = std::getenv("LAGWAVE_OZ_PAIR");
+  return v != nullptr && v[0] == '1';
+}
+
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows) {
-  const size_t nmt = div_up(rows, TM);
+  const size_t nmt = oz_mtiles(rows);
   const size_t eo = (dp.kind == 1) ? 2 * (size_t)rows * dp.ku * sizeof(double) + 256 : 0;  // DCT-II E / O sums
   return 2 * (size_t)OZ_SMAX * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256 + eo;
 }
@@ -1273,10 +1688,11 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
   static PerDeviceOnce attr;
   attr.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm2_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ2_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         2 * OZ_PACK_MAXK * (int)sizeof(double)));
   });
-  const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
+  const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = oz_mtiles(rows);
   const size_t a_slice = (size_t)nmt * nks * A_TILE;
   uint8_t *apack = dp.tc_scratch;
   int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)NS * a_slice);
@@ -1285,15 +1701,25 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
                                                                          a_slice, erow, sc, rpr, inv);
   count_launch();
   LAG_LAUNCH_CHECK();
-  const OzSched sch = oz_schedule(nks * TK);
+  const OzSched sch = oz_schedule(nks * TK, OzFmt{NB, NS});
   const int ntiles = 2 * nmt * nnt;
   const int grid = std::min(ntiles, 152);
   // E / O sums of the inverse: after the packed A slices and the row exponents, 256-byte aligned
   double *eo = reinterpret_cast<double *>(
       (reinterpret_cast<uintptr_t>(erow + 2 * (size_t)nmt * TM) + 255) & ~(uintptr_t)255);
-  oz_gemm_kernel<NB, NS><<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
-                                                    erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,
-                                                    dp.kv, sch, sc, rpr, dp.tc_err, inv, rdot, rzpart);
+  // TMA coordinates are signed 32-bit: the pair kernel addresses the slice buffers by 128-byte row
+  if (!inv && oz_pair_enabled() && 2ull * NS * a_slice / 128 < (1ull << 31)) {
+    // two-SM pairs: 256-row tile pairs x column tiles x both parities, at most one pair per two SMs
+    const int pairs = std::min(2 * (nmt / 2) * nnt, 76);
+    const CUtensorMap tmA = rows_map(apack, 2ull * NS * a_slice / 128, TM);
+    const CUtensorMap tmB = rows_map(dp.oz_b, 2ull * NS * dp.oz_slice_bytes / 128, OZ_TN / 2);
+    oz_gemm2_kernel<NB, NS><<<2 * pairs, 320, OZ2_SMEM, s>>>(tmA, tmB, erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n,
+                                                             dp.ku, dp.kv, sch, sc, rpr, dp.tc_err, rdot, rzpart);
+  } else {
+    oz_gemm_kernel<NB, NS><<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
+                                                      erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,
+                                                      dp.kv, sch, sc, rpr, dp.tc_err, inv, rdot, rzpart);
+  }
   count_launch();
   LAG_LAUNCH_CHECK();
   if (inv) {
@@ -1308,7 +1734,8 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
   if (rows <= 0) return;
   ProfScope prof(KC_DST64, s);
   const int inv = (inverse && dp.kind == 1) ? 1 : 0;
-  if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, inv);
+  if (dp.oz_nb == 8) oz_apply_fmt<8, 7>(dp, x, y, rows, rpr, sc, s, inv);
+  else if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, inv);
   else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, inv);
 }
 
@@ -1321,7 +1748,8 @@ void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, in
   if (rows <= 0) return;
   {
     ProfScope prof(KC_DST64, s);
-    if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
+    if (dp.oz_nb == 8) oz_apply_fmt<8, 7>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
+    else if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
     else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
   }
   ProfScope prof(KC_VEC, s);

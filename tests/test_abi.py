@@ -73,11 +73,12 @@ def test_no_oracle_in_product_path():
 
 def test_exact_slice_product_counts():
     # host-only: the exact-slice DST keeps the pairs i + j <= NS + 1 of NS slices per operand:
-    # 8 seven-bit slices (36 pairs) while 127^2 K <= 2^24 (K = ceil(n/2) padded to 64, up to 1024),
-    # 9 six-bit slices (45 pairs) above, none outside 16 <= n, K <= 4224
+    # 7 eight-bit slices (28 pairs, exact pairs summed in K chunks of 256) while K = ceil(n/2) padded
+    # to 64 is at most 1024, 9 six-bit slices (45 pairs) above, none outside 16 <= n, K <= 4224
     from paper_1005_0542_gb300 import lagwave as L
-    assert [L.lag_dst_f64_slice_products(n) for n in (8, 15, 16, 255, 2048)] == [0, 0, 36, 36, 36]
+    assert [L.lag_dst_f64_slice_products(n) for n in (8, 15, 16, 255, 2048)] == [0, 0, 28, 28, 28]
     assert [L.lag_dst_f64_slice_products(n) for n in (2049, 4096, 8448)] == [45, 45, 45]
     assert L.lag_dst_f64_slice_products(8449) == 0
-    assert sum(1 for i in range(1, 9) for j in range(1, 9) if i + j <= 9) == 36
+    assert sum(1 for i in range(1, 8) for j in range(1, 8) if i + j <= 8) == 28
     assert sum(1 for i in range(1, 10) for j in range(1, 10) if i + j <= 10) == 45
+    assert 255 * 255 * 256 < 2 ** 24 < 255 * 255 * 259

@@ -306,3 +306,43 @@ def test_dst_f64_exact_slices_nonfinite_row(ctx):
     ok = [0, 2, 3]
     assert rel(y[0, ok], odst.dst_x(x[:, ok])[0]) < 1e-14
     L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nx,nz,nrhs", [(16, 3, 1), (255, 130, 1), (2048, 1024, 1), (1000, 77, 5), (4096, 256, 2)])
+def test_dst_f64_two_sm_pairs_equal_one_sm_tiles(ctx, monkeypatch, nx, nz, nrhs):
+    # the exact-slice GEMM on two-SM pairs (cta_group::2: 256-row tile pairs, each SM holding half
+    # of the B columns) against the one-SM kernel: the same exact slice products and int64 sums,
+    # so the same float64 results; row counts that leave the last pair half empty, ragged columns
+    x = RNG.standard_normal((nrhs, nz, nx))
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    assert L.lag_precond_uses_tensor_cores(p) == 1
+    xd, y2, y1 = dev(x), empty(x.shape), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(y1), nrhs), ctx)
+    monkeypatch.setenv("LAGWAVE_OZ_PAIR", "1")
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(y2), nrhs), ctx)
+    monkeypatch.delenv("LAGWAVE_OZ_PAIR")
+    a, b = host(y2), host(y1)
+    assert rel(a, b) < 1e-15
+    assert rel(a, odst.dst_x(x)) < 1e-14
+    L.lag_precond_destroy(p)
+
+
+@pytest.mark.parametrize("nx", [16, 255, 1000, 2048])
+def test_dst_f64_eight_bit_slices_equal_seven_bit(ctx, monkeypatch, nx):
+    # the 8-bit exact-slice format (28 pairs, exact pairs in K chunks of 256) against the 7-bit one
+    # (36 pairs): two different exact decompositions of the same float64 products
+    nz, nrhs = 40, 2
+    x = RNG.standard_normal((nrhs, nz, nx)) * 10.0 ** RNG.uniform(-30, 30, (nrhs, nz, 1))
+    p8 = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    monkeypatch.setenv("LAGWAVE_OZ_BITS", "7")
+    p7 = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    monkeypatch.delenv("LAGWAVE_OZ_BITS")
+    xd, y8, y7 = dev(x), empty(x.shape), empty(x.shape)
+    L.check(L.lag_precond_dst(p8, ptr(xd), ptr(y8), nrhs), ctx)
+    L.check(L.lag_precond_dst(p7, ptr(xd), ptr(y7), nrhs), ctx)
+    a, b, ref = host(y8), host(y7), odst.dst_x(x)
+    sc = np.abs(ref).max(axis=-1, keepdims=True)
+    assert np.abs((a - ref) / sc).max() < 1e-14 and np.abs((b - ref) / sc).max() < 1e-14
+    assert np.abs((a - b) / sc).max() < 1e-14
+    L.lag_precond_destroy(p8)
+    L.lag_precond_destroy(p7)
