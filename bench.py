@@ -1010,6 +1010,36 @@ def capture_extensions(args):
     print(json.dumps({"capture": "ok"}))
 
 
+def capture_shot(args):
+    """Three harmonics of the 2048 x 1024 shot (--capture-shot fp64 or mixed) with every kernel
+    launched eagerly (no graphs), for `ncu -k ... -s N -c M` captures at the shot's shape: the
+    exact-slice pack and GEMM, the float64 tridiagonal solve (fp64); the split-bf16 DST kernels
+    (forward pack + GEMM, inverse pack + GEMM + butterfly with the CG dots), the float32
+    tridiagonal solve (mixed); the PCG kernels (both)."""
+    import torch
+    from paper_1005_0542_gb300 import inputs
+    from paper_1005_0542_gb300 import lagwave as L
+    os.environ["LAGWAVE_GRAPHS"] = "0"
+    ctx = L.create(0, stream=torch.cuda.current_stream().cuda_stream)
+    s = inputs.random_layered()
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=s.tol, prec=L.LAG_MIXED if args.capture_shot == "mixed" else L.LAG_FP64)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    sh = C.c_void_p()
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                              C.byref(sh)), ctx)
+    L.check(L.lag_shot_step(sh, 3), ctx)
+    torch.cuda.synchronize()
+    L.lag_shot_destroy(sh)
+    L.lag_destroy(ctx)
+    print(json.dumps({"capture": "ok"}))
+
+
 # ---------------------------------------------------------------------------------- reference arm
 def reference_arm(args):
     from paper_1005_0542_gb300 import inputs
@@ -1050,6 +1080,8 @@ def main():
     ap.add_argument("--serve-nharm", type=int, nargs=2, default=[4, 16])
     ap.add_argument("--capture-extensions", action="store_true",
                     help="launch the layered / cylindrical plan kernels once (1024 x 1024 x 16 RHS) for ncu, then exit")
+    ap.add_argument("--capture-shot", choices=["fp64", "mixed"],
+                    help="three eager harmonics of the 2048 x 1024 shot on the given path for ncu, then exit")
     ap.add_argument("--capture-kernels", action="store_true",
                     help="launch each hot kernel once (1024 x 1024 x 16 RHS) for ncu captures, then exit")
     args = ap.parse_args()
@@ -1063,6 +1095,9 @@ def main():
         return
     if args.capture_extensions:
         capture_extensions(args)
+        return
+    if args.capture_shot:
+        capture_shot(args)
         return
     if args.impl == "reference":
         if rank != 0:

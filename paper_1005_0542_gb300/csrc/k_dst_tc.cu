@@ -480,27 +480,28 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
   const size_t row0 = (size_t)rhs * rpr;
   const int es = residual_exponent(sc, rhs);  // the forward pack scaled r by 2^-e
   double a0 = 0.0, a1 = 0.0;
-  // rows round-robin over the blocks, a row's modes over the threads (no 64-bit index division)
-  for (int rl = blockIdx.x; rl < rpr; rl += gridDim.x)
-  for (int k = threadIdx.x; k < ku; k += blockDim.x) {
+  // rows round-robin over the blocks, a row's modes over the threads (no 64-bit index division);
+  // E +- O in float32 (the spectrum's precision), widened once, the CG dots in float64
+  for (int rl = blockIdx.x; rl < rpr; rl += gridDim.x) {
     const size_t row = row0 + (size_t)rl;
     const float *er = eo + row * 2 * ku;
-    double e = (double)er[k], o = (double)er[ku + k];
-    if (es != 0) {
-      e = scale_pow2(e, es);
-      o = scale_pow2(o, es);
-    }
-    const size_t i1 = row * n + k;
-    const double z1 = e + o;
-    z[i1] = z1;
-    a0 = fma(r[i1], z1, a0);
-    if (flexible) a1 = fma(z1, q[i1], a1);
-    if (k < kv) {
-      const size_t i2 = row * n + (n - 1 - k);
-      const double z2 = e - o;
-      z[i2] = z2;
-      a0 = fma(r[i2], z2, a0);
-      if (flexible) a1 = fma(z2, q[i2], a1);
+#pragma unroll 4
+    for (int k = threadIdx.x; k < ku; k += blockDim.x) {
+      const float e = er[k], o = er[ku + k];
+      const size_t i1 = row * n + k;
+      double z1 = (double)(e + o);
+      if (es != 0) z1 = scale_pow2(z1, es);
+      z[i1] = z1;
+      a0 = fma(r[i1], z1, a0);
+      if (flexible) a1 = fma(z1, q[i1], a1);
+      if (k < kv) {
+        const size_t i2 = row * n + (n - 1 - k);
+        double z2 = (double)(e - o);
+        if (es != 0) z2 = scale_pow2(z2, es);
+        z[i2] = z2;
+        a0 = fma(r[i2], z2, a0);
+        if (flexible) a1 = fma(z2, q[i2], a1);
+      }
     }
   }
   double v2[2] = {a0, a1}, tot[2];
@@ -824,7 +825,7 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
 // non-negative doubles; NaN and Inf patterns compare above every finite one).  Pass 2 cuts each
 // group of 8 consecutive values into slices from the bits and stores them 16 bytes at a time.
 // Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r with |values| < 2^e_r.
-constexpr int OZ_PACK_THREADS = 256;
+constexpr int OZ_PACK_THREADS = 128;  // 42 registers: 128-thread CTAs keep every row of a shot resident at once
 constexpr int OZ_PACK_MAXK = 4224;  // ceil(n / 2) bound of the exact-slice path (K pad <= 4224)
 // gather (DCT-II inverse): u = the even entries x[2j], v = the odd ones x[2j+1] instead of the fold.
 template <int NB, int NS>
@@ -904,14 +905,49 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
     }
     const uint32_t off = swz(r, kk);
     uint8_t *tile0 = out + (size_t)par * NS * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
+    if constexpr (NB == 8) {
+      // balanced digits straight from the bytes of T + 128 (256^0 + ... + 256^5), split into two
+      // 32-bit words: one byte permute builds 2^23 + byte as a float, one subtraction and one
+      // power-of-two multiply give the signed, pre-scaled digit (the same values as oz_slice_f)
+      uint32_t th[8], tl[8];
 #pragma unroll
-    for (int i = 1; i <= NS; ++i) {
-      uint32_t hw[4];
+      for (int q = 0; q < 8; ++q) {
+        const unsigned long long Tb = T[q] + 0x0000808080808080ull;
+        tl[q] = (uint32_t)Tb;
+        th[q] = (uint32_t)(Tb >> 32);
+      }
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        hw[q] = oz_pack2(oz_slice_f<NB, NS>(T[2 * q], i, (negm >> (2 * q)) & 1u),
-                         oz_slice_f<NB, NS>(T[2 * q + 1], i, (negm >> (2 * q + 1)) & 1u));
-      *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      for (int i = 1; i <= NS; ++i) {
+        const uint32_t cbits = (uint32_t)(127 - 8 * (i - 1)) << 23;  // 2^-(8 (i - 1))
+        const float offv = (i == 1) ? 8388608.0f : 8388736.0f;
+        uint32_t hw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float d[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int v = 2 * q + h;
+            uint32_t fb;
+            if (i == 1) fb = 0x4B000000u | ((th[v] >> 16) & 0x1ffu);
+            else if (i <= 3) fb = __byte_perm(th[v], 0x4B00u, 0x5440u | (uint32_t)(3 - i));
+            else fb = __byte_perm(tl[v], 0x4B00u, 0x5440u | (uint32_t)(7 - i));
+            const float cq = __uint_as_float(cbits | (((negm >> v) & 1u) << 31));
+            d[h] = (__uint_as_float(fb) - offv) * cq;
+          }
+          hw[q] = oz_pack2(d[0], d[1]);
+        }
+        *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 1; i <= NS; ++i) {
+        uint32_t hw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          hw[q] = oz_pack2(oz_slice_f<NB, NS>(T[2 * q], i, (negm >> (2 * q)) & 1u),
+                           oz_slice_f<NB, NS>(T[2 * q + 1], i, (negm >> (2 * q + 1)) & 1u));
+        *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      }
     }
   }
 }
@@ -1649,26 +1685,30 @@ __global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__res
   }
 }
 
-// PCG's (r, z) and beta from the exact-slice GEMM's partials: grid (blocks, nrhs), one thread per
-// row summing that row's partials of the column tiles that exist, then the block sums combined by
-// the last block in block order (deterministic, and the same alone or in a batch); beta =
-// rz_new / rz (Fletcher-Reeves), 0 on the first iteration of a solve.
-constexpr int OZ_RZ_THREADS = 128;
-__global__ void __launch_bounds__(OZ_RZ_THREADS) oz_rz_beta_kernel(const double *__restrict__ part, int rpr, int nnt,
-                                                                   int ku, int kv, KrylovScalars *sc, Reduce red) {
+// PCG's (r, z) and beta from the exact-slice GEMM's partials, per right-hand side rpr rows of
+// dst_oz_rz_parts values (one per parity, column tile and half); the slots of column tiles that
+// never run stay at the zero the buffer starts with.  grid (blocks, nrhs): each thread sums a fixed run of OZ_RZ_PER values,
+// the block sums combined by the last block in block order (deterministic, and the same alone or
+// in a batch); beta = rz_new / rz (Fletcher-Reeves), 0 on the first iteration of a solve.
+constexpr int OZ_RZ_THREADS = 256;
+constexpr int OZ_RZ_PER = 8;
+__global__ void __launch_bounds__(OZ_RZ_THREADS) oz_rz_beta_kernel(const double *__restrict__ part, size_t per_rhs,
+                                                                   KrylovScalars *sc, Reduce red) {
   const int rhs = blockIdx.y;
   if (sc[rhs].state != ST_RUN) return;
-  const int np = 4 * nnt;
-  const int rl = blockIdx.x * OZ_RZ_THREADS + threadIdx.x;
+  const double *pr = part + (size_t)rhs * per_rhs;
+  const size_t i0 = ((size_t)blockIdx.x * OZ_RZ_THREADS + threadIdx.x) * OZ_RZ_PER;
   double acc = 0.0;
-  if (rl < rpr) {
-    const double *pr = part + ((size_t)rhs * rpr + rl) * np;
-#pragma unroll 8
-    for (int sl = 0; sl < np; ++sl) {
-      const int h = sl & 1, tile = sl >> 1;
-      const int par = tile / nnt, nt = tile - par * nnt;
-      if (nt * OZ_TN + h * 64 < (par ? kv : ku)) acc += __ldg(pr + sl);
+  if (i0 + OZ_RZ_PER <= per_rhs) {
+    const double2 *p2 = reinterpret_cast<const double2 *>(pr + i0);
+#pragma unroll
+    for (int q = 0; q < OZ_RZ_PER / 2; ++q) {
+      const double2 v = __ldg(p2 + q);
+      acc += v.x;
+      acc += v.y;
     }
+  } else {
+    for (size_t i = i0; i < per_rhs; ++i) acc += pr[i];
   }
   double v1[1] = {acc}, tot[1];
   __shared__ double sh[32];
@@ -1753,9 +1793,10 @@ void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, in
     else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
   }
   ProfScope prof(KC_VEC, s);
-  const int nb = div_up(rpr, OZ_RZ_THREADS);
-  if (nb > red.nblk) throw Error(LAG_EINVAL, "exact-slice (r, z): more row blocks than the reduction holds");
-  oz_rz_beta_kernel<<<dim3(nb, nrhs), OZ_RZ_THREADS, 0, s>>>(rzpart, rpr, dp.npad_u, dp.ku, dp.kv, sc, red);
+  const size_t per_rhs = (size_t)rpr * dst_oz_rz_parts(dp);  // even: whole double2 runs per row pair
+  const int nb = (int)((per_rhs + (size_t)OZ_RZ_THREADS * OZ_RZ_PER - 1) / ((size_t)OZ_RZ_THREADS * OZ_RZ_PER));
+  if (nb > red.nblk) throw Error(LAG_EINVAL, "exact-slice (r, z): more blocks than the reduction holds");
+  oz_rz_beta_kernel<<<dim3(nb, nrhs), OZ_RZ_THREADS, 0, s>>>(rzpart, per_rhs, sc, red);
   count_launch();
   LAG_LAUNCH_CHECK();
 }

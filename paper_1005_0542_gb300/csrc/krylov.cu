@@ -115,7 +115,7 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
     wcount.alloc(ctx, 4 * sizeof(unsigned int), true);  // [0] repeats this launch, [2..3] bodies in total
     wbodies_seen = 0;
     if (p1->prec == LAG_FP64 && dst_oz_rz_fusable(p1->dst))
-      rzpart.alloc(ctx, (size_t)nrhs * p1->grid.nz * dst_oz_rz_parts(p1->dst) * sizeof(double));
+      rzpart.alloc(ctx, (size_t)nrhs * p1->grid.nz * dst_oz_rz_parts(p1->dst) * sizeof(double), true);  // zeros
     else
       rzpart.release();
   }
