@@ -40,7 +40,7 @@ size_t estimate_bytes(const lag_request &r) {
   const size_t nx = r.grid.nx, nz = r.grid.nz, n = nx * nz;
   const size_t ncomp = r.kind == 1 ? 2 : 1;
   const size_t nsrc = r.nsrc;
-  const size_t nvec = r.kind == 1 ? 3 + 2 * (size_t)r.solver.restart_k + 1 : 6;
+  const size_t nvec = r.kind == 1 ? 3 + 2 * (size_t)r.solver.restart_k + 1 : 7;
   size_t b = (nvec + 2) * n * ncomp * nsrc * 8;                 // Krylov vectors + T, S
   b += (r.kind == 1 ? 12 : 6) * n * 8;                           // operator coefficients, rho h^2
   const size_t nplans = r.kind == 1 ? 2 : 1;
