@@ -762,7 +762,7 @@ def _serve_trace(ctx, trace, active, budget_s):
             res = L.lag_result()
             res.traces_host = buf.ctypes.data_as(L.PD)
             if L.lag_serve_poll(ctx, t, C.byref(res)) == L.LAG_OK:
-                results[i] = (res.status, res.t_submit, res.t_admit, res.t_done)
+                results[i] = (res.status, res.t_submit, res.t_admit, res.t_done, res.harmonics_done)
             else:
                 pending += 1
         if pending == 0:
@@ -779,8 +779,9 @@ def _serve_trace(ctx, trace, active, budget_s):
     lat = np.array([r[3] - r[1] for _, r in done]) if done else np.zeros(1)
     queue = np.array([r[2] - r[1] for _, r in done]) if done else np.zeros(1)
     service = np.array([r[3] - r[2] for _, r in done]) if done else np.zeros(1)
-    solves = sum(q["n_harm"] for q, _ in done)
+    solves = sum(r[4] for r in results)  # every harmonic solved, the cancelled requests' included
     return {"requests": len(reqs), "completed": len(done),
+            "admitted": sum(1 for r in results if r[2] > 0), "harmonic_solves": int(solves),
             "cancelled_at_budget": sum(1 for r in results if r[0] == L.LAG_ECANCELED),
             "failed": sum(1 for r in results if r[0] not in (L.LAG_OK, L.LAG_ECANCELED)),
             "value": solves / makespan, "unit": UNIT, "makespan_s": makespan, "budget_s": budget_s,

@@ -373,6 +373,7 @@ typedef struct {
   double t_submit, t_admit, t_done;   /* seconds since the context was created             */
   long long total_iters;
   size_t device_bytes;         /* device memory the request held                           */
+  int harmonics_done;          /* harmonics solved (all of them unless cancelled or failed) */
 } lag_result;
 
 /* Failure-detection self-test (no counterpart in the paper): launches one kernel that waits on an

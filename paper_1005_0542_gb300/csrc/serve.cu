@@ -32,6 +32,7 @@ struct Request {
   double t_submit = 0, t_admit = 0, t_done = 0;
   long long iters = 0;
   size_t device_bytes = 0;
+  int harmonics = 0;
   std::string error;
 };
 
@@ -73,6 +74,7 @@ struct Server {
     r->t_done = now_seconds() - ctx->t_created;
     if (r->shot) {
       r->iters = r->shot->total_iters;
+      r->harmonics = r->shot->m;
       r->device_bytes = r->shot->device_bytes;
       lag_shot_destroy(r->shot);
       r->shot = nullptr;
@@ -279,6 +281,7 @@ int lag_serve_poll(lag_ctx *ctx, uint64_t ticket, lag_result *out) {
   out->t_done = r->t_done;
   out->total_iters = r->iters;
   out->device_bytes = r->device_bytes;
+  out->harmonics_done = r->harmonics;
   if (out->traces_host && !r->traces.empty())
     std::memcpy(out->traces_host, r->traces.data(), r->traces.size() * sizeof(double));
   if (!r->error.empty()) ctx->last_error = r->error;

@@ -58,7 +58,7 @@ class lag_request(C.Structure):
 class lag_result(C.Structure):
     _fields_ = [("status", C.c_int), ("traces_host", C.POINTER(C.c_double)), ("t_submit", C.c_double),
                 ("t_admit", C.c_double), ("t_done", C.c_double), ("total_iters", C.c_longlong),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("harmonics_done", C.c_int)]
 
 
 VP = C.c_void_p
