@@ -206,15 +206,33 @@ int  lag_precond_tridiag_f32(lag_precond *p, const float *d_dev, float *y_dev, i
 int  lag_precond_dst_f32(lag_precond *p, const float *x_dev, double *y_dev, int nrhs);
 /* 1 if the plan's DST (cylindrical: DCT-II) runs on the tcgen05 tensor cores, else 0.  Mixed plans: split-bf16 operands,
  * FP32 accumulation.  Float64 plans (n >= 16, ceil(n/2) <= 4224): exact slices -- each folded row
- * and S are cut into 9 six-bit integer slices on a power-of-two grid (54 bits), the slice products
- * are summed exactly in FP32 tensor memory (integers below 2^24) and combined in float64, so the
+ * and S are cut into small integer slices on a power-of-two grid (7 balanced 8-bit digits of a
+ * 55-bit expansion for ceil(n/2) <= 1024, else 8 seven-bit or 9 six-bit slices), the slice products
+ * are summed exactly in FP32 tensor memory (integers below 2^24) and combined in int64, so the
  * result carries float64 rounding only (relative error < 1e-14 per row in the tests).  The
  * environment variable LAGWAVE_DST_KERNEL=simt at plan creation selects the SIMT kernels. */
 int  lag_precond_uses_tensor_cores(const lag_precond *p);
 /* bf16 slice products the float64 tensor-core DST of length n forms per float64 multiply-add:
- * 36 (8 seven-bit slices) for ceil(n/2) <= 1024, 45 (9 six-bit slices) above; 0 where the
- * exact-slice path does not apply (n < 16 or ceil(n/2) > 4224). */
+ * 28 (7 balanced 8-bit digits) for ceil(n/2) <= 1024 (36 with LAGWAVE_OZ_BITS=7 in the
+ * environment), 36 (8 seven-bit slices) or 45 (9 six-bit slices) above; 0 where the exact-slice
+ * path does not apply (n < 16 or ceil(n/2) > 4224). */
 int  lag_dst_f64_slice_products(int n);
+/* The GEMM kernel that the forward transform (lag_precond_dst, and the forward DST inside
+ * lag_precond_apply and the solvers) of nrhs right-hand sides launches on this plan and device:
+ *   LAG_GEMM_SIMT           no tensor-core GEMM (SIMT kernels)
+ *   LAG_GEMM_SPLIT_BF16     mixed plan: split-bf16 operands, FP32 accumulation
+ *   LAG_GEMM_SLICE_TILES    float64 exact slices, one CTA per 128 x 128 output tile
+ *   LAG_GEMM_SLICE_STREAMK  float64 exact slices, the steps of all tiles cut into equal ranges, one
+ *                           per SM (LAGWAVE_OZ_SK=1, opt-in: one right-hand side whose tile count is
+ *                           not a multiple of the SM count)
+ *   LAG_GEMM_SLICE_PAIRS    float64 exact slices on two-SM pairs (LAGWAVE_OZ_PAIR=1, opt-in)
+ * A negative LAG_E* code for a null plan or nrhs < 1. */
+#define LAG_GEMM_SIMT 0
+#define LAG_GEMM_SPLIT_BF16 1
+#define LAG_GEMM_SLICE_TILES 2
+#define LAG_GEMM_SLICE_STREAMK 3
+#define LAG_GEMM_SLICE_PAIRS 4
+int  lag_precond_dst_gemm(lag_precond *p, int nrhs);
 /* Tensor-core DST of a mixed plan: number of bf16 products per K step (3: split hi*hi + hi*lo +
  * lo*hi, relative error ~1e-5; 2: hi*hi + lo*hi with S rounded to bf16, ~2e-3; 1: hi*hi, ~4e-3).
  * Default 3 (or the environment variable LAGWAVE_DST_PRODUCTS at plan creation).  The flexible

@@ -69,7 +69,7 @@ void lag_precond::ensure_scratch(int nrhs) {
     tc_scratch.alloc(ctx, dst_tc_scratch_bytes(dst, nrhs * grid.nz));
     dst.tc_scratch = tc_scratch.as<uint8_t>();
   } else if (dst.oz) {
-    tc_scratch.alloc(ctx, dst_oz_scratch_bytes(dst, nrhs * grid.nz));
+    tc_scratch.alloc(ctx, dst_oz_scratch_bytes(dst, nrhs * grid.nz), true);  // stream-K counters start at 0
     dst.tc_scratch = tc_scratch.as<uint8_t>();
   }
   scratch_rhs = nrhs;
@@ -419,7 +419,8 @@ int lag_precond_status(lag_precond *p) {
     LAG_CUDA_CHECK(cudaMemcpy(&h, p->dst.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h != 0)
       throw Error(LAG_ETIMEDOUT, "tensor-core DST: a bounded pipeline wait gave up (code " + std::to_string(h) +
-                                     ": 1-4 split-bf16 GEMM, 11-14 exact-slice GEMM)");
+                                     ": 1-4 split-bf16 GEMM, 11-14 exact-slice GEMM, 21-24 its two-SM pairs, "
+                                     "31-36 its stream-K variant)");
   });
 }
 
@@ -523,6 +524,18 @@ int lag_dst_f64_slice_products(int n) {
 }
 
 int lag_precond_uses_tensor_cores(const lag_precond *p) { return p ? ((p->use_tc || p->dst.oz) ? 1 : 0) : 0; }
+
+int lag_precond_dst_gemm(lag_precond *p, int nrhs) {
+  if (!p || nrhs < 1) return LAG_EINVAL;
+  if (p->use_tc) return LAG_GEMM_SPLIT_BF16;
+  if (!p->dst.oz) return LAG_GEMM_SIMT;
+  int v = LAG_GEMM_SLICE_TILES;
+  const int rc = guarded(p->ctx, [&] {
+    set_device(p->ctx);
+    v = dst_oz_gemm_variant(p->dst, nrhs * p->grid.nz, p->grid.nz, 0);
+  });
+  return rc == LAG_OK ? v : rc;
+}
 
 int lag_precond_set_layout(lag_precond *p, int partitions, int modes_per_cta) {
   if (!p || partitions < 0 || partitions > 32 || modes_per_cta < 0) return LAG_EINVAL;

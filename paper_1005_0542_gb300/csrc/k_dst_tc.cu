@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <atomic>
 #include <cstdlib>
 #include <cstdint>
 
@@ -735,6 +736,8 @@ struct OzSched {
   int8_t first[OZ_MAXU], last[OZ_MAXU];       // group start / end flags
   int8_t gsh[OZ_MAXU];  // per group: s >= 0 if its sum is an exact integer G with value G 2^-(FIX - s)
                         // (the int64 epilogue adds G << s), -1 for a rounded group (rn(v 2^FIX))
+  uint8_t ug[OZ_MAXU];  // group of each unit
+  int nstage;           // pipeline stages of one tile (each unit's K tiles in steps of OZ_KT)
 };
 
 // The epilogue's accumulator: a signed fixed-point integer in units of 2^-FIX of the pre-scaled
@@ -877,14 +880,23 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
     red[1][threadIdx.x >> 5] = b1;
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
-    unsigned long long m = 0;
-    for (int w = 0; w < OZ_PACK_THREADS / 32; ++w) m = max(m, red[threadIdx.x][w]);
-    const int E = (int)(m >> 52);
-    // |values| <= m < 2^(E - 1022) for normal m, < 2^-1022 for subnormal m; 0 for a zero row
-    const int e = (E == 0x7ff) ? OZ_EXP_NAN : (m == 0 ? 0 : (E == 0 ? -1022 : E - 1022));
-    esh[threadIdx.x] = e;
-    if (row < rows) erow[threadIdx.x * (nmt * TM) + row] = e;
+  if (threadIdx.x == 0) {
+    int e[2];
+    for (int par = 0; par < 2; ++par) {
+      unsigned long long m = 0;
+      for (int w = 0; w < OZ_PACK_THREADS / 32; ++w) m = max(m, red[par][w]);
+      const int E = (int)(m >> 52);
+      // |values| <= m < 2^(E - 1022) for normal m, < 2^-1022 for subnormal m; 0 for a zero row
+      e[par] = (E == 0x7ff) ? OZ_EXP_NAN : (m == 0 ? 0 : (E == 0 ? -1022 : E - 1022));
+    }
+    // a non-finite value anywhere in the row makes every output of the row non-finite, as in a
+    // float64 product (the middle element of an odd-length row reaches one parity only, yet its
+    // zero coefficient in the other parity's modes still gives inf x 0 = NaN there)
+    if (e[0] == OZ_EXP_NAN || e[1] == OZ_EXP_NAN) e[0] = e[1] = OZ_EXP_NAN;
+    for (int par = 0; par < 2; ++par) {
+      esh[par] = e[par];
+      if (row < rows) erow[par * (nmt * TM) + row] = e[par];
+    }
   }
   __syncthreads();
   const int mt = row / TM, r = row % TM;
@@ -1180,6 +1192,359 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_NACC * OZ_TN) : "memory");
+}
+
+// ---------------------------------------------------------------- stream-K variant
+// The same GEMM (forward transforms of one right-hand side) with the sequence of (tile, pipeline
+// stage) steps of all tiles cut into one equal range per CTA, one CTA per SM, so that every SM gets
+// the same work when the tile count is not a multiple of the SM count (a 2048 x 1024 field: 128
+// tiles on 152 SMs).  A range that starts or ends inside a group accumulates that part alone; the
+// parts of a group are added in int64 (exact for exact groups; a rounded group is rounded once per
+// part, each within the group's bound).
+// A tile that no one CTA covers whole is finished by the CTA holding its last step (the finaliser).
+// A CTA whose range starts inside a tile runs its range rotated: from the next tile boundary to its
+// end, then its first steps, so that the finaliser holds its own part in registers when it comes to
+// finish the tile.  Every other part (the end of a range, or a range inside one tile) goes to the
+// CTA's slot of `part` as int64, column-major, with a flag per epilogue warp set to the launch's
+// mark; the finaliser waits (bounded) for the flags of the CTAs before it that touch the tile, adds
+// their parts and stores the tile.  CTAs take their range index from a ticket counter as they
+// start, so a CTA only waits for CTAs that started before it, and those write their parts before
+// they wait for anything: the hand-over cannot deadlock, whatever the order in which the hardware
+// places the CTAs or other work shares the GPU.  The last CTA to finish resets the counters and
+// advances the epoch, so flags left by an aborted launch never match a later launch's mark.
+constexpr int OZ_SK_MAXG = 256;  // CTAs of a stream-K launch at most
+struct OzSkArea {
+  long long *part;  // [G][TN][TM] int64 partial tiles, one slot per CTA
+  int *ctl;         // ticket, finished, epoch (64 ints reserved)
+  int *flag;        // [G][8]
+};
+template <int NB, int NS>
+__global__ void __launch_bounds__(320, 1) oz_gemm_sk_kernel(const uint8_t *__restrict__ apack, size_t a_slice_bytes,
+                                                            const uint8_t *__restrict__ bpack, size_t b_slice_bytes,
+                                                            const int *__restrict__ erow, int eB, int nks, int nmt,
+                                                            int nnt, int rows, double *__restrict__ y, int ld, int ku,
+                                                            int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
+                                                            int *__restrict__ err, const double *__restrict__ rdot,
+                                                            double *__restrict__ rzpart, OzSkArea ska) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + OZ_NST * OZ_STAGE;
+  const uint32_t full0 = bars, empty0 = bars + 8 * OZ_NST, tfull0 = bars + 16 * OZ_NST, tempty0 = tfull0 + 8 * OZ_NACC;
+  volatile uint32_t *holder =
+      reinterpret_cast<volatile uint32_t *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 16);
+  volatile int *shared_ticket = abort_flag + 1;  // [ticket, epoch]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)holder)),
+                 "r"(OZ_NACC * OZ_TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < OZ_NST; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int a = 0; a < OZ_NACC; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 8);  // one arrive per epilogue warp
+    }
+    *abort_flag = 0;
+    int t = atomicAdd(ska.ctl, 1);
+    if (t < 0 || t >= G) {  // counters not reset: nothing is computed, the solve reports it
+      atomicExch(err, 36);
+      t = G;
+    }
+    shared_ticket[0] = t;
+    shared_ticket[1] = *reinterpret_cast<volatile int *>(ska.ctl + 2);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *holder;
+  const int d = shared_ticket[0];         // this CTA's range index (order of start)
+  const int mark = shared_ticket[1] + 1;  // flag value of this launch
+  const bool run = sc == nullptr || sc[0].state == ST_RUN;  // one right-hand side
+  const int nmtv = (rows + TM - 1) / TM;
+  const int nnt0 = (ku + OZ_TN - 1) / OZ_TN, nnt1 = (kv + OZ_TN - 1) / OZ_TN;
+  const int S = sch.nstage;
+  const int total = (run && d < G) ? nmtv * (nnt0 + nnt1) * S : 0;
+  auto range_b = [&](int c) { return (int)((long long)c * total / G); };
+  const int sk_b = range_b(d), sk_e = range_b(d + 1);
+  // the tile of the first step; a range starting inside it runs [x0, sk_e) and then [sk_b, x0)
+  const int vt0 = sk_b / (S > 0 ? S : 1);
+  const int x0 = (sk_b > vt0 * S) ? min(sk_e, (vt0 + 1) * S) : sk_b;
+  const bool finaliser = sk_b > vt0 * S && x0 == (vt0 + 1) * S;
+  auto tile_of = [&](int v, int &par, int &mt, int &nt) {
+    const int n0 = nmtv * nnt0;
+    par = v >= n0 ? 1 : 0;
+    const int w = v - par * n0, nn = par ? nnt1 : nnt0;
+    mt = w / nn;
+    nt = w - mt * nn;
+  };
+  // position of step s0: tile v, unit u and its K tile kk
+  auto locate = [&](int s0, int &v, int &u, int &kk) {
+    v = s0 / S;
+    int rem = s0 - v * S;
+    u = 0;
+    for (;;) {
+      const int nst = (sch.k1[u] - sch.k0[u] + OZ_KT - 1) / OZ_KT;
+      if (rem < nst) break;
+      rem -= nst;
+      ++u;
+    }
+    kk = sch.k0[u] + rem * OZ_KT;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int it = 0;
+      for (int pass = 0; pass < 2 && !*abort_flag; ++pass) {
+        const int rb = pass ? sk_b : x0, re = pass ? x0 : sk_e;
+        if (rb >= re) continue;
+        int v, u, kk, par, mt, nt;
+        locate(rb, v, u, kk);
+        tile_of(v, par, mt, nt);
+        const uint8_t *at = apack + ((size_t)par * NS + (sch.si[u] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
+        const uint8_t *bt = bpack + ((size_t)par * NS + (sch.sj[u] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+        for (int s = rb; s < re && !*abort_flag; ++s, ++it) {
+          const int kt = min(OZ_KT, sch.k1[u] - kk);
+          const int st_i = it % OZ_NST, use = it / OZ_NST;
+          if (it >= OZ_NST && !mbar_wait(empty0 + 8 * st_i, (use - 1) & 1)) {
+            atomicExch(err, 31);
+            *abort_flag = 1;
+            break;
+          }
+          const uint32_t st = base + st_i * OZ_STAGE;
+          const uint32_t fb = full0 + 8 * st_i;
+          mbar_expect_tx(fb, (uint32_t)(kt * (A_TILE + OZ_BT)));
+          bulk_g2s(st, at + (size_t)kk * A_TILE, (uint32_t)(kt * A_TILE), fb);
+          bulk_g2s(st + OZ_KT * A_TILE, bt + (size_t)kk * OZ_BT, (uint32_t)(kt * OZ_BT), fb);
+          kk += OZ_KT;
+          if (kk >= sch.k1[u]) {  // the next unit, or the next tile's first
+            if (++u == sch.nunits) {
+              u = 0;
+              if (s + 1 < re) tile_of(++v, par, mt, nt);
+            }
+            kk = sch.k0[u];
+            at = apack + ((size_t)par * NS + (sch.si[u] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
+            bt = bpack + ((size_t)par * NS + (sch.sj[u] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int it = 0, gc = 0;
+      uint32_t dacc = 0;
+      for (int pass = 0; pass < 2 && !*abort_flag; ++pass) {
+        const int rb = pass ? sk_b : x0, re = pass ? x0 : sk_e;
+        if (rb >= re) continue;
+        int v, u, kk;
+        locate(rb, v, u, kk);
+        for (int s = rb; s < re && !*abort_flag; ++s, ++it) {
+          const int kt = min(OZ_KT, sch.k1[u] - kk);
+          const bool start = s == rb || (kk == sch.k0[u] && sch.first[u]);
+          const bool end = s + 1 == re || (kk + OZ_KT >= sch.k1[u] && sch.last[u]);
+          if (start) {
+            const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
+            if (gc >= OZ_NACC && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) {
+              atomicExch(err, 32);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            dacc = tmem + (uint32_t)(acc * OZ_TN);
+          }
+          const int st_i = it % OZ_NST, use = it / OZ_NST;
+          if (!mbar_wait(full0 + 8 * st_i, use & 1)) {
+            atomicExch(err, 33);
+            *abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + st_i * OZ_STAGE;
+          for (int t = 0; t < kt; ++t) {
+#pragma unroll
+            for (int sub = 0; sub < TK / 16; ++sub) {
+              const uint32_t o = sub * 32;
+              mma_bf16_n128(dacc, sdesc(st + t * A_TILE + o), sdesc(st + OZ_KT * A_TILE + t * OZ_BT + o),
+                            (start && t == 0 && sub == 0) ? 0u : 1u);
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           empty0 + 8 * st_i)
+                       : "memory");
+          if (end) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tfull0 + 8 * (gc % OZ_NACC))
+                         : "memory");
+            ++gc;
+          }
+          kk += OZ_KT;
+          if (kk >= sch.k1[u]) {
+            if (++u == sch.nunits) u = 0;
+            kk = sch.k0[u];
+          }
+        }
+      }
+    }
+  } else {  // epilogue warps 2..9
+    const int lg = warp & 3, h = (warp - 2) >> 2, ew = warp - 2;
+    // this lane's part of a tile in a slot: row lg*32 + lane, columns h*64 + q (column-major)
+    const size_t pofs = (size_t)(h * 64) * TM + lg * 32 + lane;
+    int gc = 0;
+    bool stop = false;
+    long long acci[64];
+    for (int pass = 0; pass < 2 && !stop; ++pass) {
+      const int rb = pass ? sk_b : x0, re = pass ? x0 : sk_e;
+      if (rb >= re) continue;
+      int v, u, kk;
+      locate(rb, v, u, kk);
+      int s = rb;
+      while (s < re && !stop) {  // one segment: the steps of one tile in [rb, re)
+        const int vt = v, seg_b = s;
+#pragma unroll
+        for (int q = 0; q < 64; ++q) acci[q] = 0;
+        while (s < re && v == vt) {  // one accumulator: a group, or its part in [rb, re)
+          const int g = sch.ug[u];
+          for (;;) {
+            const bool end = s + 1 == re || (kk + OZ_KT >= sch.k1[u] && sch.last[u]);
+            ++s;
+            kk += OZ_KT;
+            if (kk >= sch.k1[u]) {
+              if (++u == sch.nunits) {
+                u = 0;
+                ++v;
+              }
+              kk = sch.k0[u];
+            }
+            if (end) break;
+          }
+          const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
+          const bool ok = mbar_wait(tfull0 + 8 * acc, ause & 1);
+          __syncwarp();
+          if (!ok) {
+            if (lane == 0) atomicExch(err, 34);
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int gs = sch.gsh[g];
+          constexpr int FIX = oz_fix(NB);
+          const float up = __uint_as_float((uint32_t)(127 + (gs >= 0 ? FIX - gs : FIX)) << 23);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float vv[16];
+            tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 16), vv);
+            if (gs >= 0) {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rz(vv[q] * up) << gs;
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rn(vv[q] * up);
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * acc) : "memory");
+          ++gc;
+        }
+        if (stop) break;
+        const bool whole = seg_b == vt * S && s == (vt + 1) * S;
+        if (!whole && !(finaliser && seg_b == sk_b)) {
+          // a part finished by a later CTA: to this CTA's slot, then the flag
+          long long *pp = ska.part + (size_t)d * TM * OZ_TN + pofs;
+#pragma unroll
+          for (int q = 0; q < 64; ++q) __stcg(pp + (size_t)q * TM, acci[q]);
+          __threadfence();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(ska.flag + d * 8 + ew), "r"(mark) : "memory");
+          continue;
+        }
+        if (!whole) {
+          // finaliser: add the parts of the earlier CTAs whose ranges reach into the tile
+          for (int c = d - 1; c >= 0; --c) {
+            const int cb = range_b(c), ce = range_b(c + 1);
+            if (ce <= vt * S) break;  // this range and the earlier ones end before the tile
+            if (cb == ce) continue;
+            int got = 1;
+            if (lane == 0) {
+              long long i = 0;
+              for (; i < WAIT_LIMIT; ++i) {
+                int fv;
+                asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(fv) : "l"(ska.flag + c * 8 + ew) : "memory");
+                if (fv == mark) break;
+                if (i > 32) __nanosleep(64);
+              }
+              got = i < WAIT_LIMIT ? 1 : 0;
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            __syncwarp();  // the lanes' loads below come after lane 0's acquire
+            if (!got) {
+              if (lane == 0) atomicExch(err, 35);
+              *abort_flag = 1;
+              stop = true;
+              break;
+            }
+            const long long *pp = ska.part + (size_t)c * TM * OZ_TN + pofs;
+#pragma unroll
+            for (int q = 0; q < 64; ++q) acci[q] += __ldcg(pp + (size_t)q * TM);
+            if (cb <= vt * S) break;  // the part holding the tile's first step
+          }
+          if (stop) break;
+        }
+        // the tile: one float64 rounding of each int64 sum, then the power-of-two scales
+        int par, mt, nt;
+        tile_of(vt, par, mt, nt);
+        const int row = mt * TM + lg * 32 + lane;
+        if (row < rows) {
+          const int e = erow[par * (nmt * TM) + row];
+          const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                 : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
+          const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+          const int c0 = nt * OZ_TN + h * 64;
+          const int ncols = min(64, (par ? kv : ku) - c0);
+          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+          if (rzpart == nullptr) {
+#pragma unroll
+            for (int q = 0; q < 64; ++q)
+              if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
+          } else {
+            const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
+            double dsum = 0.0;
+#pragma unroll
+            for (int q = 0; q < 64; ++q)
+              if (q < ncols) {
+                const double val = scale * (unit * __ll2double_rn(acci[q]));
+                yp[2 * q] = val;
+                dsum = fma(__ldg(rp + 2 * q), val, dsum);
+              }
+            rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dsum;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_NACC * OZ_TN) : "memory");
+  if (tid == 0) {  // the last CTA out resets the ticket and finish counters and advances the epoch
+    __threadfence();
+    if (atomicAdd(ska.ctl + 1, 1) == G - 1) {
+      atomicExch(ska.ctl, 0);
+      atomicExch(ska.ctl + 1, 0);
+      atomicAdd(ska.ctl + 2, 1);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- two-SM (cta_group::2) variant
@@ -1556,6 +1921,8 @@ static OzSched oz_schedule(int kpad, OzFmt f) {
       s.k1[nu] = (uint8_t)u.k1;
       s.first[nu] = (q == 0);
       s.last[nu] = (q + 1 == g->units.size());
+      s.ug[nu] = (uint8_t)ng;
+      s.nstage += (u.k1 - u.k0 + OZ_KT - 1) / OZ_KT;
       ++nu;
     }
     ++ng;
@@ -1664,10 +2031,42 @@ static bool oz_pair_enabled() {
   return v != nullptr && v[0] == '1';
 }
 
+// SMs of the current device, read once per device
+static int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  LAG_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(LAG_EINVAL, "device ordinal out of range");
+  int n = cache[dev].load();
+  if (n == 0) {
+    LAG_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    cache[dev].store(n);
+  }
+  return n;
+}
+// CTAs of a stream-K launch: one per SM
+static int oz_sk_ctas() { return std::min(device_sms(), OZ_SK_MAXG); }
+// stream-K is opt-in (LAGWAVE_OZ_SK=1): with every SM on its own range the CTAs no longer read the
+// same operand lines at the same time, the L2 serves every copy separately, and the kernel measured
+// slower than the tile kernel on 24 fewer SMs (178.6 against 143.3 us at 2048 modes x 1024 rows)
+static bool oz_sk_enabled() {
+  const char *v = std::getenv("LAGWAVE_OZ_SK");
+  return v != nullptr && v[0] == '1';
+}
+
+// scratch layout: the stream-K area first, at a place that does not move with the row count
+// [control 256 B][flags G x 8 ints, to 256 B][parts G x TM x TN int64], then [A slices][row
+// exponents] | 256-aligned [E / O sums (DCT-II inverse)]
+static size_t oz_sk_flag_bytes(int G) { return ((size_t)G * 8 * sizeof(int) + 255) & ~(size_t)255; }
+static size_t oz_sk_bytes() {
+  const int G = oz_sk_ctas();
+  return 256 + oz_sk_flag_bytes(G) + (size_t)G * TM * OZ_TN * sizeof(long long);
+}
+
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows) {
   const size_t nmt = oz_mtiles(rows);
   const size_t eo = (dp.kind == 1) ? 2 * (size_t)rows * dp.ku * sizeof(double) + 256 : 0;  // DCT-II E / O sums
-  return 2 * (size_t)OZ_SMAX * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256 + eo;
+  return oz_sk_bytes() + 2 * (size_t)OZ_SMAX * nmt * dp.kpad_u * A_TILE + 2 * nmt * TM * sizeof(int) + 256 + eo;
 }
 
 // DCT-II inverse butterfly: x[k] = E[k] + O[k], x[n-1-k] = E[k] - O[k] (k < ceil(n/2)); rows of
@@ -1722,6 +2121,22 @@ __global__ void __launch_bounds__(OZ_RZ_THREADS) oz_rz_beta_kernel(const double 
   }
 }
 
+// the GEMM kernel of a forward (inv = 0) or DCT-II inverse (inv = 1) transform of `rows` rows,
+// rpr rows per right-hand side
+int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv) {
+  const size_t a_slice = (size_t)oz_mtiles(rows) * dp.kpad_u * A_TILE;
+  // TMA coordinates are signed 32-bit: the pair kernel addresses the slice buffers by 128-byte row
+  if (!inv && oz_pair_enabled() && 2ull * dp.oz_ns * a_slice / 128 < (1ull << 31)) return OZ_GEMM_PAIRS;
+  // tiles that run: m tiles of the rows (not the padding one) x column tiles of each parity
+  const int vtiles = div_up(rows, TM) * (div_up(dp.ku, OZ_TN) + div_up(dp.kv, OZ_TN));
+  const int g = oz_sk_ctas();
+  // one right-hand side whose tiles leave SMs idle in the last wave: equal ranges of steps per SM
+  // (at least half as many tiles as SMs: a tile is then shared by three CTAs at most)
+  if (!inv && rows <= rpr && oz_sk_enabled() && vtiles % g != 0 && 2 * vtiles >= g && vtiles < 4 * g)
+    return OZ_GEMM_STREAMK;
+  return OZ_GEMM_TILES;
+}
+
 template <int NB, int NS>
 static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
                          cudaStream_t s, int inv, const double *rdot = nullptr, double *rzpart = nullptr) {
@@ -1729,12 +2144,13 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
   attr.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm2_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ2_SMEM));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_sk_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         2 * OZ_PACK_MAXK * (int)sizeof(double)));
   });
   const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = oz_mtiles(rows);
   const size_t a_slice = (size_t)nmt * nks * A_TILE;
-  uint8_t *apack = dp.tc_scratch;
+  uint8_t *apack = dp.tc_scratch + oz_sk_bytes();
   int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)NS * a_slice);
   const size_t pack_smem = 2 * (size_t)nks * TK * sizeof(double);
   oz_pack_a_kernel<NB, NS><<<nmt * TM, OZ_PACK_THREADS, pack_smem, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack,
@@ -1744,17 +2160,27 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
   const OzSched sch = oz_schedule(nks * TK, OzFmt{NB, NS});
   const int ntiles = 2 * nmt * nnt;
   const int grid = std::min(ntiles, 152);
+  const int variant = dst_oz_gemm_variant(dp, rows, rpr, inv);
   // E / O sums of the inverse: after the packed A slices and the row exponents, 256-byte aligned
   double *eo = reinterpret_cast<double *>(
       (reinterpret_cast<uintptr_t>(erow + 2 * (size_t)nmt * TM) + 255) & ~(uintptr_t)255);
-  // TMA coordinates are signed 32-bit: the pair kernel addresses the slice buffers by 128-byte row
-  if (!inv && oz_pair_enabled() && 2ull * NS * a_slice / 128 < (1ull << 31)) {
+  if (variant == OZ_GEMM_PAIRS) {
     // two-SM pairs: 256-row tile pairs x column tiles x both parities, at most one pair per two SMs
     const int pairs = std::min(2 * (nmt / 2) * nnt, 76);
     const CUtensorMap tmA = rows_map(apack, 2ull * NS * a_slice / 128, TM);
     const CUtensorMap tmB = rows_map(dp.oz_b, 2ull * NS * dp.oz_slice_bytes / 128, OZ_TN / 2);
     oz_gemm2_kernel<NB, NS><<<2 * pairs, 320, OZ2_SMEM, s>>>(tmA, tmB, erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n,
                                                              dp.ku, dp.kv, sch, sc, rpr, dp.tc_err, rdot, rzpart);
+  } else if (variant == OZ_GEMM_STREAMK) {
+    const int gsk = oz_sk_ctas();
+    uint8_t *area = dp.tc_scratch;
+    OzSkArea ska;
+    ska.ctl = reinterpret_cast<int *>(area);
+    ska.flag = reinterpret_cast<int *>(area + 256);
+    ska.part = reinterpret_cast<long long *>(area + 256 + oz_sk_flag_bytes(gsk));
+    oz_gemm_sk_kernel<NB, NS><<<gsk, 320, OZ_SMEM, s>>>(apack, a_slice, dp.oz_b, dp.oz_slice_bytes, erow, dp.oz_eB,
+                                                        nks, nmt, nnt, rows, y, dp.n, dp.ku, dp.kv, sch, sc,
+                                                        dp.tc_err, rdot, rzpart, ska);
   } else {
     oz_gemm_kernel<NB, NS><<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
                                                       erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,

@@ -49,6 +49,7 @@ size_t estimate_bytes(const lag_request &r) {
   b += 2 * ku * ku * 12 + ku * ku * 8 * 2;                        // DST halves (+ tensor-core copies)
   b += nplans * (5 * 3 * ((nz + 31) / 32 + 1) * nx + nx * 32 * 18) * 12;  // tridiagonal factors
   b += n * ncomp * nsrc * 8;                                     // preconditioner scratch
+  b += nplans * (2 * 9 * (nz * nsrc + 256) * (ku + 64) * 2 + 152 * 128 * 128 * 8);  // exact-slice A slices, stream-K parts
   b += ((size_t)r.lag.n_harm * (r.nt + 1 + nsrc * ncomp * r.nrcv) + (size_t)r.nt * (1 + nsrc * ncomp * r.nrcv)) * 8;
   b += (size_t)r.lag.n_harm * 16 * 8 * 40;                       // source-coefficient scratch (transient)
   return b + (4u << 20);

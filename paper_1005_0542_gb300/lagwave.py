@@ -18,6 +18,7 @@ LAG_OK, LAG_EINVAL, LAG_ENOMEM, LAG_ENOTCONV = 0, -1, -2, -3
 LAG_ENUMERIC, LAG_ECUDA, LAG_EAGAIN, LAG_ETIMEDOUT, LAG_ECANCELED = -4, -5, -6, -7, -8
 LAG_FP64, LAG_MIXED = 0, 1
 LAG_WAVELET_RICKER, LAG_WAVELET_PAPER = 0, 1
+LAG_GEMM_SIMT, LAG_GEMM_SPLIT_BF16, LAG_GEMM_SLICE_TILES, LAG_GEMM_SLICE_STREAMK, LAG_GEMM_SLICE_PAIRS = 0, 1, 2, 3, 4
 
 
 class lag_grid(C.Structure):
@@ -99,6 +100,7 @@ _PROTOS = {
     "lag_precond_autotune": (I, [VP, I, PI, PI, PI, PD]),
     "lag_precond_set_layout": (I, [VP, I, I]),
     "lag_precond_uses_tensor_cores": (I, [VP]),
+    "lag_precond_dst_gemm": (I, [VP, I]),
     "lag_precond_set_dst_products": (I, [VP, I]),
     "lag_medium_create_acoustic": (I, [VP, C.POINTER(lag_grid), PD, PD, D, C.POINTER(VP)]),
     "lag_medium_create_elastic": (I, [VP, C.POINTER(lag_grid), PD, PD, PD, D, C.POINTER(VP)]),

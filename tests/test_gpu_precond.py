@@ -317,8 +317,10 @@ def test_dst_f64_two_sm_pairs_equal_one_sm_tiles(ctx, monkeypatch, nx, nz, nrhs)
     p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
     assert L.lag_precond_uses_tensor_cores(p) == 1
     xd, y2, y1 = dev(x), empty(x.shape), empty(x.shape)
+    assert L.lag_precond_dst_gemm(p, nrhs) == L.LAG_GEMM_SLICE_TILES
     L.check(L.lag_precond_dst(p, ptr(xd), ptr(y1), nrhs), ctx)
     monkeypatch.setenv("LAGWAVE_OZ_PAIR", "1")
+    assert L.lag_precond_dst_gemm(p, nrhs) == L.LAG_GEMM_SLICE_PAIRS
     L.check(L.lag_precond_dst(p, ptr(xd), ptr(y2), nrhs), ctx)
     monkeypatch.delenv("LAGWAVE_OZ_PAIR")
     a, b = host(y2), host(y1)
@@ -346,3 +348,78 @@ def test_dst_f64_eight_bit_slices_equal_seven_bit(ctx, monkeypatch, nx):
     assert np.abs((a - b) / sc).max() < 1e-14
     L.lag_precond_destroy(p8)
     L.lag_precond_destroy(p7)
+
+
+def _streamk_expected(nx, nz, nrhs):
+    # the host's rule: one right-hand side, tiles not a multiple of the SM count, G/2 <= tiles < 4 G
+    sms = torch().cuda.get_device_properties(0).multi_processor_count
+    tiles = -(-nz // 128) * (-(-((nx + 1) // 2) // 128) + -(-(nx // 2) // 128))
+    return nrhs == 1 and tiles % sms != 0 and 2 * tiles >= sms and tiles < 4 * sms
+
+
+@pytest.mark.parametrize("nx,nz", [(2048, 1024), (2048, 640), (2000, 600), (2047, 700), (1024, 1536), (2560, 1280)])
+def test_dst_f64_stream_k_matches_tiles_and_oracle(ctx, monkeypatch, nx, nz):
+    # one right-hand side whose output tiles leave SMs idle in a last wave: the stream-K GEMM (the
+    # steps of all tiles cut into one equal range per SM, a split tile finished from int64 parts by
+    # the CTA holding its last step) against the tile kernel and the oracle's DST; ragged rows and
+    # columns, an odd length, the 7-bit format (ceil(n/2) > 1024), rows scaled over 40 decades, a
+    # non-finite row, and repeated launches (the ticket counters and epoch reset by the last CTA)
+    x = RNG.standard_normal((1, nz, nx)) * 10.0 ** RNG.uniform(-20, 20, (1, nz, 1))
+    x[0, nz // 3, nx // 2] = np.inf
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    assert L.lag_precond_dst_gemm(p, 1) == L.LAG_GEMM_SLICE_TILES  # stream-K is opt-in
+    monkeypatch.setenv("LAGWAVE_OZ_SK", "1")
+    if torch().cuda.get_device_properties(0).multi_processor_count == 152:
+        assert _streamk_expected(nx, nz, 1)  # every case here splits tiles on a 152-SM GB300
+    want = L.LAG_GEMM_SLICE_STREAMK if _streamk_expected(nx, nz, 1) else L.LAG_GEMM_SLICE_TILES
+    assert L.lag_precond_dst_gemm(p, 1) == want
+    assert L.lag_precond_dst_gemm(p, 2) == L.LAG_GEMM_SLICE_TILES
+    xd, ys, yt = dev(x), empty(x.shape), empty(x.shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(ys), 1), ctx)
+    first = host(ys)
+    assert L.lag_precond_status(p) == L.LAG_OK
+    for _ in range(3):
+        ys.fill_(7.0)  # every output is written again
+        L.check(L.lag_precond_dst(p, ptr(xd), ptr(ys), 1), ctx)
+        assert np.array_equal(host(ys), first, equal_nan=True)
+    monkeypatch.delenv("LAGWAVE_OZ_SK")
+    assert L.lag_precond_dst_gemm(p, 1) == L.LAG_GEMM_SLICE_TILES
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(yt), 1), ctx)
+    monkeypatch.setenv("LAGWAVE_OZ_SK", "1")
+    a, b = first[0], host(yt)[0]
+    bad = nz // 3
+    assert np.all(np.isnan(a[bad])) and np.all(np.isnan(b[bad]))
+    ok = np.arange(nz) != bad
+    ref = odst.dst_x(x[:, ok])[0]
+    sc = np.abs(ref).max(axis=-1, keepdims=True)
+    assert np.abs((a[ok] - b[ok]) / sc).max() < 1e-15
+    assert np.abs((a[ok] - ref) / sc).max() < 1e-14
+    # the same transform inside a batch of two runs the tile kernel and gives the same rows
+    x2 = np.concatenate([x, x[:, ::-1]], axis=0)
+    x2d, y2 = dev(x2), empty(x2.shape)
+    L.check(L.lag_precond_dst(p, ptr(x2d), ptr(y2), 2), ctx)
+    assert np.abs((host(y2)[0][ok] - b[ok]) / sc).max() == 0.0
+    # and stream-K again after the batch (its scratch regrown: counters and slots kept apart)
+    ys.fill_(7.0)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(ys), 1), ctx)
+    assert np.array_equal(host(ys), first, equal_nan=True)
+    assert L.lag_precond_status(p) == L.LAG_OK
+    monkeypatch.delenv("LAGWAVE_OZ_SK")
+    L.lag_precond_destroy(p)
+
+
+def test_dst_gemm_query(ctx, monkeypatch):
+    # the GEMM kernel a transform launches, by plan kind, right-hand sides and environment
+    pm = plan(ctx, 2048, 1024, 5.0, 5.0, 1.0, 1.0, 0.1, prec=L.LAG_MIXED)
+    assert L.lag_precond_dst_gemm(pm, 1) == L.LAG_GEMM_SPLIT_BF16
+    assert L.lag_precond_dst_gemm(pm, 0) == L.LAG_EINVAL
+    assert L.lag_precond_dst_gemm(None, 1) == L.LAG_EINVAL
+    L.lag_precond_destroy(pm)
+    p = plan(ctx, 64, 8, 5.0, 5.0, 1.0, 1.0, 0.1)  # 2 tiles: too few to split over the SMs
+    assert L.lag_precond_dst_gemm(p, 1) == L.LAG_GEMM_SLICE_TILES
+    L.lag_precond_destroy(p)
+    monkeypatch.setenv("LAGWAVE_DST_KERNEL", "simt")
+    ps = plan(ctx, 64, 8, 5.0, 5.0, 1.0, 1.0, 0.1)
+    monkeypatch.delenv("LAGWAVE_DST_KERNEL")
+    assert L.lag_precond_dst_gemm(ps, 1) == L.LAG_GEMM_SIMT
+    L.lag_precond_destroy(ps)
