@@ -226,12 +226,15 @@ int  lag_dst_f64_slice_products(int n);
  *                           per SM (LAGWAVE_OZ_SK=1, opt-in: one right-hand side whose tile count is
  *                           not a multiple of the SM count)
  *   LAG_GEMM_SLICE_PAIRS    float64 exact slices on two-SM pairs (LAGWAVE_OZ_PAIR=1, opt-in)
+ *   LAG_GEMM_SLICE_CLUSTER  float64 exact slices on clusters of 2 x 2, 1 x 2 or 2 x 1 tiles whose
+ *                           shared operand tiles are read once and multicast (LAGWAVE_OZ_CLUSTER)
  * A negative LAG_E* code for a null plan or nrhs < 1. */
 #define LAG_GEMM_SIMT 0
 #define LAG_GEMM_SPLIT_BF16 1
 #define LAG_GEMM_SLICE_TILES 2
 #define LAG_GEMM_SLICE_STREAMK 3
 #define LAG_GEMM_SLICE_PAIRS 4
+#define LAG_GEMM_SLICE_CLUSTER 5
 int  lag_precond_dst_gemm(lag_precond *p, int nrhs);
 /* Tensor-core DST of a mixed plan: number of bf16 products per K step (3: split hi*hi + hi*lo +
  * lo*hi, relative error ~1e-5; 2: hi*hi + lo*hi with S rounded to bf16, ~2e-3; 1: hi*hi, ~4e-3).

@@ -159,7 +159,7 @@ bool dst_oz_supported(int n);
 int dst_oz_products(int n);  // bf16 slice products per float64 product of a length-n transform
 size_t dst_oz_scratch_bytes(const DstPlan &dp, int rows);
 // exact-slice GEMM kernels (the values of LAG_GEMM_SLICE_* in lagwave.h)
-constexpr int OZ_GEMM_TILES = 2, OZ_GEMM_STREAMK = 3, OZ_GEMM_PAIRS = 4;
+constexpr int OZ_GEMM_TILES = 2, OZ_GEMM_STREAMK = 3, OZ_GEMM_PAIRS = 4, OZ_GEMM_CLUSTER = 5;
 int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv);
 // inverse (DCT-II plans only): gather the even / odd modes, GEMM with the inverse operands into
 // E / O sums (plan scratch), butterfly into y

@@ -1850,6 +1850,291 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ2_NACC * OZ_TN) : "memory");
 }
 
+// ---------------------------------------------------------------- cluster-multicast variant
+// The tile kernel's GEMM with the CTAs of a CM x CN cluster on a CM x CN block of output tiles:
+// the CN CTAs of a cluster row compute tiles of the same m tile and need the same A slice tiles,
+// the CM CTAs of a column the same B slice tiles.  Each K tile of a stage is read from L2 once per
+// row (A) or column (B), by one of its CTAs, and multicast into the shared memory of every CTA that
+// needs it (cp.async.bulk .multicast::cluster), so the cluster reads (CM + CN) / (2 CM CN) of the
+// tile kernel's operand bytes from L2.  Every SM still receives a full stage per step.
+// Pipeline: each CTA's "full" barrier expects the whole stage (its own copies and its peers'); its
+// "empty" barrier counts the releases of every CTA its copies write into (itself, its row and its
+// column: CM + CN - 1), and each CTA's MMA commit releases the stage in those same CTAs.  All CTAs
+// of a cluster run the same sequence of stages (the block of tiles, its units and K tiles), so the
+// stages line up; a block is skipped only when none of its tiles has work, and a CTA whose own tile
+// lies outside the valid tiles (an odd column-tile count) still copies its share and stores nothing.
+// Every wait is bounded; the cluster meets at a barrier before any CTA frees its tensor memory and
+// exits, so no CTA leaves while a peer may still copy into it or release a stage there.
+__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   bar),
+               "h"(mask)
+               : "memory");
+}
+
+template <int NB, int NS, int CM, int CN>
+__global__ void __launch_bounds__(320, 1) oz_gemm_mc_kernel(const uint8_t *__restrict__ apack, size_t a_slice_bytes,
+                                                            const uint8_t *__restrict__ bpack, size_t b_slice_bytes,
+                                                            const int *__restrict__ erow, int eB, int nks, int nmt,
+                                                            int nnt, int rows, double *__restrict__ y, int ld, int ku,
+                                                            int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
+                                                            int rpr, int *__restrict__ err, int inv,
+                                                            const double *__restrict__ rdot,
+                                                            double *__restrict__ rzpart) {
+  constexpr int CS = CM * CN;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t *gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + OZ_NST * OZ_STAGE;
+  const uint32_t full0 = bars, empty0 = bars + 8 * OZ_NST, tfull0 = bars + 16 * OZ_NST, tempty0 = tfull0 + 8 * OZ_NACC;
+  volatile uint32_t *holder =
+      reinterpret_cast<volatile uint32_t *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rank = (int)cluster_rank();
+  const int ci = rank / CN, cj = rank % CN;  // this CTA's row (m) and column (n) in the block
+  // multicast masks: the CTAs of this row (same A), of this column (same B), and both (releases)
+  uint16_t row_mask = 0, col_mask = 0;
+  for (int q = 0; q < CN; ++q) row_mask |= (uint16_t)(1u << (ci * CN + q));
+  for (int q = 0; q < CM; ++q) col_mask |= (uint16_t)(1u << (q * CN + cj));
+  const uint16_t rel_mask = row_mask | col_mask;
+  const int cluster = blockIdx.x / CS, nclusters = gridDim.x / CS;
+  const int nbm = nmt / CM, nbn = (nnt + CN - 1) / CN;  // blocks of tiles per parity (nmt is even)
+  const int nblocks = 2 * nbm * nbn;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)holder)),
+                 "r"(OZ_NACC * OZ_TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < OZ_NST; ++s) {
+      mbar_init(full0 + 8 * s, 1);            // this CTA's expect-tx arrive; the bytes of every copy
+      mbar_init(empty0 + 8 * s, CM + CN - 1);  // releases by every CTA this CTA's copies write into
+    }
+    for (int a = 0; a < OZ_NACC; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 8);  // one arrive per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();  // every CTA's barriers initialised before any copy or release reaches them
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *holder;
+
+  auto decode = [&](int b, int &par, int &bm, int &bn) {
+    bn = b % nbn;
+    bm = (b / nbn) % nbm;
+    par = b / (nbn * nbm);
+  };
+  auto wanted = [&](int par, int mt, int nt) -> bool {
+    if (nt >= nnt || nt * OZ_TN >= ((par && !inv) ? kv : ku)) return false;
+    if (mt * TM >= rows) return false;  // the padding m-tile of an odd count (A slices come in pairs)
+    if (sc == nullptr) return true;
+    const int m0 = mt * TM;
+    const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
+    for (int r = r0; r <= r1; ++r)
+      if (sc[r].state == ST_RUN) return true;
+    return false;
+  };
+  auto block_wanted = [&](int par, int bm, int bn) -> bool {
+    for (int q = 0; q < CS; ++q)
+      if (wanted(par, bm * CM + q / CN, bn * CN + q % CN)) return true;
+    return false;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer: this CTA's share of each stage, multicast to the CTAs that need it
+      int it = 0;
+      for (int b = cluster; b < nblocks && !*abort_flag; b += nclusters) {
+        int par, bm, bn;
+        decode(b, par, bm, bn);
+        if (!block_wanted(par, bm, bn)) continue;
+        const int mt = bm * CM + ci, nt = min(bn * CN + cj, nnt - 1);  // copies stay inside the slices
+        for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
+          const uint8_t *at = apack + ((size_t)par * NS + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
+          const uint8_t *bt = bpack + ((size_t)par * NS + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+          const int ke = sch.k1[pr];
+          for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, ke - kk);  // K tiles in this stage
+            const int s = it % OZ_NST, use = it / OZ_NST;
+            if (it >= OZ_NST && !mbar_wait_cluster(empty0 + 8 * s, (use - 1) & 1)) {
+              atomicExch(err, 41);
+              *abort_flag = 1;
+              break;
+            }
+            const uint32_t st = base + s * OZ_STAGE;
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, (uint32_t)(kt * (A_TILE + OZ_BT)));
+            for (int t = 0; t < kt; ++t) {
+              if (t % CN == cj) {  // A K tile t: one copy per row
+                if (CN == 1) bulk_g2s(st + t * A_TILE, at + (size_t)(kk + t) * A_TILE, A_TILE, fb);
+                else bulk_g2s_mc(st + t * A_TILE, at + (size_t)(kk + t) * A_TILE, A_TILE, fb, row_mask);
+              }
+              if (t % CM == ci) {  // B K tile t: one copy per column
+                const uint32_t dst = st + OZ_KT * A_TILE + t * OZ_BT;
+                if (CM == 1) bulk_g2s(dst, bt + (size_t)(kk + t) * OZ_BT, OZ_BT, fb);
+                else bulk_g2s_mc(dst, bt + (size_t)(kk + t) * OZ_BT, OZ_BT, fb, col_mask);
+              }
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int it = 0, gc = 0;
+      for (int b = cluster; b < nblocks && !*abort_flag; b += nclusters) {
+        int par, bm, bn;
+        decode(b, par, bm, bn);
+        if (!block_wanted(par, bm, bn)) continue;
+        uint32_t d = 0;
+        for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
+          if (sch.first[pr]) {
+            const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
+            if (gc >= OZ_NACC && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) {
+              atomicExch(err, 42);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            d = tmem + (uint32_t)(acc * OZ_TN);
+          }
+          const int kb = sch.k0[pr], ke = sch.k1[pr];
+          for (int kk = kb; kk < ke; kk += OZ_KT, ++it) {
+            const int kt = min(OZ_KT, ke - kk);
+            const int s = it % OZ_NST, use = it / OZ_NST;
+            if (!mbar_wait_cluster(full0 + 8 * s, use & 1)) {
+              atomicExch(err, 43);
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = base + s * OZ_STAGE;
+            for (int t = 0; t < kt; ++t) {
+#pragma unroll
+              for (int sub = 0; sub < TK / 16; ++sub) {
+                const uint32_t o = sub * 32;
+                mma_bf16_n128(d, sdesc(st + t * A_TILE + o), sdesc(st + OZ_KT * A_TILE + t * OZ_BT + o),
+                              (sch.first[pr] && kk == kb && t == 0 && sub == 0) ? 0u : 1u);
+              }
+            }
+            // the stage is free again in this CTA and in the CTAs whose copies wrote into it
+            if (CS == 1)
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                               empty0 + 8 * s)
+                           : "memory");
+            else
+              commit_mc(empty0 + 8 * s, rel_mask);
+          }
+          if (sch.last[pr]) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tfull0 + 8 * (gc % OZ_NACC))
+                         : "memory");
+            ++gc;
+          }
+        }
+      }
+    }
+  } else {  // epilogue warps 2..9
+    const int lg = warp & 3, h = (warp - 2) >> 2;
+    int gc = 0;
+    for (int b = cluster; b < nblocks; b += nclusters) {
+      int par, bm, bn;
+      decode(b, par, bm, bn);
+      if (!block_wanted(par, bm, bn)) continue;
+      const int mt = bm * CM + ci, nt = bn * CN + cj;
+      const bool mine = wanted(par, mt, nt);
+      const int row = mt * TM + lg * 32 + lane;
+      const bool rok = mine && row < rows;
+      const int e = rok ? erow[par * (nmt * TM) + row] : 0;
+      long long acci[64];
+#pragma unroll
+      for (int q = 0; q < 64; ++q) acci[q] = 0;
+      bool stop = false;
+      for (int g = 0; g < sch.ngroups; ++g) {
+        const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
+        const bool ok = mbar_wait(tfull0 + 8 * acc, ause & 1);
+        __syncwarp();
+        if (!ok) {
+          if (lane == 0) atomicExch(err, 44);
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int gs = sch.gsh[g];
+        constexpr int FIX = oz_fix(NB);
+        const float up = __uint_as_float((uint32_t)(127 + (gs >= 0 ? FIX - gs : FIX)) << 23);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * OZ_TN + h * 64 + c * 16), v);
+          if (gs >= 0) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rz(v[q] * up) << gs;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acci[c * 16 + q] += (long long)__float2int_rn(v[q] * up);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * acc) : "memory");
+        ++gc;
+      }
+      if (stop) break;
+      if (rok) {
+        const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
+                                               : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
+        const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+        const int c0 = nt * OZ_TN + h * 64;
+        const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
+        if (inv) {  // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]
+          double *yp = y + ((size_t)par * rows + row) * ku + c0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) yp[q] = scale * (unit * __ll2double_rn(acci[q]));
+        } else if (rzpart == nullptr) {
+          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
+        } else {
+          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
+          const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
+          double dacc = 0.0;
+#pragma unroll
+          for (int q = 0; q < 64; ++q)
+            if (q < ncols) {
+              const double v = scale * (unit * __ll2double_rn(acci[q]));
+              yp[2 * q] = v;
+              dacc = fma(__ldg(rp + 2 * q), v, dacc);
+            }
+          rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dacc;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // no CTA leaves while a peer may still copy into it or release a stage there
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_NACC * OZ_TN) : "memory");
+}
+
 // Schedule of one output tile.  Exact groups: units of one weight d < tail over one K chunk (the
 // longest multiple of 64 K values whose sum stays exact, kc), at most gmax units per accumulator.
 // The tail (d >= tail, FP32-rounded) is cut into chunks of at most 3 pairs over the whole K range,
@@ -2121,12 +2406,26 @@ __global__ void __launch_bounds__(OZ_RZ_THREADS) oz_rz_beta_kernel(const double 
   }
 }
 
+// cluster shape of the multicast kernel: LAGWAVE_OZ_CLUSTER=2x2 / 1x2 / 2x1 (rows x columns of
+// tiles), else 0 x 0 (not used)
+static void oz_cluster_shape(int &cm, int &cn) {
+  cm = cn = 0;
+  const char *v = std::getenv("LAGWAVE_OZ_CLUSTER");
+  if (v == nullptr || (v[0] != '1' && v[0] != '2') || v[1] != 'x' || (v[2] != '1' && v[2] != '2') || v[3] != 0) return;
+  cm = v[0] - '0';
+  cn = v[2] - '0';
+  if (cm * cn == 1) cm = cn = 0;
+}
+
 // the GEMM kernel of a forward (inv = 0) or DCT-II inverse (inv = 1) transform of `rows` rows,
 // rpr rows per right-hand side
 int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv) {
   const size_t a_slice = (size_t)oz_mtiles(rows) * dp.kpad_u * A_TILE;
   // TMA coordinates are signed 32-bit: the pair kernel addresses the slice buffers by 128-byte row
   if (!inv && oz_pair_enabled() && 2ull * dp.oz_ns * a_slice / 128 < (1ull << 31)) return OZ_GEMM_PAIRS;
+  int cm, cn;
+  oz_cluster_shape(cm, cn);
+  if (cm > 0) return OZ_GEMM_CLUSTER;
   // tiles that run: m tiles of the rows (not the padding one) x column tiles of each parity
   const int vtiles = div_up(rows, TM) * (div_up(dp.ku, OZ_TN) + div_up(dp.kv, OZ_TN));
   const int g = oz_sk_ctas();
@@ -2135,6 +2434,46 @@ int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv) {
   if (!inv && rows <= rpr && oz_sk_enabled() && vtiles % g != 0 && 2 * vtiles >= g && vtiles < 4 * g)
     return OZ_GEMM_STREAMK;
   return OZ_GEMM_TILES;
+}
+
+// the multicast kernel on CM x CN clusters: as many clusters as fit at once (at most one per block
+// of tiles), each walking the blocks persistently
+template <int NB, int NS, int CM, int CN>
+static void oz_launch_mc(const uint8_t *apack, size_t a_slice, const uint8_t *bpack, const DstPlan &dp, const int *erow,
+                         int nks, int nmt, int nnt, int rows, double *y, const OzSched &sch, const KrylovScalars *sc,
+                         int rpr, int inv, const double *rdot, double *rzpart, cudaStream_t s) {
+  static PerDeviceOnce attr;
+  static std::atomic<int> fit[64];
+  int dev = 0;
+  LAG_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(LAG_EINVAL, "device ordinal out of range");
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CM * CN;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(320, 1, 1);
+  cfg.dynamicSmemBytes = OZ_SMEM;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  attr.run([&] {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_mc_kernel<NB, NS, CM, CN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        OZ_SMEM));
+  });
+  if (fit[dev].load() == 0) {
+    int n = 0;
+    cfg.gridDim = dim3(CM * CN, 1, 1);
+    LAG_CUDA_CHECK(cudaOccupancyMaxActiveClusters(&n, oz_gemm_mc_kernel<NB, NS, CM, CN>, &cfg));
+    if (n < 1) throw Error(LAG_ECUDA, "exact-slice GEMM: no cluster of this shape fits on the device");
+    fit[dev].store(n);
+  }
+  const int nblocks = 2 * (nmt / CM) * ((nnt + CN - 1) / CN);
+  cfg.gridDim = dim3(CM * CN * std::min(nblocks, fit[dev].load()), 1, 1);
+  LAG_CUDA_CHECK(cudaLaunchKernelEx(&cfg, oz_gemm_mc_kernel<NB, NS, CM, CN>, apack, a_slice, bpack, dp.oz_slice_bytes,
+                                    erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n, dp.ku, dp.kv, sch, sc, rpr, dp.tc_err,
+                                    inv, rdot, rzpart));
 }
 
 template <int NB, int NS>
@@ -2171,6 +2510,17 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
     const CUtensorMap tmB = rows_map(dp.oz_b, 2ull * NS * dp.oz_slice_bytes / 128, OZ_TN / 2);
     oz_gemm2_kernel<NB, NS><<<2 * pairs, 320, OZ2_SMEM, s>>>(tmA, tmB, erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n,
                                                              dp.ku, dp.kv, sch, sc, rpr, dp.tc_err, rdot, rzpart);
+  } else if (variant == OZ_GEMM_CLUSTER) {
+    int cm, cn;
+    oz_cluster_shape(cm, cn);
+    const uint8_t *bp = inv ? dp.oz_bi : dp.oz_b;
+    double *yo = inv ? eo : y;
+    if (cm == 2 && cn == 2)
+      oz_launch_mc<NB, NS, 2, 2>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, rdot, rzpart, s);
+    else if (cm == 1)
+      oz_launch_mc<NB, NS, 1, 2>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, rdot, rzpart, s);
+    else
+      oz_launch_mc<NB, NS, 2, 1>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, rdot, rzpart, s);
   } else if (variant == OZ_GEMM_STREAMK) {
     const int gsk = oz_sk_ctas();
     uint8_t *area = dp.tc_scratch;

@@ -19,6 +19,7 @@ LAG_ENUMERIC, LAG_ECUDA, LAG_EAGAIN, LAG_ETIMEDOUT, LAG_ECANCELED = -4, -5, -6, 
 LAG_FP64, LAG_MIXED = 0, 1
 LAG_WAVELET_RICKER, LAG_WAVELET_PAPER = 0, 1
 LAG_GEMM_SIMT, LAG_GEMM_SPLIT_BF16, LAG_GEMM_SLICE_TILES, LAG_GEMM_SLICE_STREAMK, LAG_GEMM_SLICE_PAIRS = 0, 1, 2, 3, 4
+LAG_GEMM_SLICE_CLUSTER = 5
 
 
 class lag_grid(C.Structure):
