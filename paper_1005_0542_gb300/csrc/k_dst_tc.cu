@@ -737,7 +737,10 @@ struct OzSched {
   int8_t gsh[OZ_MAXU];  // per group: s >= 0 if its sum is an exact integer G with value G 2^-(FIX - s)
                         // (the int64 epilogue adds G << s), -1 for a rounded group (rn(v 2^FIX))
   uint8_t ug[OZ_MAXU];  // group of each unit
-  int nstage;           // pipeline stages of one tile (each unit's K tiles in steps of OZ_KT)
+  // fused schedules (tile kernel): a second B slice of a unit sharing A slice si (0: none), and
+  // split units whose two products fill two consecutive groups (else they share one accumulator)
+  int8_t sj2[OZ_MAXU], split[OZ_MAXU];
+  int nstage;  // pipeline stages of one tile (OZ_KT K tiles per stage; one for units of two B slices)
 };
 
 // The epilogue's accumulator: a signed fixed-point integer in units of 2^-FIX of the pre-scaled
@@ -964,10 +967,11 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
   }
 }
 
-// Persistent warp-specialised GEMM over (parity, m tile, n tile) tiles and, per tile, the pair
-// schedule: warp 0 streams A_i / B_j stages, warp 1 issues the MMAs of a group into one of four
-// tensor-memory accumulators, warps 2-9 add finished groups into float64 sums held in registers
-// (warp w: rows 32 (w % 4).., columns 64 ((w - 2) / 4)..) and store the tile once at its end.
+// Persistent warp-specialised GEMM over (parity, m tile, n tile) tiles and, per tile, the fused
+// pair schedule: warp 0 streams the stages of each unit (two K tiles of A_i and B_j, or one K tile
+// of A_i, B_j and B_j2), warp 1 issues the MMAs of a group into one of four tensor-memory
+// accumulators, warps 2-9 add finished groups into int64 sums held in registers (warp w: rows
+// 32 (w % 4).., columns 64 ((w - 2) / 4)..) and store the tile once at its end.
 template <int NB, int NS>
 __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restrict__ apack, size_t a_slice_bytes,
                                                          const uint8_t *__restrict__ bpack, size_t b_slice_bytes,
@@ -1038,6 +1042,26 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
           const uint8_t *at = apack + ((size_t)par * NS + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
           const uint8_t *bt = bpack + ((size_t)par * NS + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
           const int ke = sch.k1[pr];
+          if (sch.sj2[pr] > 0) {
+            // A_i with two B slices: one K tile per stage, A in slot 0, the B tiles in slots 2 and 3
+            // (A slot 1 stays unused: the stream into the SM, not shared memory, is the constraint)
+            const uint8_t *bt2 = bpack + ((size_t)par * NS + (sch.sj2[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+            for (int kk = sch.k0[pr]; kk < ke; ++kk, ++it) {
+              const int s = it % OZ_NST, use = it / OZ_NST;
+              if (it >= OZ_NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
+                atomicExch(err, 11);
+                *abort_flag = 1;
+                break;
+              }
+              const uint32_t st = base + s * OZ_STAGE;
+              const uint32_t fb = full0 + 8 * s;
+              mbar_expect_tx(fb, (uint32_t)(A_TILE + 2 * OZ_BT));
+              bulk_g2s(st, at + (size_t)kk * A_TILE, A_TILE, fb);
+              bulk_g2s(st + OZ_KT * A_TILE, bt + (size_t)kk * OZ_BT, OZ_BT, fb);
+              bulk_g2s(st + OZ_KT * A_TILE + OZ_BT, bt2 + (size_t)kk * OZ_BT, OZ_BT, fb);
+            }
+            continue;
+          }
           for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
             const int kt = min(OZ_KT, ke - kk);  // K tiles in this stage
             const int s = it % OZ_NST, use = it / OZ_NST;
@@ -1064,17 +1088,60 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         if (!wanted(par, mt, nt)) continue;
         uint32_t d = 0;
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
+          const bool split = sch.split[pr] != 0;
           if (sch.first[pr]) {
-            const int acc = gc % OZ_NACC, ause = gc / OZ_NACC;
-            if (gc >= OZ_NACC && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) {
+            bool ok = true;
+            for (int q = 0; q < (split ? 2 : 1); ++q) {  // a split unit fills two accumulators
+              const int acc = (gc + q) % OZ_NACC, ause = (gc + q) / OZ_NACC;
+              if (gc + q >= OZ_NACC && !mbar_wait(tempty0 + 8 * acc, (ause - 1) & 1)) ok = false;
+            }
+            if (!ok) {
               atomicExch(err, 14);
               *abort_flag = 1;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            d = tmem + (uint32_t)(acc * OZ_TN);
+            d = tmem + (uint32_t)((gc % OZ_NACC) * OZ_TN);
           }
           const int kb = sch.k0[pr], ke = sch.k1[pr];
+          if (sch.sj2[pr] > 0) {
+            // A_i with two B slices, one K tile per stage: both products into the group's
+            // accumulator, or (split) the second into the next group's
+            const uint32_t d2 = split ? tmem + (uint32_t)(((gc + 1) % OZ_NACC) * OZ_TN) : d;
+            for (int kk = kb; kk < ke; ++kk, ++it) {
+              const int s = it % OZ_NST, use = it / OZ_NST;
+              if (!mbar_wait(full0 + 8 * s, use & 1)) {
+                atomicExch(err, 12);
+                *abort_flag = 1;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t st = base + s * OZ_STAGE;
+              for (int q = 0; q < 2; ++q) {
+                const uint32_t dq = (q == 0) ? d : d2, sb = st + OZ_KT * A_TILE + q * OZ_BT;
+                // a fresh accumulator takes its first product without accumulating: the group's
+                // first K tile for the first product, and for the second of a split unit
+                const bool fresh = sch.first[pr] && kk == kb && (q == 0 || split);
+#pragma unroll
+                for (int sub = 0; sub < TK / 16; ++sub) {
+                  const uint32_t o = sub * 32;
+                  mma_bf16_n128(dq, sdesc(st + o), sdesc(sb + o), (fresh && sub == 0) ? 0u : 1u);
+                }
+              }
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                               empty0 + 8 * s)
+                           : "memory");
+            }
+            if (sch.last[pr]) {
+              for (int q = 0; q < (split ? 2 : 1); ++q) {
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tfull0 + 8 * ((gc + q) % OZ_NACC))
+                             : "memory");
+              }
+              gc += split ? 2 : 1;
+            }
+            continue;
+          }
           for (int kk = kb; kk < ke; kk += OZ_KT, ++it) {
             const int kt = min(OZ_KT, ke - kk);
             const int s = it % OZ_NST, use = it / OZ_NST;
@@ -2141,7 +2208,15 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_mc_kernel(const uint8_t *__res
 // each in its own accumulator, and the chunks are spread between the exact groups: every group
 // costs the epilogue a pass over its accumulator, so runs of short exact groups alone would hold
 // the MMA issuer waiting for accumulators, while the tail's longer groups let the epilogue catch up.
-static OzSched oz_schedule(int kpad, OzFmt f) {
+// Fused schedule (the tile kernel): pairs that share the A slice i run as one unit whose stages hold
+// one K tile of A_i and of every B_j it meets, so A_i crosses into the SM once for them all (the
+// operand stream into each SM is what bounds the GEMM).  Exact groups of one product each (gmax = 1)
+// pair up by i into "split" units, the two products filling two consecutive groups' accumulators;
+// the tail is grouped by i instead of by weight (two pairs per accumulator: products of
+// different weights share an accumulator since the slices carry their scale).  The 8-bit format:
+// 15 exact pairs in 6 split units and 3 single ones, 13 tail pairs in 6 units of two and 1 single;
+// 44 operand K tiles per K step instead of 56.
+static OzSched oz_schedule(int kpad, OzFmt f, bool fuse) {
   OzSched s{};
   const long long qmax = (f.nb == 8) ? 128 : (1LL << f.nb) - 1;  // largest digit magnitude
   const int nks = kpad / TK;
@@ -2151,10 +2226,11 @@ static OzSched oz_schedule(int kpad, OzFmt f) {
   int tail_d = (f.nb == 8) ? 7 : 8;
   for (long long k = 1024; k < kpad; k *= 2) ++tail_d;
   struct Unit {
-    int i, j, k0, k1;
+    int i, j[2], nb, k0, k1;  // A slice i with nb (1 or 2) B slices j[] over K tiles [k0, k1)
+    bool split;               // the two products fill two consecutive (exact) groups
   };
   struct Group {
-    int d;
+    int d, d2;  // weights of its products (d2: the second group of a split unit, else 0)
     std::vector<Unit> units;
   };
   std::vector<Group> exact, tail;
@@ -2170,15 +2246,49 @@ static OzSched oz_schedule(int kpad, OzFmt f) {
       for (int c0 = 0; c0 < nks; c0 += kcs) {
         const int c1 = std::min(nks, c0 + kcs);
         for (size_t q = 0; q < pairs.size(); ++q) {
-          if (q % gmax == 0) exact.push_back({d, {}});
-          exact.back().units.push_back({pairs[q].first, pairs[q].second, c0, c1});
+          if (q % gmax == 0) exact.push_back({d, 0, {}});
+          exact.back().units.push_back({pairs[q].first, {pairs[q].second, 0}, 1, c0, c1, false});
         }
       }
-    } else {
+    } else if (!fuse) {
       for (const auto &pq : pairs) {
-        if (tail.empty() || (int)tail.back().units.size() == 3) tail.push_back({tail_d, {}});
-        tail.back().units.push_back({pq.first, pq.second, 0, nks});
+        if (tail.empty() || (int)tail.back().units.size() == 3) tail.push_back({tail_d, 0, {}});
+        tail.back().units.push_back({pq.first, {pq.second, 0}, 1, 0, nks, false});
       }
+    }
+  }
+  if (fuse) {
+    // tail by A slice: the pairs (i, j) with tail <= i + j <= ns + 1, two per unit (one accumulator)
+    for (int i = 1; i <= f.ns; ++i) {
+      Unit u{i, {0, 0}, 0, 0, nks, false};
+      for (int j = 1; j <= f.ns; ++j) {
+        if (i + j < tail_d || i + j > f.ns + 1) continue;
+        if (u.nb == 2) {
+          tail.push_back({tail_d, 0, {u}});
+          u.nb = 0;
+        }
+        u.j[u.nb++] = j;
+      }
+      if (u.nb > 0) tail.push_back({tail_d, 0, {u}});
+    }
+    // exact groups of one product: by (K chunk, i), consecutive ones paired into split units
+    if (gmax == 1) {
+      std::stable_sort(exact.begin(), exact.end(), [](const Group &x, const Group &y) {
+        const Unit &a = x.units[0], &b = y.units[0];
+        return a.k0 != b.k0 ? a.k0 < b.k0 : a.i < b.i;
+      });
+      std::vector<Group> fused;
+      for (size_t q = 0; q < exact.size(); ++q) {
+        const Unit &a = exact[q].units[0];
+        if (q + 1 < exact.size() && exact[q + 1].units[0].i == a.i && exact[q + 1].units[0].k0 == a.k0) {
+          const Unit &b = exact[q + 1].units[0];
+          fused.push_back({exact[q].d, exact[q + 1].d, {{a.i, {a.j[0], b.j[0]}, 2, a.k0, a.k1, true}}});
+          ++q;
+        } else {
+          fused.push_back(exact[q]);
+        }
+      }
+      exact.swap(fused);
     }
   }
   std::vector<const Group *> order;
@@ -2192,25 +2302,29 @@ static OzSched oz_schedule(int kpad, OzFmt f) {
   for (; ie < ne; ++ie) order.push_back(&exact[ie]);
   const int fix = oz_fix(f.nb);
   int nu = 0, ng = 0;
+  auto shift = [&](int d, bool ex) { return (int8_t)((ex && fix - f.nb * (d - 2) >= 0) ? fix - f.nb * (d - 2) : -1); };
   for (const Group *g : order) {
     const bool ex = g->d < tail_d;
-    const int sh = fix - f.nb * (g->d - 2);
-    if (ng >= OZ_MAXU) throw Error(LAG_EINVAL, "exact-slice schedule: too many groups");
-    s.gsh[ng] = (int8_t)((ex && sh >= 0) ? sh : -1);
+    if (ng + 1 >= OZ_MAXU) throw Error(LAG_EINVAL, "exact-slice schedule: too many groups");
+    s.gsh[ng] = shift(g->d, ex);
+    if (g->d2 > 0) s.gsh[ng + 1] = shift(g->d2, true);
     for (size_t q = 0; q < g->units.size(); ++q) {
       if (nu >= OZ_MAXU) throw Error(LAG_EINVAL, "exact-slice schedule: too many units");
       const Unit &u = g->units[q];
       s.si[nu] = (int8_t)u.i;
-      s.sj[nu] = (int8_t)u.j;
+      s.sj[nu] = (int8_t)u.j[0];
+      s.sj2[nu] = (int8_t)(u.nb > 1 ? u.j[1] : 0);
+      s.split[nu] = u.split ? 1 : 0;
       s.k0[nu] = (uint8_t)u.k0;
       s.k1[nu] = (uint8_t)u.k1;
       s.first[nu] = (q == 0);
       s.last[nu] = (q + 1 == g->units.size());
       s.ug[nu] = (uint8_t)ng;
-      s.nstage += (u.k1 - u.k0 + OZ_KT - 1) / OZ_KT;
+      // a unit of two B slices takes one K tile per stage (A and both B tiles)
+      s.nstage += (u.nb > 1) ? (u.k1 - u.k0) : (u.k1 - u.k0 + OZ_KT - 1) / OZ_KT;
       ++nu;
     }
-    ++ng;
+    ng += (g->d2 > 0) ? 2 : 1;
   }
   s.nunits = nu;
   s.ngroups = ng;
@@ -2220,7 +2334,7 @@ static OzSched oz_schedule(int kpad, OzFmt f) {
 
 int dst_oz_products(int n) {
   const int kpad = div_up((n + 1) / 2, TK) * TK;
-  return oz_schedule(kpad, oz_format(kpad)).npairs;
+  return oz_schedule(kpad, oz_format(kpad), false).npairs;
 }
 
 bool dst_oz_supported(int n) {
@@ -2496,10 +2610,10 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
                                                                          a_slice, erow, sc, rpr, inv);
   count_launch();
   LAG_LAUNCH_CHECK();
-  const OzSched sch = oz_schedule(nks * TK, OzFmt{NB, NS});
+  const int variant = dst_oz_gemm_variant(dp, rows, rpr, inv);
+  const OzSched sch = oz_schedule(nks * TK, OzFmt{NB, NS}, variant == OZ_GEMM_TILES);
   const int ntiles = 2 * nmt * nnt;
   const int grid = std::min(ntiles, 152);
-  const int variant = dst_oz_gemm_variant(dp, rows, rpr, inv);
   // E / O sums of the inverse: after the packed A slices and the row exponents, 256-byte aligned
   double *eo = reinterpret_cast<double *>(
       (reinterpret_cast<uintptr_t>(erow + 2 * (size_t)nmt * TM) + 255) & ~(uintptr_t)255);

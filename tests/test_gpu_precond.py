@@ -429,9 +429,11 @@ def test_dst_gemm_query(ctx, monkeypatch):
 @pytest.mark.parametrize("nx,nz,nrhs", [(2048, 1024, 1), (700, 130, 3), (16, 3, 1), (1000, 77, 5), (4096, 256, 2)])
 def test_dst_f64_cluster_multicast_equals_tiles(ctx, monkeypatch, shape, nx, nz, nrhs):
     # tiles on clusters (2 x 2, 1 x 2, 2 x 1 tiles) whose shared A / B slice tiles are read from L2
-    # once and multicast into every CTA that needs them: the same exact products and int64 sums as
-    # the one-CTA tile kernel, so the same float64 bits.  An odd column-tile count (700: 3 column
-    # tiles per parity; 16: 1), padding m-tiles, batches, the 6-bit format (4096), rows over 40 decades
+    # once and multicast into every CTA that needs them, against the one-CTA tile kernel: the same
+    # exact products; the FP32-rounded tail pairs are grouped by weight here and by A slice in the
+    # tile kernel, so the two differ by those roundings only (far below the float64 rounding).  An
+    # odd column-tile count (700: 3 column tiles per parity; 16: 1), padding m-tiles, batches, the
+    # 6-bit format (4096), rows over 40 decades
     x = RNG.standard_normal((nrhs, nz, nx)) * 10.0 ** RNG.uniform(-20, 20, (nrhs, nz, 1))
     p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
     xd, yc, yt = dev(x), empty(x.shape), empty(x.shape)
@@ -441,8 +443,8 @@ def test_dst_f64_cluster_multicast_equals_tiles(ctx, monkeypatch, shape, nx, nz,
     yc.fill_(7.0)
     L.check(L.lag_precond_dst(p, ptr(xd), ptr(yc), nrhs), ctx)
     monkeypatch.delenv("LAGWAVE_OZ_CLUSTER")
-    assert np.array_equal(host(yc), host(yt))
     sc = np.abs(host(yt)).max(axis=-1, keepdims=True)
+    assert np.abs((host(yc) - host(yt)) / sc).max() < 1e-15
     assert np.abs((host(yt) - odst.dst_x(x)) / sc).max() < 1e-14
     assert L.lag_precond_status(p) == L.LAG_OK
     L.lag_precond_destroy(p)
@@ -451,7 +453,7 @@ def test_dst_f64_cluster_multicast_equals_tiles(ctx, monkeypatch, shape, nx, nz,
 @pytest.mark.parametrize("shape", ["2x2", "1x2"])
 def test_dct_f64_cluster_multicast_equals_tiles(ctx, monkeypatch, shape):
     # the cylindrical plan's forward DCT-II and its inverse (E / O sums, then the butterfly) on
-    # clusters: the same bits as the tile kernel
+    # clusters against the tile kernel (the same exact products; tail roundings grouped differently)
     nr, nz, nrhs = 300, 333, 2
     g = L.grid(nr, nz, 5.0, 4.0, cylindrical=True)
     p = C.c_void_p()
@@ -468,6 +470,7 @@ def test_dct_f64_cluster_multicast_equals_tiles(ctx, monkeypatch, shape):
         out[mode] = (host(yf), host(yi))
         if mode:
             monkeypatch.delenv("LAGWAVE_OZ_CLUSTER")
-    assert np.array_equal(out[None][0], out[shape][0]) and np.array_equal(out[None][1], out[shape][1])
+    for a, b in zip(out[None], out[shape]):
+        assert np.abs((a - b) / np.abs(a).max(axis=-1, keepdims=True)).max() < 1e-15
     assert L.lag_precond_status(p) == L.LAG_OK
     L.lag_precond_destroy(p)

@@ -238,14 +238,16 @@ def test_graph_and_eager_pcg_identical(ctx, monkeypatch):
 
 
 def test_cluster_multicast_pcg_identical(ctx, monkeypatch):
-    # the float64 PCG with its exact-slice GEMM on 2 x 2 clusters (operand tiles multicast) runs the
-    # same arithmetic as with the tile kernel, (r, z) partials included: identical fields
+    # the float64 PCG with its exact-slice GEMM on 2 x 2 clusters (operand tiles multicast, (r, z)
+    # partials in the epilogue) against the tile kernel: preconditioners equal up to the tail's FP32
+    # roundings, so fields equal to well inside the solve's tolerance
     s = inputs.random_layered(nx=600, nz=300, hx=10.0, n_harm=3, sources=[(300, 3)], f0=12.0)
     a = _shot_fields(ctx, s, L.LAG_FP64, 1e-10, s.n_harm)
     monkeypatch.setenv("LAGWAVE_OZ_CLUSTER", "2x2")
     b = _shot_fields(ctx, s, L.LAG_FP64, 1e-10, s.n_harm)
     monkeypatch.delenv("LAGWAVE_OZ_CLUSTER")
-    assert np.array_equal(a, b)
+    for m in range(s.n_harm):
+        assert np.linalg.norm(a[m] - b[m]) <= 1e-9 * np.linalg.norm(a[m])
 
 
 def test_elastic_full_size_first_harmonic_true_residual(ctx):
