@@ -759,6 +759,52 @@ __host__ __device__ constexpr int oz_fix(int) { return 38; }
 __host__ __device__ constexpr int oz_bits(int nb, int ns) { return nb == 8 ? 55 : nb * ns; }
 __host__ __device__ constexpr int oz_se(int nb, int ns) { return oz_bits(nb, ns) - nb * (ns - 1); }
 
+// The epilogue's float64 result RN(v) 2^kx of an int64 sum v (|v| < 2^63), built with integer
+// operations: the FP64 pipe of this part runs at 1/64 of the FP32 rate, and an int64 -> float64
+// conversion plus two power-of-two scalings per output kept the GEMM's epilogue busy for longer
+// than its last group's MMAs.  One rounding, to nearest even, as (double) v rounds.  Only for rows
+// whose every result stays in the normal range (oz_fast_row); the others (subnormal or overflowing
+// results, non-finite rows) take the float64 expression scale * (unit * (double) v), so every
+// output equals that expression's.
+__device__ __forceinline__ bool oz_fast_row(int e, int kx) {
+  return e != OZ_EXP_NAN && kx + 1023 >= 1 && kx + 64 + 1023 <= 2046;
+}
+__device__ __forceinline__ double oz_to_f64(long long v, int kx) {
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long u = sgn ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)u);
+  const unsigned long long m = u << (lz & 63);  // leading one at bit 63 (u = 0: m = 0)
+  const unsigned long long rem = m & 0x7ffull;
+  unsigned long long r = m >> 11;              // 53 bits, the leading one at bit 52
+  r += (rem > 0x400ull || (rem == 0x400ull && (r & 1ull))) ? 1ull : 0ull;  // to nearest even
+  // exponent field one below the biased exponent, plus r with its leading one: a carry of the
+  // rounding into bit 53 raises the exponent by one and leaves a zero fraction
+  const unsigned long long ef = (unsigned long long)(63 - lz + kx + 1022) << 52;
+  return u == 0 ? 0.0 : __longlong_as_double((long long)(sgn | (ef + r)));
+}
+
+// One epilogue thread's outputs of a tile row: the float64 values of its int64 sums (ncols of them,
+// ystride doubles apart from yp) and, with rp, the partial (r, z) of those values into *rzp.
+template <bool FAST>
+__device__ __forceinline__ void oz_store_row(const long long (&acci)[64], int ncols, int kx, double scale, double unit,
+                                             double *yp, int ystride, const double *rp, double *rzp) {
+  double dacc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 64; ++q)
+    if (q < ncols) {
+      const double v = FAST ? oz_to_f64(acci[q], kx) : scale * (unit * __ll2double_rn(acci[q]));
+      yp[ystride * q] = v;
+      if (rp != nullptr) dacc = fma(__ldg(rp + 2 * q), v, dacc);
+    }
+  if (rzp != nullptr) *rzp = dacc;
+}
+// the same for a row: the integer conversion where every result of the row is a normal float64
+__device__ __forceinline__ void oz_store(const long long (&acci)[64], int ncols, int e, int kx, double scale,
+                                         double unit, double *yp, int ystride, const double *rp, double *rzp) {
+  if (oz_fast_row(e, kx)) oz_store_row<true>(acci, ncols, kx, scale, unit, yp, ystride, rp, rzp);
+  else oz_store_row<false>(acci, ncols, kx, scale, unit, yp, ystride, rp, rzp);
+}
+
 // |v| < 2^e: NBITS-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
 template <int NBITS>
 __device__ __forceinline__ unsigned long long oz_fixed(double v, int e) {
@@ -1222,37 +1268,21 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
       if (rok) {
         // the one float64 rounding of the product: int64 -> double, then exact power-of-two scales
         // (2^-38 first, so that a row near the bottom of the float64 range meets the same
-        // subnormal rounding as its float64 product would)
+        // subnormal rounding as its float64 product would); built from integer operations where
+        // every result of the row is a normal float64
         const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
                                                : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
         const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+        const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
-        if (inv) {  // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]
-          double *yp = y + ((size_t)par * rows + row) * ku + c0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[q] = scale * (unit * __ll2double_rn(acci[q]));
-        } else if (rzpart == nullptr) {
-          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
-        } else {
-          // the CG dot (r, z) of the values just formed, one partial per (row, parity, column tile,
-          // half): PCG's beta without another sweep over r and z
-          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
-          const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
-          double dacc = 0.0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) {
-              const double v = scale * (unit * __ll2double_rn(acci[q]));
-              yp[2 * q] = v;
-              dacc = fma(__ldg(rp + 2 * q), v, dacc);
-            }
-          rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dacc;
-        }
+        // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved
+        // spectrum and, with rzpart, the CG dot (r, z) of the values just formed, one partial per
+        // (row, parity, column tile, half): PCG's beta without another sweep over r and z
+        const size_t o = inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0;
+        const bool rz = !inv && rzpart != nullptr;
+        oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2, rz ? rdot + o : nullptr,
+                 rz ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
       }
     }
   }
@@ -1578,25 +1608,12 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_sk_kernel(const uint8_t *__res
           const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
                                                  : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
           const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+          const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
           const int c0 = nt * OZ_TN + h * 64;
           const int ncols = min(64, (par ? kv : ku) - c0);
-          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
-          if (rzpart == nullptr) {
-#pragma unroll
-            for (int q = 0; q < 64; ++q)
-              if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
-          } else {
-            const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
-            double dsum = 0.0;
-#pragma unroll
-            for (int q = 0; q < 64; ++q)
-              if (q < ncols) {
-                const double val = scale * (unit * __ll2double_rn(acci[q]));
-                yp[2 * q] = val;
-                dsum = fma(__ldg(rp + 2 * q), val, dsum);
-              }
-            rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dsum;
-          }
+          const size_t o = (size_t)row * ld + par + 2 * (size_t)c0;
+          oz_store(acci, ncols, e, kx, scale, unit, y + o, 2, rzpart ? rdot + o : nullptr,
+                   rzpart ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
         }
       }
     }
@@ -1887,25 +1904,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
         const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
                                                : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
         const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+        const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, (par ? kv : ku) - c0);
-        double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
-        if (rzpart == nullptr) {
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
-        } else {
-          const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
-          double dacc = 0.0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) {
-              const double v = scale * (unit * __ll2double_rn(acci[q]));
-              yp[2 * q] = v;
-              dacc = fma(__ldg(rp + 2 * q), v, dacc);
-            }
-          rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dacc;
-        }
+        const size_t o = (size_t)row * ld + par + 2 * (size_t)c0;
+        oz_store(acci, ncols, e, kx, scale, unit, y + o, 2, rzpart ? rdot + o : nullptr,
+                 rzpart ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
       }
     }
   }
@@ -2167,31 +2171,16 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_mc_kernel(const uint8_t *__res
         const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
                                                : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
         const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+        const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
-        if (inv) {  // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]
-          double *yp = y + ((size_t)par * rows + row) * ku + c0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[q] = scale * (unit * __ll2double_rn(acci[q]));
-        } else if (rzpart == nullptr) {
-          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) yp[2 * q] = scale * (unit * __ll2double_rn(acci[q]));
-        } else {
-          double *yp = y + (size_t)row * ld + par + 2 * (size_t)c0;
-          const double *rp = rdot + (size_t)row * ld + par + 2 * (size_t)c0;
-          double dacc = 0.0;
-#pragma unroll
-          for (int q = 0; q < 64; ++q)
-            if (q < ncols) {
-              const double v = scale * (unit * __ll2double_rn(acci[q]));
-              yp[2 * q] = v;
-              dacc = fma(__ldg(rp + 2 * q), v, dacc);
-            }
-          rzpart[(size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h] = dacc;
-        }
+        // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved
+        // spectrum and, with rzpart, the CG dot (r, z) of the values just formed, one partial per
+        // (row, parity, column tile, half): PCG's beta without another sweep over r and z
+        const size_t o = inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0;
+        const bool rz = !inv && rzpart != nullptr;
+        oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2, rz ? rdot + o : nullptr,
+                 rz ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
       }
     }
   }
