@@ -81,10 +81,15 @@ static_assert(sizeof(KrylovScalars) == 80, "layout");
 // and the float64 output is multiplied by 2^e again.  Power-of-two scaling is exact; it keeps
 // residuals that are tiny in absolute terms (a weak source, a late iterate) away from float32
 // underflow, the preconditioner being linear.
+// ilogb(sqrt(rr)) = floor(ilogb(rr) / 2) for every positive finite rr (a correctly rounded square
+// root of a double below 2^(2k+2) stays below 2^(k+1)), from the bits: no float64 square root
 __device__ __forceinline__ int residual_exponent(const KrylovScalars *sc, int b) {
   const double rr = sc[b].rr;
   if (!(rr > 0.0) || !isfinite(rr)) return 0;
-  return ilogb(sqrt(rr));
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(rr);
+  const int E = (int)(bits >> 52);  // sign clear: rr > 0
+  const int lb = E ? E - 1023 : (63 - __clzll((long long)(bits & 0xfffffffffffffull))) - 1074;
+  return lb >> 1;  // arithmetic shift: floor
 }
 
 // x * 2^e by an add to the exponent field (integer ops: the FP64 pipe of this part is narrow).
@@ -100,6 +105,55 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
   if (ne <= 0) return __longlong_as_double(sign);
   if (ne >= 0x7ff) return __longlong_as_double(sign | 0x7ff0000000000000ll);
   return __longlong_as_double(b + ((long long)e << 52));
+}
+
+// (double) f * 2^e with scale_pow2's rules, from the float's bits (integer ops: conversions between
+// float and double run on the narrow FP64 pipe of this part)
+__device__ __forceinline__ double widen_pow2(float f, int e) {
+  const uint32_t fb = __float_as_uint(f);
+  const uint32_t fe = (fb >> 23) & 0xffu, fm = fb & 0x7fffffu;
+  const long long sign = (long long)(fb >> 31) << 63;
+  if (fe == 0xffu) return __longlong_as_double(sign | 0x7ff0000000000000ll | ((long long)fm << 29));  // Inf / NaN
+  int ne;
+  long long mant;
+  if (fe == 0u) {  // zero, or a float subnormal: a normal double with its leading one at bit p of fm
+    if (fm == 0u) return __longlong_as_double(sign);
+    const int p = 31 - __clz((int)fm);
+    ne = p + 874 + e;  // 2^(p - 149), double bias 1023
+    mant = ((long long)fm << (52 - p)) & 0xfffffffffffffll;
+  } else {
+    ne = (int)fe + 896 + e;  // float bias 127, double bias 1023
+    mant = (long long)fm << 29;
+  }
+  if (ne <= 0) return __longlong_as_double(sign);
+  if (ne >= 0x7ff) return __longlong_as_double(sign | 0x7ff0000000000000ll);
+  return __longlong_as_double(sign | ((long long)ne << 52) | mant);
+}
+
+// (float) scale_pow2(x, e) from the double's bits: round to nearest even, float subnormals and
+// overflow to Inf included (integer ops, as above)
+__device__ __forceinline__ float narrow_pow2(double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
+  const int E = (int)((b >> 52) & 0x7ff);
+  const unsigned long long M = b & 0xfffffffffffffull;
+  if (E == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (M ? 0x400000u | (uint32_t)(M >> 29) : 0u));
+  const int ne = E + e;
+  if (E == 0 || ne <= 0) return __uint_as_float(sign);  // scale_pow2 flushes double subnormals
+  const int u = ne - 1023;
+  if (ne >= 0x7ff || u > 127) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long m = M | (1ull << 52);
+  if (u >= -126) {  // a normal float: keep 24 bits; a carry into bit 24 raises the exponent (to Inf at most)
+    uint32_t r = (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1fffffffull);
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    return __uint_as_float(sign | (((uint32_t)(u + 126) << 23) + r));
+  }
+  const int s = -u - 97;  // a float subnormal: the mantissa in units of 2^-149
+  if (s > 54) return __uint_as_float(sign);
+  const unsigned long long r0 = m >> s, rem = m & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+  const uint32_t r = (uint32_t)r0 + ((rem > half || (rem == half && (r0 & 1ull))) ? 1u : 0u);
+  return __uint_as_float(sign | r);
 }
 
 // ST_MET (GMRES only): the residual estimate met the tolerance inside an open cycle; the true

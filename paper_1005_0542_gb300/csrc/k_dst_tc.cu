@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ 
                                                          int nks, int nmt, uint8_t *__restrict__ out,
                                                          const KrylovScalars *__restrict__ sc, int rpr, int rscale) {
   const int chunks = nks * (TK / 8);
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)nmt * TM * chunks) return;
-  const int row = (int)(t / chunks), ch = (int)(t % chunks);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < nmt TM chunks, far below 2^32
+  if (t >= (unsigned)(nmt * TM * chunks)) return;
+  const int row = (int)(t / (unsigned)chunks), ch = (int)t - row * chunks;
   const int k0 = ch * 8;
   const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
   // PCG residuals enter scaled by 2^-e (residual_exponent), undone by the inverse butterfly
@@ -204,18 +204,13 @@ __global__ void __launch_bounds__(256) pack_a_fwd_kernel(const TI *__restrict__ 
     const int j = k0 + e;
     float u = 0.f, w = 0.f;
     if (live) {
+      // (float) (x 2^es) by integer operations on the bits (the conversion would take the FP64 pipe)
       if (j < kv) {
-        double xa = (double)xr[j], xb = (double)xr[n - 1 - j];
-        if (es != 0) {
-          xa = scale_pow2(xa, es);
-          xb = scale_pow2(xb, es);
-        }
-        const float a = (float)xa, b = (float)xb;
+        const float a = narrow_pow2((double)xr[j], es), b = narrow_pow2((double)xr[n - 1 - j], es);
         u = a + b;
         w = a - b;
       } else if (j < ku) {
-        const double xm = (double)xr[j];
-        u = (float)(es != 0 ? scale_pow2(xm, es) : xm);  // middle element of an odd-length row
+        u = narrow_pow2((double)xr[j], es);  // middle element of an odd-length row
       }
     }
     split2f(u, uh[e], ul[e]);
@@ -235,20 +230,32 @@ __global__ void __launch_bounds__(256) pack_a_inv_kernel(const float *__restrict
                                                          int nks, int nmt, uint8_t *__restrict__ out,
                                                          const KrylovScalars *__restrict__ sc, int rpr) {
   const int chunks = nks * (TK / 8);
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)nmt * TM * chunks) return;
-  const int row = (int)(t / chunks), ch = (int)(t % chunks);
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;  // < nmt TM chunks, far below 2^32
+  if (t >= (unsigned)(nmt * TM * chunks)) return;
+  const int row = (int)(t / (unsigned)chunks), ch = (int)t - row * chunks;
   const int k0 = ch * 8;
   const bool live = row < rows && (sc == nullptr || sc[row / rpr].state == ST_RUN);
   const float *yr = y + (size_t)(live ? row : 0) * n;
+  float ev[8], ov[8];
+  if (live && k0 + 8 <= kv && (((size_t)row * n) & 3) == 0 && (ku & 3) == 0) {
+    // whole chunks of both halves, 16-byte aligned: two float4 loads each
+    const float4 *e4 = reinterpret_cast<const float4 *>(yr + k0), *o4 = reinterpret_cast<const float4 *>(yr + ku + k0);
+    const float4 a = __ldg(e4), b = __ldg(e4 + 1), c = __ldg(o4), d = __ldg(o4 + 1);
+    ev[0] = a.x; ev[1] = a.y; ev[2] = a.z; ev[3] = a.w; ev[4] = b.x; ev[5] = b.y; ev[6] = b.z; ev[7] = b.w;
+    ov[0] = c.x; ov[1] = c.y; ov[2] = c.z; ov[3] = c.w; ov[4] = d.x; ov[5] = d.y; ov[6] = d.z; ov[7] = d.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = k0 + e;
+      ev[e] = (live && j < ku) ? yr[j] : 0.f;
+      ov[e] = (live && j < kv) ? yr[ku + j] : 0.f;
+    }
+  }
   alignas(16) uint16_t eh[8], el[8], oh[8], ol[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
-    const int j = k0 + e;
-    const float ev = (live && j < ku) ? yr[j] : 0.f;
-    const float ov = (live && j < kv) ? yr[ku + j] : 0.f;
-    split2f(ev, eh[e], el[e]);
-    split2f(ov, oh[e], ol[e]);
+    split2f(ev[e], eh[e], el[e]);
+    split2f(ov[e], oh[e], ol[e]);
   }
   const int mt = row / TM, r = row % TM, ks = k0 / TK, kk = k0 % TK;
   const uint32_t off = swz(r, kk);
@@ -482,7 +489,8 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
   const int es = residual_exponent(sc, rhs);  // the forward pack scaled r by 2^-e
   double a0 = 0.0, a1 = 0.0;
   // rows round-robin over the blocks, a row's modes over the threads (no 64-bit index division);
-  // E +- O in float32 (the spectrum's precision), widened once, the CG dots in float64
+  // E +- O in float32 (the spectrum's precision), widened with the residual's scale by integer
+  // operations on the bits, the CG dots in float64
   for (int rl = blockIdx.x; rl < rpr; rl += gridDim.x) {
     const size_t row = row0 + (size_t)rl;
     const float *er = eo + row * 2 * ku;
@@ -490,15 +498,13 @@ __global__ void __launch_bounds__(256) butterfly_beta_kernel(const float *__rest
     for (int k = threadIdx.x; k < ku; k += blockDim.x) {
       const float e = er[k], o = er[ku + k];
       const size_t i1 = row * n + k;
-      double z1 = (double)(e + o);
-      if (es != 0) z1 = scale_pow2(z1, es);
+      const double z1 = widen_pow2(e + o, es);
       z[i1] = z1;
       a0 = fma(r[i1], z1, a0);
       if (flexible) a1 = fma(z1, q[i1], a1);
       if (k < kv) {
         const size_t i2 = row * n + (n - 1 - k);
-        double z2 = (double)(e - o);
-        if (es != 0) z2 = scale_pow2(z2, es);
+        const double z2 = widen_pow2(e - o, es);
         z[i2] = z2;
         a0 = fma(r[i2], z2, a0);
         if (flexible) a1 = fma(z2, q[i2], a1);

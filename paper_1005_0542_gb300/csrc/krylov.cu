@@ -4,6 +4,7 @@
 // of iterations where a graph cannot be used); GMRES is enqueued in chunks of steps.  The host looks
 // at a pinned copy of the per-system state after each launch.  Systems that have converged are
 // skipped by every kernel, so iterations past a system's convergence cost only launches.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -143,7 +144,10 @@ void KrylovWork::start_from_b() {
 
 void KrylovWork::start_from_r() {
   iters_this_solve = 0;
-  chunk = 2;
+  // an even count (the PCG graph's body starts from the first direction buffer), one below the
+  // previous solve's
+  predicted_first = predict > 3;
+  chunk = predicted_first ? (predict - 1) & ~1 : 2;
   if (elastic) {
     // r holds the right-hand side: copy it to b, x = 0 (set by the right-hand side kernel)
     LAG_CUDA_CHECK(cudaMemcpyAsync(b(), r(), n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, stream));
@@ -305,7 +309,12 @@ void KrylovWork::enqueue_chunk() {
     iters_this_solve += chunk;
   }
   mirror_state();
-  if (chunk < 16) chunk *= 2;
+  if (predicted_first) {
+    chunk = 2;  // after the predicted count: small chunks up to convergence
+    predicted_first = false;
+  } else if (chunk < 16) {
+    chunk *= 2;
+  }
 }
 
 void KrylovWork::mirror_state() {
@@ -344,11 +353,14 @@ int KrylovWork::poll(bool block) {
                                      std::to_string(herr[0] ? herr[0] : herr[1]) + "); the preconditioner output is invalid");
   }
   bool any_run = false, any_met = false;
+  int most = 0;
   for (int i = 0; i < nrhs; ++i) {
     if (hsc[i].state == ST_RUN) any_run = true;
     if (hsc[i].state == ST_MET) any_met = true;
+    most = std::max(most, hsc[i].iters);
   }
   if (any_run) return 0;
+  predict = most;
   if (!elastic) return 1;
   if (any_met) {
     // every open system met the tolerance estimate inside the cycle: close it (x += Z y) and

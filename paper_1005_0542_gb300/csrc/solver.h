@@ -38,6 +38,11 @@ struct KrylovWork {
   bool pending = false;
   int chunk = 2;
   int iters_this_solve = 0;
+  // iterations the last finished solve took (the most over its systems): the next solve's first
+  // chunk runs just below that many at once, then small chunks, so that eagerly launched solves
+  // issue few iterations past convergence (the next harmonic's count is within one or two)
+  int predict = 0;
+  bool predicted_first = false;
   // FGMRES bookkeeping (host): current cycle step j, restart length k
   int gj = 0, gk = 0;
   bool cycle_open = false;
