@@ -877,13 +877,14 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
   }
 }
 
-// A slices per apply: one CTA of OZ_PACK_THREADS per row, both parities.  Pass 1 folds the row
-// (float64 adds, the only float64 arithmetic) into shared memory and takes the row maximum of
-// |value| as the maximum of the bit patterns with the sign cleared (the same order for
-// non-negative doubles; NaN and Inf patterns compare above every finite one).  Pass 2 cuts each
-// group of 8 consecutive values into slices from the bits and stores them 16 bytes at a time.
+// A slices per apply: one CTA of OZ_PACK_THREADS per row, both parities.  Pass 1 stages the row in
+// shared memory and takes the row maximum of |input|; pass 2 forms each group of 8 consecutive
+// folded values u_j = x_j + x_{n-1-j}, v_j = x_j - x_{n-1-j} as exact sums of the inputs' signed
+// fixed-point expansions (at the row exponent one above the largest input, so that the sums keep
+// below 2^NBITS), cuts them into slices from the bits and stores them 16 bytes at a time: integer
+// operations only (no float64 rounding of the fold, nothing on the narrow FP64 pipe).
 // Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r with |values| < 2^e_r.
-constexpr int OZ_PACK_THREADS = 128;  // 42 registers: 128-thread CTAs keep every row of a shot resident at once
+constexpr int OZ_PACK_THREADS = 128;  // 62 registers: 128-thread CTAs keep every row of a shot resident at once
 constexpr int OZ_PACK_MAXK = 4224;  // ceil(n / 2) bound of the exact-slice path (K pad <= 4224)
 // gather (DCT-II inverse): u = the even entries x[2j], v = the odd ones x[2j+1] instead of the fold.
 template <int NB, int NS>
@@ -893,7 +894,7 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
                                                                     int *__restrict__ erow,
                                                                     const KrylovScalars *__restrict__ sc, int rpr,
                                                                     int gather) {
-  extern __shared__ double fold_sm[];  // [2][nks * TK]: u then v
+  extern __shared__ double xs[];  // the row's n inputs (n <= 2 nks TK)
   const int row = blockIdx.x;
   // rows of finished right-hand sides keep whatever slices they had: the GEMM may still cover them
   // in a tile shared with running rows, but nothing reads those rows' outputs any more (their
@@ -904,25 +905,17 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
   const double *xr = x + (size_t)(row < rows ? row : 0) * n;
   const bool odd_n = (n & 1) != 0;
   const int kp = nks * TK;
-  double *su = fold_sm, *sv = fold_sm + kp;
+  // pass 1: stage the row and take the largest |input| (per parity for the gathered DCT-II input) as
+  // the largest bit pattern with the sign cleared (the same order for non-negative doubles; NaN and
+  // Inf patterns compare above every finite one)
   unsigned long long b0 = 0, b1 = 0;
 #pragma unroll 4
-  for (int j = threadIdx.x; j < kp; j += blockDim.x) {
-    double a = 0.0, b = 0.0;
-    if (gather) {
-      if (live && j < ku) a = __ldg(xr + 2 * j);
-      if (live && j < kv) b = __ldg(xr + 2 * j + 1);
-    } else if (live && j < kv) {
-      const double x1 = __ldg(xr + j), x2 = __ldg(xr + n - 1 - j);
-      a = x1 + x2;
-      b = x1 - x2;
-    } else if (live && odd_n && j == ku - 1) {
-      a = __ldg(xr + j);  // middle element of an odd-length row
-    }
-    su[j] = a;
-    sv[j] = b;
-    b0 = max(b0, (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull);
-    b1 = max(b1, (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffull);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = live ? __ldg(xr + j) : 0.0;
+    xs[j] = v;
+    const unsigned long long m = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    if (gather && (j & 1)) b1 = max(b1, m);
+    else b0 = max(b0, m);
   }
   __shared__ unsigned long long red[2][OZ_PACK_THREADS / 32];
   __shared__ int esh[2];
@@ -939,10 +932,11 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
     int e[2];
     for (int par = 0; par < 2; ++par) {
       unsigned long long m = 0;
-      for (int w = 0; w < OZ_PACK_THREADS / 32; ++w) m = max(m, red[par][w]);
+      for (int w = 0; w < OZ_PACK_THREADS / 32; ++w) m = max(m, red[gather ? par : 0][w]);
       const int E = (int)(m >> 52);
-      // |values| <= m < 2^(E - 1022) for normal m, < 2^-1022 for subnormal m; 0 for a zero row
-      e[par] = (E == 0x7ff) ? OZ_EXP_NAN : (m == 0 ? 0 : (E == 0 ? -1022 : E - 1022));
+      // |inputs| <= m < 2^(E - 1022) for normal m, < 2^-1022 for subnormal m; 0 for a zero row.
+      // The fold's sums and differences of two inputs stay below 2^(that + 1).
+      e[par] = (E == 0x7ff) ? OZ_EXP_NAN : (m == 0 ? 0 : (E == 0 ? -1022 : E - 1022) + (gather ? 0 : 1));
     }
     // a non-finite value anywhere in the row makes every output of the row non-finite, as in a
     // float64 product (the middle element of an odd-length row reaches one parity only, yet its
@@ -955,65 +949,92 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
   }
   __syncthreads();
   const int mt = row / TM, r = row % TM;
-  // one (parity, 8-value chunk) per thread and step
-  for (int w = threadIdx.x; w < 2 * (kp / 8); w += blockDim.x) {
-    const int par = w & 1, ch = w >> 1;
+  const bool bad = esh[0] == OZ_EXP_NAN;
+  const int e0 = bad ? 0 : esh[0], e1 = bad ? 0 : esh[1];
+  // signed NBITS-bit fixed-point value of an input at exponent e (|input| < 2^(e-1) for the fold)
+  auto sfix = [&](double v, int e) -> long long {
+    const long long t = (long long)oz_fixed<oz_bits(NB, NS)>(v, e);
+    return __double_as_longlong(v) < 0 ? -t : t;
+  };
+  // pass 2: one 8-value chunk of both parities per thread and step.  The fold's sums and
+  // differences are exact integer sums of the inputs' expansions (no float64 rounding, no FP64 pipe)
+  for (int ch = threadIdx.x; ch < kp / 8; ch += blockDim.x) {
     const int k0 = ch * 8, ks = k0 / TK, kk = k0 % TK;
-    const double *src = (par ? sv : su) + k0;
-    const bool bad = esh[par] == OZ_EXP_NAN;
-    const int e = bad ? 0 : esh[par];
-    unsigned long long T[8];
-    uint32_t negm = 0;
+    long long S[2][8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const double val = src[q];
-      T[q] = bad ? 0ull : oz_fixed<oz_bits(NB, NS)>(val, e);
-      negm |= (__double_as_longlong(val) < 0 ? 1u : 0u) << q;
-    }
-    const uint32_t off = swz(r, kk);
-    uint8_t *tile0 = out + (size_t)par * NS * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
-    if constexpr (NB == 8) {
-      // balanced digits straight from the bytes of T + 128 (256^0 + ... + 256^5), split into two
-      // 32-bit words: one byte permute builds 2^23 + byte as a float, one subtraction and one
-      // power-of-two multiply give the signed, pre-scaled digit (the same values as oz_slice_f)
-      uint32_t th[8], tl[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const unsigned long long Tb = T[q] + 0x0000808080808080ull;
-        tl[q] = (uint32_t)Tb;
-        th[q] = (uint32_t)(Tb >> 32);
-      }
-#pragma unroll
-      for (int i = 1; i <= NS; ++i) {
-        const uint32_t cbits = (uint32_t)(127 - 8 * (i - 1)) << 23;  // 2^-(8 (i - 1))
-        const float offv = (i == 1) ? 8388608.0f : 8388736.0f;
-        uint32_t hw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float d[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int v = 2 * q + h;
-            uint32_t fb;
-            if (i == 1) fb = 0x4B000000u | ((th[v] >> 16) & 0x1ffu);
-            else if (i <= 3) fb = __byte_perm(th[v], 0x4B00u, 0x5440u | (uint32_t)(3 - i));
-            else fb = __byte_perm(tl[v], 0x4B00u, 0x5440u | (uint32_t)(7 - i));
-            const float cq = __uint_as_float(cbits | (((negm >> v) & 1u) << 31));
-            d[h] = (__uint_as_float(fb) - offv) * cq;
-          }
-          hw[q] = oz_pack2(d[0], d[1]);
+      const int j = k0 + q;
+      long long u = 0, w = 0;
+      if (!bad) {
+        if (gather) {
+          if (j < ku) u = sfix(xs[2 * j], e0);
+          if (j < kv) w = sfix(xs[2 * j + 1], e1);
+        } else if (j < kv) {
+          const long long a1 = sfix(xs[j], e0), a2 = sfix(xs[n - 1 - j], e0);
+          u = a1 + a2;
+          w = a1 - a2;
+        } else if (odd_n && j == ku - 1) {
+          u = sfix(xs[j], e0);  // middle element of an odd-length row
         }
-        *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
       }
-    } else {
+      S[0][q] = u;
+      S[1][q] = w;
+    }
 #pragma unroll
-      for (int i = 1; i <= NS; ++i) {
-        uint32_t hw[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          hw[q] = oz_pack2(oz_slice_f<NB, NS>(T[2 * q], i, (negm >> (2 * q)) & 1u),
-                           oz_slice_f<NB, NS>(T[2 * q + 1], i, (negm >> (2 * q + 1)) & 1u));
-        *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    for (int par = 0; par < 2; ++par) {
+      unsigned long long T[8];
+      uint32_t negm = 0;
+  #pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const long long v = S[par][q];
+        T[q] = (unsigned long long)(v < 0 ? -v : v);
+        negm |= (v < 0 ? 1u : 0u) << q;
+      }
+      const uint32_t off = swz(r, kk);
+      uint8_t *tile0 = out + (size_t)par * NS * slice_bytes + ((size_t)mt * nks + ks) * A_TILE + off;
+      if constexpr (NB == 8) {
+        // balanced digits straight from the bytes of T + 128 (256^0 + ... + 256^5), split into two
+        // 32-bit words: one byte permute builds 2^23 + byte as a float, one subtraction and one
+        // power-of-two multiply give the signed, pre-scaled digit (the same values as oz_slice_f)
+        uint32_t th[8], tl[8];
+  #pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const unsigned long long Tb = T[q] + 0x0000808080808080ull;
+          tl[q] = (uint32_t)Tb;
+          th[q] = (uint32_t)(Tb >> 32);
+        }
+  #pragma unroll
+        for (int i = 1; i <= NS; ++i) {
+          const uint32_t cbits = (uint32_t)(127 - 8 * (i - 1)) << 23;  // 2^-(8 (i - 1))
+          const float offv = (i == 1) ? 8388608.0f : 8388736.0f;
+          uint32_t hw[4];
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float d[2];
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int v = 2 * q + h;
+              uint32_t fb;
+              if (i == 1) fb = 0x4B000000u | ((th[v] >> 16) & 0x1ffu);
+              else if (i <= 3) fb = __byte_perm(th[v], 0x4B00u, 0x5440u | (uint32_t)(3 - i));
+              else fb = __byte_perm(tl[v], 0x4B00u, 0x5440u | (uint32_t)(7 - i));
+              const float cq = __uint_as_float(cbits | (((negm >> v) & 1u) << 31));
+              d[h] = (__uint_as_float(fb) - offv) * cq;
+            }
+            hw[q] = oz_pack2(d[0], d[1]);
+          }
+          *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        }
+      } else {
+  #pragma unroll
+        for (int i = 1; i <= NS; ++i) {
+          uint32_t hw[4];
+  #pragma unroll
+          for (int q = 0; q < 4; ++q)
+            hw[q] = oz_pack2(oz_slice_f<NB, NS>(T[2 * q], i, (negm >> (2 * q)) & 1u),
+                             oz_slice_f<NB, NS>(T[2 * q + 1], i, (negm >> (2 * q + 1)) & 1u));
+          *reinterpret_cast<uint4 *>(tile0 + (size_t)(i - 1) * slice_bytes) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        }
       }
     }
   }
