@@ -886,6 +886,11 @@ __global__ void oz_pack_b_kernel(const double *m0, int k0n, int n0n, int ld0, co
 // Layout [parity][slice][m tile][k stage][TM x TK]; erow[parity][row] = e_r with |values| < 2^e_r.
 constexpr int OZ_PACK_THREADS = 128;  // 62 registers: 128-thread CTAs keep every row of a shot resident at once
 constexpr int OZ_PACK_MAXK = 4224;  // ceil(n / 2) bound of the exact-slice path (K pad <= 4224)
+// the staged row's index j at j + j / 8: a thread's 8 consecutive values (or the mirrored ones)
+// then sit 9 doubles from its neighbour's, so a half-warp's 8-byte reads hit every bank once
+// (unpadded, lanes 64 bytes apart fell on two banks: 16-way conflicts)
+#define OZ_PAD(j) ((j) + ((j) >> 3))
+static size_t oz_pack_smem(int nks) { return (size_t)(2 * nks * TK + (2 * nks * TK) / 8 + 8) * sizeof(double); }
 // gather (DCT-II inverse): u = the even entries x[2j], v = the odd ones x[2j+1] instead of the fold.
 template <int NB, int NS>
 __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double *__restrict__ x, int rows, int n,
@@ -894,7 +899,7 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
                                                                     int *__restrict__ erow,
                                                                     const KrylovScalars *__restrict__ sc, int rpr,
                                                                     int gather) {
-  extern __shared__ double xs[];  // the row's n inputs (n <= 2 nks TK)
+  extern __shared__ double xs[];  // the row's n inputs (n <= 2 nks TK) at OZ_PAD(j)
   const int row = blockIdx.x;
   // rows of finished right-hand sides keep whatever slices they had: the GEMM may still cover them
   // in a tile shared with running rows, but nothing reads those rows' outputs any more (their
@@ -912,7 +917,7 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
 #pragma unroll 4
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const double v = live ? __ldg(xr + j) : 0.0;
-    xs[j] = v;
+    xs[OZ_PAD(j)] = v;
     const unsigned long long m = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
     if (gather && (j & 1)) b1 = max(b1, m);
     else b0 = max(b0, m);
@@ -967,14 +972,14 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
       long long u = 0, w = 0;
       if (!bad) {
         if (gather) {
-          if (j < ku) u = sfix(xs[2 * j], e0);
-          if (j < kv) w = sfix(xs[2 * j + 1], e1);
+          if (j < ku) u = sfix(xs[OZ_PAD(2 * j)], e0);
+          if (j < kv) w = sfix(xs[OZ_PAD(2 * j + 1)], e1);
         } else if (j < kv) {
-          const long long a1 = sfix(xs[j], e0), a2 = sfix(xs[n - 1 - j], e0);
+          const long long a1 = sfix(xs[OZ_PAD(j)], e0), a2 = sfix(xs[OZ_PAD(n - 1 - j)], e0);
           u = a1 + a2;
           w = a1 - a2;
         } else if (odd_n && j == ku - 1) {
-          u = sfix(xs[j], e0);  // middle element of an odd-length row
+          u = sfix(xs[OZ_PAD(j)], e0);  // middle element of an odd-length row
         }
       }
       S[0][q] = u;
@@ -2615,13 +2620,13 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm2_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ2_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_sk_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        2 * OZ_PACK_MAXK * (int)sizeof(double)));
+                                        (int)oz_pack_smem(OZ_PACK_MAXK / TK + 1)));
   });
   const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = oz_mtiles(rows);
   const size_t a_slice = (size_t)nmt * nks * A_TILE;
   uint8_t *apack = dp.tc_scratch + oz_sk_bytes();
   int *erow = reinterpret_cast<int *>(apack + 2 * (size_t)NS * a_slice);
-  const size_t pack_smem = 2 * (size_t)nks * TK * sizeof(double);
+  const size_t pack_smem = oz_pack_smem(nks);
   oz_pack_a_kernel<NB, NS><<<nmt * TM, OZ_PACK_THREADS, pack_smem, s>>>(x, rows, dp.n, dp.ku, dp.kv, nks, nmt, apack,
                                                                          a_slice, erow, sc, rpr, inv);
   count_launch();
