@@ -250,6 +250,38 @@ def test_cluster_multicast_pcg_identical(ctx, monkeypatch):
         assert np.linalg.norm(a[m] - b[m]) <= 1e-9 * np.linalg.norm(a[m])
 
 
+def test_eager_solves_size_their_chunks_from_the_previous_solve(ctx, monkeypatch):
+    # eagerly launched PCG solves (graphs off) run a first chunk just below the previous harmonic's
+    # iteration count, then chunks of two: the iterations launched stay within a few of those run
+    # (before: chunks of 2, 4, 8, 16, 16 ..., up to 15 past convergence per harmonic)
+    s = inputs.random_layered(nx=256, nz=128, hx=10.0, n_harm=8, sources=[(128, 3)], f0=12.0)
+    monkeypatch.setenv("LAGWAVE_GRAPHS", "0")
+    g = L.grid(s.nx, s.nz, s.hx, s.hz)
+    lag = L.laguerre(s.h, s.alpha, s.n_harm)
+    sv = L.solver(tol=1e-10, prec=L.LAG_FP64)
+    w = L.wavelet(s.f0, s.t0)
+    c_, pc = L.f64(s.c)
+    r_, pr = L.f64(s.rho)
+    t_, pt = L.f64(s.t_out)
+    sh = C.c_void_p()
+    L.check(L.lag_shot_create(ctx, C.byref(g), pc, None, pr, C.byref(lag), C.byref(sv), C.byref(w), 1,
+                              L.points(s.sources), len(s.receivers), L.points(s.receivers), s.t_out.size, pt,
+                              C.byref(sh)), ctx)
+    L.check(L.lag_shot_step(sh, 2), ctx)  # harmonics 0, 1: the first sets the prediction
+    l0 = L.lag_kernel_launches(ctx)
+    L.check(L.lag_shot_step(sh, s.n_harm - 2), ctx)
+    launched = L.lag_kernel_launches(ctx) - l0
+    its = np.zeros(s.n_harm, dtype=np.int32)
+    st = L.lag_stats(its.ctypes.data_as(L.PI), None, 0, 0.0)
+    L.check(L.lag_shot_stats(sh, C.byref(st)), ctx)
+    L.lag_shot_destroy(sh)
+    monkeypatch.delenv("LAGWAVE_GRAPHS")
+    iters = int(its[2:].sum())
+    assert iters > 0
+    # at most 8 kernels per PCG iteration, 3 iterations past convergence and 8 other kernels per harmonic
+    assert launched <= 8 * (iters + 3 * (s.n_harm - 2)) + 8 * (s.n_harm - 2), (launched, iters)
+
+
 def test_elastic_full_size_first_harmonic_true_residual(ctx):
     # the 4096 x 2048 elastic workload (2 of its surface sources, mixed path, FGMRES(20)): the first
     # harmonic meets the tolerance in the true residual b - C R_0, formed with the operator kernel
