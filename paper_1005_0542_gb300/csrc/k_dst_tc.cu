@@ -1159,15 +1159,28 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      int it = 0, gc = 0;
+      // stage ring position and phase kept incrementally; shared-memory descriptors as one OR of
+      // the constant upper bits with the stage's 16-byte address (the issuer is a single thread:
+      // its per-stage arithmetic is time the tensor pipe may sit idle)
+      constexpr uint64_t DHI = ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61) | (1ull << 16);
+      constexpr uint32_t AB = (OZ_KT * A_TILE) >> 4, BT = OZ_BT >> 4, AT = A_TILE >> 4;
+      int s = 0, it = 0, gc = 0;
+      uint32_t ph = 0;
+      auto next_stage = [&]() {
+        ++it;
+        if (++s == OZ_NST) {
+          s = 0;
+          ph ^= 1u;
+        }
+      };
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         int par, mt, nt;
         decode(t, par, mt, nt);
         if (!wanted(par, mt, nt)) continue;
         uint32_t d = 0;
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
-          const bool split = sch.split[pr] != 0;
-          if (sch.first[pr]) {
+          const bool split = sch.split[pr] != 0, first = sch.first[pr] != 0;
+          if (first) {
             bool ok = true;
             for (int q = 0; q < (split ? 2 : 1); ++q) {  // a split unit fills two accumulators
               const int acc = (gc + q) % OZ_NACC, ause = (gc + q) / OZ_NACC;
@@ -1184,31 +1197,29 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
           const int kb = sch.k0[pr], ke = sch.k1[pr];
           if (sch.sj2[pr] > 0) {
             // A_i with two B slices, one K tile per stage: both products into the group's
-            // accumulator, or (split) the second into the next group's
+            // accumulator, or (split) the second into the next group's; a fresh accumulator takes
+            // its first product without accumulating (the group's first K tile, for the first
+            // product and for the second of a split unit)
             const uint32_t d2 = split ? tmem + (uint32_t)(((gc + 1) % OZ_NACC) * OZ_TN) : d;
-            for (int kk = kb; kk < ke; ++kk, ++it) {
-              const int s = it % OZ_NST, use = it / OZ_NST;
-              if (!mbar_wait(full0 + 8 * s, use & 1)) {
+            for (int kk = kb; kk < ke; ++kk) {
+              if (!mbar_wait(full0 + 8 * s, ph)) {
                 atomicExch(err, 12);
                 *abort_flag = 1;
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t st = base + s * OZ_STAGE;
-              for (int q = 0; q < 2; ++q) {
-                const uint32_t dq = (q == 0) ? d : d2, sb = st + OZ_KT * A_TILE + q * OZ_BT;
-                // a fresh accumulator takes its first product without accumulating: the group's
-                // first K tile for the first product, and for the second of a split unit
-                const bool fresh = sch.first[pr] && kk == kb && (q == 0 || split);
+              const uint32_t sa = (base + s * OZ_STAGE) >> 4;
+              const uint32_t f1 = (first && kk == kb) ? 0u : 1u, f2 = split ? f1 : 1u;
 #pragma unroll
-                for (int sub = 0; sub < TK / 16; ++sub) {
-                  const uint32_t o = sub * 32;
-                  mma_bf16_n128(dq, sdesc(st + o), sdesc(sb + o), (fresh && sub == 0) ? 0u : 1u);
-                }
-              }
+              for (int sub = 0; sub < TK / 16; ++sub)
+                mma_bf16_n128(d, DHI | (sa + 2 * sub), DHI | (sa + AB + 2 * sub), sub == 0 ? f1 : 1u);
+#pragma unroll
+              for (int sub = 0; sub < TK / 16; ++sub)
+                mma_bf16_n128(d2, DHI | (sa + 2 * sub), DHI | (sa + AB + BT + 2 * sub), sub == 0 ? f2 : 1u);
               asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                empty0 + 8 * s)
                            : "memory");
+              next_stage();
             }
             if (sch.last[pr]) {
               for (int q = 0; q < (split ? 2 : 1); ++q) {
@@ -1220,26 +1231,26 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
             }
             continue;
           }
-          for (int kk = kb; kk < ke; kk += OZ_KT, ++it) {
-            const int kt = min(OZ_KT, ke - kk);
-            const int s = it % OZ_NST, use = it / OZ_NST;
-            if (!mbar_wait(full0 + 8 * s, use & 1)) {
+          for (int kk = kb; kk < ke; kk += OZ_KT) {
+            if (!mbar_wait(full0 + 8 * s, ph)) {
               atomicExch(err, 12);
               *abort_flag = 1;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = base + s * OZ_STAGE;
-            for (int t = 0; t < kt; ++t) {
+            const uint32_t sa = (base + s * OZ_STAGE) >> 4;
+            const uint32_t f1 = (first && kk == kb) ? 0u : 1u;
 #pragma unroll
-              for (int sub = 0; sub < TK / 16; ++sub) {
-                const uint32_t o = sub * 32;
-                mma_bf16_n128(d, sdesc(st + t * A_TILE + o), sdesc(st + OZ_KT * A_TILE + t * OZ_BT + o),
-                              (sch.first[pr] && kk == kb && t == 0 && sub == 0) ? 0u : 1u);
-              }
+            for (int sub = 0; sub < TK / 16; ++sub)
+              mma_bf16_n128(d, DHI | (sa + 2 * sub), DHI | (sa + AB + 2 * sub), sub == 0 ? f1 : 1u);
+            if (ke - kk > 1) {  // the stage's second K tile
+#pragma unroll
+              for (int sub = 0; sub < TK / 16; ++sub)
+                mma_bf16_n128(d, DHI | (sa + AT + 2 * sub), DHI | (sa + AB + BT + 2 * sub), 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
                          : "memory");
+            next_stage();
           }
           if (sch.last[pr]) {
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
