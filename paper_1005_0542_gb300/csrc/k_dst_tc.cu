@@ -712,6 +712,10 @@ constexpr int OZ_STAGE = OZ_KT * (A_TILE + OZ_BT);  // 64 KB: [A k tiles][B k ti
 constexpr int OZ_NST = 3;                  // pipeline stages
 constexpr int OZ_NACC = 4;                 // tensor-memory accumulators of 128 columns
 constexpr int OZ_SMEM = OZ_NST * OZ_STAGE + 1024 + 256;
+// the tile kernel's stages: one K tile of A and of up to two B slices (48 KB), four of them
+constexpr int OZT_STAGE = A_TILE + 2 * OZ_BT;
+constexpr int OZT_NST = 4;
+constexpr int OZT_SMEM = OZT_NST * OZT_STAGE + 1024 + 256;
 constexpr int OZ_EXP_NAN = 0x7fffffff;     // row exponent marking a non-finite row
 // pairs of weight i + j >= tail share one accumulator with FP32 rounding: together they weigh
 // < 2^-(NB (tail - 2)) of the leading products (2^-36 at tail = 8 with 6-bit slices, 2^-42 with
@@ -1062,11 +1066,11 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t *gbase = smem_raw + (base - raw);
-  const uint32_t bars = base + OZ_NST * OZ_STAGE;
-  const uint32_t full0 = bars, empty0 = bars + 8 * OZ_NST, tfull0 = bars + 16 * OZ_NST, tempty0 = tfull0 + 8 * OZ_NACC;
+  const uint32_t bars = base + OZT_NST * OZT_STAGE;
+  const uint32_t full0 = bars, empty0 = bars + 8 * OZT_NST, tfull0 = bars + 16 * OZT_NST, tempty0 = tfull0 + 8 * OZ_NACC;
   volatile uint32_t *holder =
-      reinterpret_cast<volatile uint32_t *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 8);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + OZ_NST * OZ_STAGE + 16 * OZ_NST + 16 * OZ_NACC + 16);
+      reinterpret_cast<volatile uint32_t *>(gbase + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16 * OZ_NACC + 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16 * OZ_NACC + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = 2 * nmt * nnt;
 
@@ -1077,7 +1081,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int s = 0; s < OZ_NST; ++s) {
+    for (int s = 0; s < OZT_NST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
@@ -1110,8 +1114,9 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   };
 
   if (warp == 0) {
-    if (lane == 0) {  // producer
-      int it = 0;
+    if (lane == 0) {  // producer: per stage one K tile of A_i and of its one or two B_j
+      int s = 0, it = 0;
+      uint32_t ph = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         int par, mt, nt;
         decode(t, par, mt, nt);
@@ -1119,40 +1124,26 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
           const uint8_t *at = apack + ((size_t)par * NS + (sch.si[pr] - 1)) * a_slice_bytes + (size_t)mt * nks * A_TILE;
           const uint8_t *bt = bpack + ((size_t)par * NS + (sch.sj[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
-          const int ke = sch.k1[pr];
-          if (sch.sj2[pr] > 0) {
-            // A_i with two B slices: one K tile per stage, A in slot 0, the B tiles in slots 2 and 3
-            // (A slot 1 stays unused: the stream into the SM, not shared memory, is the constraint)
-            const uint8_t *bt2 = bpack + ((size_t)par * NS + (sch.sj2[pr] - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
-            for (int kk = sch.k0[pr]; kk < ke; ++kk, ++it) {
-              const int s = it % OZ_NST, use = it / OZ_NST;
-              if (it >= OZ_NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
-                atomicExch(err, 11);
-                *abort_flag = 1;
-                break;
-              }
-              const uint32_t st = base + s * OZ_STAGE;
-              const uint32_t fb = full0 + 8 * s;
-              mbar_expect_tx(fb, (uint32_t)(A_TILE + 2 * OZ_BT));
-              bulk_g2s(st, at + (size_t)kk * A_TILE, A_TILE, fb);
-              bulk_g2s(st + OZ_KT * A_TILE, bt + (size_t)kk * OZ_BT, OZ_BT, fb);
-              bulk_g2s(st + OZ_KT * A_TILE + OZ_BT, bt2 + (size_t)kk * OZ_BT, OZ_BT, fb);
-            }
-            continue;
-          }
-          for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
-            const int kt = min(OZ_KT, ke - kk);  // K tiles in this stage
-            const int s = it % OZ_NST, use = it / OZ_NST;
-            if (it >= OZ_NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
+          const bool two = sch.sj2[pr] > 0;
+          const uint8_t *bt2 =
+              bpack + ((size_t)par * NS + (max((int)sch.sj2[pr], 1) - 1)) * b_slice_bytes + (size_t)nt * nks * OZ_BT;
+          for (int kk = sch.k0[pr]; kk < sch.k1[pr]; ++kk) {
+            if (it >= OZT_NST && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
               atomicExch(err, 11);
               *abort_flag = 1;
               break;
             }
-            const uint32_t st = base + s * OZ_STAGE;
+            const uint32_t st = base + s * OZT_STAGE;
             const uint32_t fb = full0 + 8 * s;
-            mbar_expect_tx(fb, (uint32_t)(kt * (A_TILE + OZ_BT)));
-            bulk_g2s(st, at + (size_t)kk * A_TILE, (uint32_t)(kt * A_TILE), fb);
-            bulk_g2s(st + OZ_KT * A_TILE, bt + (size_t)kk * OZ_BT, (uint32_t)(kt * OZ_BT), fb);
+            mbar_expect_tx(fb, (uint32_t)(A_TILE + (two ? 2 : 1) * OZ_BT));
+            bulk_g2s(st, at + (size_t)kk * A_TILE, A_TILE, fb);
+            bulk_g2s(st + A_TILE, bt + (size_t)kk * OZ_BT, OZ_BT, fb);
+            if (two) bulk_g2s(st + A_TILE + OZ_BT, bt2 + (size_t)kk * OZ_BT, OZ_BT, fb);
+            ++it;
+            if (++s == OZT_NST) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
         }
       }
@@ -1163,23 +1154,16 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
       // the constant upper bits with the stage's 16-byte address (the issuer is a single thread:
       // its per-stage arithmetic is time the tensor pipe may sit idle)
       constexpr uint64_t DHI = ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61) | (1ull << 16);
-      constexpr uint32_t AB = (OZ_KT * A_TILE) >> 4, BT = OZ_BT >> 4, AT = A_TILE >> 4;
-      int s = 0, it = 0, gc = 0;
+      constexpr uint32_t B1 = A_TILE >> 4, B2 = (A_TILE + OZ_BT) >> 4;
+      int s = 0, gc = 0;
       uint32_t ph = 0;
-      auto next_stage = [&]() {
-        ++it;
-        if (++s == OZ_NST) {
-          s = 0;
-          ph ^= 1u;
-        }
-      };
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         int par, mt, nt;
         decode(t, par, mt, nt);
         if (!wanted(par, mt, nt)) continue;
         uint32_t d = 0;
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
-          const bool split = sch.split[pr] != 0, first = sch.first[pr] != 0;
+          const bool split = sch.split[pr] != 0, first = sch.first[pr] != 0, two = sch.sj2[pr] > 0;
           if (first) {
             bool ok = true;
             for (int q = 0; q < (split ? 2 : 1); ++q) {  // a split unit fills two accumulators
@@ -1194,69 +1178,43 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             d = tmem + (uint32_t)((gc % OZ_NACC) * OZ_TN);
           }
+          // the second B slice's products go to the same accumulator, or (split) the next group's;
+          // a fresh accumulator takes its first product without accumulating (the group's first K
+          // tile, for the first product and for the second of a split unit)
+          const uint32_t d2 = split ? tmem + (uint32_t)(((gc + 1) % OZ_NACC) * OZ_TN) : d;
           const int kb = sch.k0[pr], ke = sch.k1[pr];
-          if (sch.sj2[pr] > 0) {
-            // A_i with two B slices, one K tile per stage: both products into the group's
-            // accumulator, or (split) the second into the next group's; a fresh accumulator takes
-            // its first product without accumulating (the group's first K tile, for the first
-            // product and for the second of a split unit)
-            const uint32_t d2 = split ? tmem + (uint32_t)(((gc + 1) % OZ_NACC) * OZ_TN) : d;
-            for (int kk = kb; kk < ke; ++kk) {
-              if (!mbar_wait(full0 + 8 * s, ph)) {
-                atomicExch(err, 12);
-                *abort_flag = 1;
-                break;
-              }
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t sa = (base + s * OZ_STAGE) >> 4;
-              const uint32_t f1 = (first && kk == kb) ? 0u : 1u, f2 = split ? f1 : 1u;
-#pragma unroll
-              for (int sub = 0; sub < TK / 16; ++sub)
-                mma_bf16_n128(d, DHI | (sa + 2 * sub), DHI | (sa + AB + 2 * sub), sub == 0 ? f1 : 1u);
-#pragma unroll
-              for (int sub = 0; sub < TK / 16; ++sub)
-                mma_bf16_n128(d2, DHI | (sa + 2 * sub), DHI | (sa + AB + BT + 2 * sub), sub == 0 ? f2 : 1u);
-              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                               empty0 + 8 * s)
-                           : "memory");
-              next_stage();
-            }
-            if (sch.last[pr]) {
-              for (int q = 0; q < (split ? 2 : 1); ++q) {
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 tfull0 + 8 * ((gc + q) % OZ_NACC))
-                             : "memory");
-              }
-              gc += split ? 2 : 1;
-            }
-            continue;
-          }
-          for (int kk = kb; kk < ke; kk += OZ_KT) {
+          for (int kk = kb; kk < ke; ++kk) {
             if (!mbar_wait(full0 + 8 * s, ph)) {
               atomicExch(err, 12);
               *abort_flag = 1;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = (base + s * OZ_STAGE) >> 4;
+            const uint32_t sa = (base + s * OZT_STAGE) >> 4;
             const uint32_t f1 = (first && kk == kb) ? 0u : 1u;
 #pragma unroll
             for (int sub = 0; sub < TK / 16; ++sub)
-              mma_bf16_n128(d, DHI | (sa + 2 * sub), DHI | (sa + AB + 2 * sub), sub == 0 ? f1 : 1u);
-            if (ke - kk > 1) {  // the stage's second K tile
+              mma_bf16_n128(d, DHI | (sa + 2 * sub), DHI | (sa + B1 + 2 * sub), sub == 0 ? f1 : 1u);
+            if (two) {
+              const uint32_t f2 = split ? f1 : 1u;
 #pragma unroll
               for (int sub = 0; sub < TK / 16; ++sub)
-                mma_bf16_n128(d, DHI | (sa + AT + 2 * sub), DHI | (sa + AB + BT + 2 * sub), 1u);
+                mma_bf16_n128(d2, DHI | (sa + 2 * sub), DHI | (sa + B2 + 2 * sub), sub == 0 ? f2 : 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
                          : "memory");
-            next_stage();
+            if (++s == OZT_NST) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
           if (sch.last[pr]) {
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             tfull0 + 8 * (gc % OZ_NACC))
-                         : "memory");
-            ++gc;
+            for (int q = 0; q < (split ? 2 : 1); ++q) {
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                               tfull0 + 8 * ((gc + q) % OZ_NACC))
+                           : "memory");
+            }
+            gc += split ? 2 : 1;
           }
         }
       }
@@ -2627,7 +2585,7 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
                          cudaStream_t s, int inv, const double *rdot = nullptr, double *rzpart = nullptr) {
   static PerDeviceOnce attr;
   attr.run([] {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZT_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm2_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ2_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_sk_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_pack_a_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2678,7 +2636,7 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
                                                         nks, nmt, nnt, rows, y, dp.n, dp.ku, dp.kv, sch, sc,
                                                         dp.tc_err, rdot, rzpart, ska);
   } else {
-    oz_gemm_kernel<NB, NS><<<grid, 320, OZ_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
+    oz_gemm_kernel<NB, NS><<<grid, 320, OZT_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
                                                       erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,
                                                       dp.kv, sch, sc, rpr, dp.tc_err, inv, rdot, rzpart);
   }
