@@ -73,7 +73,6 @@ struct TriFactors {
   int mt = 1;           // modes per CTA
   int threads = 32;     // threads per CTA (mt * P rounded up to whole warps)
   bool reg = false;     // register-resident kernel (L a power of two <= 64)
-  bool vec2 = true;     // float register kernel: two modes per thread (LAGWAVE_TRI_VEC=1: one)
   size_t smem = 0;      // dynamic shared memory of the solve kernel
   // device arrays, element type double or float: [cls][i][j] with j fastest
   void *fm = nullptr, *fc = nullptr, *fa = nullptr, *sv = nullptr, *sw = nullptr;

@@ -372,7 +372,12 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      int it = 0, tc = 0;
+      // stage position and phase kept incrementally, descriptors as one OR of the constant upper
+      // bits with the 16-byte address (a single thread's per-stage work idles the tensor pipe)
+      constexpr uint64_t DHI = ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61) | (1ull << 16);
+      constexpr uint32_t ALO = A_TILE >> 4, BHI = Cfg::A_BYTES >> 4, BLO = (Cfg::A_BYTES + B_TILE) >> 4;
+      int s = 0, tc = 0;
+      uint32_t ph = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         int par, mt, nt;
         decode(t, par, mt, nt);
@@ -385,25 +390,27 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * TMEM_COLS);
-        for (int kk = 0; kk < nks; ++kk, ++it) {
-          const int s = it % NST, use = it / NST;
-          if (!mbar_wait(full0 + 8 * s, use & 1)) {
+        for (int kk = 0; kk < nks; ++kk) {
+          if (!mbar_wait(full0 + 8 * s, ph)) {
             atomicExch(err, 2);
             *abort_flag = 1;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t st = base + s * Cfg::STAGE_BYTES;
-          const uint32_t ahi = st, alo = st + A_TILE, bhi = st + Cfg::A_BYTES, blo = bhi + B_TILE;
+          const uint32_t sa = (base + s * Cfg::STAGE_BYTES) >> 4;
+          const uint32_t f = kk == 0 ? 0u : 1u;
 #pragma unroll
-          for (int sub = 0; sub < TK / 16; ++sub) {
-            const uint32_t o = sub * 32;  // 16 bf16 along K
-            mma_bf16(d, sdesc(ahi + o), sdesc(bhi + o), (kk == 0 && sub == 0) ? 0u : 1u);
-            if (NPROD >= 3) mma_bf16(d, sdesc(ahi + o), sdesc(blo + o), 1u);
-            if (NPROD >= 2) mma_bf16(d, sdesc(alo + o), sdesc(bhi + o), 1u);
+          for (int sub = 0; sub < TK / 16; ++sub) {  // 16 bf16 along K: 32 bytes, 2 units of 16
+            mma_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + BHI + 2 * sub), sub == 0 ? f : 1u);
+            if (NPROD >= 3) mma_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + BLO + 2 * sub), 1u);
+            if (NPROD >= 2) mma_bf16(d, DHI | (sa + ALO + 2 * sub), DHI | (sa + BHI + 2 * sub), 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
                        : "memory");
+          if (++s == NST) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tfull0 + 8 * acc)
                      : "memory");

@@ -20,7 +20,6 @@
 // The column tile of MT modes x all rows lives in shared memory: the right-hand side is read
 // once and the solution written once (coalesced rows of MT consecutive modes).
 #include <algorithm>
-#include <cstdlib>
 
 #include "internal.h"
 
@@ -51,8 +50,6 @@ void tri_choose_layout(TriFactors &tf, int elem_bytes, int want_P, int want_mt, 
   tf.P = P;
   tf.L = L;
   tf.gen = general;
-  const char *vv = std::getenv("LAGWAVE_TRI_VEC");
-  tf.vec2 = !(vv != nullptr && vv[0] == '1');
   tf.ncls = general ? P : 3;
   const int n = P - 1;
   int lev = 0;
@@ -427,58 +424,23 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const T *__restrict__ d
 // occupancy target of the register kernel: 64 (float32) / 128 (float64) registers a thread at
 // L <= 32, twice that at L = 64; general systems (factor addresses per row) twice that again at
 // L >= 32
-template <typename T, int L, int MT, bool GEN, int V>
+template <typename T, int L, int MT, bool GEN>
 struct RegBounds {
-  static constexpr int threads = MT * 32 / V;
-  static constexpr int per_sm = (sizeof(T) == 8 ? 512 : 1024) / (L >= 64 ? 2 : 1) / ((GEN && L >= 32) ? 2 : 1) / V;
+  static constexpr int threads = MT * 32;
+  static constexpr int per_sm = (sizeof(T) == 8 ? 512 : 1024) / (L >= 64 ? 2 : 1) / ((GEN && L >= 32) ? 2 : 1);
   static constexpr int blocks = per_sm / threads > 0 ? per_sm / threads : 1;
 };
 
-// V consecutive modes per element access: V = 2 reads and writes two neighbouring modes with one
-// 8-byte (float) / 16-byte (double) access, halving the load / store instructions per element
-// (the float kernel is bound by its LSU instructions: one global load, one store and five factor
-// loads per element)
-template <typename T, int V>
-struct VecOf;
-template <typename T>
-struct VecOf<T, 1> {
-  static __device__ __forceinline__ void ld(const T *p, T (&o)[1]) { o[0] = *p; }
-  static __device__ __forceinline__ void st(T *p, const T (&o)[1]) { *p = o[0]; }
-};
-template <>
-struct VecOf<float, 2> {
-  static __device__ __forceinline__ void ld(const float *p, float (&o)[2]) {
-    const float2 t = *reinterpret_cast<const float2 *>(p);
-    o[0] = t.x;
-    o[1] = t.y;
-  }
-  static __device__ __forceinline__ void st(float *p, const float (&o)[2]) {
-    *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
-  }
-};
-template <>
-struct VecOf<double, 2> {
-  static __device__ __forceinline__ void ld(const double *p, double (&o)[2]) {
-    const double2 t = *reinterpret_cast<const double2 *>(p);
-    o[0] = t.x;
-    o[1] = t.y;
-  }
-  static __device__ __forceinline__ void st(double *p, const double (&o)[2]) {
-    *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
-  }
-};
-
-template <typename T, int L, int MT, bool GEN, int V>
-__global__ void __launch_bounds__(RegBounds<T, L, MT, GEN, V>::threads, RegBounds<T, L, MT, GEN, V>::blocks)
-    tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz, int nx, int P, int levels, int nf,
-                         const T *__restrict__ fm, const T *__restrict__ fc, const T *__restrict__ fa,
-                         const T *__restrict__ sv, const T *__restrict__ sw, const T *__restrict__ red,
-                         const KrylovScalars *__restrict__ sc, int pstride, int poff, int ncomp, int nplanes,
-                         int per_cta) {
-  using Vec = VecOf<T, V>;
+template <typename T, int L, int MT, bool GEN>
+__global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T, L, MT, GEN>::blocks) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
+                                                               int nx, int P, int levels, int nf,
+                                                               const T *__restrict__ fm, const T *__restrict__ fc,
+                                                               const T *__restrict__ fa, const T *__restrict__ sv,
+                                                               const T *__restrict__ sw, const T *__restrict__ red,
+                                                               const KrylovScalars *__restrict__ sc, int pstride,
+                                                               int poff, int ncomp, int nplanes, int per_cta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NCR = GEN ? 0 : 3 * L;       // staged factor rows: 3 classes x L
-  constexpr int MQ = MT / V;                 // threads per partition
   T *F = reinterpret_cast<T *>(smem_raw);    // [5][NCR][MT]: fm, fa, fc, sv, sw
   T *gF = F + 5 * NCR * MT;                  // [MT][32]
   T *gL = gF + MT * 32;
@@ -505,8 +467,7 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN, V>::threads, RegBound
       F[(4 * NCR + row) * MT + cm] = ok ? sw[g] : T(0);
     }
   }
-  // thread: modes c .. c + V - 1 (V divides nx when V > 1, so they are valid together) of partition p
-  const int c = (tid % MQ) * V, p = tid / MQ, j = j0 + c;
+  const int c = tid % MT, p = tid / MT, j = j0 + c;
   const bool col_ok = j < nx && p < P;
   const int i0 = (p == 0) ? 0 : 1;
   // factor rows of this thread's partition: stride FS between rows
@@ -529,54 +490,31 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN, V>::threads, RegBound
     const bool live = col_ok;
     const T *src = din + (size_t)b * nz * nx + j;
     T *dst = yout + (size_t)b * nz * nx + j;
-    T v[V][L];
+    T v[L];
 #pragma unroll
     for (int i = 0; i < L; ++i) {
       const int r = p * L + i;
-      T t[V];
-      if (live && r < nz) {
-        Vec::ld(src + (size_t)r * nx, t);
-      } else {
-#pragma unroll
-        for (int u = 0; u < V; ++u) t[u] = T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < V; ++u) v[u][i] = t[u];
+      v[i] = (live && r < nz) ? src[(size_t)r * nx] : T(0);
     }
-    T dsep[V];  // separator row values (p >= 1)
-#pragma unroll
-    for (int u = 0; u < V; ++u) dsep[u] = v[u][0];
+    const T dsep = v[0];  // separator row value (p >= 1)
     if (live) {
       // forward elimination over the block rows i0..L-1, then back substitution: v = T_I^{-1} d_I
-      T prev[V];
-#pragma unroll
-      for (int u = 0; u < V; ++u) prev[u] = T(0);
+      T prev = T(0);
 #pragma unroll
       for (int i = 0; i < L; ++i) {
         if (i < i0) continue;
-        T m[V], a[V];
-        Vec::ld(Fm + i * FS, m);
-        Vec::ld(Fa + i * FS, a);
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-          v[u][i] = (i == i0) ? v[u][i] * m[u] : (v[u][i] - a[u] * prev[u]) * m[u];
-          prev[u] = v[u][i];
-        }
+        const T m = Fm[i * FS];
+        v[i] = (i == i0) ? v[i] * m : (v[i] - Fa[i * FS] * prev) * m;
+        prev = v[i];
       }
 #pragma unroll
       for (int i = L - 2; i >= 0; --i) {
         if (i < i0) continue;
-        T cc[V];
-        Vec::ld(Fc + i * FS, cc);
-#pragma unroll
-        for (int u = 0; u < V; ++u) v[u][i] = v[u][i] - cc[u] * v[u][i + 1];
+        v[i] = v[i] - Fc[i * FS] * v[i + 1];
       }
-#pragma unroll
-      for (int u = 0; u < V; ++u) {
-        gF[(c + u) * 32 + p] = (i0 == 0) ? v[u][0] : v[u][1];
-        gL[(c + u) * 32 + p] = v[u][L - 1];
-        ds[(c + u) * 32 + p] = (p >= 1) ? dsep[u] : T(0);
-      }
+      gF[c * 32 + p] = (i0 == 0) ? v[0] : v[1];
+      gL[c * 32 + p] = v[L - 1];
+      ds[c * 32 + p] = (p >= 1) ? dsep : T(0);
     }
     __syncthreads();
     // separators: one warp per mode, parallel cyclic reduction in shuffles (precomputed multipliers)
@@ -605,39 +543,25 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN, V>::threads, RegBound
     __syncthreads();
     if (live) {
       // correction with the spike vectors, store
-      T xa[V], xb[V];
-#pragma unroll
-      for (int u = 0; u < V; ++u) {
-        xa[u] = xi[(c + u) * 33 + p];
-        xb[u] = (p + 1 <= P - 1) ? xi[(c + u) * 33 + p + 1] : T(0);
-      }
+      const T xa = xi[c * 33 + p];
+      const T xb = (p + 1 <= P - 1) ? xi[c * 33 + p + 1] : T(0);
 #pragma unroll
       for (int i = 0; i < L; ++i) {
         const int r = p * L + i;
-        T y[V];
-        if (i < i0) {
-#pragma unroll
-          for (int u = 0; u < V; ++u) y[u] = xa[u];
-        } else {
-          T a[V], w[V];
-          Vec::ld(Sv + i * FS, a);
-          Vec::ld(Sw + i * FS, w);
-#pragma unroll
-          for (int u = 0; u < V; ++u) y[u] = v[u][i] - xa[u] * a[u] - xb[u] * w[u];
-        }
-        if (r < nz) Vec::st(dst + (size_t)r * nx, y);
+        const T y = (i < i0) ? xa : v[i] - xa * Sv[i * FS] - xb * Sw[i * FS];
+        if (r < nz) dst[(size_t)r * nx] = y;
       }
     }
     __syncthreads();  // gF/gL/ds/xi are reused by the next right-hand side
   }
 }
 
-template <typename T, int L, int MT, bool GEN, int V>
-static void tri_reg_launch_v(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
-                             cudaStream_t s, int pstride, int poff, int ncomp) {
+template <typename T, int L, int MT, bool GEN>
+static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
+                              cudaStream_t s, int pstride, int poff, int ncomp) {
   static PerDeviceOnce attr_done;
   attr_done.run([] {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT, GEN, V>,
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT, GEN>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
   // several right-hand sides per CTA when there are plenty of CTAs anyway (factor reuse)
@@ -645,25 +569,9 @@ static void tri_reg_launch_v(const TriFactors &tf, const T *d, T *y, int nrhs, c
   int per_cta = 1;
   while (per_cta < 8 && (long long)ctas_x * ((nrhs + 2 * per_cta - 1) / (2 * per_cta)) >= 152 * 8) per_cta *= 2;
   dim3 grid(ctas_x, (nrhs + per_cta - 1) / per_cta);
-  const int threads = ((MT / V) * tf.P + 31) / 32 * 32;
-  tri_solve_reg_kernel<T, L, MT, GEN, V><<<grid, threads, tf.smem, s>>>(
+  tri_solve_reg_kernel<T, L, MT, GEN><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc, (const T *)tf.fa,
       (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, nrhs, per_cta);
-}
-
-// float, constant-coefficient (staged) factors, L <= 32: two modes per thread where the rows allow
-// 8-byte accesses (an even number of modes); general systems and longer partitions keep one (two
-// modes' registers would spill or leave one warp group per SM)
-template <typename T, int L, int MT, bool GEN>
-static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
-                              cudaStream_t s, int pstride, int poff, int ncomp) {
-  if constexpr (sizeof(T) == 4 && !GEN && MT >= 2 && L <= 32) {
-    if (tf.vec2 && (tf.nx & 1) == 0) {
-      tri_reg_launch_v<T, L, MT, GEN, 2>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
-      return;
-    }
-  }
-  tri_reg_launch_v<T, L, MT, GEN, 1>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
 }
 
 template <typename T, int L, int MT>
