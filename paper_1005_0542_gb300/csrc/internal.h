@@ -107,6 +107,14 @@ void tri_solve_f64(const TriFactors &tf, const double *d, double *y, int nplanes
 void tri_solve_f32(const TriFactors &tf, const float *d, float *y, int nplanes,
                    const KrylovScalars *sc, cudaStream_t s, int pstride = 1, int poff = 0,
                    int ncomp = 1);
+// y = T^{-1} d for nrhs one-component planes (d != y) and, per plane b, (d, y) summed in a fixed
+// order into rz_new, then PCG's Fletcher-Reeves beta = rz_new / sc[b].rz (0 on a solve's first
+// iteration) and sc[b].rz = rz_new.  Between z = S T^{-1} S r and d = S r with one symmetric S
+// (the DST-I on both sides), (d, y) = (S r, T^{-1} S r) = (r, z).  Only where
+// tri_rz_fusable (the register kernel, and no more CTAs per plane than red holds blocks).
+bool tri_rz_fusable(const TriFactors &tf, const Reduce &red);
+void tri_solve_f64_rz(const TriFactors &tf, const double *d, double *y, int nrhs, KrylovScalars *sc,
+                      const Reduce &red, cudaStream_t s);
 
 // ----------------------------------------------------------------- DST (a7, a9)
 struct DstPlan {
@@ -165,13 +173,6 @@ int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv);
 // E / O sums (plan scratch), butterfly into y
 void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int rows_per_rhs,
                   const KrylovScalars *sc, cudaStream_t s, bool inverse = false);
-// DST-I plans (S^2 = I): y = S x as above for nrhs systems of rpr rows, and PCG's (r, y) with beta
-// (Fletcher-Reeves, 0 on a solve's first iteration) into sc; rzpart: scratch of
-// nrhs * rpr * dst_oz_rz_parts(dp) doubles
-bool dst_oz_rz_fusable(const DstPlan &dp);
-size_t dst_oz_rz_parts(const DstPlan &dp);
-void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, int rpr, KrylovScalars *sc,
-                     const double *r, double *rzpart, const Reduce &red, cudaStream_t s);
 // mixed path on SIMT float32 arithmetic: float64 in -> float32 out and float32 in -> float64 out
 void dst_apply_f32_d2f(const DstPlan &dp, const double *x, float *y, int rows, int rows_per_rhs,
                        const KrylovScalars *sc, cudaStream_t s, bool rscale = false);

@@ -801,25 +801,19 @@ __device__ __forceinline__ double oz_to_f64(long long v, int kx) {
 }
 
 // One epilogue thread's outputs of a tile row: the float64 values of its int64 sums (ncols of them,
-// ystride doubles apart from yp) and, with rp, the partial (r, z) of those values into *rzp.
+// ystride doubles apart from yp).
 template <bool FAST>
 __device__ __forceinline__ void oz_store_row(const long long (&acci)[64], int ncols, int kx, double scale, double unit,
-                                             double *yp, int ystride, const double *rp, double *rzp) {
-  double dacc = 0.0;
+                                             double *yp, int ystride) {
 #pragma unroll
   for (int q = 0; q < 64; ++q)
-    if (q < ncols) {
-      const double v = FAST ? oz_to_f64(acci[q], kx) : scale * (unit * __ll2double_rn(acci[q]));
-      yp[ystride * q] = v;
-      if (rp != nullptr) dacc = fma(__ldg(rp + 2 * q), v, dacc);
-    }
-  if (rzp != nullptr) *rzp = dacc;
+    if (q < ncols) yp[ystride * q] = FAST ? oz_to_f64(acci[q], kx) : scale * (unit * __ll2double_rn(acci[q]));
 }
 // the same for a row: the integer conversion where every result of the row is a normal float64
 __device__ __forceinline__ void oz_store(const long long (&acci)[64], int ncols, int e, int kx, double scale,
-                                         double unit, double *yp, int ystride, const double *rp, double *rzp) {
-  if (oz_fast_row(e, kx)) oz_store_row<true>(acci, ncols, kx, scale, unit, yp, ystride, rp, rzp);
-  else oz_store_row<false>(acci, ncols, kx, scale, unit, yp, ystride, rp, rzp);
+                                         double unit, double *yp, int ystride) {
+  if (oz_fast_row(e, kx)) oz_store_row<true>(acci, ncols, kx, scale, unit, yp, ystride);
+  else oz_store_row<false>(acci, ncols, kx, scale, unit, yp, ystride);
 }
 
 // |v| < 2^e: NBITS-bit fixed-point expansion of |v| 2^-e, truncated (integer arithmetic on the bits)
@@ -1067,8 +1061,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
                                                          const int *__restrict__ erow, int eB, int nks, int nmt,
                                                          int nnt, int rows, double *__restrict__ y, int ld, int ku,
                                                          int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
-                                                         int rpr, int *__restrict__ err, int inv,
-                                                         const double *__restrict__ rdot, double *__restrict__ rzpart) {
+                                                         int rpr, int *__restrict__ err, int inv) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -1284,13 +1277,9 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
-        // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved
-        // spectrum and, with rzpart, the CG dot (r, z) of the values just formed, one partial per
-        // (row, parity, column tile, half): PCG's beta without another sweep over r and z
+        // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved spectrum
         const size_t o = inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0;
-        const bool rz = !inv && rzpart != nullptr;
-        oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2, rz ? rdot + o : nullptr,
-                 rz ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
+        oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2);
       }
     }
   }
@@ -1329,8 +1318,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_sk_kernel(const uint8_t *__res
                                                             const int *__restrict__ erow, int eB, int nks, int nmt,
                                                             int nnt, int rows, double *__restrict__ y, int ld, int ku,
                                                             int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
-                                                            int *__restrict__ err, const double *__restrict__ rdot,
-                                                            double *__restrict__ rzpart, OzSkArea ska) {
+                                                            int *__restrict__ err, OzSkArea ska) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -1620,8 +1608,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_sk_kernel(const uint8_t *__res
           const int c0 = nt * OZ_TN + h * 64;
           const int ncols = min(64, (par ? kv : ku) - c0);
           const size_t o = (size_t)row * ld + par + 2 * (size_t)c0;
-          oz_store(acci, ncols, e, kx, scale, unit, y + o, 2, rzpart ? rdot + o : nullptr,
-                   rzpart ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
+          oz_store(acci, ncols, e, kx, scale, unit, y + o, 2);
         }
       }
     }
@@ -1721,7 +1708,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
     oz_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const int *__restrict__ erow, int eB, int nks, int nmt, int nnt, int rows,
                     double *__restrict__ y, int ld, int ku, int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
-                    int rpr, int *__restrict__ err, const double *__restrict__ rdot, double *__restrict__ rzpart) {
+                    int rpr, int *__restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -1916,8 +1903,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, (par ? kv : ku) - c0);
         const size_t o = (size_t)row * ld + par + 2 * (size_t)c0;
-        oz_store(acci, ncols, e, kx, scale, unit, y + o, 2, rzpart ? rdot + o : nullptr,
-                 rzpart ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
+        oz_store(acci, ncols, e, kx, scale, unit, y + o, 2);
       }
     }
   }
@@ -1965,9 +1951,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_mc_kernel(const uint8_t *__res
                                                             const int *__restrict__ erow, int eB, int nks, int nmt,
                                                             int nnt, int rows, double *__restrict__ y, int ld, int ku,
                                                             int kv, OzSched sch, const KrylovScalars *__restrict__ sc,
-                                                            int rpr, int *__restrict__ err, int inv,
-                                                            const double *__restrict__ rdot,
-                                                            double *__restrict__ rzpart) {
+                                                            int rpr, int *__restrict__ err, int inv) {
   constexpr int CS = CM * CN;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -2182,13 +2166,9 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_mc_kernel(const uint8_t *__res
         const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
         const int c0 = nt * OZ_TN + h * 64;
         const int ncols = min(64, ((par && !inv) ? kv : ku) - c0);
-        // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved
-        // spectrum and, with rzpart, the CG dot (r, z) of the values just formed, one partial per
-        // (row, parity, column tile, half): PCG's beta without another sweep over r and z
+        // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved spectrum
         const size_t o = inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0;
-        const bool rz = !inv && rzpart != nullptr;
-        oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2, rz ? rdot + o : nullptr,
-                 rz ? rzpart + (size_t)row * (4 * nnt) + (par * nnt + nt) * 2 + h : nullptr);
+        oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2);
       }
     }
   }
@@ -2480,43 +2460,6 @@ __global__ void oz_butterfly_kernel(const double *__restrict__ eo, double *__res
   }
 }
 
-// PCG's (r, z) and beta from the exact-slice GEMM's partials, per right-hand side rpr rows of
-// dst_oz_rz_parts values (one per parity, column tile and half); the slots of column tiles that
-// never run stay at the zero the buffer starts with.  grid (blocks, nrhs): each thread sums a fixed run of OZ_RZ_PER values,
-// the block sums combined by the last block in block order (deterministic, and the same alone or
-// in a batch); beta = rz_new / rz (Fletcher-Reeves), 0 on the first iteration of a solve.
-constexpr int OZ_RZ_THREADS = 256;
-constexpr int OZ_RZ_PER = 8;
-__global__ void __launch_bounds__(OZ_RZ_THREADS) oz_rz_beta_kernel(const double *__restrict__ part, size_t per_rhs,
-                                                                   KrylovScalars *sc, Reduce red) {
-  const int rhs = blockIdx.y;
-  if (sc[rhs].state != ST_RUN) return;
-  const double *pr = part + (size_t)rhs * per_rhs;
-  const size_t i0 = ((size_t)blockIdx.x * OZ_RZ_THREADS + threadIdx.x) * OZ_RZ_PER;
-  double acc = 0.0;
-  if (i0 + OZ_RZ_PER <= per_rhs) {
-    const double2 *p2 = reinterpret_cast<const double2 *>(pr + i0);
-#pragma unroll
-    for (int q = 0; q < OZ_RZ_PER / 2; ++q) {
-      const double2 v = __ldg(p2 + q);
-      acc += v.x;
-      acc += v.y;
-    }
-  } else {
-    for (size_t i = i0; i < per_rhs; ++i) acc += pr[i];
-  }
-  double v1[1] = {acc}, tot[1];
-  __shared__ double sh[32];
-  block_sum<1>(v1, sh);
-  if (publish_partials<1>(red, rhs, blockIdx.x, gridDim.x, v1, tot)) {
-    KrylovScalars &S = sc[rhs];
-    const double rz_new = tot[0];
-    S.beta = (S.iters == 0) ? 0.0 : rz_new / S.rz;
-    S.rz = rz_new;
-    if (!isfinite(S.beta) || !isfinite(rz_new)) S.state = ST_NAN;
-  }
-}
-
 // cluster shape of the multicast kernel: LAGWAVE_OZ_CLUSTER=2x2 / 1x2 / 2x1 (rows x columns of
 // tiles), else 0 x 0 (not used)
 static void oz_cluster_shape(int &cm, int &cn) {
@@ -2552,7 +2495,7 @@ int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv) {
 template <int NB, int NS, int CM, int CN>
 static void oz_launch_mc(const uint8_t *apack, size_t a_slice, const uint8_t *bpack, const DstPlan &dp, const int *erow,
                          int nks, int nmt, int nnt, int rows, double *y, const OzSched &sch, const KrylovScalars *sc,
-                         int rpr, int inv, const double *rdot, double *rzpart, cudaStream_t s) {
+                         int rpr, int inv, cudaStream_t s) {
   static PerDeviceOnce attr;
   static std::atomic<int> fit[64];
   int dev = 0;
@@ -2584,12 +2527,12 @@ static void oz_launch_mc(const uint8_t *apack, size_t a_slice, const uint8_t *bp
   cfg.gridDim = dim3(CM * CN * std::min(nblocks, fit[dev].load()), 1, 1);
   LAG_CUDA_CHECK(cudaLaunchKernelEx(&cfg, oz_gemm_mc_kernel<NB, NS, CM, CN>, apack, a_slice, bpack, dp.oz_slice_bytes,
                                     erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n, dp.ku, dp.kv, sch, sc, rpr, dp.tc_err,
-                                    inv, rdot, rzpart));
+                                    inv));
 }
 
 template <int NB, int NS>
 static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows, int rpr, const KrylovScalars *sc,
-                         cudaStream_t s, int inv, const double *rdot = nullptr, double *rzpart = nullptr) {
+                         cudaStream_t s, int inv) {
   static PerDeviceOnce attr;
   attr.run([] {
     LAG_CUDA_CHECK(cudaFuncSetAttribute(oz_gemm_kernel<NB, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZT_SMEM));
@@ -2620,18 +2563,18 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
     const CUtensorMap tmA = rows_map(apack, 2ull * NS * a_slice / 128, TM);
     const CUtensorMap tmB = rows_map(dp.oz_b, 2ull * NS * dp.oz_slice_bytes / 128, OZ_TN / 2);
     oz_gemm2_kernel<NB, NS><<<2 * pairs, 320, OZ2_SMEM, s>>>(tmA, tmB, erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n,
-                                                             dp.ku, dp.kv, sch, sc, rpr, dp.tc_err, rdot, rzpart);
+                                                             dp.ku, dp.kv, sch, sc, rpr, dp.tc_err);
   } else if (variant == OZ_GEMM_CLUSTER) {
     int cm, cn;
     oz_cluster_shape(cm, cn);
     const uint8_t *bp = inv ? dp.oz_bi : dp.oz_b;
     double *yo = inv ? eo : y;
     if (cm == 2 && cn == 2)
-      oz_launch_mc<NB, NS, 2, 2>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, rdot, rzpart, s);
+      oz_launch_mc<NB, NS, 2, 2>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, s);
     else if (cm == 1)
-      oz_launch_mc<NB, NS, 1, 2>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, rdot, rzpart, s);
+      oz_launch_mc<NB, NS, 1, 2>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, s);
     else
-      oz_launch_mc<NB, NS, 2, 1>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, rdot, rzpart, s);
+      oz_launch_mc<NB, NS, 2, 1>(apack, a_slice, bp, dp, erow, nks, nmt, nnt, rows, yo, sch, sc, rpr, inv, s);
   } else if (variant == OZ_GEMM_STREAMK) {
     const int gsk = oz_sk_ctas();
     uint8_t *area = dp.tc_scratch;
@@ -2641,11 +2584,11 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
     ska.part = reinterpret_cast<long long *>(area + 256 + oz_sk_flag_bytes(gsk));
     oz_gemm_sk_kernel<NB, NS><<<gsk, 320, OZ_SMEM, s>>>(apack, a_slice, dp.oz_b, dp.oz_slice_bytes, erow, dp.oz_eB,
                                                         nks, nmt, nnt, rows, y, dp.n, dp.ku, dp.kv, sch, sc,
-                                                        dp.tc_err, rdot, rzpart, ska);
+                                                        dp.tc_err, ska);
   } else {
     oz_gemm_kernel<NB, NS><<<grid, 320, OZT_SMEM, s>>>(apack, a_slice, inv ? dp.oz_bi : dp.oz_b, dp.oz_slice_bytes,
                                                       erow, dp.oz_eB, nks, nmt, nnt, rows, inv ? eo : y, dp.n, dp.ku,
-                                                      dp.kv, sch, sc, rpr, dp.tc_err, inv, rdot, rzpart);
+                                                      dp.kv, sch, sc, rpr, dp.tc_err, inv);
   }
   count_launch();
   LAG_LAUNCH_CHECK();
@@ -2664,28 +2607,6 @@ void dst_apply_oz(const DstPlan &dp, const double *x, double *y, int rows, int r
   if (dp.oz_nb == 8) oz_apply_fmt<8, 7>(dp, x, y, rows, rpr, sc, s, inv);
   else if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, inv);
   else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, inv);
-}
-
-bool dst_oz_rz_fusable(const DstPlan &dp) { return dp.oz && dp.kind == 0; }
-size_t dst_oz_rz_parts(const DstPlan &dp) { return 4 * (size_t)dp.npad_u; }
-
-void dst_apply_oz_rz(const DstPlan &dp, const double *x, double *y, int nrhs, int rpr, KrylovScalars *sc,
-                     const double *r, double *rzpart, const Reduce &red, cudaStream_t s) {
-  const int rows = nrhs * rpr;
-  if (rows <= 0) return;
-  {
-    ProfScope prof(KC_DST64, s);
-    if (dp.oz_nb == 8) oz_apply_fmt<8, 7>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
-    else if (dp.oz_nb == 7) oz_apply_fmt<7, 8>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
-    else oz_apply_fmt<6, 9>(dp, x, y, rows, rpr, sc, s, 0, r, rzpart);
-  }
-  ProfScope prof(KC_VEC, s);
-  const size_t per_rhs = (size_t)rpr * dst_oz_rz_parts(dp);  // even: whole double2 runs per row pair
-  const int nb = (int)((per_rhs + (size_t)OZ_RZ_THREADS * OZ_RZ_PER - 1) / ((size_t)OZ_RZ_THREADS * OZ_RZ_PER));
-  if (nb > red.nblk) throw Error(LAG_EINVAL, "exact-slice (r, z): more blocks than the reduction holds");
-  oz_rz_beta_kernel<<<dim3(nb, nrhs), OZ_RZ_THREADS, 0, s>>>(rzpart, per_rhs, sc, red);
-  count_launch();
-  LAG_LAUNCH_CHECK();
 }
 
 }  // namespace lag

@@ -437,11 +437,49 @@ __global__ void __launch_bounds__(256) pcg_beta_kernel(const double *__restrict_
   }
 }
 
+// the same for (r, z) alone (Fletcher-Reeves) with n even: 16-byte pairs (every right-hand side's
+// row then starts on a 16-byte boundary), two pairs in flight per thread, and few enough registers
+// that the whole grid is resident at once (the sweep is one round of loads, latency-bound)
+__global__ void __launch_bounds__(256, 8) pcg_rz_beta_kernel(const double *__restrict__ r, const double *__restrict__ z,
+                                                             size_t n, KrylovScalars *sc, Reduce red) {
+  const int rhs = blockIdx.y;
+  if (sc[rhs].state != ST_RUN) return;
+  const double2 *r2 = reinterpret_cast<const double2 *>(r + (size_t)rhs * n);
+  const double2 *z2 = reinterpret_cast<const double2 *>(z + (size_t)rhs * n);
+  const size_t n2 = n / 2, stride = (size_t)gridDim.x * blockDim.x;
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll 1
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
+    const double2 ra = __ldg(r2 + i), za = __ldg(z2 + i);
+    double2 rb = make_double2(0.0, 0.0), zb = rb;
+    if (i + stride < n2) {
+      rb = __ldg(r2 + i + stride);
+      zb = __ldg(z2 + i + stride);
+    }
+    a0 = fma(ra.x, za.x, a0);
+    a1 = fma(ra.y, za.y, a1);
+    a0 = fma(rb.x, zb.x, a0);
+    a1 = fma(rb.y, zb.y, a1);
+  }
+  double v1[1] = {a0 + a1}, tot[1];
+  __shared__ double sh[32];
+  block_sum<1>(v1, sh);
+  if (publish_partials<1>(red, rhs, blockIdx.x, gridDim.x, v1, tot)) {
+    KrylovScalars &S = sc[rhs];
+    const double rz_new = tot[0];
+    S.zq = 0.0;
+    S.beta = (S.iters == 0) ? 0.0 : rz_new / S.rz;
+    S.rz = rz_new;
+    if (!isfinite(S.beta) || !isfinite(rz_new)) S.state = ST_NAN;
+  }
+}
+
 void pcg_beta(const double *r, const double *z, const double *q, size_t n, int nrhs, int flexible,
               KrylovScalars *sc, const Reduce &red, cudaStream_t s) {
   dim3 g(reduce_blocks(n), nrhs);
   ProfScope prof(KC_VEC, s);
-  pcg_beta_kernel<<<g, 256, 0, s>>>(r, z, q, n, flexible, sc, red);
+  if (!flexible && (n & 1) == 0) pcg_rz_beta_kernel<<<g, 256, 0, s>>>(r, z, n, sc, red);
+  else pcg_beta_kernel<<<g, 256, 0, s>>>(r, z, q, n, flexible, sc, red);
   count_launch();
   LAG_LAUNCH_CHECK();
 }

@@ -431,14 +431,18 @@ struct RegBounds {
   static constexpr int blocks = per_sm / threads > 0 ? per_sm / threads : 1;
 };
 
-template <typename T, int L, int MT, bool GEN>
+// RZ (float64, one component, din != yout): also the dot (d, y) of each plane, summed over the CTAs
+// of its modes (block sums published into rz, the last CTA combining them in CTA order), and PCG's
+// beta from it into scw (see tri_solve_f64_rz)
+template <typename T, int L, int MT, bool GEN, bool RZ>
 __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T, L, MT, GEN>::blocks) tri_solve_reg_kernel(const T *__restrict__ din, T *__restrict__ yout, int nz,
                                                                int nx, int P, int levels, int nf,
                                                                const T *__restrict__ fm, const T *__restrict__ fc,
                                                                const T *__restrict__ fa, const T *__restrict__ sv,
                                                                const T *__restrict__ sw, const T *__restrict__ red,
                                                                const KrylovScalars *__restrict__ sc, int pstride,
-                                                               int poff, int ncomp, int nplanes, int per_cta) {
+                                                               int poff, int ncomp, int nplanes, int per_cta,
+                                                               KrylovScalars *scw, Reduce rz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NCR = GEN ? 0 : 3 * L;       // staged factor rows: 3 classes x L
   T *F = reinterpret_cast<T *>(smem_raw);    // [5][NCR][MT]: fm, fa, fc, sv, sw
@@ -541,6 +545,7 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T
     }
     if (n == 0 && tid < MT) xi[tid * 33] = T(0);
     __syncthreads();
+    T dot = T(0);
     if (live) {
       // correction with the spike vectors, store
       const T xa = xi[c * 33 + p];
@@ -549,19 +554,40 @@ __global__ void __launch_bounds__(RegBounds<T, L, MT, GEN>::threads, RegBounds<T
       for (int i = 0; i < L; ++i) {
         const int r = p * L + i;
         const T y = (i < i0) ? xa : v[i] - xa * Sv[i * FS] - xb * Sw[i * FS];
-        if (r < nz) dst[(size_t)r * nx] = y;
+        if (r < nz) {
+          dst[(size_t)r * nx] = y;
+          if constexpr (RZ) dot = fma(src[(size_t)r * nx], y, dot);  // d is still intact (din != yout)
+        }
+      }
+    }
+    if constexpr (RZ) {
+      double v1[1] = {(double)dot}, tot[1];
+      __shared__ double rsh[32];
+      block_sum<1>(v1, rsh);
+      if (publish_partials<1>(rz, b, blockIdx.x, gridDim.x, v1, tot)) {
+        KrylovScalars &S = scw[b];
+        const double rz_new = tot[0];
+        S.beta = (S.iters == 0) ? 0.0 : rz_new / S.rz;
+        S.rz = rz_new;
+        if (!isfinite(S.beta) || !isfinite(rz_new)) S.state = ST_NAN;
       }
     }
     __syncthreads();  // gF/gL/ds/xi are reused by the next right-hand side
   }
 }
 
-template <typename T, int L, int MT, bool GEN>
-static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
-                              cudaStream_t s, int pstride, int poff, int ncomp) {
+// the optional (d, y) dot of a float64 solve: scalars to update and the reduction to sum into
+struct TriRz {
+  KrylovScalars *sc;
+  Reduce red;
+};
+
+template <typename T, int L, int MT, bool GEN, bool RZ>
+static void tri_reg_launch_rz(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
+                              cudaStream_t s, int pstride, int poff, int ncomp, const TriRz *rz) {
   static PerDeviceOnce attr_done;
   attr_done.run([] {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT, GEN>,
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(tri_solve_reg_kernel<T, L, MT, GEN, RZ>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   });
   // several right-hand sides per CTA when there are plenty of CTAs anyway (factor reuse)
@@ -569,38 +595,51 @@ static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, 
   int per_cta = 1;
   while (per_cta < 8 && (long long)ctas_x * ((nrhs + 2 * per_cta - 1) / (2 * per_cta)) >= 152 * 8) per_cta *= 2;
   dim3 grid(ctas_x, (nrhs + per_cta - 1) / per_cta);
-  tri_solve_reg_kernel<T, L, MT, GEN><<<grid, tf.threads, tf.smem, s>>>(
+  tri_solve_reg_kernel<T, L, MT, GEN, RZ><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc, (const T *)tf.fa,
-      (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, nrhs, per_cta);
+      (const T *)tf.sv, (const T *)tf.sw, (const T *)tf.red, sc, pstride, poff, ncomp, nrhs, per_cta,
+      rz != nullptr ? rz->sc : nullptr, rz != nullptr ? rz->red : Reduce{});
+}
+
+template <typename T, int L, int MT, bool GEN>
+static void tri_reg_launch_mt(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
+                              cudaStream_t s, int pstride, int poff, int ncomp, const TriRz *rz) {
+  if constexpr (sizeof(T) == 8) {
+    if (rz != nullptr) {
+      tri_reg_launch_rz<T, L, MT, GEN, true>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
+      return;
+    }
+  }
+  tri_reg_launch_rz<T, L, MT, GEN, false>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, nullptr);
 }
 
 template <typename T, int L, int MT>
 static void tri_reg_launch_gen(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
-                               cudaStream_t s, int pstride, int poff, int ncomp) {
-  if (tf.gen) tri_reg_launch_mt<T, L, MT, true>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
-  else tri_reg_launch_mt<T, L, MT, false>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+                               cudaStream_t s, int pstride, int poff, int ncomp, const TriRz *rz) {
+  if (tf.gen) tri_reg_launch_mt<T, L, MT, true>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
+  else tri_reg_launch_mt<T, L, MT, false>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
 }
 
 template <typename T, int L>
 static void tri_reg_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc, cudaStream_t s,
-                           int pstride, int poff, int ncomp) {
+                           int pstride, int poff, int ncomp, const TriRz *rz) {
   if constexpr (sizeof(T) == 4) {
-    if (tf.mt == 8) tri_reg_launch_gen<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    if (tf.mt == 8) tri_reg_launch_gen<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
     else if constexpr (L <= 32) {
-      if (tf.mt == 32) tri_reg_launch_gen<T, L, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
-      else tri_reg_launch_gen<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+      if (tf.mt == 32) tri_reg_launch_gen<T, L, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
+      else tri_reg_launch_gen<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
     } else {
-      tri_reg_launch_gen<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+      tri_reg_launch_gen<T, L, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
     }
   } else {
-    if (tf.mt == 8) tri_reg_launch_gen<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
-    else tri_reg_launch_gen<T, L, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+    if (tf.mt == 8) tri_reg_launch_gen<T, L, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
+    else tri_reg_launch_gen<T, L, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz);
   }
 }
 
 template <typename T>
 static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const KrylovScalars *sc,
-                       cudaStream_t s, int pstride, int poff, int ncomp) {
+                       cudaStream_t s, int pstride, int poff, int ncomp, const TriRz *rz = nullptr) {
   if (nrhs <= 0) return;
   static PerDeviceOnce attr_done;
   attr_done.run([] {
@@ -609,17 +648,18 @@ static void tri_launch(const TriFactors &tf, const T *d, T *y, int nrhs, const K
   ProfScope prof(sizeof(T) == 8 ? KC_TRI64 : KC_TRI32, s);
   if (tf.reg) {
     switch (tf.L) {
-      case 2: tri_reg_launch<T, 2>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
-      case 4: tri_reg_launch<T, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
-      case 8: tri_reg_launch<T, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
-      case 16: tri_reg_launch<T, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
-      case 32: tri_reg_launch<T, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
-      default: tri_reg_launch<T, 64>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp); break;
+      case 2: tri_reg_launch<T, 2>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz); break;
+      case 4: tri_reg_launch<T, 4>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz); break;
+      case 8: tri_reg_launch<T, 8>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz); break;
+      case 16: tri_reg_launch<T, 16>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz); break;
+      case 32: tri_reg_launch<T, 32>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz); break;
+      default: tri_reg_launch<T, 64>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp, rz); break;
     }
     count_launch();
     LAG_LAUNCH_CHECK();
     return;
   }
+  if (rz != nullptr) throw Error(LAG_EINVAL, "the (d, y) dot needs the register tridiagonal kernel");
   dim3 grid((tf.nx + tf.mt - 1) / tf.mt, nrhs);
   tri_solve_kernel<T><<<grid, tf.threads, tf.smem, s>>>(
       d, y, tf.nz, tf.nx, tf.P, tf.L, tf.levels, tf.nf, (const T *)tf.fm, (const T *)tf.fc,
@@ -636,6 +676,17 @@ void tri_solve_f64(const TriFactors &tf, const double *d, double *y, int nrhs, c
 void tri_solve_f32(const TriFactors &tf, const float *d, float *y, int nrhs, const KrylovScalars *sc,
                    cudaStream_t s, int pstride, int poff, int ncomp) {
   tri_launch<float>(tf, d, y, nrhs, sc, s, pstride, poff, ncomp);
+}
+
+bool tri_rz_fusable(const TriFactors &tf, const Reduce &red) {
+  return tf.reg && tf.mt > 0 && (tf.nx + tf.mt - 1) / tf.mt <= red.nblk;
+}
+void tri_solve_f64_rz(const TriFactors &tf, const double *d, double *y, int nrhs, KrylovScalars *sc,
+                      const Reduce &red, cudaStream_t s) {
+  if (d == y) throw Error(LAG_EINVAL, "tri_solve_f64_rz: d and y must differ");
+  if (!tri_rz_fusable(tf, red)) throw Error(LAG_EINVAL, "tri_solve_f64_rz: not available for this plan");
+  const TriRz rz{sc, red};
+  tri_launch<double>(tf, d, y, nrhs, sc, s, 1, 0, 1, &rz);
 }
 
 }  // namespace lag

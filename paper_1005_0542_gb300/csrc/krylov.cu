@@ -92,11 +92,14 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
   ncomp = elastic ? 2 : 1;
   nplane = (size_t)med->grid.nx * med->grid.nz;
   n = nplane * ncomp;
-  vecs.ctx = scal.ctx = gm.ctx = red.part.ctx = red.count.ctx = wcount.ctx = rzpart.ctx = ctx;
+  vecs.ctx = scal.ctx = gm.ctx = red.part.ctx = red.count.ctx = wcount.ctx = ctx;
   const int nvec = elastic ? (3 + (s.restart_k + 1) + s.restart_k) : 7;
   vecs.alloc(ctx, (size_t)nvec * n * nrhs * sizeof(double));
   scal.alloc(ctx, (size_t)nrhs * sizeof(KrylovScalars), true);
-  const int cap = std::max(std::max(reduce_blocks(n), stencil_blocks(med->grid)), 1);
+  // blocks per right-hand side of the reductions: the vector kernels, the stencil, and the float64
+  // tridiagonal solve that also forms (r, z) (one CTA per 4 modes at most)
+  const int cap = std::max(std::max(std::max(reduce_blocks(n), stencil_blocks(med->grid)), 1),
+                           elastic ? 1 : (med->grid.nx + 3) / 4);
   red.ensure(ctx, nrhs, cap, elastic ? s.restart_k + 1 : 2);
   if (elastic) {
     gk = s.restart_k;
@@ -115,10 +118,6 @@ void KrylovWork::setup(lag_ctx *c, lag_medium *med, lag_precond *q1, lag_precond
   if (!elastic) {
     wcount.alloc(ctx, 4 * sizeof(unsigned int), true);  // [0] repeats this launch, [2..3] bodies in total
     wbodies_seen = 0;
-    if (p1->prec == LAG_FP64 && dst_oz_rz_fusable(p1->dst))
-      rzpart.alloc(ctx, (size_t)nrhs * p1->grid.nz * dst_oz_rz_parts(p1->dst) * sizeof(double), true);  // zeros
-    else
-      rzpart.release();
   }
   // pinned mirror: the scalars, the error words of the two plans' tensor-core kernels, then the
   // PCG graph's body count
@@ -177,13 +176,15 @@ void KrylovWork::pcg_iteration() {
     dst_apply_tc_d2f(p1->dst, r(), w, rows, rpr, sc(), stream, true);
     tri_solve_f32(p1->tri32, w, w, nrhs, sc(), stream);
     dst_apply_tc_f2d_beta(p1->dst, w, z, nrhs, rpr, r(), q, flexible, sc(), rd, stream);
-  } else if (p1->prec == LAG_FP64 && rzpart.ptr != nullptr) {
-    // float64 path on the exact-slice transform: its epilogue also forms (r, z) for beta
+  } else if (p1->prec == LAG_FP64 && p1->dst.kind == 0 && tri_rz_fusable(p1->tri64, rd)) {
+    // float64 path: one symmetric DST-I S serves both transforms, so (r, z) = (S r, T^{-1} S r) and
+    // the tridiagonal solve forms it from its input and output, with beta.  Its output goes to q,
+    // whose previous content only the flexible beta reads; the direction update rewrites it.
     p1->ensure_scratch(nrhs);
     double *w = p1->scratch.as<double>();
     dst_apply_f64(p1->dst, r(), w, nrhs * rpr, rpr, sc(), stream);
-    tri_solve_f64(p1->tri64, w, w, nrhs, sc(), stream);
-    dst_apply_oz_rz(p1->dst, w, z, nrhs, rpr, sc(), r(), rzpart.as<double>(), rd, stream);
+    tri_solve_f64_rz(p1->tri64, w, q, nrhs, sc(), rd, stream);
+    dst_inverse_f64(p1->dst, q, z, nrhs * rpr, rpr, sc(), stream);
   } else {
     precond(r(), z);                                                 // z = B^{-1} r
     pcg_beta(r(), z, q, n, nrhs, flexible, sc(), rd, stream);
@@ -232,7 +233,7 @@ void KrylovWork::pcg_loop_condition(unsigned long long handle) {
 
 void KrylovWork::pcg_while() {
   p1->ensure_scratch(nrhs);
-  const void *key[4] = {p1->scratch.ptr, p1->tc_scratch.ptr, vecs.ptr, rzpart.ptr};
+  const void *key[4] = {p1->scratch.ptr, p1->tc_scratch.ptr, vecs.ptr, red.part.ptr};
   const int prod = p1->dst.tc_products;
   if (wexec != nullptr && (std::memcmp(key, wkey, sizeof(key)) != 0 || prod != wprod)) {
     cudaGraphExecDestroy(wexec);

@@ -60,7 +60,6 @@ struct KrylovWork {
   unsigned long long wbodies_seen = 0;
   bool eager_done = false;
   int pcur = 0;              // which of the two direction buffers holds the current p
-  DevBuf rzpart;             // float64 PCG: partial (r, z) sums of the exact-slice GEMM's epilogue
 
   ~KrylovWork();
   void setup(lag_ctx *ctx, lag_medium *m, lag_precond *p1, lag_precond *p2, const lag_solver &s, int nrhs,
