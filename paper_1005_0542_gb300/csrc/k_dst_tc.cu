@@ -1639,6 +1639,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_sk_kernel(const uint8_t *__res
 // "tfull" barriers (multicast); the odd CTA's epilogue warps arrive on the leader's "tempty".  Every wait is bounded; both CTAs meet at a cluster barrier before
 // they free their tensor memory and exit, so neither leaves while the other may still use it.
 constexpr int OZ2_BH = (OZ_TN / 2) * TK * 2;            // half a B stage tile: 64 columns x 64 K, 8 KB
+constexpr int OZ2_ROWB = 2048;                          // bytes per row of the slice buffers' tensor maps
 constexpr int OZ2_STAGE = OZ_KT * (A_TILE + OZ2_BH);    // 48 KB: [A k tiles][B half k tiles]
 constexpr int OZ2_NST = 4;                              // pipeline stages
 constexpr int OZ2_NACC = 2;                             // accumulators of 128 columns per CTA
@@ -1775,9 +1776,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
         if (!wanted(par, mtp, nt)) continue;
         const int mt = 2 * mtp + (int)rank;
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
-          // 128-byte row index of this K step's A tile / B half in the packed slice buffers
-          const int ya = (((par * NS + (sch.si[pr] - 1)) * nmt + mt) * nks) * TM;
-          const int yb = (((par * NS + (sch.sj[pr] - 1)) * nnt + nt) * nks) * OZ_TN + (int)rank * (OZ_TN / 2);
+          // row index (OZ2_ROWB bytes) of this unit's first A tile / B half in the packed slice buffers
+          constexpr int RA = A_TILE / OZ2_ROWB, RB = OZ_BT / OZ2_ROWB;
+          const int ya = (((par * NS + (sch.si[pr] - 1)) * nmt + mt) * nks) * RA;
+          const int yb = (((par * NS + (sch.sj[pr] - 1)) * nnt + nt) * nks) * RB + (int)rank * (OZ2_BH / OZ2_ROWB);
           const int ke = sch.k1[pr];
           for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
             const int kt = min(OZ_KT, ke - kk);
@@ -1790,8 +1792,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
             const uint32_t sa = base + st * OZ2_STAGE;
             if (rank == 0) mbar_expect_tx(full0 + 8 * st, (uint32_t)(2 * kt * (A_TILE + OZ2_BH)));
             for (int q = 0; q < kt; ++q) {
-              tma_rows2(sa + q * A_TILE, &tmA, ya + (kk + q) * TM, lead_full0 + 8 * st);
-              tma_rows2(sa + OZ_KT * A_TILE + q * OZ2_BH, &tmB, yb + (kk + q) * OZ_TN, lead_full0 + 8 * st);
+              tma_rows2(sa + q * A_TILE, &tmA, ya + (kk + q) * RA, lead_full0 + 8 * st);
+              tma_rows2(sa + OZ_KT * A_TILE + q * OZ2_BH, &tmB, yb + (kk + q) * RB, lead_full0 + 8 * st);
             }
           }
         }
@@ -2379,13 +2381,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// a buffer of pre-swizzled tiles as rows of OZ2_ROWB bytes (256 8-byte elements): a tile copy is
+// one box of whole rows, which the copy engine moves as a few long requests instead of one per
+// 128-byte row
 static CUtensorMap rows_map(const void *base, uint64_t nrows, uint32_t box_rows) {
   CUtensorMap m;
-  const cuuint64_t dims[2] = {64, (cuuint64_t)nrows};
-  const cuuint64_t strides[1] = {128};
-  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint64_t dims[2] = {OZ2_ROWB / 8, (cuuint64_t)nrows};
+  const cuuint64_t strides[1] = {OZ2_ROWB};
+  const cuuint32_t box[2] = {OZ2_ROWB / 8, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+  const CUresult r = tensor_map_encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims,
                                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -2475,8 +2480,8 @@ static void oz_cluster_shape(int &cm, int &cn) {
 // rpr rows per right-hand side
 int dst_oz_gemm_variant(const DstPlan &dp, int rows, int rpr, int inv) {
   const size_t a_slice = (size_t)oz_mtiles(rows) * dp.kpad_u * A_TILE;
-  // TMA coordinates are signed 32-bit: the pair kernel addresses the slice buffers by 128-byte row
-  if (!inv && oz_pair_enabled() && 2ull * dp.oz_ns * a_slice / 128 < (1ull << 31)) return OZ_GEMM_PAIRS;
+  // TMA coordinates are signed 32-bit: the pair kernel addresses the slice buffers by OZ2_ROWB-byte row
+  if (!inv && oz_pair_enabled() && 2ull * dp.oz_ns * a_slice / OZ2_ROWB < (1ull << 31)) return OZ_GEMM_PAIRS;
   int cm, cn;
   oz_cluster_shape(cm, cn);
   if (cm > 0) return OZ_GEMM_CLUSTER;
@@ -2560,8 +2565,8 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
   if (variant == OZ_GEMM_PAIRS) {
     // two-SM pairs: 256-row tile pairs x column tiles x both parities, at most one pair per two SMs
     const int pairs = std::min(2 * (nmt / 2) * nnt, 76);
-    const CUtensorMap tmA = rows_map(apack, 2ull * NS * a_slice / 128, TM);
-    const CUtensorMap tmB = rows_map(dp.oz_b, 2ull * NS * dp.oz_slice_bytes / 128, OZ_TN / 2);
+    const CUtensorMap tmA = rows_map(apack, 2ull * NS * a_slice / OZ2_ROWB, A_TILE / OZ2_ROWB);
+    const CUtensorMap tmB = rows_map(dp.oz_b, 2ull * NS * dp.oz_slice_bytes / OZ2_ROWB, OZ2_BH / OZ2_ROWB);
     oz_gemm2_kernel<NB, NS><<<2 * pairs, 320, OZ2_SMEM, s>>>(tmA, tmB, erow, dp.oz_eB, nks, nmt, nnt, rows, y, dp.n,
                                                              dp.ku, dp.kv, sch, sc, rpr, dp.tc_err);
   } else if (variant == OZ_GEMM_CLUSTER) {
