@@ -918,14 +918,27 @@ __global__ void __launch_bounds__(OZ_PACK_THREADS) oz_pack_a_kernel(const double
   // pass 1: stage the row and take the largest |input| (per parity for the gathered DCT-II input) as
   // the largest bit pattern with the sign cleared (the same order for non-negative doubles; NaN and
   // Inf patterns compare above every finite one)
+  // (the loads of a batch of 16 per thread all issue before any is used: a whole 2048-long row is
+  // in flight at once)
   unsigned long long b0 = 0, b1 = 0;
-#pragma unroll 4
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const double v = live ? __ldg(xr + j) : 0.0;
-    xs[OZ_PAD(j)] = v;
-    const unsigned long long m = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-    if (gather && (j & 1)) b1 = max(b1, m);
-    else b0 = max(b0, m);
+  constexpr int PB = 16;
+  for (int jb = 0; jb < n; jb += PB * blockDim.x) {
+    double vb[PB];
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int j = jb + u * blockDim.x + threadIdx.x;
+      vb[u] = (live && j < n) ? __ldg(xr + j) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int j = jb + u * blockDim.x + threadIdx.x;
+      if (j < n) {
+        xs[OZ_PAD(j)] = vb[u];
+        const unsigned long long m = (unsigned long long)__double_as_longlong(vb[u]) & 0x7fffffffffffffffull;
+        if (gather && (j & 1)) b1 = max(b1, m);
+        else b0 = max(b0, m);
+      }
+    }
   }
   __shared__ unsigned long long red[2][OZ_PACK_THREADS / 32];
   __shared__ int esh[2];
@@ -1629,20 +1642,21 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_sk_kernel(const uint8_t *__res
 // ---------------------------------------------------------------- two-SM (cta_group::2) variant
 // The same exact-slice GEMM with the MMA spread over a cluster of two CTAs on two SMs: the pair
 // computes a 256 x 128 tile per (pair, K step), each CTA holding its own 128 rows of A and half of
-// the 128 B columns in shared memory; the tensor cores of the pair exchange the B halves, so each
-// SM streams 16 + 8 KB of operands per 128 x 128 x 64 of its own output instead of 16 + 16 KB (the
-// per-SM operand stream is what bounds the one-CTA kernel).  The MMAs are issued by one thread of
+// the 128 B columns in shared memory; the tensor cores of the pair exchange the B halves.  With the
+// tile kernel's fused schedule (a K tile of A_i with one or two B_j per stage) each SM streams
+// 16 + 8 or 16 + 16 KB per 4 or 8 MMAs of 128 x 128 x 16 of its own output instead of 16 + 16 or
+// 16 + 32 KB (the per-SM operand stream is what bounds the one-CTA kernel).  The MMAs are issued by one thread of
 // the even CTA (the leader) into both CTAs' tensor memory; each CTA's epilogue adds its own rows.
 // Synchronisation across the pair: both CTAs' operand copies (TMA tensor copies of the pre-swizzled
 // slice tiles, verbatim rows of 128 bytes) complete on the leader's "full" barrier, whose expected
 // byte count the leader sets for the pair; the leader's commits arrive on both CTAs' "empty" and
 // "tfull" barriers (multicast); the odd CTA's epilogue warps arrive on the leader's "tempty".  Every wait is bounded; both CTAs meet at a cluster barrier before
 // they free their tensor memory and exit, so neither leaves while the other may still use it.
-constexpr int OZ2_BH = (OZ_TN / 2) * TK * 2;            // half a B stage tile: 64 columns x 64 K, 8 KB
+constexpr int OZ2_BH = (OZ_TN / 2) * TK * 2;            // half a B K tile: 64 columns x 64 K, 8 KB
 constexpr int OZ2_ROWB = 2048;                          // bytes per row of the slice buffers' tensor maps
-constexpr int OZ2_STAGE = OZ_KT * (A_TILE + OZ2_BH);    // 48 KB: [A k tiles][B half k tiles]
-constexpr int OZ2_NST = 4;                              // pipeline stages
-constexpr int OZ2_NACC = 2;                             // accumulators of 128 columns per CTA
+constexpr int OZ2_STAGE = A_TILE + 2 * OZ2_BH;          // 32 KB: one K tile of A and up to two B halves
+constexpr int OZ2_NST = 6;                              // pipeline stages
+constexpr int OZ2_NACC = 4;                             // accumulators of 128 columns per CTA
 constexpr int OZ2_SMEM = OZ2_NST * OZ2_STAGE + 1024 + 512;
 // kind::f16, D f32, A / B bf16 K-major, M = 256 (the pair), N = 128
 constexpr uint32_t OZ2_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
@@ -1767,81 +1781,100 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
   };
 
   if (warp == 0) {
-    if (lane == 0) {  // producer (both CTAs): own A rows, own half of the B columns
+    if (lane == 0) {  // producer (both CTAs): per stage one K tile of its A rows and of its halves of B_j, B_j2
       const uint32_t lead_full0 = map_rank(full0, 0);
-      int it = 0;
+      constexpr int RA = A_TILE / OZ2_ROWB, RB = OZ_BT / OZ2_ROWB, RH = OZ2_BH / OZ2_ROWB;
+      int s = 0, it = 0;
+      uint32_t ph = 0;
       for (int t = pair; t < ntiles && !*abort_flag; t += npairs) {
         int par, mtp, nt;
         decode(t, par, mtp, nt);
         if (!wanted(par, mtp, nt)) continue;
         const int mt = 2 * mtp + (int)rank;
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
-          // row index (OZ2_ROWB bytes) of this unit's first A tile / B half in the packed slice buffers
-          constexpr int RA = A_TILE / OZ2_ROWB, RB = OZ_BT / OZ2_ROWB;
+          // row index (OZ2_ROWB bytes) of the unit's first A tile / B halves in the packed slice buffers
+          const bool two = sch.sj2[pr] > 0;
           const int ya = (((par * NS + (sch.si[pr] - 1)) * nmt + mt) * nks) * RA;
-          const int yb = (((par * NS + (sch.sj[pr] - 1)) * nnt + nt) * nks) * RB + (int)rank * (OZ2_BH / OZ2_ROWB);
-          const int ke = sch.k1[pr];
-          for (int kk = sch.k0[pr]; kk < ke; kk += OZ_KT, ++it) {
-            const int kt = min(OZ_KT, ke - kk);
-            const int st = it % OZ2_NST, use = it / OZ2_NST;
-            if (it >= OZ2_NST && !mbar_wait(empty0 + 8 * st, (use - 1) & 1)) {
+          const int yb = (((par * NS + (sch.sj[pr] - 1)) * nnt + nt) * nks) * RB + (int)rank * RH;
+          const int yb2 = (((par * NS + (max((int)sch.sj2[pr], 1) - 1)) * nnt + nt) * nks) * RB + (int)rank * RH;
+          for (int kk = sch.k0[pr]; kk < sch.k1[pr]; ++kk) {
+            if (it >= OZ2_NST && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
               atomicExch(err, 21);
               *abort_flag = 1;
               break;
             }
-            const uint32_t sa = base + st * OZ2_STAGE;
-            if (rank == 0) mbar_expect_tx(full0 + 8 * st, (uint32_t)(2 * kt * (A_TILE + OZ2_BH)));
-            for (int q = 0; q < kt; ++q) {
-              tma_rows2(sa + q * A_TILE, &tmA, ya + (kk + q) * RA, lead_full0 + 8 * st);
-              tma_rows2(sa + OZ_KT * A_TILE + q * OZ2_BH, &tmB, yb + (kk + q) * RB, lead_full0 + 8 * st);
+            const uint32_t sa = base + s * OZ2_STAGE;
+            const uint32_t fb = lead_full0 + 8 * s;
+            // the leader expects both CTAs' bytes of the stage
+            if (rank == 0) mbar_expect_tx(full0 + 8 * s, (uint32_t)(2 * (A_TILE + (two ? 2 : 1) * OZ2_BH)));
+            tma_rows2(sa, &tmA, ya + kk * RA, fb);
+            tma_rows2(sa + A_TILE, &tmB, yb + kk * RB, fb);
+            if (two) tma_rows2(sa + A_TILE + OZ2_BH, &tmB, yb2 + kk * RB, fb);
+            ++it;
+            if (++s == OZ2_NST) {
+              s = 0;
+              ph ^= 1u;
             }
           }
         }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && rank == 0) {  // the leader: MMA issuer for the pair
-      int it = 0, gc = 0;
+    if (lane == 0 && rank == 0) {  // the leader: MMA issuer for the pair (the tile kernel's issuer)
+      constexpr uint64_t DHI = ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61) | (1ull << 16);
+      constexpr uint32_t B1 = A_TILE >> 4, B2 = (A_TILE + OZ2_BH) >> 4;
+      int s = 0, gc = 0;
+      uint32_t ph = 0;
       for (int t = pair; t < ntiles && !*abort_flag; t += npairs) {
         int par, mtp, nt;
         decode(t, par, mtp, nt);
         if (!wanted(par, mtp, nt)) continue;
         uint32_t d = 0;
         for (int pr = 0; pr < sch.nunits && !*abort_flag; ++pr) {
-          if (sch.first[pr]) {
-            const int acc = gc % OZ2_NACC, ause = gc / OZ2_NACC;
-            if (gc >= OZ2_NACC && !mbar_wait_cluster(tempty0 + 8 * acc, (ause - 1) & 1)) {
+          const bool split = sch.split[pr] != 0, first = sch.first[pr] != 0, two = sch.sj2[pr] > 0;
+          if (first) {
+            bool ok = true;
+            for (int q = 0; q < (split ? 2 : 1); ++q) {  // a split unit fills two accumulators
+              const int acc = (gc + q) % OZ2_NACC, ause = (gc + q) / OZ2_NACC;
+              if (gc + q >= OZ2_NACC && !mbar_wait_cluster(tempty0 + 8 * acc, (ause - 1) & 1)) ok = false;
+            }
+            if (!ok) {
               atomicExch(err, 24);
               *abort_flag = 1;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            d = tmem + (uint32_t)(acc * OZ_TN);
+            d = tmem + (uint32_t)((gc % OZ2_NACC) * OZ_TN);
           }
+          const uint32_t d2 = split ? tmem + (uint32_t)(((gc + 1) % OZ2_NACC) * OZ_TN) : d;
           const int kb = sch.k0[pr], ke = sch.k1[pr];
-          for (int kk = kb; kk < ke; kk += OZ_KT, ++it) {
-            const int kt = min(OZ_KT, ke - kk);
-            const int st = it % OZ2_NST, use = it / OZ2_NST;
-            if (!mbar_wait(full0 + 8 * st, use & 1)) {
+          for (int kk = kb; kk < ke; ++kk) {
+            if (!mbar_wait(full0 + 8 * s, ph)) {
               atomicExch(err, 22);
               *abort_flag = 1;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = base + st * OZ2_STAGE;
-            for (int q = 0; q < kt; ++q) {
+            const uint32_t sa = (base + s * OZ2_STAGE) >> 4;
+            const uint32_t f1 = (first && kk == kb) ? 0u : 1u;
 #pragma unroll
-              for (int sub = 0; sub < TK / 16; ++sub) {
-                const uint32_t o = sub * 32;
-                mma2_bf16(d, sdesc(sa + q * A_TILE + o), sdesc(sa + OZ_KT * A_TILE + q * OZ2_BH + o),
-                          (sch.first[pr] && kk == kb && q == 0 && sub == 0) ? 0u : 1u);
-              }
+            for (int sub = 0; sub < TK / 16; ++sub)
+              mma2_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + B1 + 2 * sub), sub == 0 ? f1 : 1u);
+            if (two) {
+              const uint32_t f2 = split ? f1 : 1u;
+#pragma unroll
+              for (int sub = 0; sub < TK / 16; ++sub)
+                mma2_bf16(d2, DHI | (sa + 2 * sub), DHI | (sa + B2 + 2 * sub), sub == 0 ? f2 : 1u);
             }
-            commit2_both(empty0 + 8 * st);
+            commit2_both(empty0 + 8 * s);
+            if (++s == OZ2_NST) {
+              s = 0;
+              ph ^= 1u;
+            }
           }
           if (sch.last[pr]) {
-            commit2_both(tfull0 + 8 * (gc % OZ2_NACC));
-            ++gc;
+            for (int q = 0; q < (split ? 2 : 1); ++q) commit2_both(tfull0 + 8 * ((gc + q) % OZ2_NACC));
+            gc += split ? 2 : 1;
           }
         }
       }
@@ -2404,9 +2437,10 @@ static int oz_mtiles(int rows) {
   return nmt + (nmt & 1);
 }
 
-// the two-SM variant is opt-in (LAGWAVE_OZ_PAIR=1): it streams a quarter fewer operand bytes per
-// SM but measured slower than the one-SM kernel (the pair's stages complete at the pace of the
-// slower SM)
+// the two-SM variant is opt-in (LAGWAVE_OZ_PAIR=1): it streams a third fewer operand bytes per SM
+// but measured slower than the one-SM kernel (133 against 113 us at a 1024 x 2048 transform: a
+// pair's stage completes only when both SMs' copies have landed on the leader's barrier, and the
+// SMs then receive 29 instead of 49 bytes per clock)
 static bool oz_pair_enabled() {
   const char *v = std::getenv("LAGWAVE_OZ_PAIR");
   return v != nullptr && v[0] == '1';
@@ -2556,7 +2590,7 @@ static void oz_apply_fmt(const DstPlan &dp, const double *x, double *y, int rows
   count_launch();
   LAG_LAUNCH_CHECK();
   const int variant = dst_oz_gemm_variant(dp, rows, rpr, inv);
-  const OzSched sch = oz_schedule(nks * TK, OzFmt{NB, NS}, variant == OZ_GEMM_TILES);
+  const OzSched sch = oz_schedule(nks * TK, OzFmt{NB, NS}, variant == OZ_GEMM_TILES || variant == OZ_GEMM_PAIRS);
   const int ntiles = 2 * nmt * nnt;
   const int grid = std::min(ntiles, 152);
   // E / O sums of the inverse: after the packed A slices and the row exponents, 256-byte aligned
