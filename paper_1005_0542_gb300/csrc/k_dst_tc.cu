@@ -1084,6 +1084,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   volatile uint32_t *holder =
       reinterpret_cast<volatile uint32_t *>(gbase + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16 * OZ_NACC + 8);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(gbase + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16 * OZ_NACC + 16);
+  // the tile whose int64 sums the epilogue left in the stage buffers for the whole CTA to store (-1: none)
+  volatile int *tail_tile = reinterpret_cast<volatile int *>(gbase + OZT_NST * OZT_STAGE + 16 * OZT_NST + 16 * OZ_NACC + 24);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = 2 * nmt * nnt;
 
@@ -1103,6 +1105,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
       mbar_init(tempty0 + 8 * a, 8);  // one arrive per epilogue warp
     }
     *abort_flag = 0;
+    *tail_tile = -1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1279,7 +1282,19 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         ++gc;
       }
       if (stop) break;
-      if (rok) {
+      if (t + (int)gridDim.x >= ntiles) {
+        // the CTA's last tile: once its last group is in, every MMA and every copy of the CTA is
+        // complete and the stage buffers are free.  The sums go there ([128 rows][128 columns] int64,
+        // column index XOR (row & 7) << 1: the rows' 16-byte writes and the columns' 8-byte reads
+        // below meet every bank once per wavefront), and the whole CTA converts and stores them.
+        long long *dump = reinterpret_cast<long long *>(gbase);
+        const int rl = lg * 32 + lane;
+#pragma unroll
+        for (int q = 0; q < 64; q += 2)
+          *reinterpret_cast<longlong2 *>(dump + rl * OZ_TN + ((h * 64 + q) ^ ((rl & 7) << 1))) =
+              make_longlong2(acci[q], acci[q + 1]);
+        if (warp == 2 && lane == 0) *tail_tile = t;
+      } else if (rok) {
         // the one float64 rounding of the product: int64 -> double, then exact power-of-two scales
         // (2^-38 first, so that a row near the bottom of the float64 range meets the same
         // subnormal rounding as its float64 product would); built from integer operations where
@@ -1293,6 +1308,47 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         // DCT-II inverse: the even / odd mode sums E, O as [par][row][ku]; else the interleaved spectrum
         const size_t o = inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0;
         oz_store(acci, ncols, e, kx, scale, unit, y + o, inv ? 1 : 2);
+      }
+    }
+  }
+  // the last tile's store: ten warps, one row at a time (the row's scale and the integer / float64
+  // choice uniform over the warp), lanes along the row's columns.  With the sums in registers, the
+  // eight epilogue warps converted and stored 64 values each after the last MMA, latency-bound with
+  // two warps per scheduler and few registers left (about 40 k clocks at a 2048 x 1024 transform)
+  __syncthreads();
+  const int tt = *tail_tile;
+  if (tt >= 0) {
+    int par, mt, nt;
+    decode(tt, par, mt, nt);
+    const long long *dump = reinterpret_cast<const long long *>(gbase);
+    const int c0 = nt * OZ_TN;
+    const int ncols = min(OZ_TN, ((par && !inv) ? kv : ku) - c0);
+    const int ys = inv ? 1 : 2;
+    for (int rl = warp; rl < TM; rl += 10) {
+      const int row = mt * TM + rl;
+      if (row >= rows) break;
+      const int e = erow[par * (nmt * TM) + row];
+      const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
+      double *yr = y + (inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0);
+      const long long *dr = dump + rl * OZ_TN;
+      const int sw = (rl & 7) << 1;
+      if (oz_fast_row(e, kx)) {
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const int col = k4 * 32 + lane;
+          const long long a = dr[col ^ sw];
+          if (col < ncols) yr[ys * col] = oz_to_f64(a, kx);
+        }
+      } else {
+        const double scale = (e == OZ_EXP_NAN) ? __longlong_as_double(0x7ff8000000000000ll)
+                                               : ldexp(1.0, e + eB - 2 * oz_se(NB, NS));
+        const double unit = 1.0 / (double)(1LL << oz_fix(NB));
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const int col = k4 * 32 + lane;
+          const long long a = dr[col ^ sw];
+          if (col < ncols) yr[ys * col] = scale * (unit * __ll2double_rn(a));
+        }
       }
     }
   }
