@@ -1293,6 +1293,7 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
         for (int q = 0; q < 64; q += 2)
           *reinterpret_cast<longlong2 *>(dump + rl * OZ_TN + ((h * 64 + q) ^ ((rl & 7) << 1))) =
               make_longlong2(acci[q], acci[q + 1]);
+        if (h == 0) reinterpret_cast<int *>(dump + TM * OZ_TN)[rl] = e;  // the rows' exponents after the sums
         if (warp == 2 && lane == 0) *tail_tile = t;
       } else if (rok) {
         // the one float64 rounding of the product: int64 -> double, then exact power-of-two scales
@@ -1313,8 +1314,8 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
   }
   // the last tile's store: ten warps, one row at a time (the row's scale and the integer / float64
   // choice uniform over the warp), lanes along the row's columns.  With the sums in registers, the
-  // eight epilogue warps converted and stored 64 values each after the last MMA, latency-bound with
-  // two warps per scheduler and few registers left (about 40 k clocks at a 2048 x 1024 transform)
+  // eight epilogue warps converted and stored 64 values each after the last MMA with few registers
+  // left; here the conversion runs at the integer pipe's rate (about one value per clock and SM)
   __syncthreads();
   const int tt = *tail_tile;
   if (tt >= 0) {
@@ -1324,10 +1325,11 @@ __global__ void __launch_bounds__(320, 1) oz_gemm_kernel(const uint8_t *__restri
     const int c0 = nt * OZ_TN;
     const int ncols = min(OZ_TN, ((par && !inv) ? kv : ku) - c0);
     const int ys = inv ? 1 : 2;
+    const int *esh = reinterpret_cast<const int *>(dump + TM * OZ_TN);
     for (int rl = warp; rl < TM; rl += 10) {
       const int row = mt * TM + rl;
       if (row >= rows) break;
-      const int e = erow[par * (nmt * TM) + row];
+      const int e = esh[rl];
       const int kx = e + eB - 2 * oz_se(NB, NS) - oz_fix(NB);
       double *yr = y + (inv ? ((size_t)par * rows + row) * ku + c0 : (size_t)row * ld + par + 2 * (size_t)c0);
       const long long *dr = dump + rl * OZ_TN;
