@@ -408,6 +408,35 @@ def test_dst_f64_stream_k_matches_tiles_and_oracle(ctx, monkeypatch, nx, nz):
     L.lag_precond_destroy(p)
 
 
+def test_dst_f64_tiles_stored_from_registers_and_by_the_whole_cta(ctx):
+    # 3 x 1024 rows of 2048: 384 output tiles on at most 152 CTAs, so a CTA stores its earlier tiles
+    # from the epilogue warps' registers and its last one through shared memory with all ten warps.
+    # Both against the oracle's DST (rows over 40 decades, rows at 1e-300 and 3e304 whose results
+    # leave the integer conversion's range, a non-finite row), and the first right-hand side
+    # bit for bit against the same rows transformed alone (128 tiles: every tile a last tile)
+    nx, nz, nrhs = 2048, 1024, 3
+    x = RNG.standard_normal((nrhs, nz, nx)) * 10.0 ** RNG.uniform(-20, 20, (nrhs, nz, 1))
+    x[0, 5] = RNG.standard_normal(nx) * 1e-300  # results normal, below the integer conversion's range
+    x[1, 700] = RNG.standard_normal(nx) * 3e304  # and above it
+    x[2, 300, 17] = np.nan
+    p = plan(ctx, nx, nz, 5.0, 5.0, 1.0, 1.0, 0.1)
+    assert L.lag_precond_dst_gemm(p, nrhs) == L.LAG_GEMM_SLICE_TILES
+    xd, y3, y1 = dev(x), empty(x.shape), empty(x[:1].shape)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(y3), nrhs), ctx)
+    L.check(L.lag_precond_dst(p, ptr(xd), ptr(y1), 1), ctx)
+    a = host(y3)
+    assert np.array_equal(a[0], host(y1)[0])
+    assert np.all(np.isnan(a[2, 300]))
+    for b in range(nrhs):
+        rows = np.arange(b, nz, 5)  # a sample of every 5th row of each right-hand side
+        rows = np.union1d(rows, [5, 700])
+        rows = rows[~((b == 2) & (rows == 300))]
+        ref = odst.dst_x(x[b:b + 1, rows])[0]
+        sc = np.abs(ref).max(axis=-1, keepdims=True)
+        assert np.abs((a[b, rows] - ref) / sc).max() < 1e-14
+    L.lag_precond_destroy(p)
+
+
 def test_dst_gemm_query(ctx, monkeypatch):
     # the GEMM kernel a transform launches, by plan kind, right-hand sides and environment
     pm = plan(ctx, 2048, 1024, 5.0, 5.0, 1.0, 1.0, 0.1, prec=L.LAG_MIXED)
