@@ -38,9 +38,9 @@ WORKLOAD = ("random_layered_2048x1024 acoustic FP64 single shot: 5 m, 20 layers 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures, with the sha1 of the
 # kernel source file at capture time (null when the kernel changed since).  See profiles/.
 NCU_TRAFFIC = {
-    # oz_pack_a_kernel<8, 7> (16.83 MB) + oz_gemm_kernel<8, 7> (59.18 MB), one 2048-mode x 1024-row
+    # oz_pack_a_kernel<8, 7> (16.83 MB) + oz_gemm_kernel<8, 7> (58.85 MB), one 2048-mode x 1024-row
     # launch each (bench.py --capture-kernels; profiles/launches_dst_f64_random_layered_2048x1024.md)
-    "dst_f64_oz": {"bytes": 76.01e6, "sha1": "8dbbb4ad0a8a",
+    "dst_f64_oz": {"bytes": 75.68e6, "sha1": "78396d00351a",
                    "section": "// ============================================================================ exact-slice FP64 DST"},
 }
 
