@@ -128,6 +128,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       : "memory");
 }
 
+// the same MMA with N = 128 (half-width tiles of the split-bf16 GEMM)
+constexpr uint32_t IDESC_H = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((TN / 2) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+__device__ __forceinline__ void mma_bf16_h(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(IDESC_H), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(
@@ -277,24 +287,31 @@ __global__ void __launch_bounds__(256) pack_a_inv_kernel(const float *__restrict
 // tile overlap the main loop of the next.  Tiles are ordered (parity, m tile, n tile), n fastest,
 // so consecutive tiles reuse the same A rows from L2.  NPROD = 3: hi*hi + hi*lo + lo*hi;
 // NPROD = 2: hi*hi + lo*hi (B = bf16(S)); NPROD = 1: hi*hi.
-template <int NPROD>
+// HALF: 128 x 128 tiles, each the 128-column half of a packed 256-column B tile (its first or last
+// 16 KB of 128-byte rows): twice the tiles, for transforms whose 128 x 256 tiles would leave most
+// SMs idle (one right-hand side: 64 tiles on 152 SMs); the stages then hold one K tile of A and
+// of the two B halves, three to six of them.
+template <int NPROD, bool HALF>
 struct TcCfg {
+  static constexpr int TNK = HALF ? TN / 2 : TN;  // output columns per tile
+  static constexpr int BT = TNK * TK * 2;          // bytes of one B K tile of the tile's columns
   static constexpr int A_BYTES = (NPROD >= 2 ? 2 : 1) * A_TILE;
-  static constexpr int B_BYTES = (NPROD >= 3 ? 2 : 1) * B_TILE;
+  static constexpr int B_BYTES = (NPROD >= 3 ? 2 : 1) * BT;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int NST = (NPROD == 3) ? 2 : (NPROD == 2 ? 3 : 4);
+  static constexpr int NST = (196608 / STAGE_BYTES) < 6 ? (196608 / STAGE_BYTES) : 6;
   static constexpr int SMEM = NST * STAGE_BYTES + 1024 + 256;
 };
 
-template <int NPROD>
+template <int NPROD, bool HALF>
 __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__restrict__ apack,
                                                              const uint8_t *__restrict__ bpack, size_t b_mat_bytes,
                                                              int nks, int nmt, int nnt, int rows, float *__restrict__ out,
                                                              int ld, int ku, int nvalid0, int nvalid1,
                                                              const KrylovScalars *__restrict__ sc, int rpr,
                                                              int *__restrict__ err) {
-  using Cfg = TcCfg<NPROD>;
+  using Cfg = TcCfg<NPROD, HALF>;
   constexpr int NST = Cfg::NST;
+  constexpr int TNK = Cfg::TNK;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
     par = t / (nnt * nmt);
   };
   auto wanted = [&](int par, int mt, int nt) -> bool {
-    if (nt * TN >= (par ? nvalid1 : nvalid0)) return false;
+    if (nt * TNK >= (par ? nvalid1 : nvalid0)) return false;
     if (sc == nullptr) return true;
     const int m0 = mt * TM;
     const int r0 = m0 / rpr, r1 = (min(m0 + TM, rows) - 1) / rpr;
@@ -354,7 +371,9 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
         decode(t, par, mt, nt);
         if (!wanted(par, mt, nt)) continue;
         const uint8_t *atiles = apack + ((size_t)par * nmt + mt) * nks * 2 * A_TILE;
-        const uint8_t *btiles = bpack + (size_t)par * b_mat_bytes + (size_t)nt * nks * 2 * B_TILE;
+        // packed B: [parity][256-column tile][K tile][hi, lo: 256 rows of 128 bytes each]
+        const uint8_t *btiles = bpack + (size_t)par * b_mat_bytes +
+                                (size_t)(HALF ? nt >> 1 : nt) * nks * 2 * B_TILE + (HALF ? (nt & 1) * Cfg::BT : 0);
         for (int kk = 0; kk < nks; ++kk, ++it) {
           const int s = it % NST, use = it / NST;
           if (it >= NST && !mbar_wait(empty0 + 8 * s, (use - 1) & 1)) {
@@ -366,7 +385,12 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
           const uint32_t fb = full0 + 8 * s;
           mbar_expect_tx(fb, Cfg::STAGE_BYTES);
           bulk_g2s(st, atiles + (size_t)kk * 2 * A_TILE, Cfg::A_BYTES, fb);
-          bulk_g2s(st + Cfg::A_BYTES, btiles + (size_t)kk * 2 * B_TILE, Cfg::B_BYTES, fb);
+          if constexpr (HALF) {  // the hi and lo halves are 32 KB apart in the packed tile
+            bulk_g2s(st + Cfg::A_BYTES, btiles + (size_t)kk * 2 * B_TILE, Cfg::BT, fb);
+            if (NPROD >= 3) bulk_g2s(st + Cfg::A_BYTES + Cfg::BT, btiles + (size_t)kk * 2 * B_TILE + B_TILE, Cfg::BT, fb);
+          } else {
+            bulk_g2s(st + Cfg::A_BYTES, btiles + (size_t)kk * 2 * B_TILE, Cfg::B_BYTES, fb);
+          }
         }
       }
     }
@@ -375,7 +399,7 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
       // stage position and phase kept incrementally, descriptors as one OR of the constant upper
       // bits with the 16-byte address (a single thread's per-stage work idles the tensor pipe)
       constexpr uint64_t DHI = ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61) | (1ull << 16);
-      constexpr uint32_t ALO = A_TILE >> 4, BHI = Cfg::A_BYTES >> 4, BLO = (Cfg::A_BYTES + B_TILE) >> 4;
+      constexpr uint32_t ALO = A_TILE >> 4, BHI = Cfg::A_BYTES >> 4, BLO = (Cfg::A_BYTES + Cfg::BT) >> 4;
       int s = 0, tc = 0;
       uint32_t ph = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
@@ -401,9 +425,15 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
           const uint32_t f = kk == 0 ? 0u : 1u;
 #pragma unroll
           for (int sub = 0; sub < TK / 16; ++sub) {  // 16 bf16 along K: 32 bytes, 2 units of 16
-            mma_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + BHI + 2 * sub), sub == 0 ? f : 1u);
-            if (NPROD >= 3) mma_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + BLO + 2 * sub), 1u);
-            if (NPROD >= 2) mma_bf16(d, DHI | (sa + ALO + 2 * sub), DHI | (sa + BHI + 2 * sub), 1u);
+            if constexpr (HALF) {
+              mma_bf16_h(d, DHI | (sa + 2 * sub), DHI | (sa + BHI + 2 * sub), sub == 0 ? f : 1u);
+              if (NPROD >= 3) mma_bf16_h(d, DHI | (sa + 2 * sub), DHI | (sa + BLO + 2 * sub), 1u);
+              if (NPROD >= 2) mma_bf16_h(d, DHI | (sa + ALO + 2 * sub), DHI | (sa + BHI + 2 * sub), 1u);
+            } else {
+              mma_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + BHI + 2 * sub), sub == 0 ? f : 1u);
+              if (NPROD >= 3) mma_bf16(d, DHI | (sa + 2 * sub), DHI | (sa + BLO + 2 * sub), 1u);
+              if (NPROD >= 2) mma_bf16(d, DHI | (sa + ALO + 2 * sub), DHI | (sa + BHI + 2 * sub), 1u);
+            }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * s)
                        : "memory");
@@ -435,10 +465,10 @@ __global__ void __launch_bounds__(192, 1) dst_tc_gemm_kernel(const uint8_t *__re
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = mt * TM + lg * 32 + lane;
-      const int n0 = nt * TN;
-      const int ncols = min(TN, (par ? nvalid1 : nvalid0) - n0);
+      const int n0 = nt * TNK;
+      const int ncols = min(TNK, (par ? nvalid1 : nvalid0) - n0);
       float *orow = out + (size_t)row * ld + (size_t)par * ku + n0;
-      for (int c0 = 0; c0 < TN; c0 += 32) {
+      for (int c0 = 0; c0 < TNK; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(acc * TMEM_COLS + c0), v);
         if (row >= rows || c0 >= ncols) continue;
@@ -573,19 +603,30 @@ void dst_build_tc(DstPlan &dp, DevBuf &store, size_t off, cudaStream_t s) {
   LAG_LAUNCH_CHECK();
 }
 
+template <int NPROD, bool HALF>
+static void gemm_launch_nh(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
+                           int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
+  static PerDeviceOnce attr;
+  attr.run([] {
+    LAG_CUDA_CHECK(cudaFuncSetAttribute(dst_tc_gemm_kernel<NPROD, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        TcCfg<NPROD, HALF>::SMEM));
+  });
+  const int nks = dp.kpad_u, nnt = dp.npad_u * (HALF ? 2 : 1), nmt = div_up(rows, TM);
+  const int ntiles = 2 * nmt * nnt;
+  const int grid = std::min(ntiles, 152);
+  dst_tc_gemm_kernel<NPROD, HALF><<<grid, 192, TcCfg<NPROD, HALF>::SMEM, s>>>(
+      apack, bpack, dp.tc_bmat_bytes, nks, nmt, nnt, rows, out, ld, dp.ku, nvalid0, nvalid1, sc, rpr, err);
+}
+static int device_sms();
+// 128 x 256 tiles unless they would leave more than half the SMs idle (then 128 x 128 tiles)
 template <int NPROD>
 static void gemm_launch_n(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
                           int nvalid0, int nvalid1, const KrylovScalars *sc, int rpr, int *err, cudaStream_t s) {
-  static PerDeviceOnce attr;
-  attr.run([] {
-    LAG_CUDA_CHECK(cudaFuncSetAttribute(dst_tc_gemm_kernel<NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        TcCfg<NPROD>::SMEM));
-  });
-  const int nks = dp.kpad_u, nnt = dp.npad_u, nmt = div_up(rows, TM);
-  const int ntiles = 2 * nmt * nnt;
-  const int grid = std::min(ntiles, 152);
-  dst_tc_gemm_kernel<NPROD><<<grid, 192, TcCfg<NPROD>::SMEM, s>>>(apack, bpack, dp.tc_bmat_bytes, nks, nmt, nnt, rows,
-                                                                   out, ld, dp.ku, nvalid0, nvalid1, sc, rpr, err);
+  const int tiles = 2 * div_up(rows, TM) * dp.npad_u;
+  if (2 * tiles <= device_sms())
+    gemm_launch_nh<NPROD, true>(dp, apack, bpack, rows, out, ld, nvalid0, nvalid1, sc, rpr, err, s);
+  else
+    gemm_launch_nh<NPROD, false>(dp, apack, bpack, rows, out, ld, nvalid0, nvalid1, sc, rpr, err, s);
 }
 
 static void gemm_launch(const DstPlan &dp, const uint8_t *apack, const uint8_t *bpack, int rows, float *out, int ld,
